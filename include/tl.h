@@ -1,0 +1,196 @@
+/*
+ * tl.h -- C ABI of the GB300 T10 Total-Lagrangian force / tangent / Hessian
+ * assembly path and the backward-Euler Newton step that consumes it.
+ *
+ * The operations follow arxiv 2604.10357 (TL-FEA Part II):
+ *   Sec. 2     eq. stepmap, eq. residual, eq. cost, eq. lambda_update
+ *   Sec. 4.1   precomputation of reference-configuration constants
+ *   Sec. 4.2   fixed-sparsity CSR patterns (built once)
+ *   Sec. 4.3   internal force, eq. F_assembly, eq. fint_local, eq. fint_global
+ *   Sec. 4.4   gradient (eq. grad_L) and Hessian (eq. hessian, eq. tangent_block)
+ *   Sec. 4.6   Newton solver, Algorithm 3
+ *
+ * Conventions shared by every call:
+ *   - Nodal vectors (q_n, v, f_int, g, ...) are float64 arrays of length
+ *     ndof = 3*nn, node-major (x, y, z of node 0, then node 1, ...).
+ *   - T10 connectivity: corners 0..3 (positively oriented), then midside
+ *     nodes on edges 4:(0,1) 5:(1,2) 6:(0,2) 7:(0,3) 8:(1,3) 9:(2,3).
+ *     Midside nodes must sit at edge midpoints (straight-sided elements).
+ *   - Except for tl_mesh_create's host inputs and the host pointers named as
+ *     such, every array argument is a DEVICE pointer owned by the caller; the
+ *     library never frees it and keeps no reference after the call returns.
+ *   - The mesh handle owns every internal buffer (pattern, slot map,
+ *     precomputed geometry, mass, solver state) and frees it in
+ *     tl_mesh_destroy.
+ *   - Calls are asynchronous on the stream given at creation unless stated
+ *     otherwise.  Device-side errors found by a kernel (an inverted element,
+ *     a non-finite value) are sticky and are returned by tl_sync.
+ *   - No call aborts, traps or prints: errors come back as tl_status and
+ *     tl_last_error(mesh) holds a one-line description.
+ *   - One GPU: the handle is bound to the device that was current at
+ *     creation.
+ */
+#ifndef TL_H_
+#define TL_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tl_status {
+  TL_OK = 0,
+  TL_ERR_INVALID_ARG = 1,   /* bad pointer, size, connectivity or geometry   */
+  TL_ERR_OOM = 2,           /* device allocation failed                       */
+  TL_ERR_CUDA = 3,          /* a CUDA runtime call failed                     */
+  TL_ERR_INVERTED = 4,      /* det F <= 0 at some quadrature point            */
+  TL_ERR_NONFINITE = 5,     /* NaN or Inf in a residual or Hessian            */
+  TL_ERR_NOT_CONVERGED = 6, /* Newton/ALM iteration caps reached              */
+  TL_ERR_SOLVER = 7,        /* the sparse direct solver failed (zero pivot)   */
+  TL_ERR_TIMEOUT = 8,       /* a bounded device-side wait expired             */
+  TL_ERR_OVERFLOW = 9,      /* nnz or an index would not fit in int32         */
+  TL_ERR_UNSUPPORTED = 10,  /* a mesh or option this build does not handle    */
+  TL_ERR_STATE = 11         /* call order violated (e.g. no pattern yet)      */
+} tl_status;
+
+typedef enum tl_material_kind { TL_SVK = 0, TL_MOONEY_RIVLIN = 1 } tl_material_kind;
+
+/* Element arithmetic precision.  TL_FP64: every element quantity in float64.
+ * TL_FP32_ELEM: element kinematics, stress and tangent in float32 with the
+ * Green strain formed as E = (H + H^T + H^T H)/2 from the displacement
+ * gradient H; nodal forces are accumulated in float64 and Hessian values are
+ * float32.  Residual, constraint rows and updates stay float64. */
+typedef enum tl_precision { TL_FP64 = 0, TL_FP32_ELEM = 1 } tl_precision;
+
+/* Material of a set of elements (Sec. 4.3 Stage 1: SVK or compressible
+ * Mooney-Rivlin, plus optional Kelvin-Voigt damping; constitutive forms as in
+ * the project notes because the paper defers them to its Part I):
+ *   SVK  : S = lambda tr(E) I + 2 mu E, lambda/mu from (E, nu)
+ *   MR   : W = C10(J^-2/3 I1 - 3) + C01(J^-4/3 I2 - 3) + kappa/2 (J-1)^2
+ *   KV   : S_v = lambda_d tr(Edot) I + 2 eta_d Edot, Edot = sym(F^T Fdot);
+ *          off when eta_d == lambda_d == 0.
+ * rho0 is the reference density (mass matrix, gravity load). */
+typedef struct tl_material {
+  int32_t kind;               /* tl_material_kind */
+  int32_t _pad;
+  double E, nu, rho0;
+  double C10, C01, kappa;
+  double eta_d, lambda_d;
+} tl_material;
+
+/* Newton / ALM controls (Algorithm 3).  The inner loop stops when
+ * ||g|| <= max(atol, rtol * ||g(v_n; lambda)||), i.e. relative to the
+ * residual at the plain previous-velocity start whatever start is used. */
+typedef struct tl_params {
+  double h;                   /* time step */
+  double rho_alm;             /* ALM penalty rho */
+  double rtol, atol;          /* inner stopping tolerances */
+  double eps_out;             /* outer stop: ||c||_2 <= eps_out */
+  double gravity[3];          /* body-force field per unit mass (f_ff) */
+  int32_t max_inner;          /* L_max */
+  int32_t max_outer;          /* K_max */
+  int32_t flags;              /* reserved, pass 0 */
+  int32_t _pad;
+} tl_params;
+
+typedef struct tl_newton_stats {
+  int32_t inner_iters;        /* Newton iterations summed over outer loops */
+  int32_t outer_iters;
+  int32_t converged;          /* 1 when inner and outer criteria were met */
+  int32_t _pad;
+  double g_ref;               /* ||g(v_n; lambda)|| at the start of the step */
+  double g_norm;              /* last inner residual norm */
+  double c_norm;              /* last ||c||_2 */
+  double ms_total;            /* wall time of the whole step */
+  double ms_assembly;         /* residual + Hessian assembly kernels */
+  double ms_solver;           /* vendor factorisation + solves */
+} tl_newton_stats;
+
+typedef struct tl_mesh_info {
+  int64_t nn, ne, ndof, nnz, nnz_node, nfixed;
+  int32_t precision, nmat;
+} tl_mesh_info;
+
+typedef struct tl_mesh tl_mesh;   /* opaque, library-owned */
+
+/* Create a mesh handle and upload it (Sec. 4.1 precomputation).
+ *   X            HOST, nn*3 float64 reference coordinates
+ *   conn         HOST, ne*10 int32 T10 connectivity (order above)
+ *   mats, nmat   HOST, material table (nmat >= 1)
+ *   mat_of_elem  HOST, ne int32 indices into mats, or NULL (all material 0)
+ *   precision    tl_precision
+ *   stream       cudaStream_t to run on (NULL = legacy default stream)
+ * Validates connectivity range, straight-sided midside nodes and a positive
+ * reference volume of every element (TL_ERR_INVALID_ARG otherwise).
+ * Synchronous.  On success *out receives the handle. */
+tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64_t ne,
+                         const tl_material* mats, int32_t nmat, const int32_t* mat_of_elem,
+                         int32_t precision, void* stream, tl_mesh** out);
+
+/* Build, once, everything that depends only on topology and the reference
+ * configuration (Sec. 4.2): the coefficient-level adjacency, the DOF-level
+ * CSR pattern of H (3x3 blocks per adjacent node pair, rows and columns
+ * ascending, full symmetric storage), the per-element slot map, the
+ * consistent mass (Sec. 4.1, integrated exactly) and the clamp constraint
+ * rows (identity rows of C_q, one per DOF of each fixed node).
+ *   fixed_nodes  HOST, nfixed int32 node ids (any order, no duplicates)
+ *   nnz_out      HOST, receives nnz of H
+ * Synchronous.  TL_ERR_OVERFLOW if nnz >= 2^31. */
+tl_status tl_build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed,
+                           int64_t* nnz_out);
+
+/* Copy the pattern out (device pointers, caller-allocated):
+ *   row_ptr   (ndof+1) int32, col (nnz) int32: the CSR of H
+ *   slot_map  (ne*900) int32 or NULL: position in values[] of K_elem entry
+ *             (r, s), r = 3a+i (row), s = 3b+k (column), element order as
+ *             given to tl_mesh_create. */
+tl_status tl_get_pattern(const tl_mesh* m, int32_t* row_ptr, int32_t* col, int32_t* slot_map);
+
+/* Internal force f_int(q_n + h v, v) (eq. residual's force term, eq. fint_local
+ * and eq. fint_global): elastic plus Kelvin-Voigt stress.  h = 0 evaluates the
+ * force at configuration q_n.  f_int: ndof float64, overwritten. */
+tl_status tl_eval_force(tl_mesh* m, const double* q_n, const double* v, double h, double* f_int);
+
+/* Element tangents (eq. tangent_block) at q = q_n + h v:
+ *   K_elem[e*900 + 30 r + s] = alpha * K_t,e + beta * D_e
+ * with K_t the stiffness (geometric term with the total second Piola-Kirchhoff
+ * stress, elastic plus viscous) and D the Kelvin-Voigt velocity tangent
+ * df/dv at fixed q.  float64 for TL_FP64 meshes, float32 for TL_FP32_ELEM. */
+tl_status tl_eval_tangent(tl_mesh* m, const double* q_n, const double* v, double h,
+                          double alpha, double beta, void* K_elem);
+
+/* CSR values of the Newton matrix (eq. hessian with the Kelvin-Voigt term):
+ *   H = M/h + h K_t + D + h^2 rho C_q^T C_q      at q = q_n + h v
+ * values: nnz entries (float64 or float32 by precision), overwritten.
+ * f_int: NULL, or ndof float64 that receives f_int(q_n + h v, v) from the same
+ * fused pass (force + tangent + assembly in one kernel). */
+tl_status tl_assemble_hessian(tl_mesh* m, const double* q_n, const double* v, double h,
+                              double rho_alm, void* values, double* f_int);
+
+/* Residual of eq. residual / eq. grad_L:
+ *   g = M (v - v_n)/h + f_int(q_n + h v, v) - f_ext - f_ff + h C_q^T (lambda + rho c)
+ * with f_ff = (row sums of M) x gravity and c = (q_n + h v - X) on clamped DOFs.
+ *   f_ext   ndof float64 or NULL (zero)
+ *   lambda  3*nfixed float64 (multiplier of DOF d of the j-th fixed node at
+ *           3j+d, fixed nodes in ascending id order), or NULL (zero)
+ *   g       ndof float64, overwritten
+ *   g_norm  1 float64 (device), receives ||g||_2 */
+tl_status tl_eval_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n,
+                           const double* v, const double* f_ext, const double* lambda,
+                           double* g, double* g_norm);
+
+/* Wait for the handle's stream and return the first sticky device-side error
+ * (TL_ERR_INVERTED, TL_ERR_NONFINITE) raised since the last tl_sync, then
+ * clear it. */
+tl_status tl_sync(tl_mesh* m);
+
+tl_status tl_mesh_info_get(const tl_mesh* m, tl_mesh_info* out);
+const char* tl_status_string(tl_status s);
+const char* tl_last_error(const tl_mesh* m);
+void tl_mesh_destroy(tl_mesh* m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TL_H_ */

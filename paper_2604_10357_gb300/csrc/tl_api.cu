@@ -1,0 +1,322 @@
+// C ABI entry points (include/tl.h): handle life cycle, reference-geometry
+// precomputation and argument checking.  Every compute step runs in the
+// kernels of tl_element.cu, tl_pattern.cu and tl_residual.cu.
+//
+// Paper: arxiv 2604.10357 Sec. 4.1 (precompute once: reference gradients,
+// Jacobians, quadrature weights, mass), Sec. 4.2 (fixed patterns), Sec. 4.3-4.4.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tl_internal.cuh"
+
+namespace tl {
+
+tl_status fail(tl_mesh* m, tl_status s, const std::string& msg) {
+  if (m) m->last_error = msg;
+  return s;
+}
+
+tl_status cuda_fail(tl_mesh* m, cudaError_t e, const char* what) {
+  if (m) m->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return TL_ERR_OOM;
+  return TL_ERR_CUDA;
+}
+
+namespace {
+
+void free_mesh(tl_mesh* m) {
+  if (!m) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(m->device);
+  void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_geo32, m->d_X, m->d_node_ptr, m->d_node_col,
+                  m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
+                  m->d_flags, m->d_partials};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  cudaSetDevice(cur);
+  delete m;
+}
+
+// Reference gradients of the barycentric coordinates of a straight-sided
+// tetrahedron: with D = [X1-X0, X2-X0, X3-X0] (columns), grad L_k = row k of
+// D^{-1} (k = 1..3), grad L_0 = -(sum), and V = det(D)/6.
+bool tet_geometry(const double* X, const int32_t* c, double out[16]) {
+  double D[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) D[d][k] = X[3 * c[k + 1] + d] - X[3 * c[0] + d];
+  const double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                     D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                     D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+  if (!(det > 0.0)) return false;
+  double inv[3][3];
+  inv[0][0] = (D[1][1] * D[2][2] - D[1][2] * D[2][1]) / det;
+  inv[0][1] = (D[0][2] * D[2][1] - D[0][1] * D[2][2]) / det;
+  inv[0][2] = (D[0][1] * D[1][2] - D[0][2] * D[1][1]) / det;
+  inv[1][0] = (D[1][2] * D[2][0] - D[1][0] * D[2][2]) / det;
+  inv[1][1] = (D[0][0] * D[2][2] - D[0][2] * D[2][0]) / det;
+  inv[1][2] = (D[0][2] * D[1][0] - D[0][0] * D[1][2]) / det;
+  inv[2][0] = (D[1][0] * D[2][1] - D[1][1] * D[2][0]) / det;
+  inv[2][1] = (D[0][1] * D[2][0] - D[0][0] * D[2][1]) / det;
+  inv[2][2] = (D[0][0] * D[1][1] - D[0][1] * D[1][0]) / det;
+  for (int d = 0; d < 3; ++d) {
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      out[3 * (k + 1) + d] = inv[k][d];
+      s += inv[k][d];
+    }
+    out[d] = -s;
+  }
+  out[12] = det / 6.0;
+  out[13] = out[14] = out[15] = 0.0;
+  return true;
+}
+
+const int kEdge[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
+
+// Reason of the last failed tl_mesh_create on this thread (no handle exists).
+thread_local std::string g_create_error;
+
+}  // namespace
+}  // namespace tl
+
+using namespace tl;
+
+extern "C" {
+
+const char* tl_status_string(tl_status s) {
+  switch (s) {
+    case TL_OK: return "ok";
+    case TL_ERR_INVALID_ARG: return "invalid argument";
+    case TL_ERR_OOM: return "out of device memory";
+    case TL_ERR_CUDA: return "CUDA error";
+    case TL_ERR_INVERTED: return "inverted element (det F <= 0)";
+    case TL_ERR_NONFINITE: return "non-finite value";
+    case TL_ERR_NOT_CONVERGED: return "not converged";
+    case TL_ERR_SOLVER: return "sparse solver failure";
+    case TL_ERR_TIMEOUT: return "device wait timed out";
+    case TL_ERR_OVERFLOW: return "index overflow";
+    case TL_ERR_UNSUPPORTED: return "unsupported";
+    case TL_ERR_STATE: return "invalid call order";
+  }
+  return "unknown status";
+}
+
+const char* tl_last_error(const tl_mesh* m) { return m ? m->last_error.c_str() : g_create_error.c_str(); }
+
+tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64_t ne, const tl_material* mats,
+                         int32_t nmat, const int32_t* mat_of_elem, int32_t precision, void* stream, tl_mesh** out) {
+  if (!out) return TL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!X || !conn || !mats || nn <= 0 || ne < 0 || nmat < 1) return TL_ERR_INVALID_ARG;
+  if (precision != TL_FP64 && precision != TL_FP32_ELEM) return TL_ERR_INVALID_ARG;
+  if (nn >= (int64_t)1 << 29) return TL_ERR_OVERFLOW;      // 9 * 3 nn row bases fit in int32
+  g_create_error.clear();
+  tl_mesh* m = new (std::nothrow) tl_mesh();
+  if (!m) return TL_ERR_OOM;
+  cudaGetDevice(&m->device);
+  m->stream = (cudaStream_t)stream;
+  m->precision = precision;
+  m->nn = nn;
+  m->ne = ne;
+  // ---- materials ----------------------------------------------------------
+  for (int k = 0; k < nmat; ++k) {
+    const tl_material& t = mats[k];
+    MaterialDev md{};
+    md.kind = t.kind;
+    if (t.kind != TL_SVK && t.kind != TL_MOONEY_RIVLIN) {
+      free_mesh(m);
+      return TL_ERR_INVALID_ARG;
+    }
+    md.lam = t.E * t.nu / ((1.0 + t.nu) * (1.0 - 2.0 * t.nu));
+    md.mu = t.E / (2.0 * (1.0 + t.nu));
+    md.C10 = t.C10;
+    md.C01 = t.C01;
+    md.kappa = t.kappa;
+    md.eta = t.eta_d;
+    md.lam_d = t.lambda_d;
+    md.kv = (t.eta_d != 0.0 || t.lambda_d != 0.0) ? 1 : 0;
+    md.rho = t.rho0;
+    m->mats.push_back(md);
+  }
+  // ---- validate connectivity and geometry; element order by material ------
+  std::vector<std::vector<int64_t>> by_mat(nmat);
+  std::vector<double> geo_user(16 * (size_t)ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    const int32_t* c = conn + 10 * e;
+    for (int a = 0; a < 10; ++a)
+      if (c[a] < 0 || c[a] >= nn) {
+        g_create_error = "element " + std::to_string(e) + " references a node out of range";
+        free_mesh(m);
+        return TL_ERR_INVALID_ARG;
+      }
+    if (!tet_geometry(X, c, &geo_user[16 * e])) {
+      g_create_error = "element " + std::to_string(e) + " has non-positive volume";
+      free_mesh(m);
+      return TL_ERR_INVALID_ARG;
+    }
+    double scale = 0.0;
+    for (int d = 0; d < 3; ++d) scale = std::max(scale, std::fabs(X[3 * c[1] + d] - X[3 * c[0] + d]));
+    for (int k = 0; k < 6; ++k)
+      for (int d = 0; d < 3; ++d) {
+        const double mid = 0.5 * (X[3 * c[kEdge[k][0]] + d] + X[3 * c[kEdge[k][1]] + d]);
+        if (std::fabs(X[3 * c[4 + k] + d] - mid) > 1e-9 * (scale + std::fabs(mid))) {
+          g_create_error = "element " + std::to_string(e) + " is not straight-sided";
+          free_mesh(m);
+          return TL_ERR_UNSUPPORTED;     // curved T10 elements are not handled
+        }
+      }
+    const int mk = mat_of_elem ? mat_of_elem[e] : 0;
+    if (mk < 0 || mk >= nmat) {
+      free_mesh(m);
+      return TL_ERR_INVALID_ARG;
+    }
+    by_mat[mk].push_back(e);
+  }
+  // internal order: material segments, each padded to a multiple of kTile
+  std::vector<int32_t> h_conn, h_user;
+  std::vector<double> h_geo64;
+  int64_t pos = 0;
+  for (int k = 0; k < nmat; ++k) {
+    if (by_mat[k].empty()) continue;
+    Segment sg;
+    sg.begin = pos;
+    sg.end = pos + (int64_t)by_mat[k].size();
+    const int64_t padded = ((int64_t)by_mat[k].size() + kTile - 1) / kTile * kTile;
+    sg.padded_end = pos + padded;
+    sg.mat = k;
+    for (int64_t i = 0; i < padded; ++i) {
+      if (i < (int64_t)by_mat[k].size()) {
+        const int64_t e = by_mat[k][i];
+        h_conn.insert(h_conn.end(), conn + 10 * e, conn + 10 * e + 10);
+        h_user.push_back((int32_t)e);
+        h_geo64.insert(h_geo64.end(), &geo_user[16 * e], &geo_user[16 * e] + 16);
+      } else {
+        h_conn.insert(h_conn.end(), 10, 0);
+        h_user.push_back(-1);
+        h_geo64.insert(h_geo64.end(), 16, 0.0);
+      }
+    }
+    pos += padded;
+    m->segs.push_back(sg);
+  }
+  m->ne_pad = pos;
+  const int64_t ne_pad = std::max<int64_t>(pos, 1);
+  std::vector<float> h_geo32(h_geo64.begin(), h_geo64.end());
+  h_conn.resize(10 * ne_pad, 0);
+  h_user.resize(ne_pad, -1);
+  h_geo64.resize(16 * ne_pad, 0.0);
+  h_geo32.resize(16 * ne_pad, 0.0f);
+  tl_status st = TL_OK;
+#define TRYC(call)                        \
+  do {                                    \
+    cudaError_t _e = (call);              \
+    if (_e != cudaSuccess) {              \
+      st = cuda_fail(m, _e, #call);       \
+      free_mesh(m);                       \
+      return st;                          \
+    }                                     \
+  } while (0)
+  TRYC(cudaMalloc(&m->d_conn, sizeof(int32_t) * 10 * ne_pad));
+  TRYC(cudaMalloc(&m->d_user_of, sizeof(int32_t) * ne_pad));
+  TRYC(cudaMalloc(&m->d_geo64, sizeof(double) * 16 * ne_pad));
+  TRYC(cudaMalloc(&m->d_geo32, sizeof(float) * 16 * ne_pad));
+  TRYC(cudaMalloc(&m->d_X, sizeof(double) * 3 * nn));
+  TRYC(cudaMalloc(&m->d_flags, sizeof(uint32_t) * 4));
+  TRYC(cudaMemcpy(m->d_conn, h_conn.data(), sizeof(int32_t) * 10 * ne_pad, cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(m->d_user_of, h_user.data(), sizeof(int32_t) * ne_pad, cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(m->d_geo64, h_geo64.data(), sizeof(double) * 16 * ne_pad, cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(m->d_geo32, h_geo32.data(), sizeof(float) * 16 * ne_pad, cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(m->d_X, X, sizeof(double) * 3 * nn, cudaMemcpyHostToDevice));
+  TRYC(cudaMemset(m->d_flags, 0, sizeof(uint32_t) * 4));
+#undef TRYC
+  *out = m;
+  return TL_OK;
+}
+
+tl_status tl_build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed, int64_t* nnz_out) {
+  if (!m || nfixed < 0 || (nfixed > 0 && !fixed_nodes)) return TL_ERR_INVALID_ARG;
+  if (m->have_pattern) return fail(m, TL_ERR_STATE, "pattern already built");
+  tl_status s = build_pattern(m, fixed_nodes, nfixed);
+  if (s != TL_OK) return s;
+  if (nnz_out) *nnz_out = m->nnz;
+  return TL_OK;
+}
+
+tl_status tl_get_pattern(const tl_mesh* m, int32_t* row_ptr, int32_t* col, int32_t* slot_map) {
+  if (!m) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return TL_ERR_STATE;
+  if (row_ptr && cudaMemcpyAsync(row_ptr, m->d_row_ptr, sizeof(int32_t) * (3 * m->nn + 1),
+                                 cudaMemcpyDeviceToDevice, m->stream) != cudaSuccess)
+    return TL_ERR_CUDA;
+  if (col && cudaMemcpyAsync(col, m->d_col, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToDevice, m->stream) !=
+                 cudaSuccess)
+    return TL_ERR_CUDA;
+  if (slot_map) return expand_slot_map(m, slot_map, m->stream);
+  return TL_OK;
+}
+
+tl_status tl_eval_force(tl_mesh* m, const double* q_n, const double* v, double h, double* f_int) {
+  if (!m || !q_n || !v || !f_int) return TL_ERR_INVALID_ARG;
+  return launch_force(m, q_n, v, h, f_int);
+}
+
+tl_status tl_eval_tangent(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
+                          void* K_elem) {
+  if (!m || !q_n || !v || !K_elem) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  return launch_tangent(m, q_n, v, h, alpha, beta, 0.0, false, nullptr, nullptr, K_elem);
+}
+
+tl_status tl_assemble_hessian(tl_mesh* m, const double* q_n, const double* v, double h, double rho_alm,
+                              void* values, double* f_int) {
+  if (!m || !q_n || !v || !values || !(h > 0.0)) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  const size_t vb = (m->precision == TL_FP32_ELEM ? sizeof(float) : sizeof(double)) * (size_t)m->nnz;
+  TL_CUDA(m, cudaMemsetAsync(values, 0, vb, m->stream));
+  tl_status s = launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, f_int != nullptr, f_int, values, nullptr);
+  if (s != TL_OK) return s;
+  return launch_add_penalty(m, h * h * rho_alm, values);
+}
+
+tl_status tl_eval_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n, const double* v,
+                           const double* f_ext, const double* lambda, double* g, double* g_norm) {
+  if (!m || !p || !q_n || !v_n || !v || !g || !g_norm || !(p->h > 0.0)) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  tl_status s = launch_force(m, q_n, v, p->h, g);      // g <- f_int(q_n + h v, v)
+  if (s != TL_OK) return s;
+  return launch_residual(m, p, q_n, v_n, v, g, f_ext, lambda, g, g_norm);
+}
+
+tl_status tl_sync(tl_mesh* m) {
+  if (!m) return TL_ERR_INVALID_ARG;
+  TL_CUDA(m, cudaStreamSynchronize(m->stream));
+  uint32_t flags = 0;
+  TL_CUDA(m, cudaMemcpy(&flags, m->d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  TL_CUDA(m, cudaMemset(m->d_flags, 0, sizeof(uint32_t)));
+  if (flags & kFlagInverted) return fail(m, TL_ERR_INVERTED, "det F <= 0 at a quadrature point");
+  if (flags & kFlagNonFinite) return fail(m, TL_ERR_NONFINITE, "non-finite residual norm");
+  if (flags & kFlagBadIndex) return fail(m, TL_ERR_UNSUPPORTED, "index outside the pattern");
+  return TL_OK;
+}
+
+tl_status tl_mesh_info_get(const tl_mesh* m, tl_mesh_info* out) {
+  if (!m || !out) return TL_ERR_INVALID_ARG;
+  out->nn = m->nn;
+  out->ne = m->ne;
+  out->ndof = 3 * m->nn;
+  out->nnz = m->nnz;
+  out->nnz_node = m->nnz_node;
+  out->nfixed = m->nfixed;
+  out->precision = m->precision;
+  out->nmat = (int32_t)m->mats.size();
+  return TL_OK;
+}
+
+void tl_mesh_destroy(tl_mesh* m) { free_mesh(m); }
+
+}  // extern "C"

@@ -1,0 +1,668 @@
+// T10 element kernels: internal force, tangent stiffness and their scatter
+// into the fixed-pattern CSR Hessian.
+//
+// Paper: arxiv 2604.10357
+//   Sec. 4.3  eq. F_assembly, eq. fint_local, eq. fint_global (Stage 1 + 2)
+//   Sec. 4.4  eq. tangent_block and the Hessian assembly (eq. hessian)
+//
+// GB300 design (differs from the paper's two-stage, thread-per-(e,q) /
+// thread-per-(e,a) kernels with a stress buffer in global memory):
+//   * one fused kernel: a CTA owns kTile = 32 consecutive elements; their
+//     connectivity, geometry and slot indices are staged in shared memory and
+//     nothing per quadrature point ever goes to global memory;
+//   * warps are specialised by role with lanes = elements, so every branch on
+//     the role is warp-uniform:
+//       qp phase:      warp w -> (quadrature point q = w/3, row i = w%3)
+//       tangent phase: warp w -> (row-pair p = w/3, row i = w%3), covering the
+//                      block rows a = p and a = 9-p (11 blocks, b >= a), so
+//                      the symmetric 30x30 is formed once (55 blocks);
+//   * the scatter goes through a per-element slot map (position k of node
+//     conn[b] in node conn[a]'s sorted adjacency), so there is no binary
+//     search: slot = 9 ptr(I) + 3 deg(I) i + 3 k + j;
+//   * TL_FP32_ELEM evaluates the element in float32 from the displacement
+//     gradient H (F = I + H, E = (H + H^T + H^T H)/2) and a cancellation-free
+//     Mooney-Rivlin stress (deviators of E, J - 1 from the invariants of H).
+#include <cstddef>
+#include <type_traits>
+
+#include "tl_internal.cuh"
+
+namespace tl {
+namespace {
+
+constexpr int E = kTile;          // elements per CTA
+constexpr int NWARP = 15;         // 5 qp x 3 rows, and 5 row pairs x 3 rows
+constexpr int NT = 32 * NWARP;    // 480 threads
+
+// Keast 5-point rule: barycentric coordinates and weights (fraction of V).
+__device__ __forceinline__ void qp_bary(int q, double L[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) L[k] = (q == 0) ? 0.25 : (k == q - 1 ? 0.5 : 1.0 / 6.0);
+}
+__device__ __forceinline__ double qp_wfrac(int q) { return q == 0 ? -0.8 : 0.45; }
+
+// Exact consistent mass of a straight-sided T10 in units of rho V / 420.
+__constant__ float c_mass420[10][10] = {
+    {6, 1, 1, 1, -4, -6, -4, -4, -6, -6},     {1, 6, 1, 1, -4, -4, -6, -6, -4, -6},
+    {1, 1, 6, 1, -6, -4, -4, -6, -6, -4},     {1, 1, 1, 6, -6, -6, -6, -4, -4, -4},
+    {-4, -4, -6, -6, 32, 16, 16, 16, 16, 8},  {-6, -4, -4, -6, 16, 32, 16, 8, 16, 16},
+    {-4, -6, -4, -6, 16, 16, 32, 16, 8, 16},  {-4, -6, -6, -4, 16, 8, 16, 32, 16, 16},
+    {-6, -4, -6, -4, 16, 16, 8, 16, 32, 16},  {-6, -6, -4, -4, 8, 16, 16, 16, 16, 32}};
+
+// midside node m (4..9) lies on corners (ei[m-4], ej[m-4])
+__device__ __forceinline__ int edge_i(int m) { return (m == 4 || m == 6 || m == 7) ? 0 : (m == 5 || m == 8) ? 1 : 2; }
+__device__ __forceinline__ int edge_j(int m) { return (m == 4) ? 1 : (m == 5 || m == 6) ? 2 : 3; }
+
+template <typename T>
+struct MatT {
+  T lam, mu, C10, C01, kappa, eta, lam_d, rho;
+};
+
+template <typename T>
+struct Args {
+  const int32_t* conn;
+  const T* geo;
+  const uint8_t* blk;
+  const int32_t* node_ptr;
+  const int32_t* user_of;
+  const double* q_n;
+  const double* v;
+  const double* X;
+  double h;
+  int64_t tile0;       // first internal element of tile 0 of this launch
+  int64_t real_end;    // internal elements >= real_end are padding
+  MatT<T> mat;
+  T alpha, beta;       // tangent = alpha K_t + beta D
+  T mass_scale;        // mass term M_e * mass_scale added to the tangent
+  double* f;           // force output (atomic add), may be null
+  T* values;           // CSR values (atomic add), may be null
+  T* K_elem;           // per-element 30x30 output (user order), may be null
+  uint32_t* flags;
+};
+
+// Per-element shared-memory strides padded to odd word counts so that lanes
+// (= elements) reading the same offset hit distinct banks.
+constexpr int kNStride = 151;    // 5 qp x 30 grad N, + 1
+constexpr int kAStride = 407;    // 5 qp x 81 tangent entries, + 2
+constexpr int kFStride = 151;    // 5 qp x 30 force entries, + 1
+constexpr int kUStride = 31;
+
+template <typename T>
+struct Smem {
+  int32_t node[10][E];
+  int32_t rbase[10][E];
+  int32_t rstr[10][E];
+  uint8_t blk[E][100];
+  T geo[16][E];
+  T u[kUStride * E];
+  T vel[kUStride * E];
+  T n[kNStride * E];
+  T fq[kFStride * E];
+  T A[kAStride * E];
+};
+
+template <typename T>
+__device__ __forceinline__ T rcbrt_t(T x);
+template <>
+__device__ __forceinline__ float rcbrt_t<float>(float x) { return rcbrtf(x); }
+template <>
+__device__ __forceinline__ double rcbrt_t<double>(double x) { return rcbrt(x); }
+
+// ---------------------------------------------------------------------------
+// Constitutive update at one quadrature point.
+// In:  Hm = displacement gradient, Fd = velocity gradient (if KV).
+// Out: F, total second Piola-Kirchhoff stress S (elastic + viscous),
+//      and everything the tangent rows need.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct QP {
+  T F[3][3];
+  T S[3][3];       // S_el + S_v
+  T Sv[3][3];      // viscous part
+  T G[3][3];       // F^{-T} (MR)
+  T Q[3][3];       // I1 F - F C (MR)
+  T B[3][3];       // F F^T
+  T C[3][3];
+  T J, I1, I2;
+};
+
+template <typename T>
+__device__ __forceinline__ void sym3_inverse(const T C[3][3], T detC, T Ci[3][3]) {
+  const T inv = T(1) / detC;
+  Ci[0][0] = (C[1][1] * C[2][2] - C[1][2] * C[2][1]) * inv;
+  Ci[0][1] = (C[0][2] * C[2][1] - C[0][1] * C[2][2]) * inv;
+  Ci[0][2] = (C[0][1] * C[1][2] - C[0][2] * C[1][1]) * inv;
+  Ci[1][1] = (C[0][0] * C[2][2] - C[0][2] * C[2][0]) * inv;
+  Ci[1][2] = (C[0][2] * C[1][0] - C[0][0] * C[1][2]) * inv;
+  Ci[2][2] = (C[0][0] * C[1][1] - C[0][1] * C[1][0]) * inv;
+  Ci[1][0] = Ci[0][1];
+  Ci[2][0] = Ci[0][2];
+  Ci[2][1] = Ci[1][2];
+}
+
+template <typename T, int MAT, bool KV>
+__device__ __forceinline__ void constitutive(const T Hm[3][3], const T Fd[3][3], const MatT<T>& mp,
+                                             QP<T>& s, bool& inverted) {
+  // F = I + H;  E = (H + H^T + H^T H)/2
+  T Em[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      s.F[i][j] = Hm[i][j] + (i == j ? T(1) : T(0));
+      T hh = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) hh += Hm[k][i] * Hm[k][j];
+      Em[i][j] = T(0.5) * (Hm[i][j] + Hm[j][i] + hh);
+    }
+  // J - 1 from the invariants of H: det(I+H) = 1 + trH + (tr^2 H - tr H^2)/2 + det H
+  const T trH = Hm[0][0] + Hm[1][1] + Hm[2][2];
+  T trH2 = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) trH2 += Hm[i][k] * Hm[k][i];
+  const T detH = Hm[0][0] * (Hm[1][1] * Hm[2][2] - Hm[1][2] * Hm[2][1]) -
+                 Hm[0][1] * (Hm[1][0] * Hm[2][2] - Hm[1][2] * Hm[2][0]) +
+                 Hm[0][2] * (Hm[1][0] * Hm[2][1] - Hm[1][1] * Hm[2][0]);
+  const T Jm1 = trH + T(0.5) * (trH * trH - trH2) + detH;
+  s.J = T(1) + Jm1;
+  if (!(s.J > T(0))) inverted = true;
+  const T trE = Em[0][0] + Em[1][1] + Em[2][2];
+
+  if (MAT == TL_SVK) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s.S[i][j] = T(2) * mp.mu * Em[i][j] + (i == j ? mp.lam * trE : T(0));
+  } else {
+    // C = I + 2E; S = C^{-1} [4a dev E + 2b((2 + 4 trE) dev E - 4 dev(E^2))] + kappa (J-1) J C^{-1}
+    // with a = C10 J^{-2/3}, b = C01 J^{-4/3}.
+    T Cm[3][3], Ci[3][3], dE[3][3], dE2[3][3];
+    T E2[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Cm[i][j] = T(2) * Em[i][j] + (i == j ? T(1) : T(0));
+        T acc = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc += Em[i][k] * Em[k][j];
+        E2[i][j] = acc;
+      }
+    const T trE2 = E2[0][0] + E2[1][1] + E2[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dE[i][j] = Em[i][j] - (i == j ? trE / T(3) : T(0));
+        dE2[i][j] = E2[i][j] - (i == j ? trE2 / T(3) : T(0));
+      }
+    const T J = s.J;
+    sym3_inverse(Cm, J * J, Ci);
+    const T r = rcbrt_t<T>(J);
+    const T a = mp.C10 * r * r;
+    const T b = mp.C01 * r * r * r * r;
+    T Mm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Mm[i][j] = T(4) * a * dE[i][j] + T(2) * b * ((T(2) + T(4) * trE) * dE[i][j] - T(4) * dE2[i][j]);
+    const T vol = mp.kappa * Jm1 * J;
+    T Sx[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T acc = vol * Ci[i][j];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc += Ci[i][k] * Mm[k][j];
+        Sx[i][j] = acc;
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s.S[i][j] = T(0.5) * (Sx[i][j] + Sx[j][i]);
+    // tangent ingredients
+    s.I1 = T(3) + T(2) * trE;
+    // I2 = (I1^2 - tr C^2)/2 ; tr C^2 = 3 + 4 trE + 4 tr E^2
+    s.I2 = T(0.5) * (s.I1 * s.I1 - (T(3) + T(4) * trE + T(4) * trE2));
+    const T Ji = T(1) / J;
+    // G = F^{-T} = cof(F) / J
+    const T(&F)[3][3] = s.F;
+    s.G[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) * Ji;
+    s.G[0][1] = (F[1][2] * F[2][0] - F[1][0] * F[2][2]) * Ji;
+    s.G[0][2] = (F[1][0] * F[2][1] - F[1][1] * F[2][0]) * Ji;
+    s.G[1][0] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * Ji;
+    s.G[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * Ji;
+    s.G[1][2] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * Ji;
+    s.G[2][0] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * Ji;
+    s.G[2][1] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * Ji;
+    s.G[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * Ji;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s.C[i][j] = Cm[i][j];
+    // Q = F (I1 I - C)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T acc = s.I1 * F[i][j];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc -= F[i][k] * Cm[k][j];
+        s.Q[i][j] = acc;
+      }
+  }
+  // B = F F^T (SVK and MR tangents, Kelvin-Voigt tangent)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += s.F[i][k] * s.F[j][k];
+      s.B[i][j] = acc;
+    }
+  if (KV) {
+    // Edot = sym(F^T Fdot) = sym(Fdot + H^T Fdot); S_v = lam_d tr(Edot) I + 2 eta Edot
+    T Ed[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T a1 = Fd[i][j], a2 = Fd[j][i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a1 += Hm[k][i] * Fd[k][j];
+          a2 += Hm[k][j] * Fd[k][i];
+        }
+        Ed[i][j] = T(0.5) * (a1 + a2);
+      }
+    const T trEd = Ed[0][0] + Ed[1][1] + Ed[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        s.Sv[i][j] = T(2) * mp.eta * Ed[i][j] + (i == j ? mp.lam_d * trEd : T(0));
+        s.S[i][j] += s.Sv[i][j];
+      }
+  }
+}
+
+// Tangent entry A^_{iJkL} for fixed row i (27 values at [J*9 + k*3 + L]),
+// scaled by wJ0:  alpha * A_t + beta * A_vis.
+template <typename T, int MAT, bool KV, int i>
+__device__ __forceinline__ void tangent_row(const QP<T>& s, const MatT<T>& mp, T alpha, T beta, T wJ, T* out) {
+  if (MAT == TL_SVK) {
+    // A_t = d_ik S_JL + lam F_iJ F_kL + mu (B_ik d_JL + F_iL F_kJ)
+    // A_v = lam_d F_iJ F_kL + eta (B_ik d_JL + F_iL F_kJ)
+    const T cFF = wJ * (alpha * mp.lam + (KV ? beta * mp.lam_d : T(0)));
+    const T cB = wJ * (alpha * mp.mu + (KV ? beta * mp.eta : T(0)));
+    const T cS = wJ * alpha;
+#pragma unroll
+    for (int J = 0; J < 3; ++J)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int L = 0; L < 3; ++L) {
+          T v = cFF * s.F[i][J] * s.F[k][L] + cB * (s.F[i][L] * s.F[k][J] + (J == L ? s.B[i][k] : T(0)));
+          if (i == k) v += cS * s.S[J][L];
+          out[J * 9 + k * 3 + L] = v;
+        }
+  } else {
+    // Mooney-Rivlin tangent (d_ik X_JL + cB B_ik d_JL + rank-one and swap terms)
+    const T r = rcbrt_t<T>(s.J);
+    const T a = mp.C10 * r * r;
+    const T b = mp.C01 * r * r * r * r;
+    const T J = s.J;
+    const T cdd = T(2) * a + T(2) * b * s.I1;
+    const T cC = -T(2) * b;
+    const T cB = -T(2) * b;
+    const T cFF = T(4) * b;
+    const T cFFs = -T(2) * b;
+    const T cFG = -(T(4) / T(3)) * a;
+    const T cQG = -(T(8) / T(3)) * b;
+    const T cGG = (T(4) / T(9)) * a * s.I1 + (T(16) / T(9)) * b * s.I2 + mp.kappa * (T(2) * J * J - J);
+    const T cGGs = (T(2) / T(3)) * a * s.I1 + (T(4) / T(3)) * b * s.I2 - mp.kappa * (J * J - J);
+    const T wa = wJ * alpha;
+    const T wb = wJ * beta;
+#pragma unroll
+    for (int Jx = 0; Jx < 3; ++Jx)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int L = 0; L < 3; ++L) {
+          const T FiJ = s.F[i][Jx], FkL = s.F[k][L], FiL = s.F[i][L], FkJ = s.F[k][Jx];
+          const T GiJ = s.G[i][Jx], GkL = s.G[k][L], GiL = s.G[i][L], GkJ = s.G[k][Jx];
+          T vA = cFF * FiJ * FkL + cFFs * FiL * FkJ + cFG * (FiJ * GkL + GiJ * FkL) +
+                 cQG * (s.Q[i][Jx] * GkL + GiJ * s.Q[k][L]) + cGG * GiJ * GkL + cGGs * GiL * GkJ;
+          if (Jx == L) vA += cB * s.B[i][k];
+          if (i == k) {
+            vA += cC * s.C[Jx][L] + (Jx == L ? cdd : T(0));
+            if (KV) vA += s.Sv[Jx][L];      // geometric term of the viscous stress
+          }
+          T v = wa * vA;
+          if (KV) v += wb * (mp.lam_d * FiJ * FkL + mp.eta * (FiL * FkJ + (Jx == L ? s.B[i][k] : T(0))));
+          out[Jx * 9 + k * 3 + L] = v;
+        }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void atomic_add_t(T* p, T v);
+template <>
+__device__ __forceinline__ void atomic_add_t<float>(float* p, float v) { atomicAdd(p, v); }
+template <>
+__device__ __forceinline__ void atomic_add_t<double>(double* p, double v) { atomicAdd(p, v); }
+
+// ---------------------------------------------------------------------------
+// Stage the tile: connectivity, row bases, slot indices, geometry and the
+// nodal displacement / velocity gathers.
+// ---------------------------------------------------------------------------
+template <typename T, bool NEED_PATTERN>
+__device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t e0) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < E * 10; t += NT) {
+    const int e = t / 10, a = t % 10;
+    const int node = A.conn[(e0 + e) * 10 + a];
+    sm.node[a][e] = node;
+    if (NEED_PATTERN) {
+      const int p0 = A.node_ptr[node], p1 = A.node_ptr[node + 1];
+      sm.rbase[a][e] = 9 * p0;
+      sm.rstr[a][e] = 3 * (p1 - p0);
+    }
+  }
+  if (NEED_PATTERN) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(A.blk + e0 * 100);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.blk[0][0]);
+    for (int t = tid; t < E * 25; t += NT) dst[t] = src[t];
+  }
+  for (int t = tid; t < E * 16; t += NT) {
+    const int e = t / 16, c = t % 16;
+    sm.geo[c][e] = A.geo[(e0 + e) * 16 + c];
+  }
+  __syncthreads();
+  const double h = A.h;
+  for (int t = tid; t < E * 30; t += NT) {
+    const int e = t / 30, c = t % 30;
+    const int a = c / 3, d = c % 3;
+    const int64_t g = 3 * (int64_t)sm.node[a][e] + d;
+    const double vv = A.v[g];
+    const double x = A.q_n[g] + h * vv;
+    sm.u[c * E + e] = T(x - A.X[g]);
+    sm.vel[c * E + e] = T(vv);
+  }
+  __syncthreads();
+}
+
+// Gradients of the 10 shape functions at barycentric point L (straight-sided
+// T10): corners (4 L_a - 1) grad L_a, midsides 4 (L_i grad L_j + L_j grad L_i).
+template <typename T>
+__device__ __forceinline__ void shape_grads(const Smem<T>& sm, int e, const double Lq[4], T n[10][3]) {
+  T gL[4][3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gL[c][d] = sm.geo[c * 3 + d][e];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) n[a][d] = (T(4) * T(Lq[a]) - T(1)) * gL[a][d];
+#pragma unroll
+  for (int m = 4; m < 10; ++m) {
+    const int i = edge_i(m), j = edge_j(m);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) n[m][d] = T(4) * (T(Lq[i]) * gL[j][d] + T(Lq[j]) * gL[i][d]);
+  }
+}
+
+// qp phase: warp w -> (q = w / 3, row i = w % 3), lane = element.
+template <typename T, int MAT, bool KV, bool WANT_A, int i>
+__device__ __forceinline__ void qp_phase(const Args<T>& A, Smem<T>& sm, bool& inverted) {
+  const int w = threadIdx.x >> 5, e = threadIdx.x & 31;
+  const int q = w / 3;
+  double Lq[4];
+  qp_bary(q, Lq);
+  const T wJ = T(qp_wfrac(q)) * sm.geo[12][e];
+  T n[10][3];
+  shape_grads(sm, e, Lq, n);
+  if (i == 0) {
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) sm.n[e * kNStride + q * 30 + a * 3 + d] = n[a][d];
+  }
+  T Hm[3][3], Fd[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Hm[r][c] = 0;
+      Fd[r][c] = 0;
+    }
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T ua = sm.u[(a * 3 + r) * E + e];
+      T va = T(0);
+      if (KV) va = sm.vel[(a * 3 + r) * E + e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Hm[r][c] += ua * n[a][c];
+        if (KV) Fd[r][c] += va * n[a][c];
+      }
+    }
+  QP<T> s;
+  constitutive<T, MAT, KV>(Hm, Fd, A.mat, s, inverted);
+  // force row i: f_a,i = wJ sum_J P_iJ n_aJ with P = F S
+  T Pi[3];
+#pragma unroll
+  for (int J = 0; J < 3; ++J) {
+    T acc = 0;
+#pragma unroll
+    for (int M = 0; M < 3; ++M) acc += s.F[i][M] * s.S[M][J];
+    Pi[J] = acc * wJ;
+  }
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+    sm.fq[e * kFStride + q * 30 + a * 3 + i] = Pi[0] * n[a][0] + Pi[1] * n[a][1] + Pi[2] * n[a][2];
+  if (WANT_A) tangent_row<T, MAT, KV, i>(s, A.mat, A.alpha, A.beta, wJ, &sm.A[e * kAStride + q * 81 + i * 27]);
+}
+
+// Force phase: warp w handles element DOFs c = w and c = w + 15.
+template <typename T>
+__device__ __forceinline__ void force_phase(const Args<T>& A, const Smem<T>& sm, int64_t e0) {
+  const int w = threadIdx.x >> 5, e = threadIdx.x & 31;
+  if (e0 + e >= A.real_end) return;
+#pragma unroll
+  for (int rep = 0; rep < 2; ++rep) {
+    const int c = w + 15 * rep;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc += sm.fq[e * kFStride + q * 30 + c];
+    const int a = c / 3, d = c % 3;
+    atomicAdd(&A.f[3 * (int64_t)sm.node[a][e] + d], double(acc));
+  }
+}
+
+// One block row of the element tangent for one element (lane) and component
+// i: K_{A0,b}[i][k] for b = A0 .. A0+NB-1, accumulated over the 5 qp, plus the
+// mass term, then scattered (the (b, A0) transposed entries too).
+template <typename T, int A0, int NB>
+__device__ __forceinline__ void tangent_blockrow(const Args<T>& A, const Smem<T>& sm, int64_t e0, int i) {
+  const int e = threadIdx.x & 31;
+  T acc[NB][3];
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+#pragma unroll 1
+  for (int q = 0; q < 5; ++q) {
+    const T* nq = &sm.n[e * kNStride + q * 30];
+    const T* Aq = &sm.A[e * kAStride + q * 81 + i * 27];
+    const T na[3] = {nq[A0 * 3], nq[A0 * 3 + 1], nq[A0 * 3 + 2]};
+    T An[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        An[k][L] = na[0] * Aq[0 * 9 + k * 3 + L] + na[1] * Aq[1 * 9 + k * 3 + L] + na[2] * Aq[2 * 9 + k * 3 + L];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int b = A0 + j;
+      const T n0b = nq[b * 3], n1b = nq[b * 3 + 1], n2b = nq[b * 3 + 2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[j][k] += An[k][0] * n0b + An[k][1] * n1b + An[k][2] * n2b;
+    }
+  }
+  if (e0 + e >= A.real_end) return;
+  const T ms = A.mass_scale * A.mat.rho * sm.geo[12][e] * T(1.0 / 420.0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    constexpr int a = A0;
+    const int b = A0 + j;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k == i) acc[j][k] += ms * T(c_mass420[a][b]);
+    if (A.values) {
+      const int s_row = sm.rbase[a][e] + sm.rstr[a][e] * i + 3 * sm.blk[e][a * 10 + b];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) atomic_add_t(&A.values[s_row + k], acc[j][k]);
+      if (j > 0) {
+        const int kb = 3 * sm.blk[e][b * 10 + a] + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomic_add_t(&A.values[sm.rbase[b][e] + sm.rstr[b][e] * k + kb], acc[j][k]);
+      }
+    }
+    if (A.K_elem) {
+      const int64_t ue = A.user_of[e0 + e];
+      T* Ke = A.K_elem + ue * 900;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Ke[(3 * a + i) * 30 + 3 * b + k] = acc[j][k];
+        if (j > 0) Ke[(3 * b + k) * 30 + 3 * a + i] = acc[j][k];
+      }
+    }
+  }
+}
+
+// Block rows a0 = P (b = P..9) and a1 = 9 - P (b = 9-P..9): 11 blocks, so the
+// 15 warps cover the 55 blocks of the symmetric 30x30 exactly once.
+template <typename T, int P>
+__device__ __forceinline__ void tangent_rows(const Args<T>& A, const Smem<T>& sm, int64_t e0, int i) {
+  tangent_blockrow<T, P, 10 - P>(A, sm, e0, i);
+  tangent_blockrow<T, 9 - P, P + 1>(A, sm, e0, i);
+}
+
+template <typename T, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
+__global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
+  const int64_t e0 = A.tile0 + (int64_t)blockIdx.x * E;
+  load_tile<T, DO_TANGENT>(A, sm, e0);
+  bool inverted = false;
+  switch ((threadIdx.x >> 5) % 3) {     // warp-uniform row of the qp phase
+    case 0: qp_phase<T, MAT, KV, DO_TANGENT, 0>(A, sm, inverted); break;
+    case 1: qp_phase<T, MAT, KV, DO_TANGENT, 1>(A, sm, inverted); break;
+    default: qp_phase<T, MAT, KV, DO_TANGENT, 2>(A, sm, inverted); break;
+  }
+  if (inverted && (e0 + (threadIdx.x & 31)) < A.real_end) atomicOr(A.flags, kFlagInverted);
+  __syncthreads();
+  if (DO_FORCE) force_phase(A, sm, e0);
+  if (DO_TANGENT) {
+    const int w = threadIdx.x >> 5;
+    const int p = w / 3, i = w % 3;
+    switch (p) {     // warp-uniform
+      case 0: tangent_rows<T, 0>(A, sm, e0, i); break;
+      case 1: tangent_rows<T, 1>(A, sm, e0, i); break;
+      case 2: tangent_rows<T, 2>(A, sm, e0, i); break;
+      case 3: tangent_rows<T, 3>(A, sm, e0, i); break;
+      default: tangent_rows<T, 4>(A, sm, e0, i); break;
+    }
+  }
+}
+
+template <typename T>
+MatT<T> to_matT(const MaterialDev& md) {
+  MatT<T> m;
+  m.lam = T(md.lam);
+  m.mu = T(md.mu);
+  m.C10 = T(md.C10);
+  m.C01 = T(md.C01);
+  m.kappa = T(md.kappa);
+  m.eta = T(md.eta);
+  m.lam_d = T(md.lam_d);
+  m.rho = T(md.rho);
+  return m;
+}
+
+template <typename T, bool DO_FORCE, bool DO_TANGENT>
+tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
+                     double mass_scale, double* f, void* values, void* K_elem) {
+  // the force-only variant does not need the tangent array (last member)
+  const size_t smem = DO_TANGENT ? sizeof(Smem<T>) : offsetof(Smem<T>, A);
+  for (const Segment& sg : m->segs) {
+    const int64_t ntiles = (sg.padded_end - sg.begin) / E;
+    if (ntiles == 0) continue;
+    Args<T> A;
+    A.conn = m->d_conn;
+    A.geo = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m->d_geo32)
+                                          : reinterpret_cast<const T*>(m->d_geo64);
+    A.blk = m->d_blk;
+    A.node_ptr = m->d_node_ptr;
+    A.user_of = m->d_user_of;
+    A.q_n = q_n;
+    A.v = v;
+    A.X = m->d_X;
+    A.h = h;
+    A.tile0 = sg.begin;
+    A.real_end = sg.end;
+    const MaterialDev& md = m->mats[sg.mat];
+    A.mat = to_matT<T>(md);
+    A.alpha = T(alpha);
+    A.beta = T(beta);
+    A.mass_scale = T(mass_scale);
+    A.f = f;
+    A.values = reinterpret_cast<T*>(values);
+    A.K_elem = reinterpret_cast<T*>(K_elem);
+    A.flags = m->d_flags;
+    void (*kern)(Args<T>) = nullptr;
+    const bool kv = md.kv != 0;
+    if (md.kind == TL_SVK)
+      kern = kv ? elem_kernel<T, TL_SVK, true, DO_FORCE, DO_TANGENT> : elem_kernel<T, TL_SVK, false, DO_FORCE, DO_TANGENT>;
+    else
+      kern = kv ? elem_kernel<T, TL_MOONEY_RIVLIN, true, DO_FORCE, DO_TANGENT>
+                : elem_kernel<T, TL_MOONEY_RIVLIN, false, DO_FORCE, DO_TANGENT>;
+    TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)ntiles, NT, smem, m->stream>>>(A);
+    TL_CUDA(m, cudaGetLastError());
+  }
+  return TL_OK;
+}
+
+}  // namespace
+
+tl_status launch_force(tl_mesh* m, const double* q_n, const double* v, double h, double* f) {
+  TL_CUDA(m, cudaMemsetAsync(f, 0, sizeof(double) * 3 * m->nn, m->stream));
+  if (m->precision == TL_FP32_ELEM)
+    return launch_all<float, true, false>(m, q_n, v, h, 0.0, 0.0, 0.0, f, nullptr, nullptr);
+  return launch_all<double, true, false>(m, q_n, v, h, 0.0, 0.0, 0.0, f, nullptr, nullptr);
+}
+
+tl_status launch_tangent(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
+                         double mass_scale, bool do_force, double* f, void* values, void* K_elem) {
+  if (do_force) {
+    TL_CUDA(m, cudaMemsetAsync(f, 0, sizeof(double) * 3 * m->nn, m->stream));
+    if (m->precision == TL_FP32_ELEM)
+      return launch_all<float, true, true>(m, q_n, v, h, alpha, beta, mass_scale, f, values, K_elem);
+    return launch_all<double, true, true>(m, q_n, v, h, alpha, beta, mass_scale, f, values, K_elem);
+  }
+  if (m->precision == TL_FP32_ELEM)
+    return launch_all<float, false, true>(m, q_n, v, h, alpha, beta, mass_scale, f, values, K_elem);
+  return launch_all<double, false, true>(m, q_n, v, h, alpha, beta, mass_scale, f, values, K_elem);
+}
+
+}  // namespace tl

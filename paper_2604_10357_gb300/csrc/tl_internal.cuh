@@ -1,0 +1,108 @@
+// Internal declarations of the T10 Total-Lagrangian GB300 library.
+// Paper: arxiv 2604.10357, Sec. 4.1-4.4 (precomputation, fixed sparsity,
+// internal force, gradient and Hessian assembly) and Algorithm 3.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tl.h"
+
+namespace tl {
+
+// Elements processed by one CTA of the element kernels; every material
+// segment of the internal element order is padded to a multiple of this.
+constexpr int kTile = 32;
+
+// Device-side sticky status bits (tl_sync turns them into tl_status).
+enum : uint32_t { kFlagInverted = 1u, kFlagNonFinite = 2u, kFlagBadIndex = 4u };
+
+struct MaterialDev {
+  int kind;          // tl_material_kind
+  int kv;            // Kelvin-Voigt on
+  double lam, mu;    // SVK Lame constants
+  double C10, C01, kappa;
+  double eta, lam_d;
+  double rho;
+};
+
+// One contiguous run of internal elements sharing a material.
+struct Segment {
+  int64_t begin, end;     // [begin, end) internal element ids (end - begin = real count)
+  int64_t padded_end;     // begin + multiple of kTile
+  int mat;                // index into the material table
+};
+
+struct Solver;   // sparse direct solver state (tl_solver.cu)
+
+}  // namespace tl
+
+struct tl_mesh {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = TL_FP64;
+  int64_t nn = 0, ne = 0, ne_pad = 0;
+  std::vector<tl::MaterialDev> mats;
+  std::vector<tl::Segment> segs;
+  std::string last_error;
+
+  // internal element order (segments by material, padded)
+  int32_t* d_conn = nullptr;      // ne_pad * 10
+  int32_t* d_user_of = nullptr;   // ne_pad: user element id, -1 for padding
+  double* d_geo64 = nullptr;      // ne_pad * 16: grad L (4x3), V, 0,0,0
+  float* d_geo32 = nullptr;       // same in float32 (TL_FP32_ELEM)
+  double* d_X = nullptr;          // 3 nn
+
+  // pattern (tl_build_pattern)
+  bool have_pattern = false;
+  int64_t nnz = 0, nnz_node = 0;
+  int32_t* d_node_ptr = nullptr;  // nn + 1
+  int32_t* d_node_col = nullptr;  // nnz_node
+  int32_t* d_row_ptr = nullptr;   // 3 nn + 1
+  int32_t* d_col = nullptr;       // nnz
+  uint8_t* d_blk = nullptr;       // ne_pad * 100: k of conn[b] in adj(conn[a])
+  double* d_mass = nullptr;       // nnz_node consistent mass M_IJ
+  double* d_mrow = nullptr;       // nn row sums of M
+  int64_t nfixed = 0;
+  int32_t* d_fixed_of_node = nullptr;  // nn: j (index in sorted fixed list) or -1
+  int32_t* d_fixed_diag = nullptr;     // 3 nfixed: CSR position of (r, r)
+
+  // scratch
+  uint32_t* d_flags = nullptr;    // sticky device status
+  double* d_partials = nullptr;   // reduction partials
+  int partials_cap = 0;
+
+  tl::Solver* solver = nullptr;
+};
+
+namespace tl {
+
+tl_status fail(tl_mesh* m, tl_status s, const std::string& msg);
+tl_status cuda_fail(tl_mesh* m, cudaError_t e, const char* what);
+
+#define TL_CUDA(m, call)                                   \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return tl::cuda_fail((m), _e, #call); \
+  } while (0)
+
+// element kernels (tl_element.cu)
+tl_status launch_force(tl_mesh* m, const double* q_n, const double* v, double h, double* f);
+tl_status launch_tangent(tl_mesh* m, const double* q_n, const double* v, double h,
+                         double alpha, double beta, double mass_scale, bool do_force,
+                         double* f, void* values, void* K_elem);
+
+// pattern kernels (tl_pattern.cu)
+tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed);
+tl_status expand_slot_map(const tl_mesh* m, int32_t* slot_map, cudaStream_t s);
+
+// residual (tl_residual.cu)
+tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n,
+                          const double* v, const double* f_int, const double* f_ext,
+                          const double* lambda, double* g, double* g_norm);
+tl_status launch_add_penalty(tl_mesh* m, double value, void* values);
+
+}  // namespace tl

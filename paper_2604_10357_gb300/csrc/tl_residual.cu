@@ -1,0 +1,124 @@
+// Residual of the velocity-level augmented Lagrangian and the clamp-row
+// contributions to the Newton matrix.
+//
+// Paper: arxiv 2604.10357
+//   eq. residual / eq. grad_L:  g = M (v - v_n)/h + f_int - f_ext - f_ff
+//                                   + h C_q^T (lambda + rho c)
+//   Sec. 4.4 (gradient): one thread per coefficient row of M, no atomics;
+//   eq. hessian: the h^2 rho C_q^T C_q term (identity rows for clamps).
+//
+// One thread per node handles its three DOFs (the mass CSR row is shared by
+// the three components); ||g||^2 is reduced per block into a partials array
+// and summed by a second one-block kernel, so the norm is deterministic.
+#include "tl_internal.cuh"
+
+namespace tl {
+namespace {
+
+constexpr int kResBlock = 256;
+
+__global__ void residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass,
+                                const double* mrow, const int32_t* fixed_of_node, const double* X, int64_t nn,
+                                double h, double rho, double gx, double gy, double gz, const double* q_n,
+                                const double* v_n, const double* v, const double* f_ext, const double* lambda,
+                                double* g /* in: f_int, out: g */, double* partials) {
+  __shared__ double red[kResBlock / 32];
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (I < nn) {
+    const int p0 = node_ptr[I], p1 = node_ptr[I + 1];
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    for (int p = p0; p < p1; ++p) {
+      const int64_t J = node_col[p];
+      const double mij = mass[p];
+      acc0 += mij * (v[3 * J] - v_n[3 * J]);
+      acc1 += mij * (v[3 * J + 1] - v_n[3 * J + 1]);
+      acc2 += mij * (v[3 * J + 2] - v_n[3 * J + 2]);
+    }
+    const double acc[3] = {acc0, acc1, acc2};
+    const double grav[3] = {gx, gy, gz};
+    const int j = fixed_of_node[I];
+    const double mr = mrow[I];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int64_t r = 3 * I + d;
+      double gd = acc[d] / h + g[r] - mr * grav[d];
+      if (f_ext) gd -= f_ext[r];
+      if (j >= 0) {
+        const double c = (q_n[r] + h * v[r]) - X[r];
+        gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
+      }
+      g[r] = gd;
+      sq += gd * gd;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < kResBlock / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void finish_norm(const double* partials, int n, double* out, uint32_t* flags) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += partials[i];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double u = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    if (threadIdx.x == 0) {
+      if (!isfinite(u)) atomicOr(flags, kFlagNonFinite);
+      *out = sqrt(u);
+    }
+  }
+}
+
+template <typename T>
+__global__ void add_diag(const int32_t* diag, int64_t n, T value, T* values) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) values[diag[t]] += value;
+}
+
+}  // namespace
+
+tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n, const double* v,
+                          const double* f_int, const double* f_ext, const double* lambda, double* g,
+                          double* g_norm) {
+  const int nb = (int)((m->nn + kResBlock - 1) / kResBlock);
+  if (nb > m->partials_cap) {
+    if (m->d_partials) cudaFree(m->d_partials);
+    m->d_partials = nullptr;
+    m->partials_cap = 0;
+    TL_CUDA(m, cudaMalloc(&m->d_partials, sizeof(double) * nb));
+    m->partials_cap = nb;
+  }
+  if (f_int != g) TL_CUDA(m, cudaMemcpyAsync(g, f_int, sizeof(double) * 3 * m->nn, cudaMemcpyDeviceToDevice, m->stream));
+  residual_kernel<<<nb, kResBlock, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow,
+                                                    m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
+                                                    p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_ext,
+                                                    lambda, g, m->d_partials);
+  TL_CUDA(m, cudaGetLastError());
+  finish_norm<<<1, 1024, 0, m->stream>>>(m->d_partials, nb, g_norm, m->d_flags);
+  TL_CUDA(m, cudaGetLastError());
+  return TL_OK;
+}
+
+tl_status launch_add_penalty(tl_mesh* m, double value, void* values) {
+  const int64_t n = 3 * m->nfixed;
+  if (n == 0) return TL_OK;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  if (m->precision == TL_FP32_ELEM)
+    add_diag<float><<<nb, 256, 0, m->stream>>>(m->d_fixed_diag, n, (float)value, (float*)values);
+  else
+    add_diag<double><<<nb, 256, 0, m->stream>>>(m->d_fixed_diag, n, value, (double*)values);
+  TL_CUDA(m, cudaGetLastError());
+  return TL_OK;
+}
+
+}  // namespace tl

@@ -1,0 +1,218 @@
+"""Python binding of the C ABI in include/tl.h (argument marshalling only).
+
+Every compute step runs in the CUDA kernels of libtl_gb300.so; this module
+only converts torch tensors / numpy arrays into pointers and sizes.  There is
+no CPU fallback: if the shared library is missing or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtl_gb300.so")
+
+TL_FP64, TL_FP32_ELEM = 0, 1
+TL_SVK, TL_MOONEY_RIVLIN = 0, 1
+
+STATUS = {0: "TL_OK", 1: "TL_ERR_INVALID_ARG", 2: "TL_ERR_OOM", 3: "TL_ERR_CUDA", 4: "TL_ERR_INVERTED",
+          5: "TL_ERR_NONFINITE", 6: "TL_ERR_NOT_CONVERGED", 7: "TL_ERR_SOLVER", 8: "TL_ERR_TIMEOUT",
+          9: "TL_ERR_OVERFLOW", 10: "TL_ERR_UNSUPPORTED", 11: "TL_ERR_STATE"}
+
+
+class TLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tl_material(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("_pad", C.c_int32), ("E", C.c_double), ("nu", C.c_double),
+                ("rho0", C.c_double), ("C10", C.c_double), ("C01", C.c_double), ("kappa", C.c_double),
+                ("eta_d", C.c_double), ("lambda_d", C.c_double)]
+
+
+class tl_params(C.Structure):
+    _fields_ = [("h", C.c_double), ("rho_alm", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
+                ("eps_out", C.c_double), ("gravity", C.c_double * 3), ("max_inner", C.c_int32),
+                ("max_outer", C.c_int32), ("flags", C.c_int32), ("_pad", C.c_int32)]
+
+
+class tl_newton_stats(C.Structure):
+    _fields_ = [("inner_iters", C.c_int32), ("outer_iters", C.c_int32), ("converged", C.c_int32),
+                ("_pad", C.c_int32), ("g_ref", C.c_double), ("g_norm", C.c_double), ("c_norm", C.c_double),
+                ("ms_total", C.c_double), ("ms_assembly", C.c_double), ("ms_solver", C.c_double)]
+
+
+class tl_mesh_info(C.Structure):
+    _fields_ = [("nn", C.c_int64), ("ne", C.c_int64), ("ndof", C.c_int64), ("nnz", C.c_int64),
+                ("nnz_node", C.c_int64), ("nfixed", C.c_int64), ("precision", C.c_int32),
+                ("nmat", C.c_int32)]
+
+
+# every symbol declared in include/tl.h, with (restype, argtypes)
+_P = C.c_void_p
+SIGNATURES = {
+    "tl_mesh_create": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P, C.c_int32, _P, _P]),
+    "tl_build_pattern": (C.c_int, [_P, _P, C.c_int64, _P]),
+    "tl_get_pattern": (C.c_int, [_P, _P, _P, _P]),
+    "tl_eval_force": (C.c_int, [_P, _P, _P, C.c_double, _P]),
+    "tl_eval_tangent": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_double, _P]),
+    "tl_assemble_hessian": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P, _P]),
+    "tl_eval_residual": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tl_sync": (C.c_int, [_P]),
+    "tl_mesh_info_get": (C.c_int, [_P, _P]),
+    "tl_status_string": (C.c_char_p, [C.c_int]),
+    "tl_last_error": (C.c_char_p, [_P]),
+    "tl_mesh_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtl_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first (paper_2604_10357_gb300.build.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def material(kind="svk", E=0.0, nu=0.0, rho0=1000.0, C10=0.0, C01=0.0, kappa=0.0, eta_d=0.0,
+             lambda_d=0.0, **_):
+    k = TL_SVK if kind in ("svk", TL_SVK) else TL_MOONEY_RIVLIN
+    return tl_material(k, 0, E, nu, rho0, C10, C01, kappa, eta_d, lambda_d)
+
+
+def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-10, gravity=(0.0, 0.0, -9.81),
+           max_inner=20, max_outer=5):
+    p = tl_params()
+    p.h, p.rho_alm, p.rtol, p.atol, p.eps_out = h, rho_alm, rtol, atol, eps_out
+    for i in range(3):
+        p.gravity[i] = gravity[i]
+    p.max_inner, p.max_outer, p.flags = max_inner, max_outer, 0
+    return p
+
+
+class Mesh:
+    """A tl_mesh handle.  Device arrays are torch CUDA tensors (float64 nodal
+    vectors of length 3 nn, node-major)."""
+
+    def __init__(self, X, conn, materials, mat_of_elem=None, precision=TL_FP64, stream=None):
+        import torch
+        self._torch = torch
+        lib = load_library()
+        self.lib = lib
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 10)
+        if isinstance(materials, dict):
+            materials = [materials]
+        mats = (tl_material * len(materials))(*[material(**m) for m in materials])
+        moe = None if mat_of_elem is None else np.ascontiguousarray(mat_of_elem, dtype=np.int32)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = lib.tl_mesh_create(X.ctypes.data_as(_P), X.shape[0], conn.ctypes.data_as(_P), conn.shape[0],
+                                C.cast(mats, _P), len(materials),
+                                None if moe is None else moe.ctypes.data_as(_P), int(precision),
+                                C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise TLError(st, lib.tl_last_error(None).decode())
+        self.h = h
+        self.nn, self.ne = X.shape[0], conn.shape[0]
+        self.ndof = 3 * self.nn
+        self.precision = precision
+        self.vdtype = torch.float32 if precision == TL_FP32_ELEM else torch.float64
+        self.nnz = None
+        self.nfixed = 0
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise TLError(st, self.lib.tl_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.tl_mesh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- ABI calls -----------------------------------------------------------
+    def build_pattern(self, fixed_nodes=()):
+        fixed = np.ascontiguousarray(np.asarray(fixed_nodes, dtype=np.int32).reshape(-1))
+        nnz = C.c_int64()
+        self._check(self.lib.tl_build_pattern(self.h, fixed.ctypes.data_as(_P) if len(fixed) else None,
+                                              len(fixed), C.byref(nnz)))
+        self.nnz = nnz.value
+        self.nfixed = len(fixed)
+        return self.nnz
+
+    def get_pattern(self, with_slot_map=False):
+        torch = self._torch
+        row_ptr = torch.empty(self.ndof + 1, dtype=torch.int32, device="cuda")
+        col = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
+        slot = torch.empty(self.ne * 900, dtype=torch.int32, device="cuda") if with_slot_map else None
+        self._check(self.lib.tl_get_pattern(self.h, _ptr(row_ptr), _ptr(col), _ptr(slot)))
+        return row_ptr, col, slot
+
+    def eval_force(self, q_n, v, h, out=None):
+        torch = self._torch
+        out = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if out is None else out
+        self._check(self.lib.tl_eval_force(self.h, _ptr(q_n), _ptr(v), float(h), _ptr(out)))
+        return out
+
+    def eval_tangent(self, q_n, v, h, alpha=1.0, beta=0.0, out=None):
+        torch = self._torch
+        out = torch.empty(self.ne * 900, dtype=self.vdtype, device="cuda") if out is None else out
+        self._check(self.lib.tl_eval_tangent(self.h, _ptr(q_n), _ptr(v), float(h), float(alpha),
+                                             float(beta), _ptr(out)))
+        return out
+
+    def assemble_hessian(self, q_n, v, h, rho_alm, values=None, f_int=None):
+        torch = self._torch
+        values = torch.empty(self.nnz, dtype=self.vdtype, device="cuda") if values is None else values
+        self._check(self.lib.tl_assemble_hessian(self.h, _ptr(q_n), _ptr(v), float(h), float(rho_alm),
+                                                 _ptr(values), _ptr(f_int)))
+        return values
+
+    def eval_residual(self, prm, q_n, v_n, v, f_ext=None, lam=None, g=None, g_norm=None):
+        torch = self._torch
+        g = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if g is None else g
+        g_norm = torch.empty(1, dtype=torch.float64, device="cuda") if g_norm is None else g_norm
+        self._check(self.lib.tl_eval_residual(self.h, C.byref(prm), _ptr(q_n), _ptr(v_n), _ptr(v),
+                                              _ptr(f_ext), _ptr(lam), _ptr(g), _ptr(g_norm)))
+        return g, g_norm
+
+    def sync(self):
+        self._check(self.lib.tl_sync(self.h))
+
+    def info(self):
+        inf = tl_mesh_info()
+        self._check(self.lib.tl_mesh_info_get(self.h, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in tl_mesh_info._fields_}
