@@ -1,0 +1,399 @@
+"""Benchmark of the T10 force + tangent + CSR-assembly hot path on GB300.
+
+One step = one pass of the hot path over the 960,000-element box
+(20 x 4 x 2 m, 200 x 40 x 20 hexes x 6 T10, SVK + Kelvin-Voigt, FP32 element
+form, FP64 residual): the fused element kernel (internal force + 30x30
+tangent + scatter into the fixed-pattern CSR Hessian, values zeroed first),
+the clamp-penalty diagonal and the residual g with its norm.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent
+replica of the workload (the assembly needs no exchange; weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "T10 force+tangent+assembly elems/s; Newton step ms to 1e-8, chosen vs plain"
+UNIT = "elems/s"
+
+# Algorithmic FP32 flops per element of the fused pass (force + tangent +
+# assembly), counted from the formulas the kernel evaluates (FMA = 2), once
+# per element, without the kernel's own redundancy; see the project design
+# notes for the line-by-line count.
+FLOPS_PER_ELEM = {("svk", False): 28_067, ("svk", True): 29_412,
+                  ("mr", False): 33_782, ("mr", True): 36_477}
+
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def fp32_alu_peak_tflops():
+    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def algorithmic_bytes_per_elem(ne, nn, nnz, value_bytes):
+    """Minimal DRAM bytes of one pass, per element: every H value written once,
+    node data (X, q_n, v) read once and f written once, per-element
+    connectivity (40 B), geometry (13 values) and slot indices (100 B) read
+    once, node row pointers read once."""
+    per_node = 72 + 24 + 4
+    per_elem = 40 + 13 * value_bytes + 100
+    return (nnz * value_bytes + nn * per_node + ne * per_elem) / ne
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu_id = gpu_id
+        self.t_marks = {}
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark(self, name):
+        self.t_marks[name] = time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            loaded = [x for x in sm if x > 0.5 * max(sm)] or sm
+            out.update(sm_mhz=statistics.median(loaded), sm_max_mhz=max(smax), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def traffic_from_profile(kernel_src):
+    """DRAM bytes per launch of the element kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "elem_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        if d.get("kernel_sha256") == h:
+            return d["dram_bytes_per_launch_full_workload"]
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_sample_workload(nx=10, ny=4, nz=4):
+    """A sub-box of the large workload: same hex size (0.1 m), material and
+    field recipe, nx*ny*nz*6 elements."""
+    from paper_2604_10357_gb300 import inputs
+    rng = np.random.default_rng(1000 + 5)
+    m = inputs.box_t10(nx, ny, nz, 0.1 * nx, 0.1 * ny, 0.1 * nz)
+    q, _ = inputs.sine_mode_field(m, 0.02, rng)
+    v = inputs.gaussian_velocity(m, 0.05, rng)
+    mat = dict(inputs.SVK_1E7, eta_d=1e3, lambda_d=1e3)
+    return m, q, v, mat
+
+
+def oracle_step_rate(budget_s=12.0, min_reps=1, nx=10, ny=4, nz=4):
+    """Elements/s of the oracle's force + tangent + CSR assembly + residual."""
+    from oracle import assembly as asm
+    m, q, v, mat = oracle_sample_workload(nx, ny, nz)
+    om = asm.OracleMesh(m.X, m.conn, [mat], fixed_nodes=m.fixed_nodes)
+    om.pattern()
+    lam = np.zeros(3 * len(m.fixed_nodes))
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        om.hessian_values(q, v, 1e-3, 1e12)
+        om.residual(v, q, v, 1e-3, None, (0, 0, -9.81), lam, 1e12)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= budget_s:
+            break
+    return reps * m.ne / el, reps, m.ne, el
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2604_10357_gb300 import build, inputs, tl
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    tl.load_library()
+
+    w = inputs.workload_large_svk_kv(scale=args.scale)
+    m = w["mesh"]
+    prec = tl.TL_FP32_ELEM if args.precision == "fp32" else tl.TL_FP64
+    stream = torch.cuda.current_stream()
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=prec, stream=stream)
+    t_pat = time.perf_counter()
+    nnz = g.build_pattern(m.fixed_nodes)
+    t_pat = time.perf_counter() - t_pat
+    h, rho = w["h"], 1e12
+    prm = tl.params(h=h, rho_alm=rho)
+    q = torch.as_tensor(w["q_n"].reshape(-1), device="cuda")
+    v = torch.as_tensor(w["v"].reshape(-1), device="cuda")
+    vdtype = torch.float32 if prec == tl.TL_FP32_ELEM else torch.float64
+    values = torch.empty(nnz, dtype=vdtype, device="cuda")
+    f = torch.empty(3 * m.nn, dtype=torch.float64, device="cuda")
+    res = torch.empty(3 * m.nn, dtype=torch.float64, device="cuda")
+    gnorm = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def step(qd, vd):
+        g.assemble_hessian(qd, vd, h, rho, values=values, f_int=f)
+        g.eval_residual(prm, qd, vd, vd, f_int=f, g=res, g_norm=gnorm)
+
+    for _ in range(args.warmup):
+        step(q, v)
+    g.sync()
+    g.timing_read()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.5)
+    g.timing_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(q, v)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    tim = g.timing_read()
+    g.timing_enable(False)
+    g.sync()
+
+    # end-to-end through the public API with host buffers: H2D of the step's
+    # inputs from pinned memory, the pass, D2H of the residual norm
+    e2e = None
+    if not args.no_e2e:
+        q_h = torch.as_tensor(w["q_n"].reshape(-1)).pin_memory()
+        v_h = torch.as_tensor(w["v"].reshape(-1)).pin_memory()
+        out_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        q_d, v_d = torch.empty_like(q), torch.empty_like(v)
+        ke = max(3, min(args.steps, 50))
+        for _ in range(2):
+            q_d.copy_(q_h, non_blocking=True)
+            v_d.copy_(v_h, non_blocking=True)
+            step(q_d, v_d)
+            out_h.copy_(gnorm, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            q_d.copy_(q_h, non_blocking=True)
+            v_d.copy_(v_h, non_blocking=True)
+            step(q_d, v_d)
+            out_h.copy_(gnorm, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / ke
+        e2e = {"value": m.ne / (ms_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(q_h.numel() * 8 + v_h.numel() * 8),
+               "d2h_bytes_per_step": int(out_h.numel() * 8), "ms_per_step": ms_e2e, "steps": ke}
+    if rank == 0:
+        sampler.stop()
+
+    # max over ranks of the timed region
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * m.ne * args.steps / (ms_max * 1e-3)
+
+    if rank != 0:
+        return None
+    kind = w["material"]["kind"]
+    kv = bool(w["material"].get("eta_d") or w["material"].get("lambda_d"))
+    vbytes = 4 if prec == tl.TL_FP32_ELEM else 8
+    elem_ms = tim["ms_element"] / max(1, tim["n_element"])
+    flops = FLOPS_PER_ELEM[(kind, kv)] * m.ne
+    bpe = algorithmic_bytes_per_elem(m.ne, m.nn, nnz, vbytes)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if prec == tl.TL_FP32_ELEM:
+        peak = fp32_alu_peak_tflops()
+        achieved = flops / (elem_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_source": "FP32 ALU: 152 SM x 128 lanes x 2 x 2070 MHz (derived, not measured)"}
+    else:
+        roofline = {"bound": "alu", "achieved": flops / (elem_ms * 1e-3) / 1e12, "peak": None,
+                    "unit": "TFLOP/s", "frac": None, "peak_source": "FP64 ALU peak not yet measured"}
+    roofline["traffic"] = traffic_from_profile(
+        os.path.join(ROOT, "paper_2604_10357_gb300", "csrc", "tl_element.cu"))
+    roofline["kernel"] = "elem_kernel (fused force + tangent + CSR scatter)"
+    roofline["kernel_ms"] = elem_ms
+    roofline["algorithmic_bytes_per_elem"] = bpe
+    roofline["hbm_frac_of_measured"] = (bpe * m.ne / (elem_ms * 1e-3)) / (hbm * 1e9)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == tl.TL_FP32_ELEM else "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "ne": m.ne, "nn": m.nn, "ndof": 3 * m.nn, "nnz": nnz,
+                   "precision": "FP32 element form, FP64 residual" if prec == tl.TL_FP32_ELEM else "FP64",
+                   "material": "SVK E=1e7 nu=0.3 + Kelvin-Voigt 1e3", "h": h,
+                   "l2": "no flush: the H values written every step (%.2f GB) exceed L2" % (nnz * vbytes / 1e9),
+                   "parallelism": f"replicas x{world}", "pattern_build_s": t_pat},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(tim["launches"]),
+        "clocks": sampler.summary(),
+    }
+    return line
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, on this arm's metric: each step a bounded
+    sample (a 4x2x2-hex sub-box of the same workload, 96 elements)."""
+    if rank != 0:
+        return None
+    from oracle import assembly as asm
+    m, q, v, mat = oracle_sample_workload(4, 2, 2)
+    om = asm.OracleMesh(m.X, m.conn, [mat], fixed_nodes=m.fixed_nodes)
+    om.pattern()
+    lam = np.zeros(3 * len(m.fixed_nodes))
+
+    def step():
+        om.hessian_values(q, v, 1e-3, 1e12)
+        om.residual(v, q, v, 1e-3, None, (0, 0, -9.81), lam, 1e12)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps * m.ne / el
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "box 20x4x2 m, 200x40x20 hex x6 = 960,000 T10, SVK+KV",
+                       "sample": f"{m.ne}-element sub-box (4x2x2 hexes, same hex size and field recipe) per step"},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                             "sample": f"{m.ne} elements per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--scale", type=float, default=1.0, help="hex-count scale of the box (1.0 = 960k T10)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if line is not None:
+        if not args.no_cpu_baseline and world == 1:
+            rate, reps, n, el = oracle_step_rate()
+            line["cpu_baseline"] = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
+                                    "sample": f"{n}-element sub-box (10x4x4 hexes) of the same workload, "
+                                              f"{reps} passes in {el:.1f} s (numpy, one thread)"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

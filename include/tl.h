@@ -171,14 +171,32 @@ tl_status tl_assemble_hessian(tl_mesh* m, const double* q_n, const double* v, do
 /* Residual of eq. residual / eq. grad_L:
  *   g = M (v - v_n)/h + f_int(q_n + h v, v) - f_ext - f_ff + h C_q^T (lambda + rho c)
  * with f_ff = (row sums of M) x gravity and c = (q_n + h v - X) on clamped DOFs.
+ *   f_int   ndof float64 holding f_int(q_n + h v, v) already (e.g. from the
+ *           fused tl_assemble_hessian pass), or NULL to evaluate it here
  *   f_ext   ndof float64 or NULL (zero)
  *   lambda  3*nfixed float64 (multiplier of DOF d of the j-th fixed node at
  *           3j+d, fixed nodes in ascending id order), or NULL (zero)
  *   g       ndof float64, overwritten
  *   g_norm  1 float64 (device), receives ||g||_2 */
 tl_status tl_eval_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n,
-                           const double* v, const double* f_ext, const double* lambda,
-                           double* g, double* g_norm);
+                           const double* v, const double* f_int, const double* f_ext,
+                           const double* lambda, double* g, double* g_norm);
+
+/* Kernel timing and launch counting (instrumentation of the calls above).
+ * While enabled, every element-kernel pass and every residual pass of this
+ * handle is bracketed by CUDA events recorded on the handle's stream.
+ * tl_timing_read synchronizes the stream, sums the elapsed times per
+ * category and resets the accumulators.  Launch counts are kept always. */
+typedef struct tl_timing {
+  double ms_element;          /* fused force / tangent / assembly kernels */
+  double ms_residual;         /* residual + norm kernels */
+  int64_t n_element;          /* element passes timed */
+  int64_t n_residual;
+  int64_t launches;           /* kernels of this library launched since the last read */
+} tl_timing;
+
+tl_status tl_timing_enable(tl_mesh* m, int32_t on);
+tl_status tl_timing_read(tl_mesh* m, tl_timing* out);
 
 /* Wait for the handle's stream and return the first sticky device-side error
  * (TL_ERR_INVERTED, TL_ERR_NONFINITE) raised since the last tl_sync, then

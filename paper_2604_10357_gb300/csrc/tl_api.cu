@@ -26,6 +26,33 @@ tl_status cuda_fail(tl_mesh* m, cudaError_t e, const char* what) {
   return TL_ERR_CUDA;
 }
 
+cudaEvent_t timer_open(tl_mesh* m) {
+  if (!m->timing) return nullptr;
+  cudaEvent_t ev = nullptr;
+  if (!m->ev_pool.empty()) {
+    ev = m->ev_pool.back();
+    m->ev_pool.pop_back();
+  } else if (cudaEventCreate(&ev) != cudaSuccess) {
+    return nullptr;
+  }
+  cudaEventRecord(ev, m->stream);
+  return ev;
+}
+
+void timer_close(tl_mesh* m, cudaEvent_t start, TimerCat cat) {
+  if (!m->timing || !start) return;
+  cudaEvent_t ev = nullptr;
+  if (!m->ev_pool.empty()) {
+    ev = m->ev_pool.back();
+    m->ev_pool.pop_back();
+  } else if (cudaEventCreate(&ev) != cudaSuccess) {
+    m->ev_pool.push_back(start);
+    return;
+  }
+  cudaEventRecord(ev, m->stream);
+  (cat == kTimeElement ? m->ev_elem : m->ev_resid).emplace_back(start, ev);
+}
+
 namespace {
 
 void free_mesh(tl_mesh* m) {
@@ -38,6 +65,15 @@ void free_mesh(tl_mesh* m) {
                   m->d_flags, m->d_partials};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+  for (auto& pr : m->ev_elem) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (auto& pr : m->ev_resid) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
   cudaSetDevice(cur);
   delete m;
 }
@@ -284,12 +320,43 @@ tl_status tl_assemble_hessian(tl_mesh* m, const double* q_n, const double* v, do
 }
 
 tl_status tl_eval_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n, const double* v,
-                           const double* f_ext, const double* lambda, double* g, double* g_norm) {
+                           const double* f_int, const double* f_ext, const double* lambda, double* g,
+                           double* g_norm) {
   if (!m || !p || !q_n || !v_n || !v || !g || !g_norm || !(p->h > 0.0)) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
-  tl_status s = launch_force(m, q_n, v, p->h, g);      // g <- f_int(q_n + h v, v)
-  if (s != TL_OK) return s;
-  return launch_residual(m, p, q_n, v_n, v, g, f_ext, lambda, g, g_norm);
+  if (!f_int) {
+    tl_status s = launch_force(m, q_n, v, p->h, g);    // g <- f_int(q_n + h v, v)
+    if (s != TL_OK) return s;
+    f_int = g;
+  }
+  return launch_residual(m, p, q_n, v_n, v, f_int, f_ext, lambda, g, g_norm);
+}
+
+tl_status tl_timing_enable(tl_mesh* m, int32_t on) {
+  if (!m) return TL_ERR_INVALID_ARG;
+  m->timing = on != 0;
+  return TL_OK;
+}
+
+tl_status tl_timing_read(tl_mesh* m, tl_timing* out) {
+  if (!m || !out) return TL_ERR_INVALID_ARG;
+  TL_CUDA(m, cudaStreamSynchronize(m->stream));
+  std::memset(out, 0, sizeof(*out));
+  auto drain = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, double& ms, int64_t& n) {
+    for (auto& pr : v) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) ms += t;
+      ++n;
+      m->ev_pool.push_back(pr.first);
+      m->ev_pool.push_back(pr.second);
+    }
+    v.clear();
+  };
+  drain(m->ev_elem, out->ms_element, out->n_element);
+  drain(m->ev_resid, out->ms_residual, out->n_residual);
+  out->launches = m->launches;
+  m->launches = 0;
+  return TL_OK;
 }
 
 tl_status tl_sync(tl_mesh* m) {

@@ -604,6 +604,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
                      double mass_scale, double* f, void* values, void* K_elem) {
   // the force-only variant does not need the tangent array (last member)
   const size_t smem = DO_TANGENT ? sizeof(Smem<T>) : offsetof(Smem<T>, A);
+  cudaEvent_t t0 = timer_open(m);
   for (const Segment& sg : m->segs) {
     const int64_t ntiles = (sg.padded_end - sg.begin) / E;
     if (ntiles == 0) continue;
@@ -639,7 +640,9 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)ntiles, NT, smem, m->stream>>>(A);
     TL_CUDA(m, cudaGetLastError());
+    ++m->launches;
   }
+  timer_close(m, t0, kTimeElement);
   return TL_OK;
 }
 

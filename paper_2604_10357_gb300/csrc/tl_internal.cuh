@@ -76,6 +76,12 @@ struct tl_mesh {
   int partials_cap = 0;
 
   tl::Solver* solver = nullptr;
+
+  // instrumentation (tl_timing_*)
+  bool timing = false;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_elem, ev_resid;
 };
 
 namespace tl {
@@ -104,5 +110,11 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
                           const double* v, const double* f_int, const double* f_ext,
                           const double* lambda, double* g, double* g_norm);
 tl_status launch_add_penalty(tl_mesh* m, double value, void* values);
+
+// instrumentation helpers (tl_api.cu): a category's event pair is opened
+// before and closed after the launches it brackets.
+enum TimerCat { kTimeElement = 0, kTimeResidual = 1 };
+cudaEvent_t timer_open(tl_mesh* m);
+void timer_close(tl_mesh* m, cudaEvent_t start, TimerCat cat);
 
 }  // namespace tl

@@ -20,8 +20,8 @@ constexpr int kResBlock = 256;
 __global__ void residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass,
                                 const double* mrow, const int32_t* fixed_of_node, const double* X, int64_t nn,
                                 double h, double rho, double gx, double gy, double gz, const double* q_n,
-                                const double* v_n, const double* v, const double* f_ext, const double* lambda,
-                                double* g /* in: f_int, out: g */, double* partials) {
+                                const double* v_n, const double* v, const double* f_int, const double* f_ext,
+                                const double* lambda, double* g, double* partials) {
   __shared__ double red[kResBlock / 32];
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double sq = 0.0;
@@ -42,7 +42,7 @@ __global__ void residual_kernel(const int32_t* node_ptr, const int32_t* node_col
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int64_t r = 3 * I + d;
-      double gd = acc[d] / h + g[r] - mr * grav[d];
+      double gd = acc[d] / h + f_int[r] - mr * grav[d];
       if (f_ext) gd -= f_ext[r];
       if (j >= 0) {
         const double c = (q_n[r] + h * v[r]) - X[r];
@@ -98,14 +98,17 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
     TL_CUDA(m, cudaMalloc(&m->d_partials, sizeof(double) * nb));
     m->partials_cap = nb;
   }
-  if (f_int != g) TL_CUDA(m, cudaMemcpyAsync(g, f_int, sizeof(double) * 3 * m->nn, cudaMemcpyDeviceToDevice, m->stream));
+  cudaEvent_t t0 = timer_open(m);
+  // f_int may alias g: each thread reads its own entries before writing them
   residual_kernel<<<nb, kResBlock, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow,
                                                     m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
-                                                    p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_ext,
-                                                    lambda, g, m->d_partials);
+                                                    p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_int,
+                                                    f_ext, lambda, g, m->d_partials);
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(m->d_partials, nb, g_norm, m->d_flags);
   TL_CUDA(m, cudaGetLastError());
+  m->launches += 2;
+  timer_close(m, t0, kTimeResidual);
   return TL_OK;
 }
 
@@ -118,6 +121,7 @@ tl_status launch_add_penalty(tl_mesh* m, double value, void* values) {
   else
     add_diag<double><<<nb, 256, 0, m->stream>>>(m->d_fixed_diag, n, value, (double*)values);
   TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
   return TL_OK;
 }
 

@@ -47,6 +47,11 @@ class tl_newton_stats(C.Structure):
                 ("ms_total", C.c_double), ("ms_assembly", C.c_double), ("ms_solver", C.c_double)]
 
 
+class tl_timing(C.Structure):
+    _fields_ = [("ms_element", C.c_double), ("ms_residual", C.c_double), ("n_element", C.c_int64),
+                ("n_residual", C.c_int64), ("launches", C.c_int64)]
+
+
 class tl_mesh_info(C.Structure):
     _fields_ = [("nn", C.c_int64), ("ne", C.c_int64), ("ndof", C.c_int64), ("nnz", C.c_int64),
                 ("nnz_node", C.c_int64), ("nfixed", C.c_int64), ("precision", C.c_int32),
@@ -62,7 +67,9 @@ SIGNATURES = {
     "tl_eval_force": (C.c_int, [_P, _P, _P, C.c_double, _P]),
     "tl_eval_tangent": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_double, _P]),
     "tl_assemble_hessian": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P, _P]),
-    "tl_eval_residual": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tl_eval_residual": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tl_timing_enable": (C.c_int, [_P, C.c_int32]),
+    "tl_timing_read": (C.c_int, [_P, _P]),
     "tl_sync": (C.c_int, [_P]),
     "tl_mesh_info_get": (C.c_int, [_P, _P]),
     "tl_status_string": (C.c_char_p, [C.c_int]),
@@ -201,13 +208,21 @@ class Mesh:
                                                  _ptr(values), _ptr(f_int)))
         return values
 
-    def eval_residual(self, prm, q_n, v_n, v, f_ext=None, lam=None, g=None, g_norm=None):
+    def eval_residual(self, prm, q_n, v_n, v, f_ext=None, lam=None, g=None, g_norm=None, f_int=None):
         torch = self._torch
         g = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if g is None else g
         g_norm = torch.empty(1, dtype=torch.float64, device="cuda") if g_norm is None else g_norm
         self._check(self.lib.tl_eval_residual(self.h, C.byref(prm), _ptr(q_n), _ptr(v_n), _ptr(v),
-                                              _ptr(f_ext), _ptr(lam), _ptr(g), _ptr(g_norm)))
+                                              _ptr(f_int), _ptr(f_ext), _ptr(lam), _ptr(g), _ptr(g_norm)))
         return g, g_norm
+
+    def timing_enable(self, on=True):
+        self._check(self.lib.tl_timing_enable(self.h, 1 if on else 0))
+
+    def timing_read(self):
+        t = tl_timing()
+        self._check(self.lib.tl_timing_read(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in tl_timing._fields_}
 
     def sync(self):
         self._check(self.lib.tl_sync(self.h))
