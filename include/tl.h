@@ -182,6 +182,32 @@ tl_status tl_eval_residual(tl_mesh* m, const tl_params* p, const double* q_n, co
                            const double* v, const double* f_int, const double* f_ext,
                            const double* lambda, double* g, double* g_norm);
 
+/* Allocation-free variant of tl_eval_residual.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * during the time-stepping loop -- for example a host application whose
+ * device memory is owned by its own pool allocator or fixed budget, or a
+ * latency-critical loop in which a cudaMalloc (which may synchronize the
+ * device) is not acceptable.
+ *   It computes the same g and ||g||_2 as tl_eval_residual, with the same
+ * kernels, but keeps its norm partials in a fixed scratch array compiled into
+ * the library (128 KiB of device memory held by every GPU that loads the
+ * library, until the process exits) instead of a buffer owned by the handle.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   f_int is required here (compute it with tl_eval_force or the fused
+ * tl_assemble_hessian pass); the other arguments are as in tl_eval_residual.
+ *   Limit: meshes of at most 4,194,304 nodes (16,384 blocks of 256 nodes);
+ * larger meshes get TL_ERR_UNSUPPORTED with a message.
+ *   The first call on a device looks up the scratch array's device address
+ * (with the mesh's device current, which this call requires); make that first
+ * call before any stream capture.  Every call shares the one scratch array:
+ * calls that overlap on the GPU (other streams, other handles) race and may
+ * return wrong norms; serialise them.  Each call writes every scratch entry it
+ * reads, so nothing needs clearing between calls. */
+tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, const double* q_n,
+                                   const double* v_n, const double* v, const double* f_int,
+                                   const double* f_ext, const double* lambda, double* g,
+                                   double* g_norm);
+
 /* Kernel timing and launch counting (instrumentation of the calls above).
  * While enabled, every element-kernel pass and every residual pass of this
  * handle is bracketed by CUDA events recorded on the handle's stream.

@@ -10,12 +10,22 @@
 // One thread per node handles its three DOFs (the mass CSR row is shared by
 // the three components); ||g||^2 is reduced per block into a partials array
 // and summed by a second one-block kernel, so the norm is deterministic.
+#include <mutex>
+
 #include "tl_internal.cuh"
 
 namespace tl {
 namespace {
 
 constexpr int kResBlock = 256;
+
+// Scratch of the allocation-free residual (tl_eval_residual_noalloc): one
+// partial sum of ||g||^2 per block of kResBlock nodes.  It lives in the
+// library image, so every GPU that loads the library holds these 128 KiB until
+// the process exits.  Every call overwrites the entries it uses before reading
+// them, so nothing has to be cleared between calls.
+constexpr int kNoAllocMaxBlocks = 16384;                    // nn <= 4,194,304
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 
 __global__ void residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass,
                                 const double* mrow, const int32_t* fixed_of_node, const double* X, int64_t nn,
@@ -112,6 +122,30 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   return TL_OK;
 }
 
+namespace {
+
+// Device address of g_noalloc_partials, looked up once per device.  In host
+// code the array's name is only a host-side stand-in, so the address must come
+// from cudaGetSymbolAddress with that device current.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+tl_status noalloc_scratch(tl_mesh* m, int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(m, TL_ERR_UNSUPPORTED, "device ordinal too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+    if (e != cudaSuccess || !ptr) return cuda_fail(m, e, "cudaGetSymbolAddress(g_noalloc_partials)");
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return TL_OK;
+}
+
+}  // namespace
+
 tl_status launch_add_penalty(tl_mesh* m, double value, void* values) {
   const int64_t n = 3 * m->nfixed;
   if (n == 0) return TL_OK;
@@ -126,3 +160,30 @@ tl_status launch_add_penalty(tl_mesh* m, double value, void* values) {
 }
 
 }  // namespace tl
+
+extern "C" tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, const double* q_n,
+                                              const double* v_n, const double* v, const double* f_int,
+                                              const double* f_ext, const double* lambda, double* g,
+                                              double* g_norm) {
+  using namespace tl;
+  if (!m || !p || !q_n || !v_n || !v || !f_int || !g || !g_norm || !(p->h > 0.0)) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  const int64_t nb = (m->nn + kResBlock - 1) / kResBlock;
+  if (nb > kNoAllocMaxBlocks)
+    return fail(m, TL_ERR_UNSUPPORTED,
+                "tl_eval_residual_noalloc handles at most 4,194,304 nodes; this mesh has " + std::to_string(m->nn));
+  int dev = -1;
+  TL_CUDA(m, cudaGetDevice(&dev));
+  if (dev != m->device) return fail(m, TL_ERR_INVALID_ARG, "the mesh's device must be current");
+  double* partials = nullptr;
+  tl_status s = noalloc_scratch(m, dev, &partials);
+  if (s != TL_OK) return s;
+  residual_kernel<<<(unsigned)nb, kResBlock, 0, m->stream>>>(
+      m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
+      p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_int, f_ext, lambda, g, partials);
+  TL_CUDA(m, cudaGetLastError());
+  finish_norm<<<1, 1024, 0, m->stream>>>(partials, (int)nb, g_norm, m->d_flags);
+  TL_CUDA(m, cudaGetLastError());
+  m->launches += 2;
+  return TL_OK;
+}

@@ -68,6 +68,7 @@ SIGNATURES = {
     "tl_eval_tangent": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_double, _P]),
     "tl_assemble_hessian": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P, _P]),
     "tl_eval_residual": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tl_eval_residual_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "tl_timing_enable": (C.c_int, [_P, C.c_int32]),
     "tl_timing_read": (C.c_int, [_P, _P]),
     "tl_sync": (C.c_int, [_P]),
@@ -214,6 +215,14 @@ class Mesh:
         g_norm = torch.empty(1, dtype=torch.float64, device="cuda") if g_norm is None else g_norm
         self._check(self.lib.tl_eval_residual(self.h, C.byref(prm), _ptr(q_n), _ptr(v_n), _ptr(v),
                                               _ptr(f_int), _ptr(f_ext), _ptr(lam), _ptr(g), _ptr(g_norm)))
+        return g, g_norm
+
+    def eval_residual_noalloc(self, prm, q_n, v_n, v, f_int, g, g_norm, f_ext=None, lam=None):
+        """tl_eval_residual_noalloc: outputs g and g_norm must be given (no
+        allocation anywhere on this path)."""
+        self._check(self.lib.tl_eval_residual_noalloc(self.h, C.byref(prm), _ptr(q_n), _ptr(v_n), _ptr(v),
+                                                      _ptr(f_int), _ptr(f_ext), _ptr(lam), _ptr(g),
+                                                      _ptr(g_norm)))
         return g, g_norm
 
     def timing_enable(self, on=True):
