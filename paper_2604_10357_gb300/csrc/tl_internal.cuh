@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/tl.h"
+#include "tl.h"
 
 namespace tl {
 

@@ -35,10 +35,24 @@ def ragged_mixed():
                 mat_of_elem=mesh.body_of_elem, h=1e-3)
 
 
+def shuffled_order():
+    """Elements in random order: most 32-element tiles then touch more nodes
+    than the FP32 kernel's shared image holds, exercising its per-entry
+    global-scatter fallback."""
+    w = inputs.workload_small_svk()
+    rng = np.random.default_rng(99)
+    m = w["mesh"]
+    perm = rng.permutation(m.ne)
+    m2 = inputs.Mesh(X=m.X, conn=m.conn[perm].copy(), fixed_nodes=m.fixed_nodes, extent=m.extent,
+                     hex_size=m.hex_size)
+    return dict(w, name="shuffled", mesh=m2)
+
+
 WORKLOADS = {
     "small_svk": inputs.workload_small_svk,
     "mid_mr_kv": inputs.workload_mid_mr_kv,
     "ragged_mixed": ragged_mixed,
+    "shuffled": shuffled_order,
 }
 
 
