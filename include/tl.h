@@ -224,6 +224,32 @@ typedef struct tl_timing {
 tl_status tl_timing_enable(tl_mesh* m, int32_t on);
 tl_status tl_timing_read(tl_mesh* m, tl_timing* out);
 
+/* One backward-Euler time step by Newton's method in the augmented-Lagrangian
+ * loop (Algorithm 3 without line search, Algorithm 1's multiplier update,
+ * eq. stepmap q = q_n + h v).  Per inner iteration: residual and ||g|| on the
+ * device (norm copied to the host for the test), Hessian assembly, numeric
+ * Cholesky factorization on the fixed pattern and solve H dv = -g (vendor
+ * sparse solver; symbolic analysis with a nested-dissection ordering is done
+ * on the first call and kept by the handle), v += dv.  After each inner loop
+ * the clamp constraints c = q - X are evaluated and, if the inner loop
+ * converged, lambda += rho c.
+ *   q_n, v_n   ndof float64 (device): previous configuration and velocity
+ *   v_init     ndof float64 start velocity (e.g. a learned warm start), or
+ *              NULL for v_n; the inner tolerance is always relative to
+ *              ||g(v_n; lambda)||
+ *   f_ext      ndof float64 applied loads, or NULL
+ *   lambda     3*nfixed float64 multipliers (in/out, persist across steps)
+ *   v_out,q_out ndof float64 outputs (v_out may not alias q_n / v_n)
+ *   stats      HOST, optional: iterations, norms, split timings
+ * For TL_FP32_ELEM meshes the Hessian, its factorization and the direction
+ * are float32 while the residual keeps a float64 force evaluation.
+ * Synchronous.  Returns TL_ERR_NOT_CONVERGED (with the last iterate in
+ * v_out / q_out) when the caps are reached, TL_ERR_SOLVER when the matrix is
+ * not positive definite. */
+tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n,
+                         const double* v_init, const double* f_ext, double* lambda,
+                         double* v_out, double* q_out, tl_newton_stats* stats);
+
 /* Wait for the handle's stream and return the first sticky device-side error
  * (TL_ERR_INVERTED, TL_ERR_NONFINITE) raised since the last tl_sync, then
  * clear it. */

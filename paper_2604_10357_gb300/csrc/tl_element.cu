@@ -361,6 +361,13 @@ tl_status launch_force(tl_mesh* m, const double* q_n, const double* v, double h,
   return launch_all<double, true, false>(m, q_n, v, h, 0.0, 0.0, 0.0, f, nullptr, nullptr);
 }
 
+tl_status launch_force_prec(tl_mesh* m, const double* q_n, const double* v, double h, double* f, bool fp64) {
+  TL_CUDA(m, cudaMemsetAsync(f, 0, sizeof(double) * 3 * m->nn, m->stream));
+  if (m->precision == TL_FP32_ELEM && !fp64)
+    return launch_all<float, true, false>(m, q_n, v, h, 0.0, 0.0, 0.0, f, nullptr, nullptr);
+  return launch_all<double, true, false>(m, q_n, v, h, 0.0, 0.0, 0.0, f, nullptr, nullptr);
+}
+
 tl_status launch_tangent(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
                          double mass_scale, bool do_force, double* f, void* values, void* K_elem) {
   if (do_force) {

@@ -76,6 +76,9 @@ struct tl_mesh {
   int partials_cap = 0;
 
   tl::Solver* solver = nullptr;
+  // Newton work buffers (tl_newton_step), allocated on first use
+  double *nw_g = nullptr, *nw_f = nullptr, *nw_dv = nullptr, *nw_scal = nullptr;
+  void* nw_values = nullptr;
 
   // instrumentation (tl_timing_*)
   bool timing = false;
@@ -97,6 +100,11 @@ tl_status cuda_fail(tl_mesh* m, cudaError_t e, const char* what);
 
 // element kernels (tl_element.cu)
 tl_status launch_force(tl_mesh* m, const double* q_n, const double* v, double h, double* f);
+// force with the element arithmetic forced to float64 when fp64 is set
+tl_status launch_force_prec(tl_mesh* m, const double* q_n, const double* v, double h, double* f, bool fp64);
+
+// sparse direct solver (tl_solver.cu)
+void solver_destroy(Solver* s);
 tl_status launch_tangent(tl_mesh* m, const double* q_n, const double* v, double h,
                          double alpha, double beta, double mass_scale, bool do_force,
                          double* f, void* values, void* K_elem);

@@ -71,6 +71,7 @@ SIGNATURES = {
     "tl_eval_residual_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "tl_timing_enable": (C.c_int, [_P, C.c_int32]),
     "tl_timing_read": (C.c_int, [_P, _P]),
+    "tl_newton_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "tl_sync": (C.c_int, [_P]),
     "tl_mesh_info_get": (C.c_int, [_P, _P]),
     "tl_status_string": (C.c_char_p, [C.c_int]),
@@ -232,6 +233,21 @@ class Mesh:
         t = tl_timing()
         self._check(self.lib.tl_timing_read(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in tl_timing._fields_}
+
+    def newton_step(self, prm, q_n, v_n, lam, v_init=None, f_ext=None, v_out=None, q_out=None,
+                    raise_on_nonconvergence=True):
+        """tl_newton_step; returns (v, q, stats dict).  lam is updated in place."""
+        torch = self._torch
+        v_out = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if v_out is None else v_out
+        q_out = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if q_out is None else q_out
+        st = tl_newton_stats()
+        rc = self.lib.tl_newton_step(self.h, C.byref(prm), _ptr(q_n), _ptr(v_n), _ptr(v_init), _ptr(f_ext),
+                                     _ptr(lam), _ptr(v_out), _ptr(q_out), C.byref(st))
+        stats = {f: getattr(st, f) for f, _ in tl_newton_stats._fields_ if f != "_pad"}
+        stats["status"] = rc
+        if rc != 0 and (raise_on_nonconvergence or rc != 6):
+            raise TLError(rc, self.lib.tl_last_error(self.h).decode())
+        return v_out, q_out, stats
 
     def sync(self):
         self._check(self.lib.tl_sync(self.h))
