@@ -82,6 +82,11 @@ typedef struct tl_material {
 /* Newton / ALM controls (Algorithm 3).  The inner loop stops when
  * ||g|| <= max(atol, rtol * ||g(v_n; lambda)||), i.e. relative to the
  * residual at the plain previous-velocity start whatever start is used. */
+typedef enum tl_linear_solver {
+  TL_SOLVER_DIRECT = 0,       /* vendor sparse Cholesky (analysis once, factor per iteration) */
+  TL_SOLVER_PCG = 1           /* preconditioned CG on the device (3x3 block Jacobi) */
+} tl_linear_solver;
+
 typedef struct tl_params {
   double h;                   /* time step */
   double rho_alm;             /* ALM penalty rho */
@@ -90,8 +95,9 @@ typedef struct tl_params {
   double gravity[3];          /* body-force field per unit mass (f_ff) */
   int32_t max_inner;          /* L_max */
   int32_t max_outer;          /* K_max */
-  int32_t flags;              /* reserved, pass 0 */
-  int32_t _pad;
+  int32_t linear_solver;      /* tl_linear_solver */
+  int32_t lin_max_iter;       /* PCG iteration cap (0: 5000) */
+  double lin_rtol;            /* PCG: ||H dv + g|| <= lin_rtol ||g|| (0: 1e-10) */
 } tl_params;
 
 typedef struct tl_newton_stats {
@@ -104,7 +110,9 @@ typedef struct tl_newton_stats {
   double c_norm;              /* last ||c||_2 */
   double ms_total;            /* wall time of the whole step */
   double ms_assembly;         /* residual + Hessian assembly kernels */
-  double ms_solver;           /* vendor factorisation + solves */
+  double ms_solver;           /* factorisation + solves (or PCG) */
+  int32_t lin_iters;          /* PCG iterations summed over the step */
+  int32_t _pad2;
 } tl_newton_stats;
 
 typedef struct tl_mesh_info {

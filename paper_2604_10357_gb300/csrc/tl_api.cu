@@ -64,6 +64,7 @@ void free_mesh(tl_mesh* m) {
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
                   m->d_flags, m->d_partials, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_values};
   solver_destroy(m->solver);
+  pcg_destroy(m->pcg);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);

@@ -37,6 +37,7 @@ struct Segment {
 };
 
 struct Solver;   // sparse direct solver state (tl_solver.cu)
+struct PcgWork;  // preconditioned CG state (tl_pcg.cu)
 
 }  // namespace tl
 
@@ -76,6 +77,7 @@ struct tl_mesh {
   int partials_cap = 0;
 
   tl::Solver* solver = nullptr;
+  tl::PcgWork* pcg = nullptr;
   // Newton work buffers (tl_newton_step), allocated on first use
   double *nw_g = nullptr, *nw_f = nullptr, *nw_dv = nullptr, *nw_scal = nullptr;
   void* nw_values = nullptr;
@@ -103,8 +105,11 @@ tl_status launch_force(tl_mesh* m, const double* q_n, const double* v, double h,
 // force with the element arithmetic forced to float64 when fp64 is set
 tl_status launch_force_prec(tl_mesh* m, const double* q_n, const double* v, double h, double* f, bool fp64);
 
-// sparse direct solver (tl_solver.cu)
+// sparse direct solver (tl_solver.cu) and PCG (tl_pcg.cu)
 void solver_destroy(Solver* s);
+void pcg_destroy(PcgWork* w);
+tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv, double rtol, int max_iter,
+                    int* iters_out);
 tl_status launch_tangent(tl_mesh* m, const double* q_n, const double* v, double h,
                          double alpha, double beta, double mass_scale, bool do_force,
                          double* f, void* values, void* K_elem);

@@ -80,8 +80,14 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
   if (m->nfixed > 0 && !lambda) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
   const auto t_start = std::chrono::steady_clock::now();
-  tl_status st = solver_setup(m);
-  if (st != TL_OK) return st;
+  const bool use_pcg = p->linear_solver == TL_SOLVER_PCG;
+  if (!use_pcg) {
+    tl_status st = solver_setup(m);
+    if (st != TL_OK) return st;
+  }
+  const double lin_rtol = p->lin_rtol > 0.0 ? p->lin_rtol : 1e-10;
+  const int lin_max = p->lin_max_iter > 0 ? p->lin_max_iter : 5000;
+  int lin_total = 0;
   const int64_t ndof = 3 * m->nn;
   const size_t vb = (m->precision == TL_FP32_ELEM ? sizeof(float) : sizeof(double));
   // work buffers: allocated on the first call, owned by the handle
@@ -160,7 +166,13 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
       NTRY(launch_tangent(m, q_n, v, p->h, p->h, 1.0, 1.0 / p->h, false, nullptr, w.values, nullptr));
       NTRY(launch_add_penalty(m, p->h * p->h * p->rho_alm, w.values));
       cudaEventRecord(ev[1], s);
-      NTRY(solver_factor_solve(m, w.values, w.g, w.dv));
+      if (use_pcg) {
+        int it = 0;
+        NTRY(pcg_solve(m, w.values, w.g, w.dv, lin_rtol, lin_max, &it));
+        lin_total += it;
+      } else {
+        NTRY(solver_factor_solve(m, w.values, w.g, w.dv));
+      }
       axpy_kernel<<<nb, 256, 0, s>>>(v, w.dv, 1.0, ndof);
       NCUDA(cudaGetLastError());
       ++m->launches;
@@ -203,6 +215,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     stats->ms_assembly = ms_asm;
     stats->ms_solver = ms_sol;
+    stats->lin_iters = lin_total;
   }
   return converged ? TL_OK : fail(m, TL_ERR_NOT_CONVERGED, "Newton / ALM iteration caps reached");
 }

@@ -35,16 +35,21 @@ class tl_material(C.Structure):
                 ("eta_d", C.c_double), ("lambda_d", C.c_double)]
 
 
+TL_SOLVER_DIRECT, TL_SOLVER_PCG = 0, 1
+
+
 class tl_params(C.Structure):
     _fields_ = [("h", C.c_double), ("rho_alm", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
                 ("eps_out", C.c_double), ("gravity", C.c_double * 3), ("max_inner", C.c_int32),
-                ("max_outer", C.c_int32), ("flags", C.c_int32), ("_pad", C.c_int32)]
+                ("max_outer", C.c_int32), ("linear_solver", C.c_int32), ("lin_max_iter", C.c_int32),
+                ("lin_rtol", C.c_double)]
 
 
 class tl_newton_stats(C.Structure):
     _fields_ = [("inner_iters", C.c_int32), ("outer_iters", C.c_int32), ("converged", C.c_int32),
                 ("_pad", C.c_int32), ("g_ref", C.c_double), ("g_norm", C.c_double), ("c_norm", C.c_double),
-                ("ms_total", C.c_double), ("ms_assembly", C.c_double), ("ms_solver", C.c_double)]
+                ("ms_total", C.c_double), ("ms_assembly", C.c_double), ("ms_solver", C.c_double),
+                ("lin_iters", C.c_int32), ("_pad2", C.c_int32)]
 
 
 class tl_timing(C.Structure):
@@ -116,12 +121,13 @@ def material(kind="svk", E=0.0, nu=0.0, rho0=1000.0, C10=0.0, C01=0.0, kappa=0.0
 
 
 def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-10, gravity=(0.0, 0.0, -9.81),
-           max_inner=20, max_outer=5):
+           max_inner=20, max_outer=5, linear_solver=TL_SOLVER_DIRECT, lin_max_iter=0, lin_rtol=0.0):
     p = tl_params()
     p.h, p.rho_alm, p.rtol, p.atol, p.eps_out = h, rho_alm, rtol, atol, eps_out
     for i in range(3):
         p.gravity[i] = gravity[i]
-    p.max_inner, p.max_outer, p.flags = max_inner, max_outer, 0
+    p.max_inner, p.max_outer = max_inner, max_outer
+    p.linear_solver, p.lin_max_iter, p.lin_rtol = linear_solver, lin_max_iter, lin_rtol
     return p
 
 
@@ -243,7 +249,7 @@ class Mesh:
         st = tl_newton_stats()
         rc = self.lib.tl_newton_step(self.h, C.byref(prm), _ptr(q_n), _ptr(v_n), _ptr(v_init), _ptr(f_ext),
                                      _ptr(lam), _ptr(v_out), _ptr(q_out), C.byref(st))
-        stats = {f: getattr(st, f) for f, _ in tl_newton_stats._fields_ if f != "_pad"}
+        stats = {f: getattr(st, f) for f, _ in tl_newton_stats._fields_ if not f.startswith("_pad")}
         stats["status"] = rc
         if rc != 0 and (raise_on_nonconvergence or rc != 6):
             raise TLError(rc, self.lib.tl_last_error(self.h).decode())

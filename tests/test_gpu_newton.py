@@ -34,8 +34,9 @@ def small_case():
     return w, om, prm, ref
 
 
+@pytest.mark.parametrize("solver", ["direct", "pcg"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_newton_step_matches_oracle(small_case, prec):
+def test_newton_step_matches_oracle(small_case, prec, solver):
     tl = _tl()
     w, om, prm, ref = small_case
     m = w["mesh"]
@@ -43,7 +44,8 @@ def test_newton_step_matches_oracle(small_case, prec):
     g.build_pattern(m.fixed_nodes)
     lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
     p = tl.params(h=prm.h, rho_alm=prm.rho_alm, rtol=prm.rtol, eps_out=prm.eps_out,
-                  max_inner=prm.max_inner, max_outer=prm.max_outer)
+                  max_inner=prm.max_inner, max_outer=prm.max_outer,
+                  linear_solver=tl.TL_SOLVER_PCG if solver == "pcg" else tl.TL_SOLVER_DIRECT)
     v, q, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
     v = v.cpu().numpy()
     assert st["converged"] == 1
