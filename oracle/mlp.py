@@ -1,0 +1,109 @@
+"""CPU oracle of the warm-start MLP (no counterpart in the paper).
+
+The paper starts every Newton solve from the previous velocity (Algorithm 3,
+v <- v_n).  The learned warm start replaces that start by
+v0 = v_n + s_out * MLP(features) on free nodes (0 on clamped nodes), with a
+per-node MLP 10 -> 64 -> 64 -> 64 -> 3, tanh hidden layers, linear output.
+Weights and activations are bfloat16, products are accumulated in float32.
+
+This module restates the forward pass, the mean-squared-error loss and the
+backward pass with plain numpy.  `bf16=True` rounds weights and stored
+activations to bfloat16 (round to nearest even) exactly where the CUDA kernels
+do; `bf16=False, dtype=float64` is the smooth reference that finite
+differences pin.
+
+Parameter vector layout (length 9219): W1 (64x10), b1 (64), W2 (64x64), b2 (64),
+W3 (64x64), b3 (64), W4 (3x64), b4 (3); W rows are outputs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SIZES = [(64, 10), (64,), (64, 64), (64,), (64, 64), (64,), (3, 64), (3,)]
+NPARAM = sum(int(np.prod(s)) for s in SIZES)
+
+
+def unpack(theta):
+    out, o = [], 0
+    for s in SIZES:
+        n = int(np.prod(s))
+        out.append(theta[o:o + n].reshape(s))
+        o += n
+    return out
+
+
+def bf16_round(x):
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as float32."""
+    x = np.asarray(x, dtype=np.float32)
+    b = x.view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    r = ((b + 0x7FFF + lsb) >> 16) << 16
+    r = np.where(np.isnan(x), b, r)
+    return r.astype(np.uint32).view(np.float32)
+
+
+def init_params(rng):
+    """Glorot-uniform weights, zero biases (float32)."""
+    theta = []
+    for s in SIZES:
+        if len(s) == 2:
+            lim = np.sqrt(6.0 / (s[0] + s[1]))
+            theta.append(rng.uniform(-lim, lim, size=s).astype(np.float32).ravel())
+        else:
+            theta.append(np.zeros(s, np.float32))
+    return np.concatenate(theta)
+
+
+def forward(theta, x, bf16=True, dtype=np.float32):
+    """Returns (out, cache).  x: (N, 10)."""
+    W1, b1, W2, b2, W3, b3, W4, b4 = [a.astype(dtype) for a in unpack(theta)]
+    rnd = bf16_round if bf16 else (lambda a: a)
+    if bf16:
+        W1, W2, W3, W4 = rnd(W1), rnd(W2), rnd(W3), rnd(W4)
+        b1, b2, b3, b4 = rnd(b1), rnd(b2), rnd(b3), rnd(b4)
+    x = rnd(np.asarray(x, dtype=dtype))
+    h1 = rnd(np.tanh(x @ W1.T + b1))
+    h2 = rnd(np.tanh(h1 @ W2.T + b2))
+    h3 = rnd(np.tanh(h2 @ W3.T + b3))
+    out = h3 @ W4.T + b4
+    return out, (x, h1, h2, h3, (W1, W2, W3, W4))
+
+
+def mse(out, target, weight):
+    """L = sum_n w_n ||out_n - target_n||^2 and dL/dout."""
+    d = out - target
+    return float(np.sum(weight[:, None] * d * d)), 2.0 * weight[:, None] * d
+
+
+def backward(theta, cache, dout):
+    """Gradient of sum(dout * out) with respect to theta (same layout)."""
+    x, h1, h2, h3, (W1, W2, W3, W4) = cache
+    g4 = dout.T @ h3
+    gb4 = dout.sum(0)
+    d3 = (dout @ W4) * (1.0 - h3 * h3)
+    g3 = d3.T @ h2
+    gb3 = d3.sum(0)
+    d2 = (d3 @ W3) * (1.0 - h2 * h2)
+    g2 = d2.T @ h1
+    gb2 = d2.sum(0)
+    d1 = (d2 @ W2) * (1.0 - h1 * h1)
+    g1 = d1.T @ x
+    gb1 = d1.sum(0)
+    return np.concatenate([a.ravel() for a in (g1, gb1, g2, gb2, g3, gb3, g4, gb4)])
+
+
+def adam_step(theta, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update on the float32 master parameters (in place)."""
+    m[:] = b1 * m + (1 - b1) * grad
+    v[:] = b2 * v + (1 - b2) * grad * grad
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    theta -= lr * mh / (np.sqrt(vh) + eps)
+    return theta
+
+
+def features(q_n, v_n, v_prev, X, fixed_mask, s_v, s_u):
+    """Per-node inputs: v_n / s_v, v_{n-1} / s_v, (q_n - X) / s_u, fixed flag."""
+    q_n, v_n, v_prev, X = (np.asarray(a).reshape(-1, 3) for a in (q_n, v_n, v_prev, X))
+    return np.concatenate([v_n / s_v, v_prev / s_v, (q_n - X) / s_u,
+                           np.asarray(fixed_mask, np.float64)[:, None]], axis=1)
