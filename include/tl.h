@@ -258,6 +258,38 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
                          const double* v_init, const double* f_ext, double* lambda,
                          double* v_out, double* q_out, tl_newton_stats* stats);
 
+/* ---- learned Newton warm start (no counterpart in the paper) -------------
+ * The paper starts each Newton solve from v_n (Algorithm 3).  These calls
+ * run a per-node MLP 10 -> 64 -> 64 -> 64 -> 3 (tanh hidden layers, linear
+ * output) with bfloat16 weights and activations and float32 accumulation,
+ * and train it.  params: 9219 bf16 values (raw uint16 bits) laid out as
+ * W1 (64x10, row = output), b1 (64), W2 (64x64), b2 (64), W3 (64x64), b3 (64),
+ * W4 (3x64), b4 (3).  All arrays are device pointers; stream is a
+ * cudaStream_t (NULL = legacy default stream).  Asynchronous. */
+
+/* out[n][3] = MLP(feats[n][10]); acts (n x 192 bf16: h1, h2, h3) or NULL. */
+tl_status tl_mlp_forward(const uint16_t* params, const float* feats, int64_t n, float* out,
+                         uint16_t* acts, void* stream);
+/* grads[9219] (float32, accumulated: zero it first) += d/dparams sum(dout * out),
+ * from the activations a forward pass saved. */
+tl_status tl_mlp_backward(const uint16_t* params, const float* feats, const uint16_t* acts,
+                          const float* dout, int64_t n, float* grads, void* stream);
+/* dout = 2 w (out - target); *loss (float64, accumulated) += sum w |out - target|^2. */
+tl_status tl_mlp_mse_grad(const float* out, const float* target, const float* weight, int64_t n,
+                          float* dout, double* loss, void* stream);
+/* One Adam step on the float32 master copy; params receives its bf16 rounding. */
+tl_status tl_mlp_adam(float* master, uint16_t* params, const float* grads, float* m1, float* m2,
+                      int64_t n, float lr, float beta1, float beta2, float eps, int32_t step,
+                      void* stream);
+/* feats[nn][10] = (v_n/s_v, v_prev/s_v, (q_n - X)/s_u, fixed flag); v_prev NULL -> v_n. */
+tl_status tl_mlp_features(tl_mesh* m, const double* q_n, const double* v_n, const double* v_prev,
+                          double s_v, double s_u, float* feats);
+/* v_init = v_n + s_out * MLP(features) on free nodes, 0 on clamped nodes.
+ * work: 13*nn float32 scratch (device). */
+tl_status tl_warm_start(tl_mesh* m, const uint16_t* params, const double* q_n, const double* v_n,
+                        const double* v_prev, double s_v, double s_u, double s_out, float* work,
+                        double* v_init);
+
 /* Wait for the handle's stream and return the first sticky device-side error
  * (TL_ERR_INVERTED, TL_ERR_NONFINITE) raised since the last tl_sync, then
  * clear it. */

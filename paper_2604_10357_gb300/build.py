@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtl_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["tl_api.cu", "tl_pattern.cu", "tl_element.cu", "tl_residual.cu", "tl_solver.cu", "tl_pcg.cu", "tl_newton.cu"]
+SOURCES = ["tl_api.cu", "tl_pattern.cu", "tl_element.cu", "tl_residual.cu", "tl_solver.cu", "tl_pcg.cu", "tl_newton.cu", "tl_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

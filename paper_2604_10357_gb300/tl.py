@@ -77,6 +77,13 @@ SIGNATURES = {
     "tl_timing_enable": (C.c_int, [_P, C.c_int32]),
     "tl_timing_read": (C.c_int, [_P, _P]),
     "tl_newton_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tl_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+    "tl_mlp_backward": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P, _P]),
+    "tl_mlp_mse_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "tl_mlp_adam": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
+                              C.c_int32, _P]),
+    "tl_mlp_features": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, _P]),
+    "tl_warm_start": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P, _P]),
     "tl_sync": (C.c_int, [_P]),
     "tl_mesh_info_get": (C.c_int, [_P, _P]),
     "tl_status_string": (C.c_char_p, [C.c_int]),
@@ -129,6 +136,50 @@ def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-10, gravity=(0.
     p.max_inner, p.max_outer = max_inner, max_outer
     p.linear_solver, p.lin_max_iter, p.lin_rtol = linear_solver, lin_max_iter, lin_rtol
     return p
+
+
+MLP_NPARAM = 9219
+
+
+def _stream_ptr():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _chk(st, what):
+    if st != 0:
+        raise TLError(st, what)
+
+
+def mlp_forward(params_bf16, feats, out=None, acts=None):
+    """params_bf16: int16 CUDA tensor (bf16 bits, 9219); feats (n, 10) float32."""
+    import torch
+    lib = load_library()
+    n = feats.shape[0]
+    out = torch.empty(n, 3, dtype=torch.float32, device="cuda") if out is None else out
+    _chk(lib.tl_mlp_forward(_ptr(params_bf16), _ptr(feats), n, _ptr(out), _ptr(acts), _stream_ptr()),
+         "tl_mlp_forward")
+    return out
+
+
+def mlp_backward(params_bf16, feats, acts, dout, grads):
+    lib = load_library()
+    _chk(lib.tl_mlp_backward(_ptr(params_bf16), _ptr(feats), _ptr(acts), _ptr(dout), feats.shape[0],
+                             _ptr(grads), _stream_ptr()), "tl_mlp_backward")
+    return grads
+
+
+def mlp_mse_grad(out, target, weight, dout, loss):
+    lib = load_library()
+    _chk(lib.tl_mlp_mse_grad(_ptr(out), _ptr(target), _ptr(weight), out.shape[0], _ptr(dout), _ptr(loss),
+                             _stream_ptr()), "tl_mlp_mse_grad")
+
+
+def mlp_adam(master, params_bf16, grads, m1, m2, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    lib = load_library()
+    _chk(lib.tl_mlp_adam(_ptr(master), _ptr(params_bf16), _ptr(grads), _ptr(m1), _ptr(m2), master.numel(),
+                         float(lr), float(beta1), float(beta2), float(eps), int(step), _stream_ptr()),
+         "tl_mlp_adam")
 
 
 class Mesh:
@@ -254,6 +305,21 @@ class Mesh:
         if rc != 0 and (raise_on_nonconvergence or rc != 6):
             raise TLError(rc, self.lib.tl_last_error(self.h).decode())
         return v_out, q_out, stats
+
+    def mlp_features(self, q_n, v_n, v_prev, s_v, s_u, feats=None):
+        torch = self._torch
+        feats = torch.empty(self.nn, 10, dtype=torch.float32, device="cuda") if feats is None else feats
+        self._check(self.lib.tl_mlp_features(self.h, _ptr(q_n), _ptr(v_n), _ptr(v_prev), float(s_v), float(s_u),
+                                             _ptr(feats)))
+        return feats
+
+    def warm_start(self, params_bf16, q_n, v_n, v_prev, s_v, s_u, s_out, work=None, v_init=None):
+        torch = self._torch
+        work = torch.empty(13 * self.nn, dtype=torch.float32, device="cuda") if work is None else work
+        v_init = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if v_init is None else v_init
+        self._check(self.lib.tl_warm_start(self.h, _ptr(params_bf16), _ptr(q_n), _ptr(v_n), _ptr(v_prev),
+                                           float(s_v), float(s_u), float(s_out), _ptr(work), _ptr(v_init)))
+        return v_init
 
     def sync(self):
         self._check(self.lib.tl_sync(self.h))
