@@ -97,7 +97,10 @@ typedef struct tl_params {
   int32_t max_outer;          /* K_max */
   int32_t linear_solver;      /* tl_linear_solver */
   int32_t lin_max_iter;       /* PCG iteration cap (0: 5000) */
-  double lin_rtol;            /* PCG: ||H dv + g|| <= lin_rtol ||g|| (0: 1e-10) */
+  double lin_rtol;            /* PCG: ||H dv + g|| <= eta ||g|| with eta = lin_rtol (0: 1e-10), */
+                              /* or, if lin_adaptive, eta = max(lin_rtol, 0.1 target / ||g||)   */
+  int32_t lin_adaptive;       /* 1: inexact Newton (solve only as tightly as the target needs) */
+  int32_t _pad3;
 } tl_params;
 
 typedef struct tl_newton_stats {
@@ -113,6 +116,7 @@ typedef struct tl_newton_stats {
   double ms_solver;           /* factorisation + solves (or PCG) */
   int32_t lin_iters;          /* PCG iterations summed over the step */
   int32_t _pad2;
+  double g_init;              /* ||g|| at the start velocity (v_init or v_n) */
 } tl_newton_stats;
 
 typedef struct tl_mesh_info {
@@ -281,14 +285,17 @@ tl_status tl_mlp_mse_grad(const float* out, const float* target, const float* we
 tl_status tl_mlp_adam(float* master, uint16_t* params, const float* grads, float* m1, float* m2,
                       int64_t n, float lr, float beta1, float beta2, float eps, int32_t step,
                       void* stream);
-/* feats[nn][10] = (v_n/s_v, v_prev/s_v, (q_n - X)/s_u, fixed flag); v_prev NULL -> v_n. */
+/* feats[nn][10] = (v_n/s_v, (v_n - v_prev)/s_d, (q_n - X)/s_u, fixed flag): the two
+ * previous velocities enter as v_n and their difference; v_prev NULL -> difference 0. */
 tl_status tl_mlp_features(tl_mesh* m, const double* q_n, const double* v_n, const double* v_prev,
-                          double s_v, double s_u, float* feats);
-/* v_init = v_n + s_out * MLP(features) on free nodes, 0 on clamped nodes.
- * work: 13*nn float32 scratch (device). */
+                          double s_v, double s_d, double s_u, float* feats);
+/* v_init = 2 v_n - v_prev + s_out * MLP(features) on free nodes, 0 on clamped
+ * nodes: the network corrects the linear extrapolation of the two previous
+ * velocities.  params NULL: extrapolation only (work unused); v_prev NULL:
+ * v_n instead of the extrapolation.  work: 13*nn float32 scratch (device). */
 tl_status tl_warm_start(tl_mesh* m, const uint16_t* params, const double* q_n, const double* v_n,
-                        const double* v_prev, double s_v, double s_u, double s_out, float* work,
-                        double* v_init);
+                        const double* v_prev, double s_v, double s_d, double s_u, double s_out,
+                        float* work, double* v_init);
 
 /* Wait for the handle's stream and return the first sticky device-side error
  * (TL_ERR_INVERTED, TL_ERR_NONFINITE) raised since the last tl_sync, then

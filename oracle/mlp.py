@@ -2,8 +2,8 @@
 
 The paper starts every Newton solve from the previous velocity (Algorithm 3,
 v <- v_n).  The learned warm start replaces that start by
-v0 = v_n + s_out * MLP(features) on free nodes (0 on clamped nodes), with a
-per-node MLP 10 -> 64 -> 64 -> 64 -> 3, tanh hidden layers, linear output.
+v0 = 2 v_n - v_{n-1} + s_out * MLP(features) on free nodes (0 on clamped
+nodes), a learned correction of linear extrapolation, with a per-node MLP 10 -> 64 -> 64 -> 64 -> 3, tanh hidden layers, linear output.
 Weights and activations are bfloat16, products are accumulated in float32.
 
 This module restates the forward pass, the mean-squared-error loss and the
@@ -102,8 +102,9 @@ def adam_step(theta, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return theta
 
 
-def features(q_n, v_n, v_prev, X, fixed_mask, s_v, s_u):
-    """Per-node inputs: v_n / s_v, v_{n-1} / s_v, (q_n - X) / s_u, fixed flag."""
+def features(q_n, v_n, v_prev, X, fixed_mask, s_v, s_d, s_u):
+    """Per-node inputs: v_n / s_v, (v_n - v_{n-1}) / s_d, (q_n - X) / s_u, fixed
+    flag (the two previous velocities enter as v_n and their difference)."""
     q_n, v_n, v_prev, X = (np.asarray(a).reshape(-1, 3) for a in (q_n, v_n, v_prev, X))
-    return np.concatenate([v_n / s_v, v_prev / s_v, (q_n - X) / s_u,
+    return np.concatenate([v_n / s_v, (v_n - v_prev) / s_d, (q_n - X) / s_u,
                            np.asarray(fixed_mask, np.float64)[:, None]], axis=1)

@@ -28,7 +28,7 @@ class NewtonParams:
     rho_alm: float = 1e12
     rtol: float = 1e-8
     atol: float = 0.0
-    eps_out: float = 1e-10
+    eps_out: float = 1e-4
     max_inner: int = 20
     max_outer: int = 5
     gravity: tuple = (0.0, 0.0, -9.81)

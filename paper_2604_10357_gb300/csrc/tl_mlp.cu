@@ -3,7 +3,8 @@
 // accumulation, its forward and backward passes, the MSE loss gradient and
 // the Adam update, all as device kernels.  The paper has no counterpart (it
 // starts Newton from v_n, Algorithm 3); the network predicts the start
-// v0 = v_n + s_out * MLP(features) on free nodes.
+// v0 = 2 v_n - v_{n-1} + s_out * MLP(features) on free nodes: a learned
+// correction of the linear extrapolation of the two previous velocities.
 //
 // Layout of the bf16 parameter vector (9219 entries): W1 (64x10), b1 (64),
 // W2 (64x64), b2 (64), W3 (64x64), b3 (64), W4 (3x64), b4 (3).
@@ -185,29 +186,35 @@ __global__ void adam_kernel(float* master, uint16_t* P, const float* g, float* m
   P[i] = bf_bits(th);
 }
 
-// inputs: v_n / s_v, v_prev / s_v, (q_n - X) / s_u, fixed flag
+// inputs: v_n / s_v, (v_n - v_prev) / s_d, (q_n - X) / s_u, fixed flag.  The
+// two previous velocities enter as v_n and their difference: in bfloat16 the
+// difference of two nearby velocities would be lost.
 __global__ void features_kernel(const double* q_n, const double* v_n, const double* v_prev, const double* X,
-                                const int32_t* fixed_of_node, int64_t nn, double inv_sv, double inv_su,
-                                float* feats) {
+                                const int32_t* fixed_of_node, int64_t nn, double inv_sv, double inv_sd,
+                                double inv_su, float* feats) {
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nn) return;
   float* f = feats + 10 * I;
   for (int d = 0; d < 3; ++d) {
     const int64_t r = 3 * I + d;
     f[d] = float(v_n[r] * inv_sv);
-    f[3 + d] = float((v_prev ? v_prev[r] : v_n[r]) * inv_sv);
+    f[3 + d] = float((v_prev ? v_n[r] - v_prev[r] : 0.0) * inv_sd);
     f[6 + d] = float((q_n[r] - X[r]) * inv_su);
   }
   f[9] = fixed_of_node[I] >= 0 ? 1.0f : 0.0f;
 }
 
-__global__ void apply_kernel(const float* out, const double* v_n, const int32_t* fixed_of_node, int64_t nn,
-                             double s_out, double* v_init) {
+// v_init = 2 v_n - v_prev (+ s_out * out), 0 on clamped nodes; out may be null.
+__global__ void apply_kernel(const float* out, const double* v_n, const double* v_prev,
+                             const int32_t* fixed_of_node, int64_t nn, double s_out, double* v_init) {
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nn) return;
   const bool fixed = fixed_of_node[I] >= 0;
-  for (int d = 0; d < 3; ++d)
-    v_init[3 * I + d] = fixed ? 0.0 : v_n[3 * I + d] + s_out * double(out[3 * I + d]);
+  for (int d = 0; d < 3; ++d) {
+    const int64_t r = 3 * I + d;
+    const double base = v_prev ? 2.0 * v_n[r] - v_prev[r] : v_n[r];
+    v_init[r] = fixed ? 0.0 : base + (out ? s_out * double(out[r]) : 0.0);
+  }
 }
 
 constexpr size_t kFwdSmem = sizeof(float) * (9220 + 2 * 64 * kLd);
@@ -263,30 +270,36 @@ tl_status tl_mlp_adam(float* master, uint16_t* params, const float* grads, float
 }
 
 tl_status tl_mlp_features(tl_mesh* m, const double* q_n, const double* v_n, const double* v_prev, double s_v,
-                          double s_u, float* feats) {
-  if (!m || !q_n || !v_n || !feats || !(s_v > 0.0) || !(s_u > 0.0)) return TL_ERR_INVALID_ARG;
+                          double s_d, double s_u, float* feats) {
+  if (!m || !q_n || !v_n || !feats || !(s_v > 0.0) || !(s_d > 0.0) || !(s_u > 0.0)) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
   features_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(q_n, v_n, v_prev, m->d_X,
                                                                          m->d_fixed_of_node, m->nn, 1.0 / s_v,
-                                                                         1.0 / s_u, feats);
+                                                                         1.0 / s_d, 1.0 / s_u, feats);
   TL_CUDA(m, cudaGetLastError());
   ++m->launches;
   return TL_OK;
 }
 
 tl_status tl_warm_start(tl_mesh* m, const uint16_t* params, const double* q_n, const double* v_n,
-                        const double* v_prev, double s_v, double s_u, double s_out, float* work, double* v_init) {
-  if (!m || !params || !work || !v_init) return TL_ERR_INVALID_ARG;
-  float* feats = work;
-  float* out = work + 10 * m->nn;
-  tl_status s = tl_mlp_features(m, q_n, v_n, v_prev, s_v, s_u, feats);
-  if (s != TL_OK) return s;
-  s = tl_mlp_forward(params, feats, m->nn, out, nullptr, m->stream);
-  if (s != TL_OK) return fail(m, s, "MLP forward launch failed");
-  apply_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(out, v_n, m->d_fixed_of_node, m->nn, s_out,
-                                                                      v_init);
+                        const double* v_prev, double s_v, double s_d, double s_u, double s_out, float* work,
+                        double* v_init) {
+  if (!m || !q_n || !v_n || !v_init || (params && !work)) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  float* out = nullptr;
+  if (params) {
+    float* feats = work;
+    out = work + 10 * m->nn;
+    tl_status s = tl_mlp_features(m, q_n, v_n, v_prev, s_v, s_d, s_u, feats);
+    if (s != TL_OK) return s;
+    s = tl_mlp_forward(params, feats, m->nn, out, nullptr, m->stream);
+    if (s != TL_OK) return fail(m, s, "MLP forward launch failed");
+    ++m->launches;
+  }
+  apply_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(out, v_n, v_prev, m->d_fixed_of_node, m->nn,
+                                                                      s_out, v_init);
   TL_CUDA(m, cudaGetLastError());
-  m->launches += 2;
+  ++m->launches;
   return TL_OK;
 }
 

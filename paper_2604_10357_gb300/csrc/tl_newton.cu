@@ -147,12 +147,13 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
   const double target = std::max(p->atol, p->rtol * g_ref);
   int inner_total = 0, outer = 0;
   bool converged = false;
-  double gn = 0.0, cn = 0.0;
+  double gn = 0.0, cn = 0.0, g_init = -1.0;
   for (outer = 1; outer <= p->max_outer; ++outer) {
     bool inner_ok = false;
     for (int l = 0; l < p->max_inner; ++l) {
       cudaEventRecord(ev[0], s);
       NTRY(residual(v, &gn));
+      if (g_init < 0.0) g_init = gn;
       if (gn <= target) {
         inner_ok = true;
         cudaEventRecord(ev[1], s);
@@ -168,7 +169,10 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
       cudaEventRecord(ev[1], s);
       if (use_pcg) {
         int it = 0;
-        NTRY(pcg_solve(m, w.values, w.g, w.dv, lin_rtol, lin_max, &it));
+        // inexact Newton: the linear residual only needs to be well below the
+        // Newton target (g_{k+1} ~ linear residual + O(|dv|^2))
+        const double eta = p->lin_adaptive ? std::min(0.5, std::max(lin_rtol, 0.1 * target / gn)) : lin_rtol;
+        NTRY(pcg_solve(m, w.values, w.g, w.dv, eta, lin_max, &it));
         lin_total += it;
       } else {
         NTRY(solver_factor_solve(m, w.values, w.g, w.dv));
@@ -216,6 +220,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
     stats->ms_assembly = ms_asm;
     stats->ms_solver = ms_sol;
     stats->lin_iters = lin_total;
+    stats->g_init = g_init;
   }
   return converged ? TL_OK : fail(m, TL_ERR_NOT_CONVERGED, "Newton / ALM iteration caps reached");
 }

@@ -42,14 +42,14 @@ class tl_params(C.Structure):
     _fields_ = [("h", C.c_double), ("rho_alm", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
                 ("eps_out", C.c_double), ("gravity", C.c_double * 3), ("max_inner", C.c_int32),
                 ("max_outer", C.c_int32), ("linear_solver", C.c_int32), ("lin_max_iter", C.c_int32),
-                ("lin_rtol", C.c_double)]
+                ("lin_rtol", C.c_double), ("lin_adaptive", C.c_int32), ("_pad3", C.c_int32)]
 
 
 class tl_newton_stats(C.Structure):
     _fields_ = [("inner_iters", C.c_int32), ("outer_iters", C.c_int32), ("converged", C.c_int32),
                 ("_pad", C.c_int32), ("g_ref", C.c_double), ("g_norm", C.c_double), ("c_norm", C.c_double),
                 ("ms_total", C.c_double), ("ms_assembly", C.c_double), ("ms_solver", C.c_double),
-                ("lin_iters", C.c_int32), ("_pad2", C.c_int32)]
+                ("lin_iters", C.c_int32), ("_pad2", C.c_int32), ("g_init", C.c_double)]
 
 
 class tl_timing(C.Structure):
@@ -82,8 +82,8 @@ SIGNATURES = {
     "tl_mlp_mse_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "tl_mlp_adam": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
                               C.c_int32, _P]),
-    "tl_mlp_features": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, _P]),
-    "tl_warm_start": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P, _P]),
+    "tl_mlp_features": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P]),
+    "tl_warm_start": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
     "tl_sync": (C.c_int, [_P]),
     "tl_mesh_info_get": (C.c_int, [_P, _P]),
     "tl_status_string": (C.c_char_p, [C.c_int]),
@@ -127,14 +127,16 @@ def material(kind="svk", E=0.0, nu=0.0, rho0=1000.0, C10=0.0, C01=0.0, kappa=0.0
     return tl_material(k, 0, E, nu, rho0, C10, C01, kappa, eta_d, lambda_d)
 
 
-def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-10, gravity=(0.0, 0.0, -9.81),
-           max_inner=20, max_outer=5, linear_solver=TL_SOLVER_DIRECT, lin_max_iter=0, lin_rtol=0.0):
+def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-4, gravity=(0.0, 0.0, -9.81),
+           max_inner=20, max_outer=5, linear_solver=TL_SOLVER_DIRECT, lin_max_iter=0, lin_rtol=0.0,
+           lin_adaptive=0):
     p = tl_params()
     p.h, p.rho_alm, p.rtol, p.atol, p.eps_out = h, rho_alm, rtol, atol, eps_out
     for i in range(3):
         p.gravity[i] = gravity[i]
     p.max_inner, p.max_outer = max_inner, max_outer
     p.linear_solver, p.lin_max_iter, p.lin_rtol = linear_solver, lin_max_iter, lin_rtol
+    p.lin_adaptive = lin_adaptive
     return p
 
 
@@ -306,19 +308,21 @@ class Mesh:
             raise TLError(rc, self.lib.tl_last_error(self.h).decode())
         return v_out, q_out, stats
 
-    def mlp_features(self, q_n, v_n, v_prev, s_v, s_u, feats=None):
+    def mlp_features(self, q_n, v_n, v_prev, s_v, s_d, s_u, feats=None):
         torch = self._torch
         feats = torch.empty(self.nn, 10, dtype=torch.float32, device="cuda") if feats is None else feats
-        self._check(self.lib.tl_mlp_features(self.h, _ptr(q_n), _ptr(v_n), _ptr(v_prev), float(s_v), float(s_u),
-                                             _ptr(feats)))
+        self._check(self.lib.tl_mlp_features(self.h, _ptr(q_n), _ptr(v_n), _ptr(v_prev), float(s_v), float(s_d),
+                                             float(s_u), _ptr(feats)))
         return feats
 
-    def warm_start(self, params_bf16, q_n, v_n, v_prev, s_v, s_u, s_out, work=None, v_init=None):
+    def warm_start(self, params_bf16, q_n, v_n, v_prev, s_v, s_d, s_u, s_out, work=None, v_init=None):
         torch = self._torch
-        work = torch.empty(13 * self.nn, dtype=torch.float32, device="cuda") if work is None else work
+        if work is None and params_bf16 is not None:
+            work = torch.empty(13 * self.nn, dtype=torch.float32, device="cuda")
         v_init = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if v_init is None else v_init
         self._check(self.lib.tl_warm_start(self.h, _ptr(params_bf16), _ptr(q_n), _ptr(v_n), _ptr(v_prev),
-                                           float(s_v), float(s_u), float(s_out), _ptr(work), _ptr(v_init)))
+                                           float(s_v), float(s_d), float(s_u), float(s_out), _ptr(work),
+                                           _ptr(v_init)))
         return v_init
 
     def sync(self):

@@ -1,0 +1,187 @@
+"""Learned Newton warm start: generate backward-Euler trajectories with the
+plain Newton step (start v_n), train the per-node MLP with the library's own
+kernels, and compare Newton iterations / time to the same 1e-8 residual from
+three starts: v_n (the paper's), linear extrapolation 2 v_n - v_{n-1}, and the
+MLP, which learns a correction of that extrapolation.  The inner tolerance is relative to the residual at v_n in every case,
+so all three converge to the same state within the Newton tolerance.
+
+Orchestration only: every array operation of the method (Newton steps,
+features, forward / backward passes, loss gradient, Adam) runs in the CUDA
+kernels behind include/tl.h; torch provides device memory, random minibatch
+indices and timing events.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import tl
+
+NPARAM = tl.MLP_NPARAM
+
+
+@dataclass
+class Trajectory:
+    q: list = field(default_factory=list)       # q_n per step (device float64)
+    v: list = field(default_factory=list)       # v_n per step
+    lam: list = field(default_factory=list)     # lambda at the start of the step
+    f_ext: list = field(default_factory=list)
+    stats: list = field(default_factory=list)
+
+
+def generate(g, X, f_ext_fn, nsteps, prm, q0=None, v0=None, record_from=0, log_every=0):
+    """Run nsteps of the plain Newton step from (q0, v0) (default: rest).
+    Returns a Trajectory with the states at the start of steps
+    record_from .. nsteps (one more state than steps)."""
+    import torch
+    nd = g.ndof
+    q = torch.as_tensor(np.asarray(X).reshape(-1) if q0 is None else q0, dtype=torch.float64, device="cuda").clone()
+    v = torch.zeros(nd, dtype=torch.float64, device="cuda") if v0 is None else v0.clone()
+    lam = torch.zeros(max(3 * g.nfixed, 1), dtype=torch.float64, device="cuda")
+    tr = Trajectory()
+    for step in range(nsteps + 1):
+        fe = torch.as_tensor(f_ext_fn(step), dtype=torch.float64, device="cuda") if f_ext_fn else None
+        if step >= record_from:
+            tr.q.append(q.clone())
+            tr.v.append(v.clone())
+            tr.lam.append(lam.clone())
+            tr.f_ext.append(fe)
+        if step == nsteps:
+            break
+        v_new, q_new, st = g.newton_step(prm, q, v, lam, f_ext=fe)
+        if step >= record_from:
+            tr.stats.append(st)
+        q, v = q_new.clone(), v_new.clone()
+        if log_every and step % log_every == 0:
+            print(f"  step {step}: {st['inner_iters']} Newton iterations, {st['ms_total']:.1f} ms", flush=True)
+    return tr
+
+
+@dataclass
+class WarmStartModel:
+    params: object          # int16 CUDA tensor of bf16 bits (9219)
+    s_v: float
+    s_d: float
+    s_u: float
+    s_out: float
+
+    def to_npz(self, path):
+        np.savez(path, params=self.params.cpu().numpy(), s_v=self.s_v, s_d=self.s_d, s_u=self.s_u, s_out=self.s_out)
+
+    @classmethod
+    def from_npz(cls, path):
+        import torch
+        d = np.load(path)
+        return cls(torch.as_tensor(d["params"], device="cuda"), float(d["s_v"]), float(d["s_d"]), float(d["s_u"]),
+                   float(d["s_out"]))
+
+
+def _scales(g, tr, idx, X):
+    """Standard deviations of velocity, velocity difference, displacement and
+    velocity change over the training steps (torch reductions)."""
+    import torch
+    Xd = torch.as_tensor(np.asarray(X).reshape(-1), device="cuda")
+    sv = torch.cat([tr.v[i] for i in idx]).std().item()
+    sd = torch.cat([tr.v[i] - tr.v[i - 1] for i in idx if i > 0]).std().item()
+    su = torch.cat([tr.q[i] - Xd for i in idx]).std().item()
+    so = torch.cat([tr.v[i + 1] - 2.0 * tr.v[i] + tr.v[i - 1] for i in idx if i > 0]).std().item()
+    return tuple(max(x, 1e-12) for x in (sv, sd, su, so))
+
+
+def _glorot_init(rng):
+    sizes = [(64, 10), (64,), (64, 64), (64,), (64, 64), (64,), (3, 64), (3,)]
+    out = []
+    for sz in sizes:
+        if len(sz) == 2:
+            lim = np.sqrt(6.0 / (sz[0] + sz[1]))
+            out.append(rng.uniform(-lim, lim, size=sz).astype(np.float32).ravel())
+        else:
+            out.append(np.zeros(sz, np.float32))
+    return np.concatenate(out)
+
+
+def train(g, tr, X, fixed_nodes, train_idx, iters=2000, lr=2e-3, seed=0, log_every=0):
+    """Fit the MLP to predict (v_{t+1} - 2 v_t + v_{t-1}) / s_out (the error of
+    linear extrapolation) from the features at step t (mean squared error over
+    free nodes).  Each iteration uses every
+    node of one randomly drawn training step; Adam on a float32 master copy."""
+    import torch
+    rng = np.random.default_rng(seed)
+    s_v, s_d, s_u, s_out = _scales(g, tr, train_idx, X)
+    nn = g.nn
+    master = torch.as_tensor(_glorot_init(rng), device="cuda")
+    P = torch.empty(NPARAM, dtype=torch.int16, device="cuda")
+    m1 = torch.zeros(NPARAM, dtype=torch.float32, device="cuda")
+    m2 = torch.zeros_like(m1)
+    grads = torch.zeros_like(m1)
+    tl.mlp_adam(master, P, grads, m1, m2, lr=0.0, step=1)          # P <- bf16(master)
+    fixed = np.zeros(nn, bool)
+    fixed[np.asarray(fixed_nodes, dtype=np.int64)] = True
+    weight = torch.as_tensor(np.where(fixed, 0.0, 1.0 / max(1, (~fixed).sum())).astype(np.float32), device="cuda")
+    feats = torch.empty(nn, 10, dtype=torch.float32, device="cuda")
+    acts = torch.empty(nn, 192, dtype=torch.int16, device="cuda")
+    out = torch.empty(nn, 3, dtype=torch.float32, device="cuda")
+    dout = torch.empty_like(out)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    history = []
+    for it in range(iters):
+        t = int(rng.choice(train_idx[train_idx > 0]))
+        v_prev = tr.v[t - 1]
+        g.mlp_features(tr.q[t], tr.v[t], v_prev, s_v, s_d, s_u, feats)
+        target = ((tr.v[t + 1] - 2.0 * tr.v[t] + v_prev) / s_out).to(torch.float32).view(nn, 3)
+        tl.mlp_forward(P, feats, out=out, acts=acts)
+        loss.zero_()
+        tl.mlp_mse_grad(out, target, weight, dout, loss)
+        grads.zero_()
+        tl.mlp_backward(P, feats, acts, dout, grads)
+        tl.mlp_adam(master, P, grads, m1, m2, lr=lr * (0.1 ** (it / max(1, iters))), step=it + 1)
+        if log_every and (it % log_every == 0 or it == iters - 1):
+            history.append((it, loss.item()))
+            print(f"  iter {it}: loss {history[-1][1]:.4e}", flush=True)
+    return WarmStartModel(P, s_v, s_d, s_u, s_out), history
+
+
+def evaluate(g, tr, test_idx, prm, model=None):
+    """Newton iterations and time to the same tolerance from v_n, from linear
+    extrapolation and (if given) from the MLP, on the stored test steps."""
+    import torch
+    modes = ["v_n", "extrapolation"] + (["mlp"] if model is not None else [])
+    res = {m: dict(iters=[], ms=[], ms_start=[], dev=[], g0=[], lin=[]) for m in modes}
+    work = torch.empty(13 * g.nn, dtype=torch.float32, device="cuda")
+    vinit = torch.empty(g.ndof, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for t in test_idx:
+        v_prev = tr.v[t - 1] if t > 0 else tr.v[t]
+        ref = tr.v[t + 1]
+        for mode in modes:
+            e0.record()
+            if mode == "v_n":
+                vi = None
+            elif mode == "extrapolation":
+                g.warm_start(None, tr.q[t], tr.v[t], v_prev, 1.0, 1.0, 1.0, 0.0, v_init=vinit)
+                vi = vinit
+            else:
+                g.warm_start(model.params, tr.q[t], tr.v[t], v_prev, model.s_v, model.s_d, model.s_u,
+                             model.s_out, work=work, v_init=vinit)
+                vi = vinit
+            e1.record()
+            torch.cuda.synchronize()
+            ms_start = e0.elapsed_time(e1)
+            lam = tr.lam[t].clone()
+            t0 = time.perf_counter()
+            v_new, _, st = g.newton_step(prm, tr.q[t], tr.v[t], lam, v_init=vi, f_ext=tr.f_ext[t])
+            ms = 1e3 * (time.perf_counter() - t0)
+            r = res[mode]
+            r["iters"].append(st["inner_iters"])
+            r["ms"].append(ms + ms_start)
+            r["ms_start"].append(ms_start)
+            r["dev"].append((torch.linalg.norm(v_new - ref) / torch.linalg.norm(ref)).item())
+            r["g0"].append(st["g_init"] / st["g_ref"])
+            r["lin"].append(st["lin_iters"])
+    summary = {m: dict(mean_iters=float(np.mean(r["iters"])), mean_ms=float(np.mean(r["ms"])),
+                       mean_ms_start=float(np.mean(r["ms_start"])), max_rel_dev=float(np.max(r["dev"])),
+                       median_g0_ratio=float(np.median(r["g0"])), mean_lin_iters=float(np.mean(r["lin"])))
+               for m, r in res.items()}
+    return summary, res
