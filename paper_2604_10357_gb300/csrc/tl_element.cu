@@ -54,6 +54,8 @@ struct Args {
   T* values;           // CSR values (atomic add), may be null
   T* K_elem;           // per-element 30x30 output (user order), may be null
   uint32_t* flags;
+  int32_t nnz;         // length of values (bounds of the vector reductions)
+  int32_t v4_ok;       // values is 16-byte aligned
 };
 
 // Per-element shared-memory strides padded to odd word counts so that lanes
@@ -269,6 +271,137 @@ __device__ __forceinline__ void tangent_blockrow(const Args<T>& A, const Smem<T>
   }
 }
 
+// Accumulate block row A0 (blocks b = A0 .. A0+NB-1, component i) over the 5
+// quadrature points and add the mass term; no scatter.
+template <typename T, int A0, int NB>
+__device__ __forceinline__ void accumulate_blockrow(const Args<T>& A, const Smem<T>& sm, int i, T (&acc)[NB][3]) {
+  const int e = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+#pragma unroll 1
+  for (int q = 0; q < 5; ++q) {
+    const T* nq = &sm.n[e * kNStride + q * 30];
+    const T* Aq = &sm.A[e * kAStride + q * 81 + i * 27];
+    const T na[3] = {nq[A0 * 3], nq[A0 * 3 + 1], nq[A0 * 3 + 2]};
+    T An[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        An[k][L] = na[0] * Aq[0 * 9 + k * 3 + L] + na[1] * Aq[1 * 9 + k * 3 + L] + na[2] * Aq[2 * 9 + k * 3 + L];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int b = A0 + j;
+      const T n0b = nq[b * 3], n1b = nq[b * 3 + 1], n2b = nq[b * 3 + 2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[j][k] += An[k][0] * n0b + An[k][1] * n1b + An[k][2] * n2b;
+    }
+  }
+  const T ms = A.mass_scale * A.mat.rho * sm.geo[12][e] * T(1.0 / 420.0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k == i) acc[j][k] += ms * T(c_mass420[A0][A0 + j]);
+}
+
+__device__ __forceinline__ void red_v4(float* p, float x, float y, float z, float w) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+__device__ __forceinline__ void red_v2(float* p, float x, float y) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
+}
+
+// Add the run values[s .. s+2] += (x0, x1, x2) with one 16-byte reduction when
+// the run starts at offset 0 or 1 of an aligned 4-float chunk (the other lane
+// adds 0 to the neighbouring entry), else an 8-byte and a 4-byte one.
+__device__ __forceinline__ void red_run(const Args<float>& A, int s, float x0, float x1, float x2) {
+  float* p = A.values;
+  if (A.v4_ok) {
+    const int r = s & 3;
+    if (r == 1) {
+      red_v4(p + s - 1, 0.0f, x0, x1, x2);
+      return;
+    }
+    if (r == 0 && s + 4 <= A.nnz) {
+      red_v4(p + s, x0, x1, x2, 0.0f);
+      return;
+    }
+    if (r == 0 || r == 2) {
+      red_v2(p + s, x0, x1);
+      atomicAdd(p + s + 2, x2);
+      return;
+    }
+    atomicAdd(p + s, x0);          // r == 3: s + 1 is 16-byte aligned
+    red_v2(p + s + 1, x1, x2);
+    return;
+  }
+  atomicAdd(p + s, x0);
+  atomicAdd(p + s + 1, x1);
+  atomicAdd(p + s + 2, x2);
+}
+
+// FP32 assembly of block rows a0 = P and a1 = 9 - P, in two halves around a
+// block-wide barrier.  The three warps (P, i) of one element hold the rows i
+// of the same blocks; the first half issues those rows and parks them in an
+// exchange buffer X (32 elements x 55 blocks x 9 floats, its own shared
+// memory, after the Smem struct); after the barrier, the second half reads
+// column i of each off-diagonal block from X, i.e. row i of the transposed
+// block (b, a).  Every write is a contiguous run of three CSR entries
+// (row 3I+i, columns 3J..3J+2) issued as vector reductions.
+template <int P>
+__device__ __forceinline__ void tangent_xchg_direct(const Args<float>& A, const Smem<float>& sm, float* X,
+                                                    int64_t e0, int i) {
+  constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
+  const int e = threadIdx.x & 31;
+  float acc0[n0][3], acc1[n1][3];
+  accumulate_blockrow<float, a0, n0>(A, sm, i, acc0);
+  accumulate_blockrow<float, a1, n1>(A, sm, i, acc1);
+  const int base = e * 495 + P * 99 + i * 3;
+#pragma unroll
+  for (int j = 0; j < n0; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[base + j * 9 + k] = acc0[j][k];
+#pragma unroll
+  for (int j = 0; j < n1; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[base + (n0 + j) * 9 + k] = acc1[j][k];
+  if (e0 + e >= A.real_end) return;
+#pragma unroll
+  for (int j = 0; j < n0; ++j)
+    red_run(A, sm.rbase[a0][e] + sm.rstr[a0][e] * i + 3 * sm.blk[e][a0 * 10 + a0 + j], acc0[j][0], acc0[j][1],
+            acc0[j][2]);
+#pragma unroll
+  for (int j = 0; j < n1; ++j)
+    red_run(A, sm.rbase[a1][e] + sm.rstr[a1][e] * i + 3 * sm.blk[e][a1 * 10 + a1 + j], acc1[j][0], acc1[j][1],
+            acc1[j][2]);
+}
+
+template <int P>
+__device__ __forceinline__ void tangent_xchg_transposed(const Args<float>& A, const Smem<float>& sm,
+                                                        const float* X, int64_t e0, int i) {
+  constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
+  const int e = threadIdx.x & 31;
+  if (e0 + e >= A.real_end) return;
+  const int xb = e * 495 + P * 99;
+#pragma unroll
+  for (int j = 1; j < n0; ++j) {
+    const int b = a0 + j;
+    red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a0], X[xb + j * 9 + i],
+            X[xb + j * 9 + 3 + i], X[xb + j * 9 + 6 + i]);
+  }
+#pragma unroll
+  for (int j = 1; j < n1; ++j) {
+    const int b = a1 + j;
+    red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a1], X[xb + (n0 + j) * 9 + i],
+            X[xb + (n0 + j) * 9 + 3 + i], X[xb + (n0 + j) * 9 + 6 + i]);
+  }
+}
+
+constexpr int kXFloats = 32 * 55 * 9;   // exchange buffer of the FP32 assembly
+
 // Block rows a0 = P (b = P..9) and a1 = 9 - P (b = 9-P..9): 11 blocks, so the
 // 15 warps cover the 55 blocks of the symmetric 30x30 exactly once.
 template <typename T, int P>
@@ -295,6 +428,27 @@ __global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A) {
   if (DO_TANGENT) {
     const int w = threadIdx.x >> 5;
     const int p = w / 3, i = w % 3;
+    if constexpr (std::is_same<T, float>::value) {
+      if (A.values && !A.K_elem) {     // kernel-argument test: uniform over the block
+        float* X = reinterpret_cast<float*>(smem_raw + sizeof(Smem<float>));
+        switch (p) {                   // warp-uniform
+          case 0: tangent_xchg_direct<0>(A, sm, X, e0, i); break;
+          case 1: tangent_xchg_direct<1>(A, sm, X, e0, i); break;
+          case 2: tangent_xchg_direct<2>(A, sm, X, e0, i); break;
+          case 3: tangent_xchg_direct<3>(A, sm, X, e0, i); break;
+          default: tangent_xchg_direct<4>(A, sm, X, e0, i); break;
+        }
+        __syncthreads();               // reached by every thread of the block
+        switch (p) {
+          case 0: tangent_xchg_transposed<0>(A, sm, X, e0, i); break;
+          case 1: tangent_xchg_transposed<1>(A, sm, X, e0, i); break;
+          case 2: tangent_xchg_transposed<2>(A, sm, X, e0, i); break;
+          case 3: tangent_xchg_transposed<3>(A, sm, X, e0, i); break;
+          default: tangent_xchg_transposed<4>(A, sm, X, e0, i); break;
+        }
+        return;
+      }
+    }
     switch (p) {     // warp-uniform
       case 0: tangent_rows<T, 0>(A, sm, e0, i); break;
       case 1: tangent_rows<T, 1>(A, sm, e0, i); break;
@@ -308,8 +462,11 @@ __global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A) {
 template <typename T, bool DO_FORCE, bool DO_TANGENT>
 tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
                      double mass_scale, double* f, void* values, void* K_elem) {
-  // the force-only variant does not need the tangent array (last member)
-  const size_t smem = DO_TANGENT ? sizeof(Smem<T>) : offsetof(Smem<T>, A);
+  // the force-only variant does not need the tangent array (last member);
+  // the FP32 CSR assembly adds its exchange buffer after the struct
+  const bool xchg = std::is_same<T, float>::value && DO_TANGENT && values && !K_elem;
+  const size_t smem = DO_TANGENT ? sizeof(Smem<T>) + (xchg ? sizeof(float) * kXFloats : 0)
+                                 : offsetof(Smem<T>, A);
   cudaEvent_t t0 = timer_open(m);
   for (const Segment& sg : m->segs) {
     const int64_t ntiles = (sg.padded_end - sg.begin) / E;
@@ -336,6 +493,8 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     A.values = reinterpret_cast<T*>(values);
     A.K_elem = reinterpret_cast<T*>(K_elem);
     A.flags = m->d_flags;
+    A.nnz = (int32_t)m->nnz;
+    A.v4_ok = ((reinterpret_cast<uintptr_t>(values) & 15u) == 0) ? 1 : 0;
     void (*kern)(Args<T>) = nullptr;
     const bool kv = md.kv != 0;
     if (md.kind == TL_SVK)
