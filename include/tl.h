@@ -100,7 +100,8 @@ typedef struct tl_params {
   double lin_rtol;            /* PCG: ||H dv + g|| <= eta ||g|| with eta = lin_rtol (0: 1e-10), */
                               /* or, if lin_adaptive, eta = max(lin_rtol, 0.1 target / ||g||)   */
   int32_t lin_adaptive;       /* 1: inexact Newton (solve only as tightly as the target needs) */
-  int32_t _pad3;
+  int32_t use_graph;          /* 1: run the step as one captured CUDA graph with device-side */
+                              /* convergence control (PCG only; see tl_newton_step)           */
 } tl_params;
 
 typedef struct tl_newton_stats {
@@ -255,12 +256,54 @@ tl_status tl_timing_read(tl_mesh* m, tl_timing* out);
  *   stats      HOST, optional: iterations, norms, split timings
  * For TL_FP32_ELEM meshes the Hessian, its factorization and the direction
  * are float32 while the residual keeps a float64 force evaluation.
+ *   Inner solver (p->linear_solver): TL_SOLVER_DIRECT = vendor sparse
+ * Cholesky; TL_SOLVER_PCG = block-Jacobi conjugate gradients on the device to
+ * ||H dv + g|| <= eta ||g|| (eta from lin_rtol / lin_adaptive; with
+ * TL_FP32_ELEM eta is at least 1e-6, the resolution of a float32 H).  PCG
+ * stops early when p.Hp <= 0 (H not positive definite along p).
+ *   p->use_graph = 1 (PCG only) runs the whole step as one captured CUDA
+ * graph: the loops are conditional graph nodes, the tests on ||g||, ||c||
+ * and the PCG residual are made on the device, and the host waits once.
+ * The caller's arrays are copied into handle-owned buffers around the graph
+ * launch; the graph is captured on the first call and again whenever the
+ * parameters, the precision or the autotuner's choice change.  PCG iteration
+ * counts are multiples of 8 in this mode; ms_assembly / ms_solver are 0.
  * Synchronous.  Returns TL_ERR_NOT_CONVERGED (with the last iterate in
- * v_out / q_out) when the caps are reached, TL_ERR_SOLVER when the matrix is
- * not positive definite. */
+ * v_out / q_out) when the caps are reached, TL_ERR_SOLVER when the direct
+ * factorization meets a zero pivot, TL_ERR_NONFINITE on a non-finite norm,
+ * TL_ERR_UNSUPPORTED for use_graph with the direct solver. */
 tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n,
                          const double* v_init, const double* f_ext, double* lambda,
                          double* v_out, double* q_out, tl_newton_stats* stats);
+
+/* ---- autotuner of the launch shapes (no counterpart in the paper) --------
+ * Times, on this handle's mesh at the state (q_n, v, h), every compiled
+ * variant of the two hot launches and keeps the fastest for later calls:
+ *   element pass (fused force + tangent + CSR assembly): persistent grid
+ *     (SMs x resident CTAs) or one CTA per 32-element tile; for
+ *     TL_FP32_ELEM also the scatter (exchanged 3-entry runs issued as vector
+ *     reductions, or one scalar reduction per entry);
+ *   PCG product H p: 4, 8 or 16 lanes per node.
+ * reps timed launches per variant after one warm-up.  Needs the pattern;
+ * allocates and frees one CSR values array and one force array.  Synchronous.
+ * The result does not change any computed value beyond the rounding order of
+ * the reductions.  ms_element[k]: k = 2*(1-xchg) + full_grid; ms_spmv[k]:
+ * 4, 8, 16 lanes. */
+typedef struct tl_tune_result {
+  int32_t spmv_group;         /* lanes per node in H p */
+  int32_t elem_xchg;          /* 1: exchanged vector runs (FP32 assembly) */
+  int32_t elem_full_grid;     /* 1: one CTA per tile; 0: persistent grid */
+  int32_t _pad;
+  float ms_element[4];        /* measured element-pass times (0: not applicable) */
+  float ms_spmv[3];
+  float _pad2;
+} tl_tune_result;
+
+tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,
+                      tl_tune_result* out);
+/* Current choice (timings zero), and an explicit choice (validated). */
+tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out);
+tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in);
 
 /* ---- learned Newton warm start (no counterpart in the paper) -------------
  * The paper starts each Newton solve from v_n (Algorithm 3).  These calls

@@ -65,6 +65,7 @@ void free_mesh(tl_mesh* m) {
                   m->d_flags, m->d_partials, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_values};
   solver_destroy(m->solver);
   pcg_destroy(m->pcg);
+  newton_graph_destroy(m->ngraph);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
@@ -157,6 +158,9 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
   tl_mesh* m = new (std::nothrow) tl_mesh();
   if (!m) return TL_ERR_OOM;
   cudaGetDevice(&m->device);
+  if (cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess ||
+      m->num_sms < 1)
+    m->num_sms = 1;
   m->stream = (cudaStream_t)stream;
   m->precision = precision;
   m->nn = nn;

@@ -1,0 +1,604 @@
+// T10 element kernels: internal force, tangent stiffness and their scatter
+// into the fixed-pattern CSR Hessian.  Templates only: the tl_element_*.cu
+// files instantiate them (one translation unit per precision and pass, so the
+// build compiles them in parallel) and tl_element.cu dispatches.
+//
+// Paper: arxiv 2604.10357
+//   Sec. 4.3  eq. F_assembly, eq. fint_local, eq. fint_global (Stage 1 + 2)
+//   Sec. 4.4  eq. tangent_block and the Hessian assembly (eq. hessian)
+//
+// GB300 design (differs from the paper's two-stage, thread-per-(e,q) /
+// thread-per-(e,a) kernels with a stress buffer in global memory):
+//   * one fused kernel: a CTA owns kTile = 32 consecutive elements; their
+//     connectivity, geometry and slot indices are staged in shared memory and
+//     nothing per quadrature point ever goes to global memory;
+//   * warps are specialised by role with lanes = elements, so every branch on
+//     the role is warp-uniform:
+//       qp phase:      warp w -> (quadrature point q = w/3, row i = w%3)
+//       tangent phase: warp w -> (row-pair p = w/3, row i = w%3), covering the
+//                      block rows a = p and a = 9-p (11 blocks, b >= a), so
+//                      the symmetric 30x30 is formed once (55 blocks);
+//   * the scatter goes through a per-element slot map (position k of node
+//     conn[b] in node conn[a]'s sorted adjacency), so there is no binary
+//     search: slot = 9 ptr(I) + 3 deg(I) i + 3 k + j;
+//   * TL_FP32_ELEM evaluates the element in float32 from the displacement
+//     gradient H (F = I + H, E = (H + H^T + H^T H)/2) and a cancellation-free
+//     Mooney-Rivlin stress (deviators of E, J - 1 from the invariants of H).
+#pragma once
+
+#include <algorithm>
+#include <cstddef>
+#include <type_traits>
+
+#include "tl_element_common.cuh"
+
+namespace tl {
+namespace elem {
+
+constexpr int E = kTile;          // elements per CTA
+constexpr int NWARP = 15;         // 5 qp x 3 rows, and 5 row pairs x 3 rows
+constexpr int NT = 32 * NWARP;    // 480 threads
+
+template <typename T>
+struct Args {
+  const int32_t* conn;
+  const T* geo;
+  const uint8_t* blk;
+  const int32_t* node_ptr;
+  const int32_t* user_of;
+  const double* q_n;
+  const double* v;
+  const double* X;
+  double h;
+  int64_t real_end;    // internal elements >= real_end are padding (per segment)
+  MatT<T> mat;
+  T alpha, beta;       // tangent = alpha K_t + beta D
+  T mass_scale;        // mass term M_e * mass_scale added to the tangent
+  double* f;           // force output (atomic add), may be null
+  T* values;           // CSR values (atomic add), may be null
+  T* K_elem;           // per-element 30x30 output (user order), may be null
+  uint32_t* flags;
+  int32_t nnz;         // length of values (bounds of the vector reductions)
+  int32_t v4_ok;       // values is 16-byte aligned
+  int32_t xchg;        // FP32 CSR assembly through the exchange buffer
+};
+
+// Per-element shared-memory strides padded to odd word counts so that lanes
+// (= elements) reading the same offset hit distinct banks.
+constexpr int kNStride = 151;    // 5 qp x 30 grad N, + 1
+constexpr int kAStride = 407;    // 5 qp x 81 tangent entries, + 2
+constexpr int kFStride = 151;    // 5 qp x 30 force entries, + 1
+constexpr int kUStride = 31;
+
+template <typename T>
+struct Smem {
+  int32_t node[10][E];
+  int32_t rbase[10][E];
+  int32_t rstr[10][E];
+  uint8_t blk[E][100];
+  T geo[16][E];
+  T u[kUStride * E];
+  T vel[kUStride * E];
+  T n[kNStride * E];
+  T fq[kFStride * E];
+  T A[kAStride * E];
+};
+
+// ---------------------------------------------------------------------------
+// Stage the tile: connectivity, row bases, slot indices, geometry and the
+// nodal displacement / velocity gathers.
+// ---------------------------------------------------------------------------
+template <typename T, bool NEED_PATTERN>
+__device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t e0) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < E * 10; t += NT) {
+    const int e = t / 10, a = t % 10;
+    const int node = A.conn[(e0 + e) * 10 + a];
+    sm.node[a][e] = node;
+    if (NEED_PATTERN) {
+      const int p0 = A.node_ptr[node], p1 = A.node_ptr[node + 1];
+      sm.rbase[a][e] = 9 * p0;
+      sm.rstr[a][e] = 3 * (p1 - p0);
+    }
+  }
+  if (NEED_PATTERN) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(A.blk + e0 * 100);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.blk[0][0]);
+    for (int t = tid; t < E * 25; t += NT) dst[t] = src[t];
+  }
+  for (int t = tid; t < E * 16; t += NT) {
+    const int e = t / 16, c = t % 16;
+    sm.geo[c][e] = A.geo[(e0 + e) * 16 + c];
+  }
+  __syncthreads();
+  const double h = A.h;
+  for (int t = tid; t < E * 30; t += NT) {
+    const int e = t / 30, c = t % 30;
+    const int a = c / 3, d = c % 3;
+    const int64_t g = 3 * (int64_t)sm.node[a][e] + d;
+    const double vv = A.v[g];
+    const double x = A.q_n[g] + h * vv;
+    sm.u[c * E + e] = T(x - A.X[g]);
+    sm.vel[c * E + e] = T(vv);
+  }
+  __syncthreads();
+}
+
+// Gradients of the 10 shape functions at barycentric point L (straight-sided
+// T10): corners (4 L_a - 1) grad L_a, midsides 4 (L_i grad L_j + L_j grad L_i).
+template <typename T>
+__device__ __forceinline__ void shape_grads(const Smem<T>& sm, int e, const double Lq[4], T n[10][3]) {
+  T gL[4][3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gL[c][d] = sm.geo[c * 3 + d][e];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) n[a][d] = (T(4) * T(Lq[a]) - T(1)) * gL[a][d];
+#pragma unroll
+  for (int m = 4; m < 10; ++m) {
+    const int i = edge_i(m), j = edge_j(m);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) n[m][d] = T(4) * (T(Lq[i]) * gL[j][d] + T(Lq[j]) * gL[i][d]);
+  }
+}
+
+// qp phase: warp w -> (q = w / 3, row i = w % 3), lane = element.
+template <typename T, int MAT, bool KV, bool WANT_A, int i>
+__device__ __forceinline__ void qp_phase(const Args<T>& A, Smem<T>& sm, bool& inverted) {
+  const int w = threadIdx.x >> 5, e = threadIdx.x & 31;
+  const int q = w / 3;
+  double Lq[4];
+  qp_bary(q, Lq);
+  const T wJ = T(qp_wfrac(q)) * sm.geo[12][e];
+  T n[10][3];
+  shape_grads(sm, e, Lq, n);
+  if (i == 0) {
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) sm.n[e * kNStride + q * 30 + a * 3 + d] = n[a][d];
+  }
+  T Hm[3][3], Fd[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Hm[r][c] = 0;
+      Fd[r][c] = 0;
+    }
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T ua = sm.u[(a * 3 + r) * E + e];
+      T va = T(0);
+      if (KV) va = sm.vel[(a * 3 + r) * E + e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Hm[r][c] += ua * n[a][c];
+        if (KV) Fd[r][c] += va * n[a][c];
+      }
+    }
+  QP<T> s;
+  constitutive<T, MAT, KV>(Hm, Fd, A.mat, s, inverted);
+  // force row i: f_a,i = wJ sum_J P_iJ n_aJ with P = F S
+  T Pi[3];
+#pragma unroll
+  for (int J = 0; J < 3; ++J) {
+    T acc = 0;
+#pragma unroll
+    for (int M = 0; M < 3; ++M) acc += s.F[i][M] * s.S[M][J];
+    Pi[J] = acc * wJ;
+  }
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+    sm.fq[e * kFStride + q * 30 + a * 3 + i] = Pi[0] * n[a][0] + Pi[1] * n[a][1] + Pi[2] * n[a][2];
+  if (WANT_A) tangent_row<T, MAT, KV, i>(s, A.mat, A.alpha, A.beta, wJ, &sm.A[e * kAStride + q * 81 + i * 27]);
+}
+
+// Force phase: warp w handles element DOFs c = w and c = w + 15.
+template <typename T>
+__device__ __forceinline__ void force_phase(const Args<T>& A, const Smem<T>& sm, int64_t e0) {
+  const int w = threadIdx.x >> 5, e = threadIdx.x & 31;
+  if (e0 + e >= A.real_end) return;
+#pragma unroll
+  for (int rep = 0; rep < 2; ++rep) {
+    const int c = w + 15 * rep;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc += sm.fq[e * kFStride + q * 30 + c];
+    const int a = c / 3, d = c % 3;
+    atomicAdd(&A.f[3 * (int64_t)sm.node[a][e] + d], double(acc));
+  }
+}
+
+// One block row of the element tangent for one element (lane) and component
+// i: K_{A0,b}[i][k] for b = A0 .. A0+NB-1, accumulated over the 5 qp, plus the
+// mass term, then scattered (the (b, A0) transposed entries too).
+template <typename T, int A0, int NB>
+__device__ __forceinline__ void tangent_blockrow(const Args<T>& A, const Smem<T>& sm, int64_t e0, int i) {
+  const int e = threadIdx.x & 31;
+  T acc[NB][3];
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+#pragma unroll 1
+  for (int q = 0; q < 5; ++q) {
+    const T* nq = &sm.n[e * kNStride + q * 30];
+    const T* Aq = &sm.A[e * kAStride + q * 81 + i * 27];
+    const T na[3] = {nq[A0 * 3], nq[A0 * 3 + 1], nq[A0 * 3 + 2]};
+    T An[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        An[k][L] = na[0] * Aq[0 * 9 + k * 3 + L] + na[1] * Aq[1 * 9 + k * 3 + L] + na[2] * Aq[2 * 9 + k * 3 + L];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int b = A0 + j;
+      const T n0b = nq[b * 3], n1b = nq[b * 3 + 1], n2b = nq[b * 3 + 2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[j][k] += An[k][0] * n0b + An[k][1] * n1b + An[k][2] * n2b;
+    }
+  }
+  if (e0 + e >= A.real_end) return;
+  const T ms = A.mass_scale * A.mat.rho * sm.geo[12][e] * T(1.0 / 420.0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    constexpr int a = A0;
+    const int b = A0 + j;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k == i) acc[j][k] += ms * T(c_mass420[a][b]);
+    if (A.values) {
+      const int s_row = sm.rbase[a][e] + sm.rstr[a][e] * i + 3 * sm.blk[e][a * 10 + b];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) atomic_add_t(&A.values[s_row + k], acc[j][k]);
+      if (j > 0) {
+        const int kb = 3 * sm.blk[e][b * 10 + a] + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomic_add_t(&A.values[sm.rbase[b][e] + sm.rstr[b][e] * k + kb], acc[j][k]);
+      }
+    }
+    if (A.K_elem) {
+      const int64_t ue = A.user_of[e0 + e];
+      T* Ke = A.K_elem + ue * 900;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Ke[(3 * a + i) * 30 + 3 * b + k] = acc[j][k];
+        if (j > 0) Ke[(3 * b + k) * 30 + 3 * a + i] = acc[j][k];
+      }
+    }
+  }
+}
+
+// Accumulate block row A0 (blocks b = A0 .. A0+NB-1, component i) over the 5
+// quadrature points and add the mass term; no scatter.
+template <typename T, int A0, int NB>
+__device__ __forceinline__ void accumulate_blockrow(const Args<T>& A, const Smem<T>& sm, int i, T (&acc)[NB][3]) {
+  const int e = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+#pragma unroll 1
+  for (int q = 0; q < 5; ++q) {
+    const T* nq = &sm.n[e * kNStride + q * 30];
+    const T* Aq = &sm.A[e * kAStride + q * 81 + i * 27];
+    const T na[3] = {nq[A0 * 3], nq[A0 * 3 + 1], nq[A0 * 3 + 2]};
+    T An[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        An[k][L] = na[0] * Aq[0 * 9 + k * 3 + L] + na[1] * Aq[1 * 9 + k * 3 + L] + na[2] * Aq[2 * 9 + k * 3 + L];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int b = A0 + j;
+      const T n0b = nq[b * 3], n1b = nq[b * 3 + 1], n2b = nq[b * 3 + 2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[j][k] += An[k][0] * n0b + An[k][1] * n1b + An[k][2] * n2b;
+    }
+  }
+  const T ms = A.mass_scale * A.mat.rho * sm.geo[12][e] * T(1.0 / 420.0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k == i) acc[j][k] += ms * T(c_mass420[A0][A0 + j]);
+}
+
+__device__ __forceinline__ void red_v4(float* p, float x, float y, float z, float w) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+__device__ __forceinline__ void red_v2(float* p, float x, float y) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
+}
+
+// Add the run values[s .. s+2] += (x0, x1, x2) with one 16-byte reduction when
+// the run starts at offset 0 or 1 of an aligned 4-float chunk (the other lane
+// adds 0 to the neighbouring entry), else an 8-byte and a 4-byte one.
+__device__ __forceinline__ void red_run(const Args<float>& A, int s, float x0, float x1, float x2) {
+  float* p = A.values;
+  if (A.v4_ok) {
+    const int r = s & 3;
+    if (r == 1) {
+      red_v4(p + s - 1, 0.0f, x0, x1, x2);
+      return;
+    }
+    if (r == 0 && s + 4 <= A.nnz) {
+      red_v4(p + s, x0, x1, x2, 0.0f);
+      return;
+    }
+    if (r == 0 || r == 2) {
+      red_v2(p + s, x0, x1);
+      atomicAdd(p + s + 2, x2);
+      return;
+    }
+    atomicAdd(p + s, x0);          // r == 3: s + 1 is 16-byte aligned
+    red_v2(p + s + 1, x1, x2);
+    return;
+  }
+  atomicAdd(p + s, x0);
+  atomicAdd(p + s + 1, x1);
+  atomicAdd(p + s + 2, x2);
+}
+
+// FP32 assembly of block rows a0 = P and a1 = 9 - P, in two halves around a
+// block-wide barrier.  The three warps (P, i) of one element hold the rows i
+// of the same blocks; the first half issues those rows and parks them in an
+// exchange buffer X (32 elements x 55 blocks x 9 floats, its own shared
+// memory, after the Smem struct); after the barrier, the second half reads
+// column i of each off-diagonal block from X, i.e. row i of the transposed
+// block (b, a).  Every write is a contiguous run of three CSR entries
+// (row 3I+i, columns 3J..3J+2) issued as vector reductions.
+template <int P>
+__device__ __forceinline__ void tangent_xchg_direct(const Args<float>& A, const Smem<float>& sm, float* X,
+                                                    int64_t e0, int i) {
+  constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
+  const int e = threadIdx.x & 31;
+  float acc0[n0][3], acc1[n1][3];
+  accumulate_blockrow<float, a0, n0>(A, sm, i, acc0);
+  accumulate_blockrow<float, a1, n1>(A, sm, i, acc1);
+  const int base = e * 495 + P * 99 + i * 3;
+#pragma unroll
+  for (int j = 0; j < n0; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[base + j * 9 + k] = acc0[j][k];
+#pragma unroll
+  for (int j = 0; j < n1; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[base + (n0 + j) * 9 + k] = acc1[j][k];
+  if (e0 + e >= A.real_end) return;
+#pragma unroll
+  for (int j = 0; j < n0; ++j)
+    red_run(A, sm.rbase[a0][e] + sm.rstr[a0][e] * i + 3 * sm.blk[e][a0 * 10 + a0 + j], acc0[j][0], acc0[j][1],
+            acc0[j][2]);
+#pragma unroll
+  for (int j = 0; j < n1; ++j)
+    red_run(A, sm.rbase[a1][e] + sm.rstr[a1][e] * i + 3 * sm.blk[e][a1 * 10 + a1 + j], acc1[j][0], acc1[j][1],
+            acc1[j][2]);
+}
+
+template <int P>
+__device__ __forceinline__ void tangent_xchg_transposed(const Args<float>& A, const Smem<float>& sm,
+                                                        const float* X, int64_t e0, int i) {
+  constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
+  const int e = threadIdx.x & 31;
+  if (e0 + e >= A.real_end) return;
+  const int xb = e * 495 + P * 99;
+#pragma unroll
+  for (int j = 1; j < n0; ++j) {
+    const int b = a0 + j;
+    red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a0], X[xb + j * 9 + i],
+            X[xb + j * 9 + 3 + i], X[xb + j * 9 + 6 + i]);
+  }
+#pragma unroll
+  for (int j = 1; j < n1; ++j) {
+    const int b = a1 + j;
+    red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a1], X[xb + (n0 + j) * 9 + i],
+            X[xb + (n0 + j) * 9 + 3 + i], X[xb + (n0 + j) * 9 + 6 + i]);
+  }
+}
+
+constexpr int kXFloats = 32 * 55 * 9;   // exchange buffer of the FP32 assembly
+
+// Block rows a0 = P (b = P..9) and a1 = 9 - P (b = 9-P..9): 11 blocks, so the
+// 15 warps cover the 55 blocks of the symmetric 30x30 exactly once.
+template <typename T, int P>
+__device__ __forceinline__ void tangent_rows(const Args<T>& A, const Smem<T>& sm, int64_t e0, int i) {
+  tangent_blockrow<T, P, 10 - P>(A, sm, e0, i);
+  tangent_blockrow<T, 9 - P, P + 1>(A, sm, e0, i);
+}
+
+// One tile of 32 elements starting at internal element e0.
+template <typename T, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
+__device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_raw, int64_t e0) {
+  Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
+  load_tile<T, DO_TANGENT>(A, sm, e0);
+  bool inverted = false;
+  switch ((threadIdx.x >> 5) % 3) {     // warp-uniform row of the qp phase
+    case 0: qp_phase<T, MAT, KV, DO_TANGENT, 0>(A, sm, inverted); break;
+    case 1: qp_phase<T, MAT, KV, DO_TANGENT, 1>(A, sm, inverted); break;
+    default: qp_phase<T, MAT, KV, DO_TANGENT, 2>(A, sm, inverted); break;
+  }
+  if (inverted && (e0 + (threadIdx.x & 31)) < A.real_end) atomicOr(A.flags, kFlagInverted);
+  __syncthreads();
+  if (DO_FORCE) force_phase(A, sm, e0);
+  if (DO_TANGENT) {
+    const int w = threadIdx.x >> 5;
+    const int p = w / 3, i = w % 3;
+    if constexpr (std::is_same<T, float>::value) {
+      if (A.xchg) {                    // kernel-argument test: uniform over the block
+        float* X = reinterpret_cast<float*>(smem_raw + sizeof(Smem<float>));
+        switch (p) {                   // warp-uniform
+          case 0: tangent_xchg_direct<0>(A, sm, X, e0, i); break;
+          case 1: tangent_xchg_direct<1>(A, sm, X, e0, i); break;
+          case 2: tangent_xchg_direct<2>(A, sm, X, e0, i); break;
+          case 3: tangent_xchg_direct<3>(A, sm, X, e0, i); break;
+          default: tangent_xchg_direct<4>(A, sm, X, e0, i); break;
+        }
+        __syncthreads();               // reached by every thread of the block
+        switch (p) {
+          case 0: tangent_xchg_transposed<0>(A, sm, X, e0, i); break;
+          case 1: tangent_xchg_transposed<1>(A, sm, X, e0, i); break;
+          case 2: tangent_xchg_transposed<2>(A, sm, X, e0, i); break;
+          case 3: tangent_xchg_transposed<3>(A, sm, X, e0, i); break;
+          default: tangent_xchg_transposed<4>(A, sm, X, e0, i); break;
+        }
+        return;
+      }
+    }
+    switch (p) {     // warp-uniform
+      case 0: tangent_rows<T, 0>(A, sm, e0, i); break;
+      case 1: tangent_rows<T, 1>(A, sm, e0, i); break;
+      case 2: tangent_rows<T, 2>(A, sm, e0, i); break;
+      case 3: tangent_rows<T, 3>(A, sm, e0, i); break;
+      default: tangent_rows<T, 4>(A, sm, e0, i); break;
+    }
+  }
+}
+
+// Segment table of one launch: the material segments of the internal element
+// order (each a whole number of tiles), walked by one persistent grid.
+constexpr int kMaxSeg = 64;
+
+template <typename T>
+struct SegEntry {
+  int64_t begin;       // first internal element
+  int64_t real_end;    // elements >= real_end are padding
+  int32_t tile_end;    // cumulative tile count up to and including this segment
+  int32_t combo;       // 2 * material kind + Kelvin-Voigt
+  MatT<T> mat;
+};
+
+template <typename T>
+struct SegTable {
+  SegEntry<T> s[kMaxSeg];
+  int32_t nseg;
+  int32_t ntiles;
+};
+
+// Persistent element kernel: CTA b takes tiles b, b + gridDim.x, ... over all
+// segments; COMBO < 4 compiles one (material, Kelvin-Voigt) pair, COMBO = 4
+// all four with a block-uniform dispatch per tile (multi-material meshes and
+// batches of bodies).
+template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT>
+__global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int sg = 0, t_begin = 0;
+  for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    if (t != (int)blockIdx.x) __syncthreads();     // the previous tile's shared data is consumed
+    while (t >= S.s[sg].tile_end) {                // tiles ascend: sg only grows, and t < ntiles
+      t_begin = S.s[sg].tile_end;
+      ++sg;
+    }
+    Args<T> a = A;
+    a.mat = S.s[sg].mat;
+    a.real_end = S.s[sg].real_end;
+    const int64_t e0 = S.s[sg].begin + (int64_t)(t - t_begin) * E;
+    if constexpr (COMBO < 4) {
+      elem_tile<T, COMBO / 2, (COMBO % 2) != 0, DO_FORCE, DO_TANGENT>(a, smem_raw, e0);
+    } else {
+      switch (S.s[sg].combo) {                     // block-uniform
+        case 0: elem_tile<T, TL_SVK, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
+        case 1: elem_tile<T, TL_SVK, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
+        case 2: elem_tile<T, TL_MOONEY_RIVLIN, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
+        default: elem_tile<T, TL_MOONEY_RIVLIN, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
+      }
+    }
+  }
+}
+
+template <typename T, bool DO_FORCE, bool DO_TANGENT>
+tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
+                     double mass_scale, double* f, void* values, void* K_elem) {
+  // the force-only variant does not need the tangent array (last member);
+  // the FP32 CSR assembly adds its exchange buffer after the struct
+  const bool xchg = std::is_same<T, float>::value && DO_TANGENT && values && !K_elem && m->tune.elem_xchg;
+  const size_t smem = DO_TANGENT ? sizeof(Smem<T>) + (xchg ? sizeof(float) * kXFloats : 0)
+                                 : offsetof(Smem<T>, A);
+  Args<T> A;
+  A.conn = m->d_conn;
+  A.geo = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m->d_geo32)
+                                        : reinterpret_cast<const T*>(m->d_geo64);
+  A.blk = m->d_blk;
+  A.node_ptr = m->d_node_ptr;
+  A.user_of = m->d_user_of;
+  A.q_n = q_n;
+  A.v = v;
+  A.X = m->d_X;
+  A.h = h;
+  A.real_end = 0;
+  A.mat = MatT<T>{};
+  A.alpha = T(alpha);
+  A.beta = T(beta);
+  A.mass_scale = T(mass_scale);
+  A.f = f;
+  A.values = reinterpret_cast<T*>(values);
+  A.K_elem = reinterpret_cast<T*>(K_elem);
+  A.flags = m->d_flags;
+  A.nnz = (int32_t)m->nnz;
+  A.v4_ok = ((reinterpret_cast<uintptr_t>(values) & 15u) == 0) ? 1 : 0;
+  A.xchg = xchg ? 1 : 0;
+  cudaEvent_t t0 = timer_open(m);
+  // Segments in groups of at most kMaxSeg, one persistent launch per group.
+  // The float32 kernels include an all-materials variant; the float64 ones
+  // (heavier, compiled per material) take one launch per run of segments of
+  // the same (material, Kelvin-Voigt) pair.
+  constexpr bool kMixed = std::is_same<T, float>::value;
+  size_t k = 0;
+  while (k < m->segs.size()) {
+    SegTable<T> S;
+    S.nseg = 0;
+    S.ntiles = 0;
+    int combo0 = -1;
+    bool mixed = false;
+    for (; k < m->segs.size() && S.nseg < kMaxSeg; ++k) {
+      const Segment& sg = m->segs[k];
+      const int64_t nt = (sg.padded_end - sg.begin) / E;
+      if (nt == 0) continue;
+      const MaterialDev& md = m->mats[sg.mat];
+      const int combo = 2 * (md.kind == TL_SVK ? 0 : 1) + (md.kv ? 1 : 0);
+      if (!kMixed && combo0 >= 0 && combo != combo0) break;   // next launch starts here
+      SegEntry<T>& se = S.s[S.nseg++];
+      se.begin = sg.begin;
+      se.real_end = sg.end;
+      S.ntiles += (int32_t)nt;
+      se.tile_end = S.ntiles;
+      se.combo = combo;
+      se.mat = to_matT<T>(md);
+      if (combo0 < 0) combo0 = combo;
+      mixed = mixed || combo != combo0;
+    }
+    if (S.ntiles == 0) continue;
+    void (*kern)(Args<T>, SegTable<T>) = nullptr;
+    switch (mixed ? 4 : combo0) {
+      case 0: kern = elem_kernel<T, 0, DO_FORCE, DO_TANGENT>; break;
+      case 1: kern = elem_kernel<T, 1, DO_FORCE, DO_TANGENT>; break;
+      case 2: kern = elem_kernel<T, 2, DO_FORCE, DO_TANGENT>; break;
+      case 3: kern = elem_kernel<T, 3, DO_FORCE, DO_TANGENT>; break;
+      default:
+        if constexpr (kMixed) kern = elem_kernel<T, 4, DO_FORCE, DO_TANGENT>;
+        break;
+    }
+    if (!kern) return fail(m, TL_ERR_UNSUPPORTED, "element kernel selection");
+    TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 1;
+    TL_CUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+    const int grid = m->tune.elem_full_grid ? S.ntiles
+                                            : (int)std::min<int64_t>(S.ntiles, (int64_t)m->num_sms * std::max(occ, 1));
+    kern<<<(unsigned)grid, NT, smem, m->stream>>>(A, S);
+    TL_CUDA(m, cudaGetLastError());
+    ++m->launches;
+  }
+  timer_close(m, t0, kTimeElement);
+  return TL_OK;
+}
+
+}  // namespace elem
+}  // namespace tl

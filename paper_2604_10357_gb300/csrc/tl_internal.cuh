@@ -36,13 +36,24 @@ struct Segment {
   int mat;                // index into the material table
 };
 
-struct Solver;   // sparse direct solver state (tl_solver.cu)
-struct PcgWork;  // preconditioned CG state (tl_pcg.cu)
+struct Solver;       // sparse direct solver state (tl_solver.cu)
+struct PcgWork;      // preconditioned CG state (tl_pcg.cu)
+struct NewtonGraph;  // captured Newton step (tl_newton.cu)
+
+// Launch shapes picked per handle by the autotuner (tl_tune.cu).
+struct Tune {
+  int spmv_group = 8;     // lanes per node in the PCG product H p (4, 8, 16)
+  int elem_xchg = 1;      // FP32 assembly: 1 = exchanged vector runs, 0 = scalar scatter
+  int elem_full_grid = 0; // element kernels: 0 = persistent grid (SMs x occupancy), 1 = one CTA per tile
+  int tuned = 0;
+  int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
+};
 
 }  // namespace tl
 
 struct tl_mesh {
   int device = 0;
+  int num_sms = 1;                // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   int precision = TL_FP64;
   int64_t nn = 0, ne = 0, ne_pad = 0;
@@ -78,6 +89,8 @@ struct tl_mesh {
 
   tl::Solver* solver = nullptr;
   tl::PcgWork* pcg = nullptr;
+  tl::NewtonGraph* ngraph = nullptr;
+  tl::Tune tune;
   // Newton work buffers (tl_newton_step), allocated on first use
   double *nw_g = nullptr, *nw_f = nullptr, *nw_dv = nullptr, *nw_scal = nullptr;
   void* nw_values = nullptr;
@@ -100,6 +113,12 @@ tl_status cuda_fail(tl_mesh* m, cudaError_t e, const char* what);
     if (_e != cudaSuccess) return tl::cuda_fail((m), _e, #call); \
   } while (0)
 
+#define TL_TRY(call)                 \
+  do {                               \
+    tl_status _s = (call);           \
+    if (_s != TL_OK) return _s;      \
+  } while (0)
+
 // element kernels (tl_element.cu)
 tl_status launch_force(tl_mesh* m, const double* q_n, const double* v, double h, double* f);
 // force with the element arithmetic forced to float64 when fp64 is set
@@ -108,6 +127,12 @@ tl_status launch_force_prec(tl_mesh* m, const double* q_n, const double* v, doub
 // sparse direct solver (tl_solver.cu) and PCG (tl_pcg.cu)
 void solver_destroy(Solver* s);
 void pcg_destroy(PcgWork* w);
+void newton_graph_destroy(NewtonGraph* g);
+tl_status pcg_ensure(tl_mesh* m);
+double* pcg_scalars(tl_mesh* m);   // slot 3: r.r of the current PCG iterate
+tl_status pcg_prepare(tl_mesh* m, const void* values, const double* g, double* dv);
+tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count);
+tl_status pcg_spmv_only(tl_mesh* m, const void* values, int group);   // Ap = H p, for the autotuner
 tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv, double rtol, int max_iter,
                     int* iters_out);
 tl_status launch_tangent(tl_mesh* m, const double* q_n, const double* v, double h,
@@ -123,6 +148,7 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
                           const double* v, const double* f_int, const double* f_ext,
                           const double* lambda, double* g, double* g_norm);
 tl_status launch_add_penalty(tl_mesh* m, double value, void* values);
+tl_status residual_ensure(tl_mesh* m);
 
 // instrumentation helpers (tl_api.cu): a category's event pair is opened
 // before and closed after the launches it brackets.

@@ -15,8 +15,10 @@
 // the convergence test keeps a float64 force evaluation (flag below), since a
 // float32 force has a noise floor of ~1e-7 of the element force scale, above a
 // 1e-8 relative target in steps close to equilibrium.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 #include "tl_internal.cuh"
 
@@ -39,10 +41,12 @@ __global__ void q_from_v(const double* q_n, const double* v, double h, int64_t n
 
 // c_j = q_n + h v - X at every clamped DOF (the j-th fixed node's d-th DOF is
 // constraint 3j+d); optionally lambda += rho c; ||c||^2 into out (one block).
+// (update_flag, when given, is read on the device instead of update_lambda.)
 __global__ void clamp_constraint(const int32_t* fixed_of_node, const double* X,
                                  const double* q_n, const double* v, double h, int64_t nn, double rho,
-                                 int update_lambda, double* lambda, double* out) {
+                                 int update_lambda, const int32_t* update_flag, double* lambda, double* out) {
   __shared__ double red[32];
+  if (update_flag) update_lambda = *update_flag;
   double sq = 0.0;
   for (int64_t I = threadIdx.x; I < nn; I += blockDim.x) {
     const int j = fixed_of_node[I];
@@ -64,9 +68,370 @@ __global__ void clamp_constraint(const int32_t* fixed_of_node, const double* X,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Captured Newton step (tl_params.use_graph): the loops of Algorithm 3 run as
+// conditional nodes of one CUDA graph, and the convergence tests that the
+// host makes in the loop above (the ||g|| and ||c|| transfers) are made by
+// one-thread control kernels that set the loop conditions.  Every loop is
+// bounded by its own counter (max_outer, max_inner, lin_max_iter), so the
+// graph always ends.
+
+struct NewtonCtl {
+  double g_ref, target, gn, g_init, cn, tol2, eta;
+  int32_t l, inner_total, outer, inner_ok, converged, lin_total, pcg_it, abort;
+};
+
+__global__ void ctl_reset(NewtonCtl* c) {
+  NewtonCtl z = {};
+  z.g_init = -1.0;
+  *c = z;
+}
+
+// reference norm at v_n -> inner target; arm the outer loop
+__global__ void ctl_target(NewtonCtl* c, const double* gnorm, double atol, double rtol,
+                           cudaGraphConditionalHandle h_out) {
+  const double g = *gnorm;
+  c->g_ref = g;
+  c->target = fmax(atol, rtol * g);
+  const bool ok = isfinite(g);
+  if (!ok) c->abort = 1;
+  cudaGraphSetConditional(h_out, ok ? 1u : 0u);
+}
+
+__global__ void ctl_outer_begin(NewtonCtl* c, cudaGraphConditionalHandle h_in) {
+  c->l = 0;
+  c->inner_ok = 0;
+  cudaGraphSetConditional(h_in, 1u);
+}
+
+// inner test: stop on ||g|| <= target (or a non-finite norm); otherwise take
+// a Newton step, counted against max_inner
+__global__ void ctl_inner(NewtonCtl* c, const double* gnorm, int max_inner, double lin_rtol, int adaptive,
+                          double eta_min, cudaGraphConditionalHandle h_in, cudaGraphConditionalHandle h_step) {
+  const double g = *gnorm;
+  c->gn = g;
+  if (!isfinite(g) || c->abort) {
+    c->abort = 1;
+    cudaGraphSetConditional(h_step, 0u);
+    cudaGraphSetConditional(h_in, 0u);
+    return;
+  }
+  if (c->g_init < 0.0) c->g_init = g;
+  if (g <= c->target) {
+    c->inner_ok = 1;
+    cudaGraphSetConditional(h_step, 0u);
+    cudaGraphSetConditional(h_in, 0u);
+    return;
+  }
+  c->eta = fmax(eta_min, adaptive ? fmin(0.5, fmax(lin_rtol, 0.1 * c->target / g)) : lin_rtol);
+  c->l += 1;
+  c->inner_total += 1;
+  cudaGraphSetConditional(h_step, 1u);
+  cudaGraphSetConditional(h_in, c->l < max_inner ? 1u : 0u);
+}
+
+__global__ void ctl_pcg_arm(NewtonCtl* c, const double* pscal, int lin_max, cudaGraphConditionalHandle h_pcg) {
+  const double rr0 = pscal[3];
+  c->tol2 = c->eta * c->eta * rr0;
+  c->pcg_it = 0;
+  cudaGraphSetConditional(h_pcg, (rr0 > c->tol2 && lin_max > 0) ? 1u : 0u);
+}
+
+__global__ void ctl_pcg(NewtonCtl* c, const double* pscal, int chunk, int lin_max,
+                        cudaGraphConditionalHandle h_pcg) {
+  c->pcg_it += chunk;
+  const double rr = pscal[3];
+  if (!isfinite(rr)) {
+    c->abort = 1;
+    cudaGraphSetConditional(h_pcg, 0u);
+    return;
+  }
+  const bool breakdown = pscal[6] != 0.0;
+  cudaGraphSetConditional(h_pcg, (rr > c->tol2 && c->pcg_it < lin_max && !breakdown) ? 1u : 0u);
+}
+
+__global__ void ctl_pcg_done(NewtonCtl* c) { c->lin_total += c->pcg_it; }
+
+__global__ void ctl_outer(NewtonCtl* c, const double* cnorm, double eps_out, int max_outer,
+                          cudaGraphConditionalHandle h_out) {
+  c->outer += 1;
+  c->cn = *cnorm;
+  if (c->abort) {
+    cudaGraphSetConditional(h_out, 0u);
+    return;
+  }
+  if (c->inner_ok && c->cn <= eps_out) {
+    c->converged = 1;
+    cudaGraphSetConditional(h_out, 0u);
+    return;
+  }
+  cudaGraphSetConditional(h_out, c->outer < max_outer ? 1u : 0u);
+}
+
+constexpr int kPcgChunk = 8;   // PCG iterations between two device-side checks
+
+// A float32 Hessian (TL_FP32_ELEM) is symmetric only to rounding and defines
+// the Newton direction to about 1e-7 relative: PCG is not asked for more.
+double pcg_eta_min(const tl_mesh* m) { return m->precision == TL_FP32_ELEM ? 1e-6 : 0.0; }
+
 }  // namespace
 
 tl_status launch_force_prec(tl_mesh* m, const double* q_n, const double* v, double h, double* f, bool fp64);
+
+struct NewtonGraph {
+  tl_params key = {};
+  int precision = -1;
+  int64_t tune_gen = -1;
+  cudaStream_t cs = nullptr;            // capture stream (the graph is launched on the handle's stream)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double *q_n = nullptr, *v_n = nullptr, *v = nullptr, *f_ext = nullptr, *lam = nullptr, *q_out = nullptr;
+  NewtonCtl* ctl = nullptr;
+  NewtonCtl* ctl_host = nullptr;        // pinned
+};
+
+void newton_graph_destroy(NewtonGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  void* ptrs[] = {g->q_n, g->v_n, g->v, g->f_ext, g->lam, g->q_out, g->ctl};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (g->ctl_host) cudaFreeHost(g->ctl_host);
+  if (g->cs) cudaStreamDestroy(g->cs);
+  delete g;
+}
+
+namespace {
+
+cudaError_t capture_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  return cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault);
+}
+
+// append a conditional node to the capture of s; its (empty) body is returned
+cudaError_t capture_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Records the whole step into G->graph.  Runs with m->stream = G->cs.
+tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
+  cudaStream_t s = G->cs;
+  const int64_t ndof = 3 * m->nn;
+  const unsigned nb = (unsigned)((ndof + 255) / 256);
+  const size_t vb = (m->precision == TL_FP32_ELEM ? sizeof(float) : sizeof(double));
+  const double lin_rtol = p->lin_rtol > 0.0 ? p->lin_rtol : 1e-10;
+  const int lin_max = p->lin_max_iter > 0 ? p->lin_max_iter : 5000;
+  double *g = m->nw_g, *f = m->nw_f, *dv = m->nw_dv, *scal = m->nw_scal;
+  void* values = m->nw_values;
+  NewtonCtl* c = G->ctl;
+  cudaGraphConditionalHandle h_out = 0, h_in = 0, h_step = 0, h_pcg = 0;
+  cudaGraph_t b_outer = nullptr, b_inner = nullptr, b_step = nullptr, b_pcg = nullptr, tmp = nullptr;
+  auto end_capture = [&](cudaGraph_t* out) { return cudaStreamEndCapture(s, out); };
+  // top level: reference residual at v_n, the outer loop, q = q_n + h v
+  TL_CUDA(m, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  {
+    tl_status st = TL_OK;
+    cudaError_t e = capture_handle(s, &h_out);
+    if (e == cudaSuccess) {
+      ctl_reset<<<1, 1, 0, s>>>(c);
+      st = launch_force_prec(m, G->q_n, G->v_n, p->h, f, true);
+      if (st == TL_OK) st = launch_residual(m, p, G->q_n, G->v_n, G->v_n, f, G->f_ext, G->lam, g, scal);
+      if (st == TL_OK) {
+        ctl_target<<<1, 1, 0, s>>>(c, scal, p->atol, p->rtol, h_out);
+        e = capture_conditional(s, h_out, cudaGraphCondTypeWhile, &b_outer);
+        if (e == cudaSuccess) q_from_v<<<nb, 256, 0, s>>>(G->q_n, G->v, p->h, ndof, G->q_out);
+      }
+    }
+    cudaGraph_t top = nullptr;
+    cudaError_t e2 = end_capture(&top);
+    G->graph = top;
+    if (st != TL_OK) return st;
+    TL_CUDA(m, e);
+    TL_CUDA(m, e2);
+  }
+  // outer body: inner loop, clamp rows and multiplier update, outer test
+  TL_CUDA(m, cudaStreamBeginCaptureToGraph(s, b_outer, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    cudaError_t e = capture_handle(s, &h_in);
+    if (e == cudaSuccess) {
+      ctl_outer_begin<<<1, 1, 0, s>>>(c, h_in);
+      e = capture_conditional(s, h_in, cudaGraphCondTypeWhile, &b_inner);
+    }
+    if (e == cudaSuccess) {
+      clamp_constraint<<<1, 1024, 0, s>>>(m->d_fixed_of_node, m->d_X, G->q_n, G->v, p->h, m->nn, p->rho_alm, 0,
+                                           &c->inner_ok, G->lam, scal + 1);
+      ctl_outer<<<1, 1, 0, s>>>(c, scal + 1, p->eps_out, p->max_outer, h_out);
+    }
+    cudaError_t e2 = end_capture(&tmp);
+    TL_CUDA(m, e);
+    TL_CUDA(m, e2);
+  }
+  // inner body: residual at v, inner test, conditional Newton step
+  TL_CUDA(m, cudaStreamBeginCaptureToGraph(s, b_inner, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    tl_status st = TL_OK;
+    cudaError_t e = capture_handle(s, &h_step);
+    if (e == cudaSuccess) {
+      st = launch_force_prec(m, G->q_n, G->v, p->h, f, true);
+      if (st == TL_OK) st = launch_residual(m, p, G->q_n, G->v_n, G->v, f, G->f_ext, G->lam, g, scal);
+      if (st == TL_OK) {
+        ctl_inner<<<1, 1, 0, s>>>(c, scal, p->max_inner, lin_rtol, p->lin_adaptive, pcg_eta_min(m), h_in,
+                                  h_step);
+        e = capture_conditional(s, h_step, cudaGraphCondTypeIf, &b_step);
+      }
+    }
+    cudaError_t e2 = end_capture(&tmp);
+    if (st != TL_OK) return st;
+    TL_CUDA(m, e);
+    TL_CUDA(m, e2);
+  }
+  // Newton step: assemble H (eq. hessian), PCG loop, v += dv
+  TL_CUDA(m, cudaStreamBeginCaptureToGraph(s, b_step, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    tl_status st = TL_OK;
+    cudaError_t e = capture_handle(s, &h_pcg);
+    if (e == cudaSuccess) e = cudaMemsetAsync(values, 0, vb * m->nnz, s);
+    if (e == cudaSuccess) {
+      st = launch_tangent(m, G->q_n, G->v, p->h, p->h, 1.0, 1.0 / p->h, false, nullptr, values, nullptr);
+      if (st == TL_OK) st = launch_add_penalty(m, p->h * p->h * p->rho_alm, values);
+      if (st == TL_OK) st = pcg_prepare(m, values, g, dv);
+      if (st == TL_OK) {
+        ctl_pcg_arm<<<1, 1, 0, s>>>(c, pcg_scalars(m), lin_max, h_pcg);
+        e = capture_conditional(s, h_pcg, cudaGraphCondTypeWhile, &b_pcg);
+        if (e == cudaSuccess) {
+          ctl_pcg_done<<<1, 1, 0, s>>>(c);
+          axpy_kernel<<<nb, 256, 0, s>>>(G->v, dv, 1.0, ndof);
+        }
+      }
+    }
+    cudaError_t e2 = end_capture(&tmp);
+    if (st != TL_OK) return st;
+    TL_CUDA(m, e);
+    TL_CUDA(m, e2);
+  }
+  // PCG body: kPcgChunk iterations and the device-side residual test
+  TL_CUDA(m, cudaStreamBeginCaptureToGraph(s, b_pcg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    tl_status st = pcg_iterations(m, values, dv, kPcgChunk);
+    if (st == TL_OK) ctl_pcg<<<1, 1, 0, s>>>(c, pcg_scalars(m), kPcgChunk, lin_max, h_pcg);
+    cudaError_t e2 = end_capture(&tmp);
+    if (st != TL_OK) return st;
+    TL_CUDA(m, e2);
+  }
+  TL_CUDA(m, cudaGraphInstantiate(&G->exec, G->graph, 0));
+  return TL_OK;
+}
+
+// (Re)build the graph when the parameters or the element precision change.
+tl_status ensure_graph(tl_mesh* m, const tl_params* p) {
+  const int64_t ndof = 3 * m->nn;
+  NewtonGraph* G = m->ngraph;
+  if (G && G->exec && G->precision == m->precision && G->tune_gen == m->tune.generation &&
+      std::memcmp(&G->key, p, sizeof(tl_params)) == 0)
+    return TL_OK;
+  if (!G) {
+    G = new NewtonGraph();
+    m->ngraph = G;
+    TL_CUDA(m, cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking));
+    TL_CUDA(m, cudaMalloc(&G->q_n, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&G->v_n, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&G->v, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&G->f_ext, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&G->q_out, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&G->lam, sizeof(double) * std::max<int64_t>(1, 3 * m->nfixed)));
+    TL_CUDA(m, cudaMalloc(&G->ctl, sizeof(NewtonCtl)));
+    TL_CUDA(m, cudaMallocHost(&G->ctl_host, sizeof(NewtonCtl)));
+  }
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->graph) cudaGraphDestroy(G->graph);
+  G->exec = nullptr;
+  G->graph = nullptr;
+  // allocations the captured launches need happen before the capture
+  TL_TRY(pcg_ensure(m));
+  TL_TRY(residual_ensure(m));
+  TL_CUDA(m, cudaStreamSynchronize(m->stream));
+  cudaStream_t user = m->stream;
+  const bool timing = m->timing;
+  m->stream = G->cs;
+  m->timing = false;
+  const tl_status st = capture_step(m, p, G);
+  m->stream = user;
+  m->timing = timing;
+  if (st != TL_OK) {
+    if (G->graph) cudaGraphDestroy(G->graph);
+    G->graph = nullptr;
+    cudaGetLastError();
+    return st;
+  }
+  G->key = *p;
+  G->precision = m->precision;
+  G->tune_gen = m->tune.generation;
+  return TL_OK;
+}
+
+}  // namespace
+
+// The step as one graph launch between device copies of the caller's arrays.
+tl_status newton_step_graph(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n,
+                            const double* v_init, const double* f_ext, double* lambda, double* v_out, double* q_out,
+                            tl_newton_stats* stats, std::chrono::steady_clock::time_point t_start) {
+  TL_TRY(ensure_graph(m, p));
+  NewtonGraph* G = m->ngraph;
+  cudaStream_t s = m->stream;
+  const size_t vbytes = sizeof(double) * 3 * m->nn;
+  const size_t lbytes = sizeof(double) * 3 * m->nfixed;
+  TL_CUDA(m, cudaMemcpyAsync(G->q_n, q_n, vbytes, cudaMemcpyDeviceToDevice, s));
+  TL_CUDA(m, cudaMemcpyAsync(G->v_n, v_n, vbytes, cudaMemcpyDeviceToDevice, s));
+  TL_CUDA(m, cudaMemcpyAsync(G->v, v_init ? v_init : v_n, vbytes, cudaMemcpyDeviceToDevice, s));
+  if (f_ext)
+    TL_CUDA(m, cudaMemcpyAsync(G->f_ext, f_ext, vbytes, cudaMemcpyDeviceToDevice, s));
+  else
+    TL_CUDA(m, cudaMemsetAsync(G->f_ext, 0, vbytes, s));
+  if (lbytes) TL_CUDA(m, cudaMemcpyAsync(G->lam, lambda, lbytes, cudaMemcpyDeviceToDevice, s));
+  TL_CUDA(m, cudaGraphLaunch(G->exec, s));
+  TL_CUDA(m, cudaMemcpyAsync(v_out, G->v, vbytes, cudaMemcpyDeviceToDevice, s));
+  TL_CUDA(m, cudaMemcpyAsync(q_out, G->q_out, vbytes, cudaMemcpyDeviceToDevice, s));
+  if (lbytes) TL_CUDA(m, cudaMemcpyAsync(lambda, G->lam, lbytes, cudaMemcpyDeviceToDevice, s));
+  TL_CUDA(m, cudaMemcpyAsync(G->ctl_host, G->ctl, sizeof(NewtonCtl), cudaMemcpyDeviceToHost, s));
+  TL_CUDA(m, cudaStreamSynchronize(s));
+  const NewtonCtl& c = *G->ctl_host;
+  if (stats) {
+    stats->inner_iters = c.inner_total;
+    stats->outer_iters = c.outer;
+    stats->converged = c.converged;
+    stats->g_ref = c.g_ref;
+    stats->g_norm = c.gn;
+    stats->c_norm = c.cn;
+    stats->ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    stats->ms_assembly = 0.0;   // not split inside the graph
+    stats->ms_solver = 0.0;
+    stats->lin_iters = c.lin_total;
+    stats->g_init = c.g_init;
+  }
+  if (c.abort) return fail(m, TL_ERR_NONFINITE, "non-finite residual in the captured Newton step");
+  return c.converged ? TL_OK : fail(m, TL_ERR_NOT_CONVERGED, "Newton / ALM iteration caps reached");
+}
 
 }  // namespace tl
 
@@ -81,6 +446,8 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
   const auto t_start = std::chrono::steady_clock::now();
   const bool use_pcg = p->linear_solver == TL_SOLVER_PCG;
+  if (p->use_graph && !use_pcg)
+    return fail(m, TL_ERR_UNSUPPORTED, "use_graph needs the PCG inner solver (the direct solver is not captured)");
   if (!use_pcg) {
     tl_status st = solver_setup(m);
     if (st != TL_OK) return st;
@@ -98,6 +465,8 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
     TL_CUDA(m, cudaMalloc(&m->nw_scal, sizeof(double) * 4));
     TL_CUDA(m, cudaMalloc(&m->nw_values, vb * m->nnz));
   }
+  if (p->use_graph)
+    return newton_step_graph(m, p, q_n, v_n, v_init, f_ext, lambda, v_out, q_out, stats, t_start);
   struct {
     double *g, *f, *dv, *scal;
     void* values;
@@ -171,7 +540,8 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
         int it = 0;
         // inexact Newton: the linear residual only needs to be well below the
         // Newton target (g_{k+1} ~ linear residual + O(|dv|^2))
-        const double eta = p->lin_adaptive ? std::min(0.5, std::max(lin_rtol, 0.1 * target / gn)) : lin_rtol;
+        const double eta = std::max(
+            pcg_eta_min(m), p->lin_adaptive ? std::min(0.5, std::max(lin_rtol, 0.1 * target / gn)) : lin_rtol);
         NTRY(pcg_solve(m, w.values, w.g, w.dv, eta, lin_max, &it));
         lin_total += it;
       } else {
@@ -190,7 +560,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
       ++inner_total;
     }
     clamp_constraint<<<1, 1024, 0, s>>>(m->d_fixed_of_node, m->d_X, q_n, v, p->h, m->nn, p->rho_alm,
-                                         inner_ok ? 1 : 0, lambda, w.scal + 1);
+                                         inner_ok ? 1 : 0, nullptr, lambda, w.scal + 1);
     NCUDA(cudaGetLastError());
     ++m->launches;
     NCUDA(cudaMemcpyAsync(&cn, w.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));

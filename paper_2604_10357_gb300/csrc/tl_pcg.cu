@@ -6,11 +6,15 @@
 // converged state is the same to the Newton tolerance.
 //
 // Preconditioner: the inverse of each node's 3x3 diagonal block of H
-// (block Jacobi), formed once per factorization call.  One warp per CSR row
-// for the product H p (FP64 or FP32 values, FP64 vectors); dot products are
-// reduced per block into partials and finished by a one-block kernel that
-// also forms alpha / beta on the device; the host reads the residual norm
-// every kCheck iterations.
+// (block Jacobi), formed once per factorization call.  The product H p runs
+// per node (FP64 or FP32 values, FP64 vectors): the three rows of a node have
+// the same columns, so a group of lanes walks the node's neighbour list once,
+// reads each neighbour's index and p values once for all three rows (the
+// column array of the DOF CSR is not read), and reduces the three sums in
+// the group.  Dot products are reduced per block into partials and finished
+// by a one-block kernel; alpha and beta are formed on the device.  The host
+// reads the residual norm every kCheck iterations, or the check runs on the
+// device inside the captured Newton graph.
 #include <cmath>
 
 #include "tl_internal.cuh"
@@ -87,23 +91,42 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
-// Ap = H p (one warp per row) and the partial dot products p . Ap
-template <typename T>
-__global__ void spmv_dot(const T* __restrict__ vals, const int32_t* __restrict__ col,
-                         const int32_t* __restrict__ row_ptr, int64_t n, const double* __restrict__ p,
-                         double* __restrict__ Ap, double* part) {
+// Ap = H p with a group of G lanes per node I (rows 3I..3I+2): lane l takes
+// the neighbours j = l, l+G, ..., reads node_col once, p[3J..3J+2] once and
+// the three 3-entry runs (row 3I+d starts at 9 ptr(I) + 3 deg(I) d), and the
+// group reduces the three sums.  Partial dot products p . Ap per block.
+template <typename T, int G>
+__global__ void spmv_node(const T* __restrict__ vals, const int32_t* __restrict__ node_ptr,
+                          const int32_t* __restrict__ node_col, int64_t nn, const double* __restrict__ p,
+                          double* __restrict__ Ap, double* part) {
   __shared__ double red[kBlock / 32];
-  const int lane = threadIdx.x & 31;
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  double dot = 0.0;
-  if (row < n) {
-    double acc = 0.0;
-    for (int k = row_ptr[row] + lane; k < row_ptr[row + 1]; k += 32) acc += double(vals[k]) * p[col[k]];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      Ap[row] = acc;
-      dot = acc * p[row];
+  const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int l = threadIdx.x & (G - 1);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, dot = 0.0;
+  if (I < nn) {
+    const int p0 = node_ptr[I], deg = node_ptr[I + 1] - p0;
+    const T* v0 = vals + 9 * (int64_t)p0;
+    const T* v1 = v0 + 3 * deg;
+    const T* v2 = v1 + 3 * deg;
+    for (int j = l; j < deg; j += G) {
+      const int64_t J = node_col[p0 + j];
+      const double x0 = p[3 * J], x1 = p[3 * J + 1], x2 = p[3 * J + 2];
+      s0 += double(v0[3 * j]) * x0 + double(v0[3 * j + 1]) * x1 + double(v0[3 * j + 2]) * x2;
+      s1 += double(v1[3 * j]) * x0 + double(v1[3 * j + 1]) * x1 + double(v1[3 * j + 2]) * x2;
+      s2 += double(v2[3 * j]) * x0 + double(v2[3 * j + 1]) * x1 + double(v2[3 * j + 2]) * x2;
     }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (I < nn && l == 0) {
+    Ap[3 * I] = s0;
+    Ap[3 * I + 1] = s1;
+    Ap[3 * I + 2] = s2;
+    dot = s0 * p[3 * I] + s1 * p[3 * I + 1] + s2 * p[3 * I + 2];
   }
   const double t = block_sum(dot, red);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -118,13 +141,17 @@ __global__ void finish_sum(const double* part, int n, double* scal, int slot) {
   if (threadIdx.x == 0) scal[slot] = s;
 }
 
-// scal layout: 0 rz (current), 1 pAp, 2 rz_new, 3 rr, 4 alpha, 5 beta
+// scal layout: 0 rz (current), 1 pAp, 2 rz_new, 3 rr, 6 breakdown flag
 // x += alpha p; r -= alpha Ap; z = P r; partials of r.z and r.r
 __global__ void update_xr(double* x, double* r, double* z, const double* p, const double* Ap, const double* binv,
-                          const double* scal, int64_t nn, double* part_rz, double* part_rr) {
+                          double* scal, int64_t nn, double* part_rz, double* part_rr) {
   __shared__ double red[kBlock / 32];
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const double alpha = scal[0] / scal[1];
+  // pAp <= 0: H is not positive definite along p (CG breakdown); stop moving
+  // and raise the breakdown slot, which ends the iteration at the next check
+  const bool ok = scal[1] > 0.0;
+  const double alpha = ok ? scal[0] / scal[1] : 0.0;
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) scal[6] = 1.0;
   double rz = 0.0, rr = 0.0;
   if (I < nn) {
     double rv[3];
@@ -154,7 +181,7 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
 // p = z + beta p with beta = rz_new / rz, then rz <- rz_new
 __global__ void update_p(double* p, const double* z, int64_t n, double* scal) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const double beta = scal[2] / scal[0];
+  const double beta = scal[0] != 0.0 ? scal[2] / scal[0] : 0.0;
   if (i < n) p[i] = z[i] + beta * p[i];
 }
 
@@ -162,9 +189,10 @@ __global__ void roll_rz(double* scal) { scal[0] = scal[2]; }
 
 // start: x = 0, r = b = -g, z = P r, p = z; partials of r.z and r.r
 __global__ void pcg_start(const double* g, double* x, double* r, double* z, double* p, const double* binv,
-                          int64_t nn, double* part_rz, double* part_rr) {
+                          int64_t nn, double* part_rz, double* part_rr, double* scal) {
   __shared__ double red[kBlock / 32];
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I == 0) scal[6] = 0.0;
   double rz = 0.0, rr = 0.0;
   if (I < nn) {
     double rv[3];
@@ -201,67 +229,129 @@ void pcg_destroy(PcgWork* w) {
   delete w;
 }
 
-// Solve H dv = -g to ||r|| <= rtol ||g||.  values in assembly CSR order.
-tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv, double rtol, int max_iter,
-                    int* iters_out) {
-  cudaStream_t s = m->stream;
+// Allocate the PCG work arrays once per handle (no-op afterwards).
+tl_status pcg_ensure(tl_mesh* m) {
+  if (m->pcg) return TL_OK;
   const int64_t nn = m->nn, n = 3 * nn;
-  if (!m->pcg) {
-    PcgWork* w = new PcgWork();
-    m->pcg = w;
-    w->nparts = (int)std::max<int64_t>((nn + kBlock - 1) / kBlock, (32 * n + kBlock - 1) / kBlock);
-    TL_CUDA(m, cudaMalloc(&w->r, sizeof(double) * n));
-    TL_CUDA(m, cudaMalloc(&w->z, sizeof(double) * n));
-    TL_CUDA(m, cudaMalloc(&w->p, sizeof(double) * n));
-    TL_CUDA(m, cudaMalloc(&w->Ap, sizeof(double) * n));
-    TL_CUDA(m, cudaMalloc(&w->binv, sizeof(double) * 9 * nn));
-    TL_CUDA(m, cudaMalloc(&w->part, sizeof(double) * 2 * w->nparts));
-    TL_CUDA(m, cudaMalloc(&w->scal, sizeof(double) * 8));
-    TL_CUDA(m, cudaMalloc(&w->diag_k, sizeof(int32_t) * nn));
-    node_diag_pos<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(m->d_node_ptr, m->d_node_col, nn, w->diag_k);
-    TL_CUDA(m, cudaGetLastError());
-  }
+  PcgWork* w = new PcgWork();
+  m->pcg = w;
+  w->nparts = (int)std::max<int64_t>((nn + kBlock - 1) / kBlock, (16 * nn + kBlock - 1) / kBlock);
+  TL_CUDA(m, cudaMalloc(&w->r, sizeof(double) * n));
+  TL_CUDA(m, cudaMalloc(&w->z, sizeof(double) * n));
+  TL_CUDA(m, cudaMalloc(&w->p, sizeof(double) * n));
+  TL_CUDA(m, cudaMalloc(&w->Ap, sizeof(double) * n));
+  TL_CUDA(m, cudaMalloc(&w->binv, sizeof(double) * 9 * nn));
+  TL_CUDA(m, cudaMalloc(&w->part, sizeof(double) * 2 * w->nparts));
+  TL_CUDA(m, cudaMalloc(&w->scal, sizeof(double) * 8));
+  TL_CUDA(m, cudaMalloc(&w->diag_k, sizeof(int32_t) * nn));
+  node_diag_pos<<<(unsigned)((nn + 255) / 256), 256, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, nn, w->diag_k);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
+  return TL_OK;
+}
+
+double* pcg_scalars(tl_mesh* m) { return m->pcg ? m->pcg->scal : nullptr; }
+
+// Block-Jacobi factors of H, x = 0, r = -g, z = P r, p = z, and the scalars
+// rz (slot 0) and rr (slot 3); asynchronous.
+tl_status pcg_prepare(tl_mesh* m, const void* values, const double* g, double* dv) {
+  TL_TRY(pcg_ensure(m));
   PcgWork* w = m->pcg;
-  const bool fp32 = m->precision == TL_FP32_ELEM;
+  cudaStream_t s = m->stream;
+  const int64_t nn = m->nn;
   const unsigned nbn = (unsigned)((nn + kBlock - 1) / kBlock);
-  const unsigned nbr = (unsigned)((32 * n + kBlock - 1) / kBlock);
-  const unsigned nbv = (unsigned)((n + kBlock - 1) / kBlock);
-  if (fp32)
+  if (m->precision == TL_FP32_ELEM)
     block_jacobi<float><<<nbn, kBlock, 0, s>>>((const float*)values, m->d_node_ptr, w->diag_k, nn, w->binv);
   else
     block_jacobi<double><<<nbn, kBlock, 0, s>>>((const double*)values, m->d_node_ptr, w->diag_k, nn, w->binv);
   double* part_rz = w->part;
   double* part_rr = w->part + w->nparts;
-  pcg_start<<<nbn, kBlock, 0, s>>>(g, dv, w->r, w->z, w->p, w->binv, nn, part_rz, part_rr);
+  pcg_start<<<nbn, kBlock, 0, s>>>(g, dv, w->r, w->z, w->p, w->binv, nn, part_rz, part_rr, w->scal);
   finish_sum<<<1, 1024, 0, s>>>(part_rz, nbn, w->scal, 0);
   finish_sum<<<1, 1024, 0, s>>>(part_rr, nbn, w->scal, 3);
+  TL_CUDA(m, cudaGetLastError());
+  m->launches += 4;
+  return TL_OK;
+}
+
+template <typename T, int G>
+void launch_spmv(tl_mesh* m, const void* values, PcgWork* w, unsigned* nblocks) {
+  const int64_t nn = m->nn;
+  const unsigned nb = (unsigned)((G * nn + kBlock - 1) / kBlock);
+  spmv_node<T, G><<<nb, kBlock, 0, m->stream>>>((const T*)values, m->d_node_ptr, m->d_node_col, nn, w->p, w->Ap,
+                                                w->part);
+  *nblocks = nb;
+}
+
+tl_status pcg_spmv_only(tl_mesh* m, const void* values, int group) {
+  TL_TRY(pcg_ensure(m));
+  PcgWork* w = m->pcg;
+  unsigned nbs = 0;
+  const bool fp32 = m->precision == TL_FP32_ELEM;
+  if (group == 4) fp32 ? launch_spmv<float, 4>(m, values, w, &nbs) : launch_spmv<double, 4>(m, values, w, &nbs);
+  else if (group == 16) fp32 ? launch_spmv<float, 16>(m, values, w, &nbs) : launch_spmv<double, 16>(m, values, w, &nbs);
+  else fp32 ? launch_spmv<float, 8>(m, values, w, &nbs) : launch_spmv<double, 8>(m, values, w, &nbs);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
+  return TL_OK;
+}
+
+// `count` PCG iterations (7 launches each); asynchronous, no host reads.
+tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) {
+  PcgWork* w = m->pcg;
+  cudaStream_t s = m->stream;
+  const int64_t nn = m->nn, n = 3 * nn;
+  const bool fp32 = m->precision == TL_FP32_ELEM;
+  const unsigned nbn = (unsigned)((nn + kBlock - 1) / kBlock);
+  const unsigned nbv = (unsigned)((n + kBlock - 1) / kBlock);
+  double* part_rz = w->part;
+  double* part_rr = w->part + w->nparts;
+  for (int k = 0; k < count; ++k) {
+    unsigned nbs = 0;
+    const int G = m->tune.spmv_group;
+    if (fp32) {
+      if (G == 4) launch_spmv<float, 4>(m, values, w, &nbs);
+      else if (G == 16) launch_spmv<float, 16>(m, values, w, &nbs);
+      else launch_spmv<float, 8>(m, values, w, &nbs);
+    } else {
+      if (G == 4) launch_spmv<double, 4>(m, values, w, &nbs);
+      else if (G == 16) launch_spmv<double, 16>(m, values, w, &nbs);
+      else launch_spmv<double, 8>(m, values, w, &nbs);
+    }
+    finish_sum<<<1, 1024, 0, s>>>(w->part, (int)nbs, w->scal, 1);
+    update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr);
+    finish_sum<<<1, 1024, 0, s>>>(part_rz, nbn, w->scal, 2);
+    finish_sum<<<1, 1024, 0, s>>>(part_rr, nbn, w->scal, 3);
+    update_p<<<nbv, kBlock, 0, s>>>(w->p, w->z, n, w->scal);
+    roll_rz<<<1, 1, 0, s>>>(w->scal);
+    m->launches += 7;
+  }
+  TL_CUDA(m, cudaGetLastError());
+  return TL_OK;
+}
+
+// Solve H dv = -g to ||r|| <= rtol ||g|| (host-driven: the residual norm is
+// read every kCheck iterations).  values in assembly CSR order.
+tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv, double rtol, int max_iter,
+                    int* iters_out) {
+  cudaStream_t s = m->stream;
+  TL_TRY(pcg_prepare(m, values, g, dv));
+  PcgWork* w = m->pcg;
   double rr0 = 0.0;
   TL_CUDA(m, cudaMemcpyAsync(&rr0, w->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
   TL_CUDA(m, cudaStreamSynchronize(s));
   const double tol2 = rtol * rtol * rr0;
   int it = 0;
-  m->launches += 4;
-  while (it < max_iter) {
-    for (int k = 0; k < kCheck && it < max_iter; ++k, ++it) {
-      if (fp32)
-        spmv_dot<float><<<nbr, kBlock, 0, s>>>((const float*)values, m->d_col, m->d_row_ptr, n, w->p, w->Ap, w->part);
-      else
-        spmv_dot<double><<<nbr, kBlock, 0, s>>>((const double*)values, m->d_col, m->d_row_ptr, n, w->p, w->Ap,
-                                                w->part);
-      finish_sum<<<1, 1024, 0, s>>>(w->part, nbr, w->scal, 1);
-      update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr);
-      finish_sum<<<1, 1024, 0, s>>>(part_rz, nbn, w->scal, 2);
-      finish_sum<<<1, 1024, 0, s>>>(part_rr, nbn, w->scal, 3);
-      update_p<<<nbv, kBlock, 0, s>>>(w->p, w->z, n, w->scal);
-      roll_rz<<<1, 1, 0, s>>>(w->scal);
-      m->launches += 7;
-    }
-    TL_CUDA(m, cudaGetLastError());
-    double rr = 0.0;
-    TL_CUDA(m, cudaMemcpyAsync(&rr, w->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+  while (it < max_iter && rr0 > tol2) {
+    const int k = std::min(kCheck, max_iter - it);
+    TL_TRY(pcg_iterations(m, values, dv, k));
+    it += k;
+    double sc[4] = {0.0, 0.0, 0.0, 0.0};   // slots 3..6
+    TL_CUDA(m, cudaMemcpyAsync(sc, w->scal + 3, sizeof(sc), cudaMemcpyDeviceToHost, s));
     TL_CUDA(m, cudaStreamSynchronize(s));
+    const double rr = sc[0];
     if (!std::isfinite(rr)) return fail(m, TL_ERR_NONFINITE, "PCG residual not finite");
-    if (rr <= tol2) break;
+    if (rr <= tol2 || sc[3] != 0.0) break;
   }
   if (iters_out) *iters_out = it;
   return TL_OK;

@@ -97,9 +97,8 @@ __global__ void add_diag(const int32_t* diag, int64_t n, T value, T* values) {
 
 }  // namespace
 
-tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n, const double* v,
-                          const double* f_int, const double* f_ext, const double* lambda, double* g,
-                          double* g_norm) {
+// Norm partials owned by the handle (one per block of kResBlock nodes).
+tl_status residual_ensure(tl_mesh* m) {
   const int nb = (int)((m->nn + kResBlock - 1) / kResBlock);
   if (nb > m->partials_cap) {
     if (m->d_partials) cudaFree(m->d_partials);
@@ -108,6 +107,14 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
     TL_CUDA(m, cudaMalloc(&m->d_partials, sizeof(double) * nb));
     m->partials_cap = nb;
   }
+  return TL_OK;
+}
+
+tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, const double* v_n, const double* v,
+                          const double* f_int, const double* f_ext, const double* lambda, double* g,
+                          double* g_norm) {
+  const int nb = (int)((m->nn + kResBlock - 1) / kResBlock);
+  TL_TRY(residual_ensure(m));
   cudaEvent_t t0 = timer_open(m);
   // f_int may alias g: each thread reads its own entries before writing them
   residual_kernel<<<nb, kResBlock, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow,

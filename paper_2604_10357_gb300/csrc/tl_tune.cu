@@ -1,0 +1,140 @@
+// Autotuner of the launch shapes (no counterpart in the paper).
+//
+// The best shape of the two hot launches depends on the mesh (node degrees,
+// element order, material mix) and on the element precision, so it is chosen
+// by timing, on the handle's own mesh and state, every variant that the
+// library compiles:
+//   * element pass (fused force + tangent + CSR assembly): persistent grid
+//     (SMs x resident CTAs, tiles taken round-robin) or one CTA per tile;
+//     for the float32 form also the scatter strategy (exchanged 3-entry runs
+//     as vector reductions, or one scalar reduction per entry);
+//   * PCG product H p: 4, 8 or 16 lanes per node.
+// Each variant is warmed up once and timed over `reps` launches with CUDA
+// events on the handle's stream; the fastest is kept in the handle and used by
+// every later call (a captured Newton graph is rebuilt on its next use).
+#include <vector>
+
+#include "tl_internal.cuh"
+
+using namespace tl;
+
+namespace {
+
+template <typename F>
+tl_status time_reps(tl_mesh* m, int reps, F&& launch, float* ms_out) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  TL_CUDA(m, cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return fail(m, TL_ERR_CUDA, "event creation");
+  }
+  tl_status st = launch();                       // warm-up (and first-use setup)
+  if (st == TL_OK) {
+    cudaEventRecord(a, m->stream);
+    for (int r = 0; r < reps && st == TL_OK; ++r) st = launch();
+    cudaEventRecord(b, m->stream);
+  }
+  if (st == TL_OK && cudaEventSynchronize(b) == cudaSuccess) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    *ms_out = t / (float)reps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return st;
+}
+
+}  // namespace
+
+extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,
+                                 tl_tune_result* out) {
+  if (!m || !q_n || !v || reps < 1) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, TL_ERR_CUDA, "cudaSetDevice");
+  const bool fp32 = m->precision == TL_FP32_ELEM;
+  const size_t vb = fp32 ? sizeof(float) : sizeof(double);
+  void* values = nullptr;
+  double* f = nullptr;
+  TL_CUDA(m, cudaMalloc(&values, vb * (size_t)m->nnz));
+  if (cudaMalloc(&f, sizeof(double) * 3 * m->nn) != cudaSuccess) {
+    cudaFree(values);
+    return fail(m, TL_ERR_OOM, "autotune buffers");
+  }
+  const Tune saved = m->tune;
+  tl_tune_result r = {};
+  tl_status st = TL_OK;
+  // element pass: (xchg, full grid) variants
+  struct V { int xchg, full; };
+  std::vector<V> variants = {{1, 0}, {1, 1}};
+  if (fp32) variants.insert(variants.end(), {{0, 0}, {0, 1}});
+  float best = 1e30f;
+  Tune chosen = saved;
+  for (size_t k = 0; k < variants.size() && st == TL_OK; ++k) {
+    m->tune.elem_xchg = variants[k].xchg;
+    m->tune.elem_full_grid = variants[k].full;
+    float ms = 0.f;
+    st = time_reps(m, reps, [&]() {
+      tl_status s2 = launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
+      return s2;
+    }, &ms);
+    if (st != TL_OK) break;
+    const int slot = (variants[k].xchg ? 0 : 2) + variants[k].full;
+    r.ms_element[slot] = ms;
+    if (ms < best) {
+      best = ms;
+      chosen.elem_xchg = variants[k].xchg;
+      chosen.elem_full_grid = variants[k].full;
+    }
+  }
+  // PCG product: lanes per node
+  if (st == TL_OK) st = pcg_ensure(m);
+  best = 1e30f;
+  const int groups[3] = {4, 8, 16};
+  for (int k = 0; k < 3 && st == TL_OK; ++k) {
+    float ms = 0.f;
+    st = time_reps(m, reps, [&]() { return pcg_spmv_only(m, values, groups[k]); }, &ms);
+    if (st != TL_OK) break;
+    r.ms_spmv[k] = ms;
+    if (ms < best) {
+      best = ms;
+      chosen.spmv_group = groups[k];
+    }
+  }
+  cudaStreamSynchronize(m->stream);
+  cudaFree(values);
+  cudaFree(f);
+  if (st != TL_OK) {
+    m->tune = saved;
+    return st;
+  }
+  chosen.tuned = 1;
+  chosen.generation = saved.generation + 1;
+  m->tune = chosen;
+  r.spmv_group = chosen.spmv_group;
+  r.elem_xchg = chosen.elem_xchg;
+  r.elem_full_grid = chosen.elem_full_grid;
+  if (out) *out = r;
+  return TL_OK;
+}
+
+extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
+  if (!m || !out) return TL_ERR_INVALID_ARG;
+  tl_tune_result r = {};
+  r.spmv_group = m->tune.spmv_group;
+  r.elem_xchg = m->tune.elem_xchg;
+  r.elem_full_grid = m->tune.elem_full_grid;
+  *out = r;
+  return TL_OK;
+}
+
+extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
+  if (!m || !in) return TL_ERR_INVALID_ARG;
+  if (in->spmv_group != 4 && in->spmv_group != 8 && in->spmv_group != 16) return TL_ERR_INVALID_ARG;
+  if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1))
+    return TL_ERR_INVALID_ARG;
+  m->tune.spmv_group = in->spmv_group;
+  m->tune.elem_xchg = in->elem_xchg;
+  m->tune.elem_full_grid = in->elem_full_grid;
+  m->tune.generation += 1;
+  return TL_OK;
+}

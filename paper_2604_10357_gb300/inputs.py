@@ -137,10 +137,27 @@ def cylinder_t10(nr, nz, R, Lz, fixed_face_z0=True):
 # Nodal fields
 # ---------------------------------------------------------------------------
 
-def uniform_perturbation(mesh, frac, rng):
-    """q = X + U(-frac*h_i, frac*h_i) per axis per node; clamped nodes stay at X."""
-    h = np.asarray(mesh.hex_size)
-    d = rng.uniform(-1.0, 1.0, size=mesh.X.shape) * (frac * h)[None, :]
+def uniform_perturbation(mesh, frac, rng, local=False):
+    """q = X + U(-frac*h_i, frac*h_i) per axis per node; clamped nodes stay at X.
+    h_i is the hex edge of the structured grid, or with local=True the node's
+    own spacing: half the smallest altitude of the elements at the node (the
+    cylinder's square-to-disk map makes rim elements much flatter than the
+    grid spacing)."""
+    if local:
+        c = mesh.conn[:, :4]
+        P = mesh.X[c]
+        vol6 = np.abs(np.einsum("ij,ij->i", P[:, 1] - P[:, 0],
+                                np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0])))
+        faces = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
+        area2 = np.stack([np.linalg.norm(np.cross(P[:, j] - P[:, i], P[:, k] - P[:, i]), axis=1)
+                          for i, j, k in faces], axis=1)
+        he = 0.5 * vol6 / area2.max(axis=1)          # half the smallest altitude
+        hn = np.full(mesh.nn, np.inf)
+        np.minimum.at(hn, mesh.conn.ravel(), np.repeat(he, 10))
+        scale = (frac * hn)[:, None]
+    else:
+        scale = (frac * np.asarray(mesh.hex_size))[None, :]
+    d = rng.uniform(-1.0, 1.0, size=mesh.X.shape) * scale
     d[mesh.fixed_nodes] = 0.0
     return mesh.X + d
 
@@ -307,7 +324,7 @@ def workload_warm_start_svk():
 def workload_batched(nbodies=48, seed=1000 + 3, lo=1000, hi=60000):
     """48 independent bodies, element counts log-uniform in [lo, hi]; half
     boxes (aspect 1:1:1 .. 10:1:1), half cylinders; half SVK, half MR; +-2%
-    nodal perturbation; one face clamped per body."""
+    nodal perturbation of each node's own spacing; one face clamped per body."""
     rng = np.random.default_rng(seed)
     meshes, mats, qs, vs = [], [], [], []
     for b in range(nbodies):
@@ -322,7 +339,7 @@ def workload_batched(nbodies=48, seed=1000 + 3, lo=1000, hi=60000):
             nr = max(1, int(round((target / 48.0) ** (1.0 / 3.0))))
             nz = max(1, int(round(target / (24.0 * nr * nr))))
             m = cylinder_t10(nr, nz, 0.1 * nr, 0.1 * nz)
-        q = uniform_perturbation(m, 0.02, rng)
+        q = uniform_perturbation(m, 0.02, rng, local=True)
         v = gaussian_velocity(m, 0.01, rng)
         meshes.append(m)
         qs.append(q)

@@ -42,7 +42,7 @@ class tl_params(C.Structure):
     _fields_ = [("h", C.c_double), ("rho_alm", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
                 ("eps_out", C.c_double), ("gravity", C.c_double * 3), ("max_inner", C.c_int32),
                 ("max_outer", C.c_int32), ("linear_solver", C.c_int32), ("lin_max_iter", C.c_int32),
-                ("lin_rtol", C.c_double), ("lin_adaptive", C.c_int32), ("_pad3", C.c_int32)]
+                ("lin_rtol", C.c_double), ("lin_adaptive", C.c_int32), ("use_graph", C.c_int32)]
 
 
 class tl_newton_stats(C.Structure):
@@ -61,6 +61,12 @@ class tl_mesh_info(C.Structure):
     _fields_ = [("nn", C.c_int64), ("ne", C.c_int64), ("ndof", C.c_int64), ("nnz", C.c_int64),
                 ("nnz_node", C.c_int64), ("nfixed", C.c_int64), ("precision", C.c_int32),
                 ("nmat", C.c_int32)]
+
+
+class tl_tune_result(C.Structure):
+    _fields_ = [("spmv_group", C.c_int32), ("elem_xchg", C.c_int32), ("elem_full_grid", C.c_int32),
+                ("_pad", C.c_int32), ("ms_element", C.c_float * 4), ("ms_spmv", C.c_float * 3),
+                ("_pad2", C.c_float)]
 
 
 # every symbol declared in include/tl.h, with (restype, argtypes)
@@ -84,6 +90,9 @@ SIGNATURES = {
                               C.c_int32, _P]),
     "tl_mlp_features": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P]),
     "tl_warm_start": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
+    "tl_autotune": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, _P]),
+    "tl_tune_get": (C.c_int, [_P, _P]),
+    "tl_tune_set": (C.c_int, [_P, _P]),
     "tl_sync": (C.c_int, [_P]),
     "tl_mesh_info_get": (C.c_int, [_P, _P]),
     "tl_status_string": (C.c_char_p, [C.c_int]),
@@ -129,7 +138,7 @@ def material(kind="svk", E=0.0, nu=0.0, rho0=1000.0, C10=0.0, C01=0.0, kappa=0.0
 
 def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-4, gravity=(0.0, 0.0, -9.81),
            max_inner=20, max_outer=5, linear_solver=TL_SOLVER_DIRECT, lin_max_iter=0, lin_rtol=0.0,
-           lin_adaptive=0):
+           lin_adaptive=0, use_graph=0):
     p = tl_params()
     p.h, p.rho_alm, p.rtol, p.atol, p.eps_out = h, rho_alm, rtol, atol, eps_out
     for i in range(3):
@@ -137,10 +146,16 @@ def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-4, gravity=(0.0
     p.max_inner, p.max_outer = max_inner, max_outer
     p.linear_solver, p.lin_max_iter, p.lin_rtol = linear_solver, lin_max_iter, lin_rtol
     p.lin_adaptive = lin_adaptive
+    p.use_graph = use_graph
     return p
 
 
 MLP_NPARAM = 9219
+
+
+def _tune_dict(r):
+    return dict(spmv_group=r.spmv_group, elem_xchg=r.elem_xchg, elem_full_grid=r.elem_full_grid,
+                ms_element=list(r.ms_element), ms_spmv=list(r.ms_spmv))
 
 
 def _stream_ptr():
@@ -284,6 +299,22 @@ class Mesh:
                                                       _ptr(f_int), _ptr(f_ext), _ptr(lam), _ptr(g),
                                                       _ptr(g_norm)))
         return g, g_norm
+
+    def autotune(self, q_n, v, h, reps=5):
+        """tl_autotune: time the launch-shape variants on this mesh, keep the fastest."""
+        r = tl_tune_result()
+        self._check(self.lib.tl_autotune(self.h, _ptr(q_n), _ptr(v), float(h), int(reps), C.byref(r)))
+        return _tune_dict(r)
+
+    def tune_get(self):
+        r = tl_tune_result()
+        self._check(self.lib.tl_tune_get(self.h, C.byref(r)))
+        return _tune_dict(r)
+
+    def tune_set(self, spmv_group=8, elem_xchg=1, elem_full_grid=0):
+        r = tl_tune_result()
+        r.spmv_group, r.elem_xchg, r.elem_full_grid = spmv_group, elem_xchg, elem_full_grid
+        self._check(self.lib.tl_tune_set(self.h, C.byref(r)))
 
     def timing_enable(self, on=True):
         self._check(self.lib.tl_timing_enable(self.h, 1 if on else 0))

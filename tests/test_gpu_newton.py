@@ -34,7 +34,7 @@ def small_case():
     return w, om, prm, ref
 
 
-@pytest.mark.parametrize("solver", ["direct", "pcg"])
+@pytest.mark.parametrize("solver", ["direct", "pcg", "pcg_graph"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_newton_step_matches_oracle(small_case, prec, solver):
     tl = _tl()
@@ -45,7 +45,8 @@ def test_newton_step_matches_oracle(small_case, prec, solver):
     lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
     p = tl.params(h=prm.h, rho_alm=prm.rho_alm, rtol=prm.rtol, eps_out=prm.eps_out,
                   max_inner=prm.max_inner, max_outer=prm.max_outer,
-                  linear_solver=tl.TL_SOLVER_PCG if solver == "pcg" else tl.TL_SOLVER_DIRECT)
+                  linear_solver=tl.TL_SOLVER_DIRECT if solver == "direct" else tl.TL_SOLVER_PCG,
+                  use_graph=1 if solver == "pcg_graph" else 0)
     v, q, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
     v = v.cpu().numpy()
     assert st["converged"] == 1
@@ -92,3 +93,104 @@ def test_newton_warm_start_reaches_same_state(small_case):
     assert st1["converged"] == 1 and st1["inner_iters"] <= st0["inner_iters"]
     assert st1["g_ref"] == pytest.approx(st0["g_ref"], rel=1e-12)
     assert np.linalg.norm(v.cpu().numpy() - ref["v"]) <= 1e-8 * np.linalg.norm(ref["v"])
+
+
+def _run_pair(tl, g, w, prm_kw, nsteps=3, v_init_fn=None):
+    """The same steps through the host-driven loop and the captured graph."""
+    m = w["mesh"]
+    out = {}
+    for use_graph in (0, 1):
+        p = tl.params(linear_solver=tl.TL_SOLVER_PCG, use_graph=use_graph, **prm_kw)
+        q = _dev(w["q_n"])
+        v = _dev(w["v"])
+        lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+        fe = _dev(0.5 * np.random.default_rng(7).normal(size=m.X.shape))
+        hist = []
+        for k in range(nsteps):
+            vi = v_init_fn(v) if v_init_fn else None
+            v_new, q_new, st = g.newton_step(p, q, v, lam, v_init=vi, f_ext=fe)
+            hist.append(st)
+            q, v = q_new.clone(), v_new.clone()
+        out[use_graph] = (v.cpu().numpy(), q.cpu().numpy(), lam.cpu().numpy(), hist)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("adaptive", [0, 1])
+def test_newton_graph_equals_host_loop(prec, adaptive):
+    """The captured step runs the same kernels with the same arguments in the
+    same order, and makes the same tests on the device: the same Newton and
+    ALM iteration counts, PCG counts within one check interval per solve, and
+    the same converged velocities and multipliers over several steps (with a
+    start different from v_n and an external force).  The scatter uses
+    atomics, so two runs of either path agree to rounding, not bit for bit."""
+    tl = _tl()
+    if prec == "fp32":
+        # the 15,360-element MR + KV mesh at a mild state (0.25% sine-mode
+        # amplitude): at the full 5% state H is indefinite and a plain
+        # Newton step inverts elements
+        w = inputs.workload_mid_mr_kv()
+        X = w["mesh"].X
+        w = dict(w, q_n=X + 0.05 * (w["q_n"] - X), v=0.2 * w["v"])
+    else:
+        w = inputs.workload_small_svk()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64 if prec == "fp64" else tl.TL_FP32_ELEM)
+    g.build_pattern(m.fixed_nodes)
+    res = _run_pair(tl, g, w, dict(h=w["h"], rtol=1e-8, lin_adaptive=adaptive),
+                    v_init_fn=lambda v: 1.01 * v)
+    (v0, q0, l0, h0), (v1, q1, l1, h1) = res[0], res[1]
+    for a, b in zip(h0, h1):
+        for key in ("inner_iters", "outer_iters", "converged", "status"):
+            assert a[key] == b[key], (key, a, b)
+        assert abs(a["lin_iters"] - b["lin_iters"]) <= 8 * a["inner_iters"], (a, b)
+        assert b["g_ref"] == pytest.approx(a["g_ref"], rel=1e-9)
+        assert b["g_init"] == pytest.approx(a["g_init"], rel=1e-6)
+        assert b["g_norm"] <= 1e-8 * b["g_ref"] and b["converged"] == 1
+    assert np.linalg.norm(v1 - v0) <= 1e-8 * np.linalg.norm(v0)
+    assert np.linalg.norm(q1 - q0) <= 1e-12 * np.linalg.norm(q0)
+    assert np.abs(l1 - l0).max() <= 1e-6 * np.abs(l0).max()
+
+
+def test_newton_graph_caps_and_rebuild():
+    """Iteration caps end the captured loops with NOT_CONVERGED and the same
+    statistics as the host loop; a parameter change rebuilds the graph and a
+    repeat reuses it with identical results."""
+    tl = _tl()
+    w = inputs.workload_small_svk()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+    g.build_pattern(m.fixed_nodes)
+    stats = {}
+    for use_graph in (0, 1):
+        p = tl.params(h=w["h"], rtol=1e-14, max_inner=2, max_outer=2, linear_solver=tl.TL_SOLVER_PCG,
+                      lin_max_iter=16, use_graph=use_graph)
+        lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+        _, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam, raise_on_nonconvergence=False)
+        stats[use_graph] = st
+    assert stats[1]["status"] == stats[0]["status"] != 0
+    for key in ("inner_iters", "outer_iters", "converged", "lin_iters"):
+        assert stats[0][key] == stats[1][key], key
+    assert stats[1]["inner_iters"] == 4 and stats[1]["outer_iters"] == 2
+    assert stats[1]["lin_iters"] <= 4 * 16
+    runs = []
+    for rtol in (1e-8, 1e-6, 1e-8):
+        p = tl.params(h=w["h"], rtol=rtol, linear_solver=tl.TL_SOLVER_PCG, use_graph=1)
+        lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+        v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+        runs.append((v.cpu().numpy(), st))
+    assert np.linalg.norm(runs[2][0] - runs[0][0]) <= 1e-8 * np.linalg.norm(runs[0][0])
+    assert runs[2][1]["inner_iters"] == runs[0][1]["inner_iters"]
+    assert runs[1][1]["inner_iters"] <= runs[0][1]["inner_iters"]
+
+
+def test_newton_graph_needs_pcg():
+    tl = _tl()
+    w = inputs.workload_small_svk()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+    g.build_pattern(m.fixed_nodes)
+    p = tl.params(h=w["h"], linear_solver=tl.TL_SOLVER_DIRECT, use_graph=1)
+    lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+    with pytest.raises(tl.TLError):
+        g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)

@@ -36,9 +36,9 @@ def ragged_mixed():
 
 
 def shuffled_order():
-    """Elements in random order: most 32-element tiles then touch more nodes
-    than the FP32 kernel's shared image holds, exercising its per-entry
-    global-scatter fallback."""
+    """Elements in random order: the 32 elements of a tile share few nodes,
+    so their CSR runs land in unrelated rows at every alignment of the
+    vector reductions."""
     w = inputs.workload_small_svk()
     rng = np.random.default_rng(99)
     m = w["mesh"]

@@ -1,0 +1,84 @@
+"""The launch-shape autotuner: it times every compiled variant on the mesh and
+keeps the fastest, and every variant computes the same thing - the Hessian of
+each element-pass variant matches the oracle, and the Newton step converges
+to the same state with each PCG product shape."""
+import numpy as np
+import pytest
+
+from oracle import assembly as asm
+from paper_2604_10357_gb300 import inputs
+
+from helpers import TOL_FP32, values_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _tl():
+    from paper_2604_10357_gb300 import build, tl
+    build.build()
+    return tl
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(-1), device="cuda")
+
+
+def test_autotune_reports_and_keeps_a_choice():
+    tl = _tl()
+    w = inputs.workload_mid_mr_kv()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
+    g.build_pattern(m.fixed_nodes)
+    rep = g.autotune(_dev(w["q_n"]), _dev(w["v"]), w["h"], reps=3)
+    assert rep["spmv_group"] in (4, 8, 16)
+    assert rep["elem_xchg"] in (0, 1) and rep["elem_full_grid"] in (0, 1)
+    assert all(t > 0 for t in rep["ms_element"]) and all(t > 0 for t in rep["ms_spmv"])
+    k = 2 * (1 - rep["elem_xchg"]) + rep["elem_full_grid"]
+    assert rep["ms_element"][k] == min(rep["ms_element"])
+    assert rep["ms_spmv"][(4, 8, 16).index(rep["spmv_group"])] == min(rep["ms_spmv"])
+    cur = g.tune_get()
+    assert (cur["spmv_group"], cur["elem_xchg"], cur["elem_full_grid"]) == \
+        (rep["spmv_group"], rep["elem_xchg"], rep["elem_full_grid"])
+    with pytest.raises(tl.TLError):
+        g.tune_set(spmv_group=5)
+
+
+@pytest.mark.parametrize("xchg", [0, 1])
+@pytest.mark.parametrize("full_grid", [0, 1])
+def test_every_element_variant_matches_oracle(xchg, full_grid):
+    tl = _tl()
+    w = inputs.workload_small_svk()
+    m = w["mesh"]
+    om = asm.OracleMesh(m.X, m.conn, [w["material"]], fixed_nodes=m.fixed_nodes)
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
+    g.build_pattern(m.fixed_nodes)
+    g.tune_set(spmv_group=8, elem_xchg=xchg, elem_full_grid=full_grid)
+    h, rho = w["h"], 1e12
+    vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho).cpu().numpy().astype(np.float64)
+    ref = om.hessian_values(w["q_n"], w["v"], h, rho)
+    _, _, row_ptr, col = om.pattern()
+    pen = asm.csr_positions(row_ptr, col, om.fixed_dofs, om.fixed_dofs)
+    rest = np.ones(len(ref), bool)
+    rest[pen] = False
+    emax, e2 = values_error(vals[rest], ref[rest])
+    assert emax < TOL_FP32 and e2 < TOL_FP32
+
+
+@pytest.mark.parametrize("group", [4, 8, 16])
+def test_every_spmv_shape_converges_to_the_same_state(group):
+    tl = _tl()
+    w = inputs.workload_small_svk()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+    g.build_pattern(m.fixed_nodes)
+    p = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG)
+    out = {}
+    for gr in (8, group):
+        g.tune_set(spmv_group=gr)
+        lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+        v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+        assert st["converged"] == 1
+        out[gr] = v.cpu().numpy()
+    assert np.linalg.norm(out[group] - out[8]) <= 1e-9 * np.linalg.norm(out[8])
