@@ -325,6 +325,58 @@ def run_ours(args, rank, world):
     return line
 
 
+def run_newton(args):
+    """Newton step ms to the 1e-8 relative residual on the 103,680-element
+    cantilever (12 x 1.2 x 1.2 m, SVK, gravity + seeded tip loads), on the
+    held-out steps of the warm-start trajectory (steps 1101.. of the trajectory
+    from rest; the network was trained on steps 1..1099).  'plain' = the
+    paper's step: FP64 element form, start v_n, host-driven loop (||g|| read
+    back every iteration), PCG to 1e-10 (plus the vendor direct solver with
+    --newton-direct); 'chosen' = FP32 element form, learned warm start,
+    inexact-Newton PCG, the whole step as one captured CUDA graph.  Both from
+    the same stored states to the same target; the trajectory itself is
+    generated (untimed) with the plain step in its graph form."""
+    import torch
+
+    from paper_2604_10357_gb300 import inputs, tl, warmstart
+    w = inputs.workload_warm_start_svk()
+    m = w["mesh"]
+    g64 = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+    g64.build_pattern(m.fixed_nodes)
+    g32 = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
+    g32.build_pattern(m.fixed_nodes)
+    plain = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG)
+    gen = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, use_graph=1)
+    chosen = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, use_graph=1)
+    t0_step, n_eval = 1101, args.newton_steps
+    t_gen = time.time()
+    tr = warmstart.generate(g64, m.X, w["f_ext"], t0_step + n_eval + 1, gen, record_from=t0_step - 1)
+    t_gen = time.time() - t_gen
+    test_idx = list(range(1, n_eval + 1))          # trajectory-local indices (record_from offset)
+    model_path = os.path.join(ROOT, "paper_2604_10357_gb300", "data", "warmstart_box120x12x12.npz")
+    model = warmstart.WarmStartModel.from_npz(model_path) if os.path.exists(model_path) else None
+    c_mode = "mlp" if model is not None else "extrapolation"
+    # one untimed pass of each arm first (graph capture, first-use allocations)
+    warmstart.evaluate(g64, tr, test_idx[:1], plain, modes=["v_n"])
+    warmstart.evaluate(g32, tr, test_idx[:1], chosen, model, modes=[c_mode])
+    p_sum, _ = warmstart.evaluate(g64, tr, test_idx, plain, modes=["v_n"])
+    c_sum, _ = warmstart.evaluate(g32, tr, test_idx, chosen, model, modes=[c_mode])
+    out = {"workload": w["name"], "ndof": 3 * m.nn, "steps": [t0_step, t0_step + n_eval - 1],
+           "target": "||g|| <= 1e-8 ||g(v_n)||", "trajectory_generation_s": t_gen,
+           "plain": dict(p_sum["v_n"], desc="FP64 element form, start v_n, host loop, PCG 1e-10"),
+           "chosen": dict(c_sum[c_mode], desc=f"FP32 element form, start {c_mode}, inexact-Newton PCG, "
+                                                "captured graph"),
+           "speedup": p_sum["v_n"]["mean_ms"] / c_sum[c_mode]["mean_ms"],
+           "model": os.path.relpath(model_path, ROOT) if model is not None else None}
+    if args.newton_direct:
+        direct = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_DIRECT)
+        d_sum, _ = warmstart.evaluate(g64, tr, test_idx[:1], direct, modes=["v_n"])
+        out["plain_direct"] = dict(d_sum["v_n"], desc="FP64, start v_n, cuSOLVER sparse Cholesky (1 step)")
+    g64.close()
+    g32.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, on this arm's metric: each step a bounded
     sample (a 4x2x2-hex sub-box of the same workload, 96 elements)."""
@@ -367,6 +419,9 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--scale", type=float, default=1.0, help="hex-count scale of the box (1.0 = 960k T10)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-newton", action="store_true")
+    ap.add_argument("--newton-steps", type=int, default=10)
+    ap.add_argument("--newton-direct", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -389,6 +444,8 @@ def main():
             line["cpu_baseline"] = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
                                     "sample": f"{n}-element sub-box (10x4x4 hexes) of the same workload, "
                                               f"{reps} passes in {el:.1f} s (numpy, one thread)"}
+        if not args.no_newton and world == 1:
+            line["newton"] = run_newton(args)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch
