@@ -348,7 +348,7 @@ def run_newton(args):
     plain = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG)
     gen = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, use_graph=1)
     chosen = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, use_graph=1)
-    t0_step, n_eval = 1101, args.newton_steps
+    t0_step, n_eval = args.newton_start, args.newton_steps
     t_gen = time.time()
     tr = warmstart.generate(g64, m.X, w["f_ext"], t0_step + n_eval + 1, gen, record_from=t0_step - 1)
     t_gen = time.time() - t_gen
@@ -422,6 +422,9 @@ def main():
     ap.add_argument("--no-newton", action="store_true")
     ap.add_argument("--newton-steps", type=int, default=10)
     ap.add_argument("--newton-direct", action="store_true")
+    ap.add_argument("--newton-start", type=int, default=1101,
+                    help="first evaluated step of the cantilever trajectory (1101: the held-out window)")
+    ap.add_argument("--newton-only", action="store_true", help="run only the Newton comparison and print it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -432,6 +435,10 @@ def main():
         line = run_reference(args, rank, world)
         if line is not None:
             print(json.dumps(line), flush=True)
+        return
+    if args.newton_only:
+        if rank == 0:
+            print(json.dumps(run_newton(args)), flush=True)
         return
     if world > 1:
         import torch

@@ -62,7 +62,7 @@ void free_mesh(tl_mesh* m) {
   cudaSetDevice(m->device);
   void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_geo32, m->d_X, m->d_node_ptr, m->d_node_col,
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
-                  m->d_flags, m->d_partials, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_values};
+                  m->d_flags, m->d_tile_counters, m->d_partials, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_values};
   solver_destroy(m->solver);
   pcg_destroy(m->pcg);
   newton_graph_destroy(m->ngraph);
@@ -269,6 +269,7 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
   TRYC(cudaMalloc(&m->d_geo32, sizeof(float) * 16 * ne_pad));
   TRYC(cudaMalloc(&m->d_X, sizeof(double) * 3 * nn));
   TRYC(cudaMalloc(&m->d_flags, sizeof(uint32_t) * 4));
+  TRYC(cudaMalloc(&m->d_tile_counters, sizeof(int) * kTileCounters));
   TRYC(cudaMemcpy(m->d_conn, h_conn.data(), sizeof(int32_t) * 10 * ne_pad, cudaMemcpyHostToDevice));
   TRYC(cudaMemcpy(m->d_user_of, h_user.data(), sizeof(int32_t) * ne_pad, cudaMemcpyHostToDevice));
   TRYC(cudaMemcpy(m->d_geo64, h_geo64.data(), sizeof(double) * 16 * ne_pad, cudaMemcpyHostToDevice));

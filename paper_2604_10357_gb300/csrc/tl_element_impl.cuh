@@ -483,17 +483,21 @@ struct SegTable {
   int32_t ntiles;
 };
 
-// Persistent element kernel: CTA b takes tiles b, b + gridDim.x, ... over all
-// segments; COMBO < 4 compiles one (material, Kelvin-Voigt) pair, COMBO = 4
-// all four with a block-uniform dispatch per tile (multi-material meshes and
-// batches of bodies).
+// Persistent element kernel: CTA b starts with tile b and then takes the next
+// unprocessed tile from a device counter (zeroed before the launch), so SMs
+// that run faster take more tiles; with counter == nullptr it takes tiles
+// b + gridDim.x, b + 2 gridDim.x, ...  Tiles ascend in every CTA, so the
+// segment of a tile is found by walking the table forward.  COMBO < 4
+// compiles one (material, Kelvin-Voigt) pair, COMBO = 4 all four with a
+// block-uniform dispatch per tile (multi-material meshes and batches).
 template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT>
-__global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S) {
+__global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_next;
   int sg = 0, t_begin = 0;
-  for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
-    if (t != (int)blockIdx.x) __syncthreads();     // the previous tile's shared data is consumed
-    while (t >= S.s[sg].tile_end) {                // tiles ascend: sg only grows, and t < ntiles
+  int t = blockIdx.x;
+  while (t < S.ntiles) {
+    while (t >= S.s[sg].tile_end) {                // t < ntiles = tile_end of the last segment
       t_begin = S.s[sg].tile_end;
       ++sg;
     }
@@ -511,6 +515,10 @@ __global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S) {
         default: elem_tile<T, TL_MOONEY_RIVLIN, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
       }
     }
+    __syncthreads();                               // this tile's shared data is consumed
+    if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t + (int)gridDim.x;
+    __syncthreads();
+    t = s_next;
   }
 }
 
@@ -552,6 +560,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   // the same (material, Kelvin-Voigt) pair.
   constexpr bool kMixed = std::is_same<T, float>::value;
   size_t k = 0;
+  int nlaunch = 0;
   while (k < m->segs.size()) {
     SegTable<T> S;
     S.nseg = 0;
@@ -576,7 +585,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       mixed = mixed || combo != combo0;
     }
     if (S.ntiles == 0) continue;
-    void (*kern)(Args<T>, SegTable<T>) = nullptr;
+    void (*kern)(Args<T>, SegTable<T>, int*) = nullptr;
     switch (mixed ? 4 : combo0) {
       case 0: kern = elem_kernel<T, 0, DO_FORCE, DO_TANGENT>; break;
       case 1: kern = elem_kernel<T, 1, DO_FORCE, DO_TANGENT>; break;
@@ -590,9 +599,15 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 1;
     TL_CUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
-    const int grid = m->tune.elem_full_grid ? S.ntiles
-                                            : (int)std::min<int64_t>(S.ntiles, (int64_t)m->num_sms * std::max(occ, 1));
-    kern<<<(unsigned)grid, NT, smem, m->stream>>>(A, S);
+    const bool full = m->tune.elem_full_grid != 0;
+    const int grid = full ? S.ntiles : (int)std::min<int64_t>(S.ntiles, (int64_t)m->num_sms * std::max(occ, 1));
+    int* counter = nullptr;
+    if (!full && nlaunch < kTileCounters) {
+      counter = m->d_tile_counters + nlaunch;
+      TL_CUDA(m, cudaMemsetAsync(counter, 0, sizeof(int), m->stream));
+    }
+    ++nlaunch;
+    kern<<<(unsigned)grid, NT, smem, m->stream>>>(A, S, counter);
     TL_CUDA(m, cudaGetLastError());
     ++m->launches;
   }

@@ -17,6 +17,9 @@ namespace tl {
 // segment of the internal element order is padded to a multiple of this.
 constexpr int kTile = 32;
 
+// Tile counters of the persistent element launches (one per launch of a pass).
+constexpr int kTileCounters = 256;
+
 // Device-side sticky status bits (tl_sync turns them into tl_status).
 enum : uint32_t { kFlagInverted = 1u, kFlagNonFinite = 2u, kFlagBadIndex = 4u };
 
@@ -84,6 +87,7 @@ struct tl_mesh {
 
   // scratch
   uint32_t* d_flags = nullptr;    // sticky device status
+  int* d_tile_counters = nullptr; // kTileCounters dynamic tile queues
   double* d_partials = nullptr;   // reduction partials
   int partials_cap = 0;
 

@@ -16,6 +16,7 @@
 // reads the residual norm every kCheck iterations, or the check runs on the
 // device inside the captured Newton graph.
 #include <cmath>
+#include <type_traits>
 
 #include "tl_internal.cuh"
 
@@ -24,6 +25,7 @@ namespace tl {
 struct PcgWork {
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *binv = nullptr, *part = nullptr,
          *scal = nullptr;
+  float* p32 = nullptr;        // float32 copy of p (float32 element form)
   int32_t* diag_k = nullptr;   // per node: position of I in its own adjacency
   int nparts = 0;
 };
@@ -95,25 +97,39 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // the neighbours j = l, l+G, ..., reads node_col once, p[3J..3J+2] once and
 // the three 3-entry runs (row 3I+d starts at 9 ptr(I) + 3 deg(I) d), and the
 // group reduces the three sums.  Partial dot products p . Ap per block.
+// With float32 values (the float32 element form) the products and the lane
+// sums are float32 on a float32 copy of p (GB300 runs float64 arithmetic at
+// 1/64 of the float32 rate; a float32 H defines the product to ~1e-7 anyway),
+// and only the three node sums are widened: Ap and p.Ap stay float64.
+template <typename T> struct SpmvAcc { using type = double; };
+template <> struct SpmvAcc<float> { using type = float; };
+
 template <typename T, int G>
 __global__ void spmv_node(const T* __restrict__ vals, const int32_t* __restrict__ node_ptr,
                           const int32_t* __restrict__ node_col, int64_t nn, const double* __restrict__ p,
-                          double* __restrict__ Ap, double* part) {
+                          const float* __restrict__ p32, double* __restrict__ Ap, double* part) {
+  using A = typename SpmvAcc<T>::type;
   __shared__ double red[kBlock / 32];
   const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   const int l = threadIdx.x & (G - 1);
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, dot = 0.0;
+  A s0 = 0, s1 = 0, s2 = 0;
+  double dot = 0.0;
   if (I < nn) {
     const int p0 = node_ptr[I], deg = node_ptr[I + 1] - p0;
     const T* v0 = vals + 9 * (int64_t)p0;
     const T* v1 = v0 + 3 * deg;
     const T* v2 = v1 + 3 * deg;
     for (int j = l; j < deg; j += G) {
-      const int64_t J = node_col[p0 + j];
-      const double x0 = p[3 * J], x1 = p[3 * J + 1], x2 = p[3 * J + 2];
-      s0 += double(v0[3 * j]) * x0 + double(v0[3 * j + 1]) * x1 + double(v0[3 * j + 2]) * x2;
-      s1 += double(v1[3 * j]) * x0 + double(v1[3 * j + 1]) * x1 + double(v1[3 * j + 2]) * x2;
-      s2 += double(v2[3 * j]) * x0 + double(v2[3 * j + 1]) * x1 + double(v2[3 * j + 2]) * x2;
+      const int J = node_col[p0 + j];
+      A x0, x1, x2;
+      if constexpr (std::is_same<A, float>::value) {
+        x0 = p32[3 * J]; x1 = p32[3 * J + 1]; x2 = p32[3 * J + 2];
+      } else {
+        x0 = p[3 * (int64_t)J]; x1 = p[3 * (int64_t)J + 1]; x2 = p[3 * (int64_t)J + 2];
+      }
+      s0 += A(v0[3 * j]) * x0 + A(v0[3 * j + 1]) * x1 + A(v0[3 * j + 2]) * x2;
+      s1 += A(v1[3 * j]) * x0 + A(v1[3 * j + 1]) * x1 + A(v1[3 * j + 2]) * x2;
+      s2 += A(v2[3 * j]) * x0 + A(v2[3 * j + 1]) * x1 + A(v2[3 * j + 2]) * x2;
     }
   }
 #pragma unroll
@@ -123,10 +139,11 @@ __global__ void spmv_node(const T* __restrict__ vals, const int32_t* __restrict_
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
   if (I < nn && l == 0) {
-    Ap[3 * I] = s0;
-    Ap[3 * I + 1] = s1;
-    Ap[3 * I + 2] = s2;
-    dot = s0 * p[3 * I] + s1 * p[3 * I + 1] + s2 * p[3 * I + 2];
+    const double d0 = s0, d1 = s1, d2 = s2;
+    Ap[3 * I] = d0;
+    Ap[3 * I + 1] = d1;
+    Ap[3 * I + 2] = d2;
+    dot = d0 * p[3 * I] + d1 * p[3 * I + 1] + d2 * p[3 * I + 2];
   }
   const double t = block_sum(dot, red);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -179,17 +196,21 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
 }
 
 // p = z + beta p with beta = rz_new / rz, then rz <- rz_new
-__global__ void update_p(double* p, const double* z, int64_t n, double* scal) {
+__global__ void update_p(double* p, float* p32, const double* z, int64_t n, double* scal) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double beta = scal[0] != 0.0 ? scal[2] / scal[0] : 0.0;
-  if (i < n) p[i] = z[i] + beta * p[i];
+  if (i < n) {
+    const double v = z[i] + beta * p[i];
+    p[i] = v;
+    if (p32) p32[i] = float(v);
+  }
 }
 
 __global__ void roll_rz(double* scal) { scal[0] = scal[2]; }
 
 // start: x = 0, r = b = -g, z = P r, p = z; partials of r.z and r.r
-__global__ void pcg_start(const double* g, double* x, double* r, double* z, double* p, const double* binv,
-                          int64_t nn, double* part_rz, double* part_rr, double* scal) {
+__global__ void pcg_start(const double* g, double* x, double* r, double* z, double* p, float* p32,
+                          const double* binv, int64_t nn, double* part_rz, double* part_rr, double* scal) {
   __shared__ double red[kBlock / 32];
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I == 0) scal[6] = 0.0;
@@ -206,6 +227,7 @@ __global__ void pcg_start(const double* g, double* x, double* r, double* z, doub
       const double zd = B[3 * d] * rv[0] + B[3 * d + 1] * rv[1] + B[3 * d + 2] * rv[2];
       z[3 * I + d] = zd;
       p[3 * I + d] = zd;
+      if (p32) p32[3 * I + d] = float(zd);
       rz += rv[d] * zd;
       rr += rv[d] * rv[d];
     }
@@ -223,7 +245,7 @@ __global__ void pcg_start(const double* g, double* x, double* r, double* z, doub
 
 void pcg_destroy(PcgWork* w) {
   if (!w) return;
-  void* ptrs[] = {w->r, w->z, w->p, w->Ap, w->binv, w->part, w->scal, w->diag_k};
+  void* ptrs[] = {w->r, w->z, w->p, w->Ap, w->binv, w->part, w->scal, w->diag_k, w->p32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete w;
@@ -244,6 +266,11 @@ tl_status pcg_ensure(tl_mesh* m) {
   TL_CUDA(m, cudaMalloc(&w->part, sizeof(double) * 2 * w->nparts));
   TL_CUDA(m, cudaMalloc(&w->scal, sizeof(double) * 8));
   TL_CUDA(m, cudaMalloc(&w->diag_k, sizeof(int32_t) * nn));
+  TL_CUDA(m, cudaMemsetAsync(w->p, 0, sizeof(double) * n, m->stream));
+  if (m->precision == TL_FP32_ELEM) {
+    TL_CUDA(m, cudaMalloc(&w->p32, sizeof(float) * n));
+    TL_CUDA(m, cudaMemsetAsync(w->p32, 0, sizeof(float) * n, m->stream));
+  }
   node_diag_pos<<<(unsigned)((nn + 255) / 256), 256, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, nn, w->diag_k);
   TL_CUDA(m, cudaGetLastError());
   ++m->launches;
@@ -266,7 +293,8 @@ tl_status pcg_prepare(tl_mesh* m, const void* values, const double* g, double* d
     block_jacobi<double><<<nbn, kBlock, 0, s>>>((const double*)values, m->d_node_ptr, w->diag_k, nn, w->binv);
   double* part_rz = w->part;
   double* part_rr = w->part + w->nparts;
-  pcg_start<<<nbn, kBlock, 0, s>>>(g, dv, w->r, w->z, w->p, w->binv, nn, part_rz, part_rr, w->scal);
+  float* p32 = m->precision == TL_FP32_ELEM ? w->p32 : nullptr;
+  pcg_start<<<nbn, kBlock, 0, s>>>(g, dv, w->r, w->z, w->p, p32, w->binv, nn, part_rz, part_rr, w->scal);
   finish_sum<<<1, 1024, 0, s>>>(part_rz, nbn, w->scal, 0);
   finish_sum<<<1, 1024, 0, s>>>(part_rr, nbn, w->scal, 3);
   TL_CUDA(m, cudaGetLastError());
@@ -278,8 +306,8 @@ template <typename T, int G>
 void launch_spmv(tl_mesh* m, const void* values, PcgWork* w, unsigned* nblocks) {
   const int64_t nn = m->nn;
   const unsigned nb = (unsigned)((G * nn + kBlock - 1) / kBlock);
-  spmv_node<T, G><<<nb, kBlock, 0, m->stream>>>((const T*)values, m->d_node_ptr, m->d_node_col, nn, w->p, w->Ap,
-                                                w->part);
+  spmv_node<T, G><<<nb, kBlock, 0, m->stream>>>((const T*)values, m->d_node_ptr, m->d_node_col, nn, w->p, w->p32,
+                                                w->Ap, w->part);
   *nblocks = nb;
 }
 
@@ -322,7 +350,7 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
     update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr);
     finish_sum<<<1, 1024, 0, s>>>(part_rz, nbn, w->scal, 2);
     finish_sum<<<1, 1024, 0, s>>>(part_rr, nbn, w->scal, 3);
-    update_p<<<nbv, kBlock, 0, s>>>(w->p, w->z, n, w->scal);
+    update_p<<<nbv, kBlock, 0, s>>>(w->p, fp32 ? w->p32 : nullptr, w->z, n, w->scal);
     roll_rz<<<1, 1, 0, s>>>(w->scal);
     m->launches += 7;
   }

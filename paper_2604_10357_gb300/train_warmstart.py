@@ -2,6 +2,7 @@
 
     python -m paper_2604_10357_gb300.train_warmstart [--steps 1300] [--holdout 200]
         [--iters 4000] [--out PATH] [--report PATH]
+    python -m paper_2604_10357_gb300.train_warmstart --collapse-log PATH [--steps 1400]
 
 Box 12 x 1.2 x 1.2 m (120 x 12 x 12 hexes x 6 T10, SVK E = 1e7, nu = 0.3,
 rho = 1000), clamped at x = 0, gravity plus a seeded tip load U(0, 500) N in a
@@ -16,6 +17,10 @@ freely about the clamp, the root is compressed until the SVK energy loses
 convexity (min corner J 0.58 at step 1350), elements invert from step ~1358
 on and Newton stops converging at step ~1370.  The default trajectory is
 therefore 1,300 steps (min J about 0.67 at its end), not 2,000.
+--collapse-log runs the trajectory only (no training) and writes one JSON line
+per step: Newton / PCG iterations, convergence, ||g(v_n)||, mean tip
+deflection and the smallest deformed / reference volume ratio of the corner
+tetrahedra (torch reductions on the device, diagnostics only).
 """
 from __future__ import annotations
 
@@ -32,6 +37,40 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_MODEL = os.path.join(HERE, "data", "warmstart_box120x12x12.npz")
 
 
+def collapse_log(nsteps, path):
+    import torch
+    build.build()
+    w = inputs.workload_warm_start_svk()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+    g.build_pattern(m.fixed_nodes)
+    prm = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, use_graph=1)
+    X = torch.as_tensor(m.X, device="cuda")
+    corners = torch.as_tensor(m.conn[:, :4].astype(np.int64), device="cuda")
+
+    def signed_vol(P):
+        return torch.linalg.det(torch.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], 1))
+
+    V0 = signed_vol(X[corners])
+    tip = torch.as_tensor(np.nonzero(np.isclose(m.X[:, 0], m.X[:, 0].max()))[0], device="cuda")
+    q = X.reshape(-1).clone()
+    v = torch.zeros_like(q)
+    lam = torch.zeros(3 * g.nfixed, dtype=torch.float64, device="cuda")
+    with open(path, "w") as out:
+        for step in range(nsteps):
+            fe = torch.as_tensor(w["f_ext"](step), dtype=torch.float64, device="cuda")
+            v_new, q_new, st = g.newton_step(prm, q, v, lam, f_ext=fe, raise_on_nonconvergence=False)
+            qn = q_new.view(-1, 3)
+            row = dict(step=step, newton=st["inner_iters"], outer=st["outer_iters"], converged=st["converged"],
+                       g_ref=st["g_ref"], pcg=st["lin_iters"],
+                       tip=(qn[tip] - X[tip]).mean(0).tolist(),
+                       min_volume_ratio=(signed_vol(qn[corners]) / V0).min().item())
+            out.write(json.dumps(row) + "\n")
+            if step % 100 == 0:
+                print(row, flush=True)
+            q, v = q_new.clone(), v_new.clone()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=1300)
@@ -41,7 +80,11 @@ def main():
     ap.add_argument("--out", default=DEFAULT_MODEL)
     ap.add_argument("--report", default=None)
     ap.add_argument("--eval-steps", type=int, default=100)
+    ap.add_argument("--collapse-log", default=None)
     args = ap.parse_args()
+    if args.collapse_log:
+        collapse_log(args.steps, args.collapse_log)
+        return
     import torch
     build.build()
     w = inputs.workload_warm_start_svk()
@@ -61,6 +104,7 @@ def main():
     t0 = time.time()
     model, hist = warmstart.train(g64, tr, m.X, m.fixed_nodes, train_idx, iters=args.iters, lr=args.lr,
                                   log_every=500)
+    print(f"validation loss {model.val_loss:.4e}, output shrinkage alpha {model.alpha:.3f}", flush=True)
     t_train = time.time() - t0
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     model.to_npz(args.out)
@@ -77,6 +121,7 @@ def main():
                   train_steps=[int(train_idx[0]), int(train_idx[-1])],
                   test_steps=[int(test_idx[0]), int(test_idx[-1])],
                   generation_s=t_gen, training_s=t_train, loss_history=hist,
+                  val_loss=model.val_loss, alpha=model.alpha,
                   plain_fp64_vn_pcg=plain["v_n"], fp64_adaptive=fp64_starts, fp32_adaptive=fp32_starts,
                   fp32_adaptive_graph=fp32_graph,
                   speedup_chosen_vs_plain=plain["v_n"]["mean_ms"] / fp32_graph["mlp"]["mean_ms"])

@@ -65,17 +65,21 @@ class WarmStartModel:
     s_v: float
     s_d: float
     s_u: float
-    s_out: float
+    s_out: float            # output scale (shrinkage included)
+    alpha: float = 1.0      # shrinkage factor chosen on the validation steps
+    val_loss: float = float("nan")
 
     def to_npz(self, path):
-        np.savez(path, params=self.params.cpu().numpy(), s_v=self.s_v, s_d=self.s_d, s_u=self.s_u, s_out=self.s_out)
+        np.savez(path, params=self.params.cpu().numpy(), s_v=self.s_v, s_d=self.s_d, s_u=self.s_u, s_out=self.s_out,
+                 alpha=self.alpha, val_loss=self.val_loss)
 
     @classmethod
     def from_npz(cls, path):
         import torch
         d = np.load(path)
         return cls(torch.as_tensor(d["params"], device="cuda"), float(d["s_v"]), float(d["s_d"]), float(d["s_u"]),
-                   float(d["s_out"]))
+                   float(d["s_out"]), float(d["alpha"]) if "alpha" in d else 1.0,
+                   float(d["val_loss"]) if "val_loss" in d else float("nan"))
 
 
 def _scales(g, tr, idx, X):
@@ -102,14 +106,25 @@ def _glorot_init(rng):
     return np.concatenate(out)
 
 
-def train(g, tr, X, fixed_nodes, train_idx, iters=2000, lr=2e-3, seed=0, log_every=0):
+def train(g, tr, X, fixed_nodes, train_idx, iters=2000, lr=2e-3, seed=0, log_every=0, val_frac=0.1,
+          eval_every=100):
     """Fit the MLP to predict (v_{t+1} - 2 v_t + v_{t-1}) / s_out (the error of
     linear extrapolation) from the features at step t (mean squared error over
-    free nodes).  Each iteration uses every
-    node of one randomly drawn training step; Adam on a float32 master copy."""
+    free nodes).  Each iteration uses every node of one randomly drawn
+    training step; Adam on a float32 master copy.
+
+    Model selection on the last `val_frac` of the training steps (never
+    trained on): the parameters with the lowest validation loss are kept, and
+    the output scale is shrunk by the least-squares factor alpha in [0, 1] of
+    the network output against the validation targets, so a network that does
+    not generalise falls back towards plain extrapolation (alpha = 0)."""
     import torch
     rng = np.random.default_rng(seed)
-    s_v, s_d, s_u, s_out = _scales(g, tr, train_idx, X)
+    train_idx = np.asarray(train_idx)
+    train_idx = train_idx[train_idx > 0]
+    n_val = max(1, int(round(val_frac * len(train_idx))))
+    fit_idx, val_idx = train_idx[:-n_val], train_idx[-n_val:]
+    s_v, s_d, s_u, s_out = _scales(g, tr, fit_idx, X)
     nn = g.nn
     master = torch.as_tensor(_glorot_init(rng), device="cuda")
     P = torch.empty(NPARAM, dtype=torch.int16, device="cuda")
@@ -125,22 +140,54 @@ def train(g, tr, X, fixed_nodes, train_idx, iters=2000, lr=2e-3, seed=0, log_eve
     out = torch.empty(nn, 3, dtype=torch.float32, device="cuda")
     dout = torch.empty_like(out)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def target_of(t):
+        return ((tr.v[t + 1] - 2.0 * tr.v[t] + tr.v[t - 1]) / s_out).to(torch.float32).view(nn, 3)
+
+    val_pick = val_idx[np.linspace(0, len(val_idx) - 1, min(10, len(val_idx))).astype(int)]
+
+    def val_loss():
+        tot = 0.0
+        for t in val_pick:
+            g.mlp_features(tr.q[t], tr.v[t], tr.v[t - 1], s_v, s_d, s_u, feats)
+            tl.mlp_forward(P, feats, out=out)
+            loss.zero_()
+            tl.mlp_mse_grad(out, target_of(t), weight, dout, loss)
+            tot += loss.item()
+        return tot / len(val_pick)
+
     history = []
+    best = (val_loss(), P.clone())
+    history.append((0, float("nan"), best[0]))
     for it in range(iters):
-        t = int(rng.choice(train_idx[train_idx > 0]))
-        v_prev = tr.v[t - 1]
-        g.mlp_features(tr.q[t], tr.v[t], v_prev, s_v, s_d, s_u, feats)
-        target = ((tr.v[t + 1] - 2.0 * tr.v[t] + v_prev) / s_out).to(torch.float32).view(nn, 3)
+        t = int(rng.choice(fit_idx))
+        g.mlp_features(tr.q[t], tr.v[t], tr.v[t - 1], s_v, s_d, s_u, feats)
         tl.mlp_forward(P, feats, out=out, acts=acts)
         loss.zero_()
-        tl.mlp_mse_grad(out, target, weight, dout, loss)
+        tl.mlp_mse_grad(out, target_of(t), weight, dout, loss)
         grads.zero_()
         tl.mlp_backward(P, feats, acts, dout, grads)
         tl.mlp_adam(master, P, grads, m1, m2, lr=lr * (0.1 ** (it / max(1, iters))), step=it + 1)
-        if log_every and (it % log_every == 0 or it == iters - 1):
-            history.append((it, loss.item()))
-            print(f"  iter {it}: loss {history[-1][1]:.4e}", flush=True)
-    return WarmStartModel(P, s_v, s_d, s_u, s_out), history
+        if (it + 1) % eval_every == 0 or it == iters - 1:
+            vl = val_loss()
+            history.append((it + 1, loss.item(), vl))
+            if vl < best[0]:
+                best = (vl, P.clone())
+            if log_every and ((it + 1) % log_every == 0 or it == iters - 1):
+                print(f"  iter {it + 1}: train loss {loss.item():.4e}, validation loss {vl:.4e}", flush=True)
+    P.copy_(best[1])
+    # output shrinkage fitted on the validation steps
+    num = den = 0.0
+    for t in val_pick:
+        g.mlp_features(tr.q[t], tr.v[t], tr.v[t - 1], s_v, s_d, s_u, feats)
+        tl.mlp_forward(P, feats, out=out)
+        wt = weight.view(nn, 1).double()
+        num += (wt * out.double() * target_of(t).double()).sum().item()
+        den += (wt * out.double() * out.double()).sum().item()
+    alpha = float(min(1.0, max(0.0, num / den))) if den > 0 else 0.0
+    model = WarmStartModel(P, s_v, s_d, s_u, alpha * s_out)
+    model.alpha, model.val_loss = alpha, best[0]
+    return model, history
 
 
 def evaluate(g, tr, test_idx, prm, model=None, modes=None):
