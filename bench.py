@@ -347,7 +347,8 @@ def run_newton(args):
     g32.build_pattern(m.fixed_nodes)
     plain = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG)
     gen = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, use_graph=1)
-    chosen = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, use_graph=1)
+    chosen = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1,
+                       use_graph=0 if args.newton_no_graph else 1)
     t0_step, n_eval = args.newton_start, args.newton_steps
     t_gen = time.time()
     tr = warmstart.generate(g64, m.X, w["f_ext"], t0_step + n_eval + 1, gen, record_from=t0_step - 1)
@@ -365,7 +366,7 @@ def run_newton(args):
            "target": "||g|| <= 1e-8 ||g(v_n)||", "trajectory_generation_s": t_gen,
            "plain": dict(p_sum["v_n"], desc="FP64 element form, start v_n, host loop, PCG 1e-10"),
            "chosen": dict(c_sum[c_mode], desc=f"FP32 element form, start {c_mode}, inexact-Newton PCG, "
-                                                "captured graph"),
+                                                + ("host loop" if args.newton_no_graph else "captured graph")),
            "speedup": p_sum["v_n"]["mean_ms"] / c_sum[c_mode]["mean_ms"],
            "model": os.path.relpath(model_path, ROOT) if model is not None else None}
     if args.newton_direct:
@@ -425,6 +426,9 @@ def main():
     ap.add_argument("--newton-start", type=int, default=1101,
                     help="first evaluated step of the cantilever trajectory (1101: the held-out window)")
     ap.add_argument("--newton-only", action="store_true", help="run only the Newton comparison and print it")
+    ap.add_argument("--newton-no-graph", action="store_true",
+                    help="chosen arm from the host loop (same kernels; for launch lists, which do not see "
+                         "kernels inside conditional graph nodes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

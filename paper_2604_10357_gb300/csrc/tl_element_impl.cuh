@@ -145,11 +145,32 @@ __device__ __forceinline__ void shape_grads(const Smem<T>& sm, int e, const doub
   }
 }
 
-// qp phase: warp w -> (q = w / 3, row i = w % 3), lane = element.
+// Row i of the force and of the scaled tangent at one quadrature point.
 template <typename T, int MAT, bool KV, bool WANT_A, int i>
+__device__ __forceinline__ void qp_rows(const Args<T>& A, Smem<T>& sm, const QP<T>& s, const T (&n)[10][3],
+                                        T wJ, int e, int q) {
+  // force row i: f_a,i = wJ sum_J P_iJ n_aJ with P = F S
+  T Pi[3];
+#pragma unroll
+  for (int J = 0; J < 3; ++J) {
+    T acc = 0;
+#pragma unroll
+    for (int M = 0; M < 3; ++M) acc += s.F[i][M] * s.S[M][J];
+    Pi[J] = acc * wJ;
+  }
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+    sm.fq[e * kFStride + q * 30 + a * 3 + i] = Pi[0] * n[a][0] + Pi[1] * n[a][1] + Pi[2] * n[a][2];
+  if (WANT_A) tangent_row<T, MAT, KV, i>(s, A.mat, A.alpha, A.beta, wJ, &sm.A[e * kAStride + q * 81 + i * 27]);
+}
+
+// qp phase: warp w -> (q = w / 3, row i = w % 3), lane = element.  The
+// kinematics and the constitutive update are shared by the three rows (one
+// copy of their code); only the row-specific part is compiled per row.
+template <typename T, int MAT, bool KV, bool WANT_A>
 __device__ __forceinline__ void qp_phase(const Args<T>& A, Smem<T>& sm, bool& inverted) {
   const int w = threadIdx.x >> 5, e = threadIdx.x & 31;
-  const int q = w / 3;
+  const int q = w / 3, i = w % 3;
   double Lq[4];
   qp_bary(q, Lq);
   const T wJ = T(qp_wfrac(q)) * sm.geo[12][e];
@@ -184,19 +205,11 @@ __device__ __forceinline__ void qp_phase(const Args<T>& A, Smem<T>& sm, bool& in
     }
   QP<T> s;
   constitutive<T, MAT, KV>(Hm, Fd, A.mat, s, inverted);
-  // force row i: f_a,i = wJ sum_J P_iJ n_aJ with P = F S
-  T Pi[3];
-#pragma unroll
-  for (int J = 0; J < 3; ++J) {
-    T acc = 0;
-#pragma unroll
-    for (int M = 0; M < 3; ++M) acc += s.F[i][M] * s.S[M][J];
-    Pi[J] = acc * wJ;
+  switch (i) {     // warp-uniform
+    case 0: qp_rows<T, MAT, KV, WANT_A, 0>(A, sm, s, n, wJ, e, q); break;
+    case 1: qp_rows<T, MAT, KV, WANT_A, 1>(A, sm, s, n, wJ, e, q); break;
+    default: qp_rows<T, MAT, KV, WANT_A, 2>(A, sm, s, n, wJ, e, q); break;
   }
-#pragma unroll
-  for (int a = 0; a < 10; ++a)
-    sm.fq[e * kFStride + q * 30 + a * 3 + i] = Pi[0] * n[a][0] + Pi[1] * n[a][1] + Pi[2] * n[a][2];
-  if (WANT_A) tangent_row<T, MAT, KV, i>(s, A.mat, A.alpha, A.beta, wJ, &sm.A[e * kAStride + q * 81 + i * 27]);
 }
 
 // Force phase: warp w handles element DOFs c = w and c = w + 15.
@@ -319,28 +332,26 @@ __device__ __forceinline__ void red_v2(float* p, float x, float y) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
 }
 
-// Add the run values[s .. s+2] += (x0, x1, x2) with one 16-byte reduction when
-// the run starts at offset 0 or 1 of an aligned 4-float chunk (the other lane
-// adds 0 to the neighbouring entry), else an 8-byte and a 4-byte one.
+// Add the run values[s .. s+2] += (x0, x1, x2).  The run is placed in the
+// 16-byte chunk that contains s (zeros in the other lanes) and issued as one
+// 16-byte reduction, plus an 8-byte one for the part that spills into the
+// next chunk when s is at offset 2 or 3: the instruction sequence does not
+// depend on the offset (no divergence), and a lane adds 0 to neighbouring
+// entries, which leaves them unchanged.  The last entries of the matrix use
+// scalar reductions so no access passes the end of values.
 __device__ __forceinline__ void red_run(const Args<float>& A, int s, float x0, float x1, float x2) {
   float* p = A.values;
-  if (A.v4_ok) {
-    const int r = s & 3;
-    if (r == 1) {
-      red_v4(p + s - 1, 0.0f, x0, x1, x2);
-      return;
-    }
-    if (r == 0 && s + 4 <= A.nnz) {
-      red_v4(p + s, x0, x1, x2, 0.0f);
-      return;
-    }
-    if (r == 0 || r == 2) {
-      red_v2(p + s, x0, x1);
-      atomicAdd(p + s + 2, x2);
-      return;
-    }
-    atomicAdd(p + s, x0);          // r == 3: s + 1 is 16-byte aligned
-    red_v2(p + s + 1, x1, x2);
+  const int r = s & 3;
+  const int base = s - r;
+  if (A.v4_ok && base + 8 <= A.nnz) {
+    const float w0 = r == 0 ? x0 : 0.0f;
+    const float w1 = r == 0 ? x1 : (r == 1 ? x0 : 0.0f);
+    const float w2 = r == 0 ? x2 : (r == 1 ? x1 : (r == 2 ? x0 : 0.0f));
+    const float w3 = r == 1 ? x2 : (r == 2 ? x1 : (r == 3 ? x0 : 0.0f));
+    const float w4 = r == 2 ? x2 : (r == 3 ? x1 : 0.0f);
+    const float w5 = r == 3 ? x2 : 0.0f;
+    red_v4(p + base, w0, w1, w2, w3);
+    if (r >= 2) red_v2(p + base + 4, w4, w5);
     return;
   }
   atomicAdd(p + s, x0);
@@ -348,17 +359,18 @@ __device__ __forceinline__ void red_run(const Args<float>& A, int s, float x0, f
   atomicAdd(p + s + 2, x2);
 }
 
-// FP32 assembly of block rows a0 = P and a1 = 9 - P, in two halves around a
-// block-wide barrier.  The three warps (P, i) of one element hold the rows i
-// of the same blocks; the first half issues those rows and parks them in an
-// exchange buffer X (32 elements x 55 blocks x 9 floats, its own shared
-// memory, after the Smem struct); after the barrier, the second half reads
-// column i of each off-diagonal block from X, i.e. row i of the transposed
-// block (b, a).  Every write is a contiguous run of three CSR entries
-// (row 3I+i, columns 3J..3J+2) issued as vector reductions.
+// FP32 assembly of block rows a0 = P and a1 = 9 - P.  The three warps (P, i)
+// of one element accumulate the rows i of the same 11 blocks and park them in
+// an exchange buffer X (32 elements x 55 blocks x 9 floats, its own shared
+// memory after the Smem struct).  After a block-wide barrier each warp issues,
+// from X, row i of each of its blocks (a, b) and row i of the transposed block
+// (b, a), i.e. column i of (a, b): every write is a contiguous run of three
+// CSR entries (row 3I+i, columns 3J..3J+2).  The scatter loop is not unrolled
+// (it is bound by the L2 reductions, and unrolled copies of it for every
+// block-row pair made the kernel miss in the instruction cache).
 template <int P>
-__device__ __forceinline__ void tangent_xchg_direct(const Args<float>& A, const Smem<float>& sm, float* X,
-                                                    int64_t e0, int i) {
+__device__ __forceinline__ void tangent_xchg_accumulate(const Args<float>& A, const Smem<float>& sm, float* X,
+                                                        int i) {
   constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
   const int e = threadIdx.x & 31;
   float acc0[n0][3], acc1[n1][3];
@@ -373,35 +385,24 @@ __device__ __forceinline__ void tangent_xchg_direct(const Args<float>& A, const 
   for (int j = 0; j < n1; ++j)
 #pragma unroll
     for (int k = 0; k < 3; ++k) X[base + (n0 + j) * 9 + k] = acc1[j][k];
-  if (e0 + e >= A.real_end) return;
-#pragma unroll
-  for (int j = 0; j < n0; ++j)
-    red_run(A, sm.rbase[a0][e] + sm.rstr[a0][e] * i + 3 * sm.blk[e][a0 * 10 + a0 + j], acc0[j][0], acc0[j][1],
-            acc0[j][2]);
-#pragma unroll
-  for (int j = 0; j < n1; ++j)
-    red_run(A, sm.rbase[a1][e] + sm.rstr[a1][e] * i + 3 * sm.blk[e][a1 * 10 + a1 + j], acc1[j][0], acc1[j][1],
-            acc1[j][2]);
 }
 
-template <int P>
-__device__ __forceinline__ void tangent_xchg_transposed(const Args<float>& A, const Smem<float>& sm,
-                                                        const float* X, int64_t e0, int i) {
-  constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
+__device__ __forceinline__ void tangent_xchg_scatter(const Args<float>& A, const Smem<float>& sm, const float* X,
+                                                     int64_t e0, int P, int i) {
   const int e = threadIdx.x & 31;
   if (e0 + e >= A.real_end) return;
-  const int xb = e * 495 + P * 99;
-#pragma unroll
-  for (int j = 1; j < n0; ++j) {
-    const int b = a0 + j;
-    red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a0], X[xb + j * 9 + i],
-            X[xb + j * 9 + 3 + i], X[xb + j * 9 + 6 + i]);
-  }
-#pragma unroll
-  for (int j = 1; j < n1; ++j) {
-    const int b = a1 + j;
-    red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a1], X[xb + (n0 + j) * 9 + i],
-            X[xb + (n0 + j) * 9 + 3 + i], X[xb + (n0 + j) * 9 + 6 + i]);
+  const int n0 = 10 - P;
+  const float* xb = X + e * 495 + P * 99;
+#pragma unroll 1
+  for (int j = 0; j < 11; ++j) {
+    const int a = j < n0 ? P : 9 - P;
+    const int b = j < n0 ? P + j : 9 - P + (j - n0);
+    const float* blkv = xb + j * 9;
+    red_run(A, sm.rbase[a][e] + sm.rstr[a][e] * i + 3 * sm.blk[e][a * 10 + b], blkv[3 * i], blkv[3 * i + 1],
+            blkv[3 * i + 2]);
+    if (b != a)
+      red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a], blkv[i], blkv[3 + i],
+              blkv[6 + i]);
   }
 }
 
@@ -421,11 +422,7 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
   Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
   load_tile<T, DO_TANGENT>(A, sm, e0);
   bool inverted = false;
-  switch ((threadIdx.x >> 5) % 3) {     // warp-uniform row of the qp phase
-    case 0: qp_phase<T, MAT, KV, DO_TANGENT, 0>(A, sm, inverted); break;
-    case 1: qp_phase<T, MAT, KV, DO_TANGENT, 1>(A, sm, inverted); break;
-    default: qp_phase<T, MAT, KV, DO_TANGENT, 2>(A, sm, inverted); break;
-  }
+  qp_phase<T, MAT, KV, DO_TANGENT>(A, sm, inverted);
   if (inverted && (e0 + (threadIdx.x & 31)) < A.real_end) atomicOr(A.flags, kFlagInverted);
   __syncthreads();
   if (DO_FORCE) force_phase(A, sm, e0);
@@ -436,20 +433,14 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
       if (A.xchg) {                    // kernel-argument test: uniform over the block
         float* X = reinterpret_cast<float*>(smem_raw + sizeof(Smem<float>));
         switch (p) {                   // warp-uniform
-          case 0: tangent_xchg_direct<0>(A, sm, X, e0, i); break;
-          case 1: tangent_xchg_direct<1>(A, sm, X, e0, i); break;
-          case 2: tangent_xchg_direct<2>(A, sm, X, e0, i); break;
-          case 3: tangent_xchg_direct<3>(A, sm, X, e0, i); break;
-          default: tangent_xchg_direct<4>(A, sm, X, e0, i); break;
+          case 0: tangent_xchg_accumulate<0>(A, sm, X, i); break;
+          case 1: tangent_xchg_accumulate<1>(A, sm, X, i); break;
+          case 2: tangent_xchg_accumulate<2>(A, sm, X, i); break;
+          case 3: tangent_xchg_accumulate<3>(A, sm, X, i); break;
+          default: tangent_xchg_accumulate<4>(A, sm, X, i); break;
         }
         __syncthreads();               // reached by every thread of the block
-        switch (p) {
-          case 0: tangent_xchg_transposed<0>(A, sm, X, e0, i); break;
-          case 1: tangent_xchg_transposed<1>(A, sm, X, e0, i); break;
-          case 2: tangent_xchg_transposed<2>(A, sm, X, e0, i); break;
-          case 3: tangent_xchg_transposed<3>(A, sm, X, e0, i); break;
-          default: tangent_xchg_transposed<4>(A, sm, X, e0, i); break;
-        }
+        tangent_xchg_scatter(A, sm, X, e0, p, i);
         return;
       }
     }
