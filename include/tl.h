@@ -282,21 +282,22 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *   element pass (fused force + tangent + CSR assembly): persistent grid
  *     (SMs x resident CTAs) or one CTA per 32-element tile; for
  *     TL_FP32_ELEM also the scatter (exchanged 3-entry runs issued as vector
- *     reductions, or one scalar reduction per entry);
+ *     reductions, or one scalar reduction per entry) and the prefetch of the
+ *     next tile (cp.async into shared memory, or none);
  *   PCG product H p: 4, 8 or 16 lanes per node.
  * reps timed launches per variant after one warm-up.  Needs the pattern;
  * allocates and frees one CSR values array and one force array.  Synchronous.
  * The result does not change any computed value beyond the rounding order of
- * the reductions.  ms_element[k]: k = 2*(1-xchg) + full_grid; ms_spmv[k]:
- * 4, 8, 16 lanes. */
+ * the reductions.  ms_element[k]: k = 4*(1-prefetch) + 2*(1-xchg) + full_grid;
+ * ms_spmv[k]: 4, 8, 16 lanes. */
 typedef struct tl_tune_result {
   int32_t spmv_group;         /* lanes per node in H p */
   int32_t elem_xchg;          /* 1: exchanged vector runs (FP32 assembly) */
   int32_t elem_full_grid;     /* 1: one CTA per tile; 0: persistent grid */
-  int32_t _pad;
-  float ms_element[4];        /* measured element-pass times (0: not applicable) */
+  int32_t elem_prefetch;      /* 1: cp.async prefetch of the next tile (FP32) */
+  float ms_element[8];        /* measured element-pass times (0: not measured) */
   float ms_spmv[3];
-  float _pad2;
+  float _pad;
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-Wno-deprecated-declarations", "-I", INCLUDE,
                     "--expt-relaxed-constexpr", "-cudart", "shared"]
     if ptxas_verbose:
         flags += ["-Xptxas", "-v"]

@@ -61,6 +61,7 @@ struct Args {
   int32_t nnz;         // length of values (bounds of the vector reductions)
   int32_t v4_ok;       // values is 16-byte aligned
   int32_t xchg;        // FP32 CSR assembly through the exchange buffer
+  int32_t pf_off;      // byte offset of the prefetch buffer in shared memory (-1: none)
 };
 
 // Per-element shared-memory strides padded to odd word counts so that lanes
@@ -124,15 +125,118 @@ __device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Prefetch of the next tile (float32 kernels).  While a CTA computes tile t it
+// copies, with cp.async, the raw data of its next tile into a buffer of its
+// own: stage 1 (issued after tile t is staged) the connectivity, geometry and
+// slot-block rows; stage 2 (issued once stage 1 has landed, after the qp
+// phase) the row-pointer pairs and the nodal q_n, v and X of those nodes.  The
+// next tile is then staged from shared memory only.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Prefetch {
+  int32_t conn[E * 10];          // element-major rows, as in global memory
+  T geo[E * 16];
+  uint8_t blk[E * 100];
+  int32_t nptr[2][10][E];        // node_ptr[node], node_ptr[node + 1]
+  double qn[30 * E], vv[30 * E], XX[30 * E];   // [c][e], c = 3 a + d
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Stage 1: the tile's rows of conn (1,280 B), geo (32 x 16 T) and blk
+// (3,200 B) are contiguous and 16-byte aligned (tiles start at multiples of
+// 32 elements; the arrays come from cudaMalloc).
+template <typename T>
+__device__ __forceinline__ void prefetch_stage1(const Args<T>& A, Prefetch<T>& P, int64_t e0) {
+  const int tid = threadIdx.x;
+  const unsigned char* c = reinterpret_cast<const unsigned char*>(A.conn + e0 * 10);
+  const unsigned char* g = reinterpret_cast<const unsigned char*>(A.geo + e0 * 16);
+  const unsigned char* b = A.blk + e0 * 100;
+  constexpr int nc = E * 10 * 4 / 16, ng = E * 16 * (int)sizeof(T) / 16, nb = E * 100 / 16;
+  for (int k = tid; k < nc + ng + nb; k += NT) {
+    if (k < nc) cp_async16(reinterpret_cast<unsigned char*>(P.conn) + 16 * k, c + 16 * k);
+    else if (k < nc + ng) cp_async16(reinterpret_cast<unsigned char*>(P.geo) + 16 * (k - nc), g + 16 * (k - nc));
+    else cp_async16(P.blk + 16 * (k - nc - ng), b + 16 * (k - nc - ng));
+  }
+  cp_async_commit();
+}
+
+// Stage 2 (after stage 1 is visible to the block): row pointers and nodal data.
+template <typename T>
+__device__ __forceinline__ void prefetch_stage2(const Args<T>& A, Prefetch<T>& P) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < E * 10; t += NT) {
+    const int e = t / 10, a = t % 10;
+    const int node = P.conn[t];
+    cp_async4(&P.nptr[0][a][e], A.node_ptr + node);
+    cp_async4(&P.nptr[1][a][e], A.node_ptr + node + 1);
+  }
+  for (int t = tid; t < E * 30; t += NT) {
+    const int e = t / 30, c = t % 30;
+    const int64_t g = 3 * (int64_t)P.conn[e * 10 + c / 3] + c % 3;
+    cp_async8(&P.qn[c * E + e], A.q_n + g);
+    cp_async8(&P.vv[c * E + e], A.v + g);
+    cp_async8(&P.XX[c * E + e], A.X + g);
+  }
+  cp_async_commit();
+}
+
+// Stage the next tile from the prefetch buffer (as load_tile does from global).
+template <typename T, bool NEED_PATTERN>
+__device__ __forceinline__ void unpack_tile(const Args<T>& A, Smem<T>& sm, const Prefetch<T>& P) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < E * 10; t += NT) {
+    const int e = t / 10, a = t % 10;
+    sm.node[a][e] = P.conn[t];
+    if (NEED_PATTERN) {
+      const int p0 = P.nptr[0][a][e], p1 = P.nptr[1][a][e];
+      sm.rbase[a][e] = 9 * p0;
+      sm.rstr[a][e] = 3 * (p1 - p0);
+    }
+  }
+  if (NEED_PATTERN) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(P.blk);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.blk[0][0]);
+    for (int t = tid; t < E * 25; t += NT) dst[t] = src[t];
+  }
+  for (int t = tid; t < E * 16; t += NT) {
+    const int e = t / 16, c = t % 16;
+    sm.geo[c][e] = P.geo[t];
+  }
+  const double h = A.h;
+  for (int t = tid; t < E * 30; t += NT) {
+    const int c = t / E, e = t % E;
+    const double vv = P.vv[t];
+    const double x = P.qn[t] + h * vv;
+    sm.u[c * E + e] = T(x - P.XX[t]);
+    sm.vel[c * E + e] = T(vv);
+  }
+  __syncthreads();
+}
+
 // Gradients of the 10 shape functions at barycentric point L (straight-sided
 // T10): corners (4 L_a - 1) grad L_a, midsides 4 (L_i grad L_j + L_j grad L_i).
 template <typename T>
-__device__ __forceinline__ void shape_grads(const Smem<T>& sm, int e, const double Lq[4], T n[10][3]) {
+__device__ __forceinline__ void shape_grads(const T (&geo)[16][E], int e, const double Lq[4], T n[10][3]) {
   T gL[4][3];
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) gL[c][d] = sm.geo[c * 3 + d][e];
+    for (int d = 0; d < 3; ++d) gL[c][d] = geo[c * 3 + d][e];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -175,7 +279,7 @@ __device__ __forceinline__ void qp_phase(const Args<T>& A, Smem<T>& sm, bool& in
   qp_bary(q, Lq);
   const T wJ = T(qp_wfrac(q)) * sm.geo[12][e];
   T n[10][3];
-  shape_grads(sm, e, Lq, n);
+  shape_grads(sm.geo, e, Lq, n);
   if (i == 0) {
 #pragma unroll
     for (int a = 0; a < 10; ++a)
@@ -416,15 +520,20 @@ __device__ __forceinline__ void tangent_rows(const Args<T>& A, const Smem<T>& sm
   tangent_blockrow<T, 9 - P, P + 1>(A, sm, e0, i);
 }
 
-// One tile of 32 elements starting at internal element e0.
+// One tile of 32 elements starting at internal element e0, already staged in
+// shared memory.  With a prefetch buffer P the next tile (first element
+// e0_next >= 0) is fetched while this one computes.
 template <typename T, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
-__device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_raw, int64_t e0) {
+__device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_raw, int64_t e0,
+                                          Prefetch<T>* P, int64_t e0_next) {
   Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
-  load_tile<T, DO_TANGENT>(A, sm, e0);
+  if (P && e0_next >= 0) prefetch_stage1(A, *P, e0_next);
   bool inverted = false;
   qp_phase<T, MAT, KV, DO_TANGENT>(A, sm, inverted);
   if (inverted && (e0 + (threadIdx.x & 31)) < A.real_end) atomicOr(A.flags, kFlagInverted);
+  if (P) cp_async_wait_all();
   __syncthreads();
+  if (P && e0_next >= 0) prefetch_stage2(A, *P);
   if (DO_FORCE) force_phase(A, sm, e0);
   if (DO_TANGENT) {
     const int w = threadIdx.x >> 5;
@@ -454,6 +563,103 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Force-only pass (the residual's internal force): 5 warps, warp q evaluates
+// quadrature point q of the tile's 32 elements (lanes) once and all three
+// force rows, so the constitutive update is not repeated per row as in the
+// 15-warp kernel, which splits the rows to spread the tangent work.  Small
+// shared memory, one CTA per tile, several CTAs per SM.
+// ---------------------------------------------------------------------------
+constexpr int NTF = 160;
+
+template <typename T>
+struct SmemF {
+  int32_t node[10][E];
+  T geo[16][E];
+  T u[kUStride * E];
+  T vel[kUStride * E];
+  T fq[kFStride * E];
+};
+
+template <typename T, int MAT, bool KV>
+__device__ __forceinline__ void force_tile(const Args<T>& A, SmemF<T>& sm, int64_t e0) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < E * 10; t += NTF) {
+    const int e = t / 10, a = t % 10;
+    sm.node[a][e] = A.conn[(e0 + e) * 10 + a];
+  }
+  for (int t = tid; t < E * 16; t += NTF) {
+    const int e = t / 16, c = t % 16;
+    sm.geo[c][e] = A.geo[(e0 + e) * 16 + c];
+  }
+  __syncthreads();
+  const double h = A.h;
+  for (int t = tid; t < E * 30; t += NTF) {
+    const int e = t / 30, c = t % 30;
+    const int64_t g = 3 * (int64_t)sm.node[c / 3][e] + c % 3;
+    const double vv = A.v[g];
+    const double x = A.q_n[g] + h * vv;
+    sm.u[c * E + e] = T(x - A.X[g]);
+    sm.vel[c * E + e] = T(vv);
+  }
+  __syncthreads();
+  const int q = tid >> 5, e = tid & 31;
+  double Lq[4];
+  qp_bary(q, Lq);
+  const T wJ = T(qp_wfrac(q)) * sm.geo[12][e];
+  T n[10][3];
+  shape_grads(sm.geo, e, Lq, n);
+  T Hm[3][3], Fd[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Hm[r][c] = 0;
+      Fd[r][c] = 0;
+    }
+#pragma unroll
+  for (int a = 0; a < 10; ++a)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T ua = sm.u[(a * 3 + r) * E + e];
+      T va = T(0);
+      if (KV) va = sm.vel[(a * 3 + r) * E + e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Hm[r][c] += ua * n[a][c];
+        if (KV) Fd[r][c] += va * n[a][c];
+      }
+    }
+  QP<T> s;
+  bool inverted = false;
+  constitutive<T, MAT, KV>(Hm, Fd, A.mat, s, inverted);
+  if (inverted && e0 + e < A.real_end) atomicOr(A.flags, kFlagInverted);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T Pi[3];
+#pragma unroll
+    for (int J = 0; J < 3; ++J) {
+      T acc = 0;
+#pragma unroll
+      for (int M = 0; M < 3; ++M) acc += s.F[i][M] * s.S[M][J];
+      Pi[J] = acc * wJ;
+    }
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+      sm.fq[e * kFStride + q * 30 + a * 3 + i] = Pi[0] * n[a][0] + Pi[1] * n[a][1] + Pi[2] * n[a][2];
+  }
+  __syncthreads();
+  // sum over the quadrature points and scatter (lanes = elements)
+  for (int t = tid; t < E * 30; t += NTF) {
+    const int c = t / E, ee = t % E;
+    if (e0 + ee >= A.real_end) continue;
+    T acc = 0;
+#pragma unroll
+    for (int qq = 0; qq < 5; ++qq) acc += sm.fq[ee * kFStride + qq * 30 + c];
+    atomicAdd(&A.f[3 * (int64_t)sm.node[c / 3][ee] + c % 3], double(acc));
+  }
+}
+
 // Segment table of one launch: the material segments of the internal element
 // order (each a whole number of tiles), walked by one persistent grid.
 constexpr int kMaxSeg = 64;
@@ -474,42 +680,102 @@ struct SegTable {
   int32_t ntiles;
 };
 
+// One tile through the kernel of its (material, Kelvin-Voigt) pair.
+template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT>
+__device__ __forceinline__ void dispatch_tile(const Args<T>& a, unsigned char* smem_raw, int64_t e0, int combo,
+                                              Prefetch<T>* P, int64_t e0_next) {
+  if constexpr (COMBO < 4) {
+    elem_tile<T, COMBO / 2, (COMBO % 2) != 0, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next);
+  } else {
+    switch (combo) {                                 // block-uniform
+      case 0: elem_tile<T, TL_SVK, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
+      case 1: elem_tile<T, TL_SVK, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
+      case 2: elem_tile<T, TL_MOONEY_RIVLIN, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
+      default: elem_tile<T, TL_MOONEY_RIVLIN, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
+    }
+  }
+}
+
+// Walks the segment table forward (tile indices only grow).
+struct SegWalk {
+  int sg = 0, t_begin = 0;
+  template <typename T>
+  __device__ __forceinline__ int64_t e0(const SegTable<T>& S, int t) {
+    while (t >= S.s[sg].tile_end) {                  // t < ntiles = tile_end of the last segment
+      t_begin = S.s[sg].tile_end;
+      ++sg;
+    }
+    return S.s[sg].begin + (int64_t)(t - t_begin) * E;
+  }
+};
+
+// One CTA per tile; the tile's segment by a forward walk from the start.
+template <typename T, int COMBO>
+__global__ void __launch_bounds__(NTF) force_kernel(Args<T> A, SegTable<T> S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemF<T>& sm = *reinterpret_cast<SmemF<T>*>(smem_raw);
+  const int t = blockIdx.x;
+  if (t >= S.ntiles) return;
+  SegWalk w;
+  const int64_t e0 = w.e0(S, t);
+  Args<T> a = A;
+  a.mat = S.s[w.sg].mat;
+  a.real_end = S.s[w.sg].real_end;
+  if constexpr (COMBO < 4) {
+    force_tile<T, COMBO / 2, (COMBO % 2) != 0>(a, sm, e0);
+  } else {
+    switch (S.s[w.sg].combo) {                       // block-uniform
+      case 0: force_tile<T, TL_SVK, false>(a, sm, e0); break;
+      case 1: force_tile<T, TL_SVK, true>(a, sm, e0); break;
+      case 2: force_tile<T, TL_MOONEY_RIVLIN, false>(a, sm, e0); break;
+      default: force_tile<T, TL_MOONEY_RIVLIN, true>(a, sm, e0); break;
+    }
+  }
+}
+
+
 // Persistent element kernel: CTA b starts with tile b and then takes the next
 // unprocessed tile from a device counter (zeroed before the launch), so SMs
 // that run faster take more tiles; with counter == nullptr it takes tiles
 // b + gridDim.x, b + 2 gridDim.x, ...  Tiles ascend in every CTA, so the
 // segment of a tile is found by walking the table forward.  COMBO < 4
 // compiles one (material, Kelvin-Voigt) pair, COMBO = 4 all four with a
-// block-uniform dispatch per tile (multi-material meshes and batches).
+// block-uniform dispatch per tile (multi-material meshes and batches).  The
+// float32 kernels prefetch the next tile (A.pf_off >= 0).
 template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT>
 __global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next;
-  int sg = 0, t_begin = 0;
+  Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
+  Prefetch<T>* P = A.pf_off >= 0 ? reinterpret_cast<Prefetch<T>*>(smem_raw + A.pf_off) : nullptr;
+  SegWalk cur, nxt;
   int t = blockIdx.x;
-  while (t < S.ntiles) {
-    while (t >= S.s[sg].tile_end) {                // t < ntiles = tile_end of the last segment
-      t_begin = S.s[sg].tile_end;
-      ++sg;
-    }
+  if (t >= S.ntiles) return;                         // uniform over the block
+  int64_t e0 = cur.e0(S, t);
+  load_tile<T, DO_TANGENT>(A, sm, e0);
+  if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t + (int)gridDim.x;
+  __syncthreads();
+  while (true) {
+    const int t_next = s_next;
     Args<T> a = A;
-    a.mat = S.s[sg].mat;
-    a.real_end = S.s[sg].real_end;
-    const int64_t e0 = S.s[sg].begin + (int64_t)(t - t_begin) * E;
-    if constexpr (COMBO < 4) {
-      elem_tile<T, COMBO / 2, (COMBO % 2) != 0, DO_FORCE, DO_TANGENT>(a, smem_raw, e0);
+    a.mat = S.s[cur.sg].mat;
+    a.real_end = S.s[cur.sg].real_end;
+    nxt = cur;
+    const int64_t e0_next = (P && t_next < S.ntiles) ? nxt.e0(S, t_next) : -1;
+    dispatch_tile<T, COMBO, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, S.s[cur.sg].combo, P, e0_next);
+    if (P) cp_async_wait_all();
+    __syncthreads();                                 // this tile's shared data is consumed
+    if (t_next >= S.ntiles) break;
+    if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t_next + (int)gridDim.x;
+    t = t_next;
+    if (P) {
+      cur = nxt;
+      e0 = e0_next;
+      unpack_tile<T, DO_TANGENT>(A, sm, *P);         // ends with a barrier (also publishes s_next)
     } else {
-      switch (S.s[sg].combo) {                     // block-uniform
-        case 0: elem_tile<T, TL_SVK, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
-        case 1: elem_tile<T, TL_SVK, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
-        case 2: elem_tile<T, TL_MOONEY_RIVLIN, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
-        default: elem_tile<T, TL_MOONEY_RIVLIN, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0); break;
-      }
+      e0 = cur.e0(S, t);
+      load_tile<T, DO_TANGENT>(A, sm, e0);           // ends with a barrier (also publishes s_next)
     }
-    __syncthreads();                               // this tile's shared data is consumed
-    if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t + (int)gridDim.x;
-    __syncthreads();
-    t = s_next;
   }
 }
 
@@ -519,8 +785,15 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   // the force-only variant does not need the tangent array (last member);
   // the FP32 CSR assembly adds its exchange buffer after the struct
   const bool xchg = std::is_same<T, float>::value && DO_TANGENT && values && !K_elem && m->tune.elem_xchg;
-  const size_t smem = DO_TANGENT ? sizeof(Smem<T>) + (xchg ? sizeof(float) * kXFloats : 0)
-                                 : offsetof(Smem<T>, A);
+  size_t smem = DO_TANGENT ? sizeof(Smem<T>) + (xchg ? sizeof(float) * kXFloats : 0)
+                           : offsetof(Smem<T>, A);
+  // the float32 kernels prefetch the next tile into a buffer after the rest
+  int pf_off = -1;
+  if (std::is_same<T, float>::value && m->tune.elem_prefetch) {
+    smem = (smem + 15) / 16 * 16;
+    pf_off = (int)smem;
+    smem += sizeof(Prefetch<T>);
+  }
   Args<T> A;
   A.conn = m->d_conn;
   A.geo = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m->d_geo32)
@@ -544,6 +817,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   A.nnz = (int32_t)m->nnz;
   A.v4_ok = ((reinterpret_cast<uintptr_t>(values) & 15u) == 0) ? 1 : 0;
   A.xchg = xchg ? 1 : 0;
+  A.pf_off = pf_off;
   cudaEvent_t t0 = timer_open(m);
   // Segments in groups of at most kMaxSeg, one persistent launch per group.
   // The float32 kernels include an all-materials variant; the float64 ones
@@ -576,6 +850,25 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       mixed = mixed || combo != combo0;
     }
     if (S.ntiles == 0) continue;
+    if constexpr (DO_FORCE && !DO_TANGENT) {
+      void (*fkern)(Args<T>, SegTable<T>) = nullptr;
+      switch (mixed ? 4 : combo0) {
+        case 0: fkern = force_kernel<T, 0>; break;
+        case 1: fkern = force_kernel<T, 1>; break;
+        case 2: fkern = force_kernel<T, 2>; break;
+        case 3: fkern = force_kernel<T, 3>; break;
+        default:
+          if constexpr (kMixed) fkern = force_kernel<T, 4>;
+          break;
+      }
+      if (!fkern) return fail(m, TL_ERR_UNSUPPORTED, "force kernel selection");
+      const size_t fsmem = sizeof(SmemF<T>);
+      TL_CUDA(m, cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+      fkern<<<(unsigned)S.ntiles, NTF, fsmem, m->stream>>>(A, S);
+      TL_CUDA(m, cudaGetLastError());
+      ++m->launches;
+      continue;
+    }
     void (*kern)(Args<T>, SegTable<T>, int*) = nullptr;
     switch (mixed ? 4 : combo0) {
       case 0: kern = elem_kernel<T, 0, DO_FORCE, DO_TANGENT>; break;

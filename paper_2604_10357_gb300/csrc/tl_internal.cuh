@@ -48,6 +48,7 @@ struct Tune {
   int spmv_group = 8;     // lanes per node in the PCG product H p (4, 8, 16)
   int elem_xchg = 1;      // FP32 assembly: 1 = exchanged vector runs, 0 = scalar scatter
   int elem_full_grid = 0; // element kernels: 0 = persistent grid (SMs x occupancy), 1 = one CTA per tile
+  int elem_prefetch = 1;  // float32 element kernels: 1 = prefetch the next tile with cp.async
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };

@@ -11,10 +11,12 @@
 // the same columns, so a group of lanes walks the node's neighbour list once,
 // reads each neighbour's index and p values once for all three rows (the
 // column array of the DOF CSR is not read), and reduces the three sums in
-// the group.  Dot products are reduced per block into partials and finished
-// by a one-block kernel; alpha and beta are formed on the device.  The host
-// reads the residual norm every kCheck iterations, or the check runs on the
-// device inside the captured Newton graph.
+// the group.  Dot products are reduced per block into partials that the last
+// block of the same launch sums (three launches per iteration: H p with p.Hp,
+// the x / r / z update with r.z and r.r, the p update); alpha and beta are
+// formed on the device from alternating r.z slots.  The host reads the
+// residual norm every kCheck iterations, or the check runs on the device
+// inside the captured Newton graph.
 #include <cmath>
 #include <type_traits>
 
@@ -26,6 +28,7 @@ struct PcgWork {
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *binv = nullptr, *part = nullptr,
          *scal = nullptr;
   float* p32 = nullptr;        // float32 copy of p (float32 element form)
+  unsigned* tickets = nullptr; // last-block counters of the two fused reductions
   int32_t* diag_k = nullptr;   // per node: position of I in its own adjacency
   int nparts = 0;
 };
@@ -93,6 +96,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// The last block to finish a pass sums the per-block partials in a fixed
+// order (deterministic) and writes the total: a ticket counter (zero between
+// passes; the last block resets it) replaces a separate one-block launch.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ bool is_last;
+  __threadfence();                       // this block's partials before its ticket
+  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;                        // uniform over the block
+}
+
+__device__ __forceinline__ double sum_partials(const double* part, int n, double* red) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += __ldcg(part + i);
+  return block_sum(t, red);
+}
+
 // Ap = H p with a group of G lanes per node I (rows 3I..3I+2): lane l takes
 // the neighbours j = l, l+G, ..., reads node_col once, p[3J..3J+2] once and
 // the three 3-entry runs (row 3I+d starts at 9 ptr(I) + 3 deg(I) d), and the
@@ -107,7 +128,8 @@ template <> struct SpmvAcc<float> { using type = float; };
 template <typename T, int G>
 __global__ void spmv_node(const T* __restrict__ vals, const int32_t* __restrict__ node_ptr,
                           const int32_t* __restrict__ node_col, int64_t nn, const double* __restrict__ p,
-                          const float* __restrict__ p32, double* __restrict__ Ap, double* part) {
+                          const float* __restrict__ p32, double* __restrict__ Ap, double* part, double* scal,
+                          unsigned* ticket) {
   using A = typename SpmvAcc<T>::type;
   __shared__ double red[kBlock / 32];
   const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
@@ -147,6 +169,14 @@ __global__ void spmv_node(const T* __restrict__ vals, const int32_t* __restrict_
   }
   const double t = block_sum(dot, red);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (last_block(ticket)) {
+    __syncthreads();
+    const double tot = sum_partials(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      scal[1] = tot;
+      *ticket = 0u;
+    }
+  }
 }
 
 // finish a partial sum: scal[slot] = sum(part)
@@ -158,16 +188,19 @@ __global__ void finish_sum(const double* part, int n, double* scal, int slot) {
   if (threadIdx.x == 0) scal[slot] = s;
 }
 
-// scal layout: 0 rz (current), 1 pAp, 2 rz_new, 3 rr, 6 breakdown flag
-// x += alpha p; r -= alpha Ap; z = P r; partials of r.z and r.r
+// scal layout: 0 and 2 r.z of alternate iterations (iteration k reads slot
+// 2 (k % 2) and writes slot 2 ((k + 1) % 2)), 1 p.Ap, 3 r.r, 6 breakdown flag.
+// x += alpha p; r -= alpha Ap; z = P r; r.z and r.r finished by the last block
 __global__ void update_xr(double* x, double* r, double* z, const double* p, const double* Ap, const double* binv,
-                          double* scal, int64_t nn, double* part_rz, double* part_rr) {
+                          double* scal, int64_t nn, double* part_rz, double* part_rr, int parity,
+                          unsigned* ticket) {
   __shared__ double red[kBlock / 32];
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // pAp <= 0: H is not positive definite along p (CG breakdown); stop moving
   // and raise the breakdown slot, which ends the iteration at the next check
+  const int rz_old = 2 * parity, rz_new = 2 - 2 * parity;
   const bool ok = scal[1] > 0.0;
-  const double alpha = ok ? scal[0] / scal[1] : 0.0;
+  const double alpha = ok ? scal[rz_old] / scal[1] : 0.0;
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) scal[6] = 1.0;
   double rz = 0.0, rr = 0.0;
   if (I < nn) {
@@ -193,20 +226,30 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
     part_rz[blockIdx.x] = a;
     part_rr[blockIdx.x] = b;
   }
+  if (last_block(ticket)) {
+    __syncthreads();
+    const double trz = sum_partials(part_rz, gridDim.x, red);
+    __syncthreads();
+    const double trr = sum_partials(part_rr, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      scal[rz_new] = trz;
+      scal[3] = trr;
+      *ticket = 0u;
+    }
+  }
 }
 
-// p = z + beta p with beta = rz_new / rz, then rz <- rz_new
-__global__ void update_p(double* p, float* p32, const double* z, int64_t n, double* scal) {
+// p = z + beta p with beta = (r.z new) / (r.z old)
+__global__ void update_p(double* p, float* p32, const double* z, int64_t n, const double* scal, int parity) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const double beta = scal[0] != 0.0 ? scal[2] / scal[0] : 0.0;
+  const double rz_old = scal[2 * parity], rz_new = scal[2 - 2 * parity];
+  const double beta = rz_old != 0.0 ? rz_new / rz_old : 0.0;
   if (i < n) {
     const double v = z[i] + beta * p[i];
     p[i] = v;
     if (p32) p32[i] = float(v);
   }
 }
-
-__global__ void roll_rz(double* scal) { scal[0] = scal[2]; }
 
 // start: x = 0, r = b = -g, z = P r, p = z; partials of r.z and r.r
 __global__ void pcg_start(const double* g, double* x, double* r, double* z, double* p, float* p32,
@@ -245,7 +288,7 @@ __global__ void pcg_start(const double* g, double* x, double* r, double* z, doub
 
 void pcg_destroy(PcgWork* w) {
   if (!w) return;
-  void* ptrs[] = {w->r, w->z, w->p, w->Ap, w->binv, w->part, w->scal, w->diag_k, w->p32};
+  void* ptrs[] = {w->r, w->z, w->p, w->Ap, w->binv, w->part, w->scal, w->diag_k, w->p32, w->tickets};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete w;
@@ -267,6 +310,8 @@ tl_status pcg_ensure(tl_mesh* m) {
   TL_CUDA(m, cudaMalloc(&w->scal, sizeof(double) * 8));
   TL_CUDA(m, cudaMalloc(&w->diag_k, sizeof(int32_t) * nn));
   TL_CUDA(m, cudaMemsetAsync(w->p, 0, sizeof(double) * n, m->stream));
+  TL_CUDA(m, cudaMalloc(&w->tickets, sizeof(unsigned) * 2));
+  TL_CUDA(m, cudaMemsetAsync(w->tickets, 0, sizeof(unsigned) * 2, m->stream));
   if (m->precision == TL_FP32_ELEM) {
     TL_CUDA(m, cudaMalloc(&w->p32, sizeof(float) * n));
     TL_CUDA(m, cudaMemsetAsync(w->p32, 0, sizeof(float) * n, m->stream));
@@ -307,7 +352,7 @@ void launch_spmv(tl_mesh* m, const void* values, PcgWork* w, unsigned* nblocks) 
   const int64_t nn = m->nn;
   const unsigned nb = (unsigned)((G * nn + kBlock - 1) / kBlock);
   spmv_node<T, G><<<nb, kBlock, 0, m->stream>>>((const T*)values, m->d_node_ptr, m->d_node_col, nn, w->p, w->p32,
-                                                w->Ap, w->part);
+                                                w->Ap, w->part, w->scal, w->tickets);
   *nblocks = nb;
 }
 
@@ -324,7 +369,7 @@ tl_status pcg_spmv_only(tl_mesh* m, const void* values, int group) {
   return TL_OK;
 }
 
-// `count` PCG iterations (7 launches each); asynchronous, no host reads.
+// `count` PCG iterations (3 launches each); asynchronous, no host reads.
 tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) {
   PcgWork* w = m->pcg;
   cudaStream_t s = m->stream;
@@ -346,13 +391,12 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
       else if (G == 16) launch_spmv<double, 16>(m, values, w, &nbs);
       else launch_spmv<double, 8>(m, values, w, &nbs);
     }
-    finish_sum<<<1, 1024, 0, s>>>(w->part, (int)nbs, w->scal, 1);
-    update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr);
-    finish_sum<<<1, 1024, 0, s>>>(part_rz, nbn, w->scal, 2);
-    finish_sum<<<1, 1024, 0, s>>>(part_rr, nbn, w->scal, 3);
-    update_p<<<nbv, kBlock, 0, s>>>(w->p, fp32 ? w->p32 : nullptr, w->z, n, w->scal);
-    roll_rz<<<1, 1, 0, s>>>(w->scal);
-    m->launches += 7;
+    (void)nbs;
+    const int parity = k & 1;            // chunks start at even iterations (count is 8 except the last)
+    update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr,
+                                     parity, w->tickets + 1);
+    update_p<<<nbv, kBlock, 0, s>>>(w->p, fp32 ? w->p32 : nullptr, w->z, n, w->scal, parity);
+    m->launches += 3;
   }
   TL_CUDA(m, cudaGetLastError());
   return TL_OK;

@@ -7,9 +7,10 @@
 //   Sec. 4.4 (gradient): one thread per coefficient row of M, no atomics;
 //   eq. hessian: the h^2 rho C_q^T C_q term (identity rows for clamps).
 //
-// One thread per node handles its three DOFs (the mass CSR row is shared by
-// the three components); ||g||^2 is reduced per block into a partials array
-// and summed by a second one-block kernel, so the norm is deterministic.
+// A group of four lanes per node handles its three DOFs (the mass CSR row is
+// shared by the three components); ||g||^2 is reduced per block into a
+// partials array and summed by a second one-block kernel, so the norm is
+// deterministic.
 #include <mutex>
 
 #include "tl_internal.cuh"
@@ -27,24 +28,40 @@ constexpr int kResBlock = 256;
 constexpr int kNoAllocMaxBlocks = 16384;                    // nn <= 4,194,304
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 
-__global__ void residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass,
-                                const double* mrow, const int32_t* fixed_of_node, const double* X, int64_t nn,
-                                double h, double rho, double gx, double gy, double gz, const double* q_n,
-                                const double* v_n, const double* v, const double* f_int, const double* f_ext,
-                                const double* lambda, double* g, double* partials) {
-  __shared__ double red[kResBlock / 32];
-  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double sq = 0.0;
+// kResLanes lanes per node: lane l sums the mass row entries l, l + kResLanes,
+// ... (the rows have ~28 entries), the group combines the three sums and its
+// first lane forms the node's three residual components.  A block holds
+// kResBlock nodes, so the partial count is the same as with one thread per
+// node.
+constexpr int kResLanes = 4;
+
+__global__ void __launch_bounds__(kResBlock * kResLanes)
+    residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass, const double* mrow,
+                    const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double rho, double gx,
+                    double gy, double gz, const double* q_n, const double* v_n, const double* v,
+                    const double* f_int, const double* f_ext, const double* lambda, double* g,
+                    double* partials) {
+  __shared__ double red[kResBlock * kResLanes / 32];
+  const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kResLanes;
+  const int l = threadIdx.x & (kResLanes - 1);
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, sq = 0.0;
   if (I < nn) {
     const int p0 = node_ptr[I], p1 = node_ptr[I + 1];
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
-    for (int p = p0; p < p1; ++p) {
+    for (int p = p0 + l; p < p1; p += kResLanes) {
       const int64_t J = node_col[p];
       const double mij = mass[p];
       acc0 += mij * (v[3 * J] - v_n[3 * J]);
       acc1 += mij * (v[3 * J + 1] - v_n[3 * J + 1]);
       acc2 += mij * (v[3 * J + 2] - v_n[3 * J + 2]);
     }
+  }
+#pragma unroll
+  for (int o = kResLanes / 2; o > 0; o >>= 1) {
+    acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+    acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+    acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+  }
+  if (I < nn && l == 0) {
     const double acc[3] = {acc0, acc1, acc2};
     const double grav[3] = {gx, gy, gz};
     const int j = fixed_of_node[I];
@@ -66,7 +83,7 @@ __global__ void residual_kernel(const int32_t* node_ptr, const int32_t* node_col
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double t = threadIdx.x < kResBlock / 32 ? red[threadIdx.x] : 0.0;
+    double t = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
@@ -117,7 +134,7 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   TL_TRY(residual_ensure(m));
   cudaEvent_t t0 = timer_open(m);
   // f_int may alias g: each thread reads its own entries before writing them
-  residual_kernel<<<nb, kResBlock, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow,
+  residual_kernel<<<nb, kResBlock * kResLanes, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow,
                                                     m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
                                                     p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_int,
                                                     f_ext, lambda, g, m->d_partials);
@@ -185,7 +202,7 @@ extern "C" tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, co
   double* partials = nullptr;
   tl_status s = noalloc_scratch(m, dev, &partials);
   if (s != TL_OK) return s;
-  residual_kernel<<<(unsigned)nb, kResBlock, 0, m->stream>>>(
+  residual_kernel<<<(unsigned)nb, kResBlock * kResLanes, 0, m->stream>>>(
       m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
       p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_int, f_ext, lambda, g, partials);
   TL_CUDA(m, cudaGetLastError());

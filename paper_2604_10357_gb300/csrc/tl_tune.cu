@@ -5,9 +5,10 @@
 // by timing, on the handle's own mesh and state, every variant that the
 // library compiles:
 //   * element pass (fused force + tangent + CSR assembly): persistent grid
-//     (SMs x resident CTAs, tiles taken round-robin) or one CTA per tile;
+//     (SMs x resident CTAs, tiles from a device counter) or one CTA per tile;
 //     for the float32 form also the scatter strategy (exchanged 3-entry runs
-//     as vector reductions, or one scalar reduction per entry);
+//     as vector reductions, or one scalar reduction per entry) and the
+//     cp.async prefetch of the next tile (or none);
 //   * PCG product H p: 4, 8 or 16 lanes per node.
 // Each variant is warmed up once and timed over `reps` launches with CUDA
 // events on the handle's stream; the fastest is kept in the handle and used by
@@ -63,13 +64,17 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   const Tune saved = m->tune;
   tl_tune_result r = {};
   tl_status st = TL_OK;
-  // element pass: (xchg, full grid) variants
-  struct V { int xchg, full; };
-  std::vector<V> variants = {{1, 0}, {1, 1}};
-  if (fp32) variants.insert(variants.end(), {{0, 0}, {0, 1}});
+  // element pass: (prefetch, xchg, full grid) variants; the float64 kernels
+  // have neither the exchange nor the prefetch
+  struct V { int pf, xchg, full; };
+  std::vector<V> variants;
+  for (int pf = fp32 ? 1 : 0; pf >= 0; --pf)
+    for (int xchg = fp32 ? 1 : 0; xchg >= 0; --xchg)
+      for (int full = 0; full <= 1; ++full) variants.push_back({pf, xchg, full});
   float best = 1e30f;
   Tune chosen = saved;
   for (size_t k = 0; k < variants.size() && st == TL_OK; ++k) {
+    m->tune.elem_prefetch = variants[k].pf;
     m->tune.elem_xchg = variants[k].xchg;
     m->tune.elem_full_grid = variants[k].full;
     float ms = 0.f;
@@ -78,10 +83,11 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
       return s2;
     }, &ms);
     if (st != TL_OK) break;
-    const int slot = (variants[k].xchg ? 0 : 2) + variants[k].full;
+    const int slot = 4 * (1 - variants[k].pf) + 2 * (1 - variants[k].xchg) + variants[k].full;
     r.ms_element[slot] = ms;
     if (ms < best) {
       best = ms;
+      chosen.elem_prefetch = variants[k].pf;
       chosen.elem_xchg = variants[k].xchg;
       chosen.elem_full_grid = variants[k].full;
     }
@@ -113,6 +119,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.spmv_group = chosen.spmv_group;
   r.elem_xchg = chosen.elem_xchg;
   r.elem_full_grid = chosen.elem_full_grid;
+  r.elem_prefetch = chosen.elem_prefetch;
   if (out) *out = r;
   return TL_OK;
 }
@@ -123,6 +130,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.spmv_group = m->tune.spmv_group;
   r.elem_xchg = m->tune.elem_xchg;
   r.elem_full_grid = m->tune.elem_full_grid;
+  r.elem_prefetch = m->tune.elem_prefetch;
   *out = r;
   return TL_OK;
 }
@@ -130,9 +138,11 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
 extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   if (!m || !in) return TL_ERR_INVALID_ARG;
   if (in->spmv_group != 4 && in->spmv_group != 8 && in->spmv_group != 16) return TL_ERR_INVALID_ARG;
-  if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1))
+  if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1) ||
+      (in->elem_prefetch != 0 && in->elem_prefetch != 1))
     return TL_ERR_INVALID_ARG;
   m->tune.spmv_group = in->spmv_group;
+  m->tune.elem_prefetch = in->elem_prefetch;
   m->tune.elem_xchg = in->elem_xchg;
   m->tune.elem_full_grid = in->elem_full_grid;
   m->tune.generation += 1;
