@@ -282,9 +282,12 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *   element pass (fused force + tangent + CSR assembly): persistent grid
  *     (SMs x resident CTAs) or one CTA per 32-element tile; for
  *     TL_FP32_ELEM also the scatter (exchanged 3-entry runs issued as vector
- *     reductions, or one scalar reduction per entry) and the prefetch of the
- *     next tile (cp.async into shared memory, or none);
- *   PCG product H p: 4, 8 or 16 lanes per node.
+ *     reductions, or one scalar reduction per entry), the prefetch of the
+ *     next tile (cp.async into shared memory, or none) and warp
+ *     specialisation (5 extra warps issue a tile's reductions while the
+ *     compute warps evaluate the next tile);
+ *   PCG product H p: 4, 8 or 16 lanes per node;
+ *   residual: 1 or 4 lanes per node.
  * reps timed launches per variant after one warm-up.  Needs the pattern;
  * allocates and frees one CSR values array and one force array.  Synchronous.
  * The result does not change any computed value beyond the rounding order of
@@ -295,8 +298,12 @@ typedef struct tl_tune_result {
   int32_t elem_xchg;          /* 1: exchanged vector runs (FP32 assembly) */
   int32_t elem_full_grid;     /* 1: one CTA per tile; 0: persistent grid */
   int32_t elem_prefetch;      /* 1: cp.async prefetch of the next tile (FP32) */
-  float ms_element[8];        /* measured element-pass times (0: not measured) */
+  int32_t elem_ws;            /* 1: warp-specialised scatter (FP32; with xchg, prefetch, persistent grid) */
+  int32_t residual_lanes;     /* lanes per node in the residual: 1 or 4 */
+  float ms_element[8];        /* measured element-pass times without warp specialisation (0: not measured) */
+  float ms_ws;                /* measured time of the warp-specialised variant (0: not measured) */
   float ms_spmv[3];
+  float ms_residual[2];       /* residual with 1 and 4 lanes per node */
   float _pad;
 } tl_tune_result;
 

@@ -39,6 +39,25 @@ constexpr int E = kTile;          // elements per CTA
 constexpr int NWARP = 15;         // 5 qp x 3 rows, and 5 row pairs x 3 rows
 constexpr int NT = 32 * NWARP;    // 480 threads
 
+// Warp-specialised variant (float32 CSR assembly): the 15 compute warps plus 5
+// scatter warps.  Barrier 1 synchronises the compute warps only; barriers 2
+// and 3 hand the exchange buffer between compute and scatter warps.
+constexpr int NWS = 5;                 // scatter warps
+constexpr int NTW = 32 * (NWARP + NWS);  // 640 threads
+enum : int { kBarCompute = 1, kBarFull = 2, kBarEmpty = 3 };
+
+template <bool WS>
+__device__ __forceinline__ void bar_compute() {
+  if constexpr (WS) asm volatile("bar.sync 1, 480;" ::: "memory");
+  else __syncthreads();
+}
+__device__ __forceinline__ void bar_sync_all(int id) {
+  asm volatile("bar.sync %0, 640;" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_all(int id) {
+  asm volatile("bar.arrive %0, 640;" ::"r"(id) : "memory");
+}
+
 template <typename T>
 struct Args {
   const int32_t* conn;
@@ -62,6 +81,7 @@ struct Args {
   int32_t v4_ok;       // values is 16-byte aligned
   int32_t xchg;        // FP32 CSR assembly through the exchange buffer
   int32_t pf_off;      // byte offset of the prefetch buffer in shared memory (-1: none)
+  int32_t meta_off;    // byte offset of the second scatter-metadata buffer (warp-specialised kernel)
 };
 
 // Per-element shared-memory strides padded to odd word counts so that lanes
@@ -71,12 +91,18 @@ constexpr int kAStride = 407;    // 5 qp x 81 tangent entries, + 2
 constexpr int kFStride = 151;    // 5 qp x 30 force entries, + 1
 constexpr int kUStride = 31;
 
-template <typename T>
-struct Smem {
-  int32_t node[10][E];
+// Per-tile scatter metadata: CSR row bases and strides of the 10 nodes and
+// the slot blocks of the 32 elements.
+struct TileMeta {
   int32_t rbase[10][E];
   int32_t rstr[10][E];
   uint8_t blk[E][100];
+};
+
+template <typename T>
+struct Smem {
+  int32_t node[10][E];
+  TileMeta meta;
   T geo[16][E];
   T u[kUStride * E];
   T vel[kUStride * E];
@@ -89,8 +115,8 @@ struct Smem {
 // Stage the tile: connectivity, row bases, slot indices, geometry and the
 // nodal displacement / velocity gathers.
 // ---------------------------------------------------------------------------
-template <typename T, bool NEED_PATTERN>
-__device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t e0) {
+template <typename T, bool NEED_PATTERN, bool WS = false>
+__device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t e0, TileMeta& mt) {
   const int tid = threadIdx.x;
   for (int t = tid; t < E * 10; t += NT) {
     const int e = t / 10, a = t % 10;
@@ -98,23 +124,23 @@ __device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t
     sm.node[a][e] = node;
     if (NEED_PATTERN) {
       const int p0 = A.node_ptr[node], p1 = A.node_ptr[node + 1];
-      sm.rbase[a][e] = 9 * p0;
-      sm.rstr[a][e] = 3 * (p1 - p0);
+      mt.rbase[a][e] = 9 * p0;
+      mt.rstr[a][e] = 3 * (p1 - p0);
     }
   }
   if (NEED_PATTERN) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(A.blk + e0 * 100);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.blk[0][0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&mt.blk[0][0]);
     for (int t = tid; t < E * 25; t += NT) dst[t] = src[t];
   }
   for (int t = tid; t < E * 16; t += NT) {
     const int e = t / 16, c = t % 16;
     sm.geo[c][e] = A.geo[(e0 + e) * 16 + c];
   }
-  __syncthreads();
+  bar_compute<WS>();
   const double h = A.h;
   for (int t = tid; t < E * 30; t += NT) {
-    const int e = t / 30, c = t % 30;
+    const int c = t / E, e = t % E;
     const int a = c / 3, d = c % 3;
     const int64_t g = 3 * (int64_t)sm.node[a][e] + d;
     const double vv = A.v[g];
@@ -122,7 +148,7 @@ __device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t
     sm.u[c * E + e] = T(x - A.X[g]);
     sm.vel[c * E + e] = T(vv);
   }
-  __syncthreads();
+  bar_compute<WS>();
 }
 
 // ---------------------------------------------------------------------------
@@ -179,14 +205,15 @@ __device__ __forceinline__ void prefetch_stage1(const Args<T>& A, Prefetch<T>& P
 template <typename T>
 __device__ __forceinline__ void prefetch_stage2(const Args<T>& A, Prefetch<T>& P) {
   const int tid = threadIdx.x;
+  // element index fastest: consecutive threads write consecutive words
   for (int t = tid; t < E * 10; t += NT) {
-    const int e = t / 10, a = t % 10;
-    const int node = P.conn[t];
+    const int a = t / E, e = t % E;
+    const int node = P.conn[e * 10 + a];
     cp_async4(&P.nptr[0][a][e], A.node_ptr + node);
     cp_async4(&P.nptr[1][a][e], A.node_ptr + node + 1);
   }
   for (int t = tid; t < E * 30; t += NT) {
-    const int e = t / 30, c = t % 30;
+    const int c = t / E, e = t % E;
     const int64_t g = 3 * (int64_t)P.conn[e * 10 + c / 3] + c % 3;
     cp_async8(&P.qn[c * E + e], A.q_n + g);
     cp_async8(&P.vv[c * E + e], A.v + g);
@@ -196,21 +223,21 @@ __device__ __forceinline__ void prefetch_stage2(const Args<T>& A, Prefetch<T>& P
 }
 
 // Stage the next tile from the prefetch buffer (as load_tile does from global).
-template <typename T, bool NEED_PATTERN>
-__device__ __forceinline__ void unpack_tile(const Args<T>& A, Smem<T>& sm, const Prefetch<T>& P) {
+template <typename T, bool NEED_PATTERN, bool WS = false>
+__device__ __forceinline__ void unpack_tile(const Args<T>& A, Smem<T>& sm, const Prefetch<T>& P, TileMeta& mt) {
   const int tid = threadIdx.x;
   for (int t = tid; t < E * 10; t += NT) {
-    const int e = t / 10, a = t % 10;
-    sm.node[a][e] = P.conn[t];
+    const int a = t / E, e = t % E;
+    sm.node[a][e] = P.conn[e * 10 + a];
     if (NEED_PATTERN) {
       const int p0 = P.nptr[0][a][e], p1 = P.nptr[1][a][e];
-      sm.rbase[a][e] = 9 * p0;
-      sm.rstr[a][e] = 3 * (p1 - p0);
+      mt.rbase[a][e] = 9 * p0;
+      mt.rstr[a][e] = 3 * (p1 - p0);
     }
   }
   if (NEED_PATTERN) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(P.blk);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.blk[0][0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&mt.blk[0][0]);
     for (int t = tid; t < E * 25; t += NT) dst[t] = src[t];
   }
   for (int t = tid; t < E * 16; t += NT) {
@@ -225,7 +252,7 @@ __device__ __forceinline__ void unpack_tile(const Args<T>& A, Smem<T>& sm, const
     sm.u[c * E + e] = T(x - P.XX[t]);
     sm.vel[c * E + e] = T(vv);
   }
-  __syncthreads();
+  bar_compute<WS>();
 }
 
 // Gradients of the 10 shape functions at barycentric point L (straight-sided
@@ -372,13 +399,13 @@ __device__ __forceinline__ void tangent_blockrow(const Args<T>& A, const Smem<T>
     for (int k = 0; k < 3; ++k)
       if (k == i) acc[j][k] += ms * T(c_mass420[a][b]);
     if (A.values) {
-      const int s_row = sm.rbase[a][e] + sm.rstr[a][e] * i + 3 * sm.blk[e][a * 10 + b];
+      const int s_row = sm.meta.rbase[a][e] + sm.meta.rstr[a][e] * i + 3 * sm.meta.blk[e][a * 10 + b];
 #pragma unroll
       for (int k = 0; k < 3; ++k) atomic_add_t(&A.values[s_row + k], acc[j][k]);
       if (j > 0) {
-        const int kb = 3 * sm.blk[e][b * 10 + a] + i;
+        const int kb = 3 * sm.meta.blk[e][b * 10 + a] + i;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) atomic_add_t(&A.values[sm.rbase[b][e] + sm.rstr[b][e] * k + kb], acc[j][k]);
+        for (int k = 0; k < 3; ++k) atomic_add_t(&A.values[sm.meta.rbase[b][e] + sm.meta.rstr[b][e] * k + kb], acc[j][k]);
       }
     }
     if (A.K_elem) {
@@ -474,12 +501,15 @@ __device__ __forceinline__ void red_run(const Args<float>& A, int s, float x0, f
 // block-row pair made the kernel miss in the instruction cache).
 template <int P>
 __device__ __forceinline__ void tangent_xchg_accumulate(const Args<float>& A, const Smem<float>& sm, float* X,
-                                                        int i) {
+                                                        int i, bool wait_empty = false) {
   constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
   const int e = threadIdx.x & 31;
   float acc0[n0][3], acc1[n1][3];
   accumulate_blockrow<float, a0, n0>(A, sm, i, acc0);
   accumulate_blockrow<float, a1, n1>(A, sm, i, acc1);
+  // warp-specialised kernel: the scatter warps must have finished issuing the
+  // previous tile from X (every compute warp takes this branch alike)
+  if (wait_empty) bar_sync_all(kBarEmpty);
   const int base = e * 495 + P * 99 + i * 3;
 #pragma unroll
   for (int j = 0; j < n0; ++j)
@@ -491,10 +521,10 @@ __device__ __forceinline__ void tangent_xchg_accumulate(const Args<float>& A, co
     for (int k = 0; k < 3; ++k) X[base + (n0 + j) * 9 + k] = acc1[j][k];
 }
 
-__device__ __forceinline__ void tangent_xchg_scatter(const Args<float>& A, const Smem<float>& sm, const float* X,
-                                                     int64_t e0, int P, int i) {
+__device__ __forceinline__ void tangent_xchg_scatter(const Args<float>& A, const TileMeta& mt, const float* X,
+                                                     int64_t e0, int64_t real_end, int P, int i) {
   const int e = threadIdx.x & 31;
-  if (e0 + e >= A.real_end) return;
+  if (e0 + e >= real_end) return;
   const int n0 = 10 - P;
   const float* xb = X + e * 495 + P * 99;
 #pragma unroll 1
@@ -502,10 +532,10 @@ __device__ __forceinline__ void tangent_xchg_scatter(const Args<float>& A, const
     const int a = j < n0 ? P : 9 - P;
     const int b = j < n0 ? P + j : 9 - P + (j - n0);
     const float* blkv = xb + j * 9;
-    red_run(A, sm.rbase[a][e] + sm.rstr[a][e] * i + 3 * sm.blk[e][a * 10 + b], blkv[3 * i], blkv[3 * i + 1],
+    red_run(A, mt.rbase[a][e] + mt.rstr[a][e] * i + 3 * mt.blk[e][a * 10 + b], blkv[3 * i], blkv[3 * i + 1],
             blkv[3 * i + 2]);
     if (b != a)
-      red_run(A, sm.rbase[b][e] + sm.rstr[b][e] * i + 3 * sm.blk[e][b * 10 + a], blkv[i], blkv[3 + i],
+      red_run(A, mt.rbase[b][e] + mt.rstr[b][e] * i + 3 * mt.blk[e][b * 10 + a], blkv[i], blkv[3 + i],
               blkv[6 + i]);
   }
 }
@@ -549,7 +579,7 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
           default: tangent_xchg_accumulate<4>(A, sm, X, i); break;
         }
         __syncthreads();               // reached by every thread of the block
-        tangent_xchg_scatter(A, sm, X, e0, p, i);
+        tangent_xchg_scatter(A, sm.meta, X, e0, A.real_end, p, i);
         return;
       }
     }
@@ -752,7 +782,7 @@ __global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S, i
   int t = blockIdx.x;
   if (t >= S.ntiles) return;                         // uniform over the block
   int64_t e0 = cur.e0(S, t);
-  load_tile<T, DO_TANGENT>(A, sm, e0);
+  load_tile<T, DO_TANGENT>(A, sm, e0, sm.meta);
   if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t + (int)gridDim.x;
   __syncthreads();
   while (true) {
@@ -771,12 +801,128 @@ __global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S, i
     if (P) {
       cur = nxt;
       e0 = e0_next;
-      unpack_tile<T, DO_TANGENT>(A, sm, *P);         // ends with a barrier (also publishes s_next)
+      unpack_tile<T, DO_TANGENT>(A, sm, *P, sm.meta);  // ends with a barrier (also publishes s_next)
     } else {
       e0 = cur.e0(S, t);
-      load_tile<T, DO_TANGENT>(A, sm, e0);           // ends with a barrier (also publishes s_next)
+      load_tile<T, DO_TANGENT>(A, sm, e0, sm.meta);    // ends with a barrier (also publishes s_next)
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised float32 CSR assembly: 15 compute warps as above and 5
+// scatter warps.  The compute warps stage, evaluate and accumulate tile k and
+// park its blocks in X; the scatter warps issue tile k's reductions from X
+// while the compute warps already evaluate tile k + 1, so the L2 reduction
+// traffic overlaps the arithmetic instead of following it.  Hand-off of X by
+// named barriers (every arrive is matched by exactly one sync):
+//   compute, tile k >= 1: bar.sync EMPTY (tile k - 1 issued), write X(k),
+//                         bar.arrive FULL;  after the last tile n - 1: bar.sync
+//                         EMPTY, mark the end, bar.arrive FULL  (n + 1 FULL
+//                         arrives, n EMPTY syncs)
+//   scatter, k = 0, 1, ...: bar.sync FULL; stop at the end mark; issue tile k;
+//                         bar.arrive EMPTY  (n + 1 FULL syncs, n EMPTY arrives)
+// The scatter metadata (row bases, strides, slot blocks) of consecutive tiles
+// alternate between two buffers, so staging tile k + 1 does not disturb the
+// scatter of tile k.
+// ---------------------------------------------------------------------------
+template <int MAT, bool KV, bool DO_FORCE>
+__device__ __forceinline__ void ws_tile(const Args<float>& A, unsigned char* smem_raw, float* X,
+                                        Prefetch<float>* P, int64_t e0, int64_t e0_next, bool wait_empty) {
+  Smem<float>& sm = *reinterpret_cast<Smem<float>*>(smem_raw);
+  if (e0_next >= 0) prefetch_stage1(A, *P, e0_next);
+  bool inverted = false;
+  qp_phase<float, MAT, KV, true>(A, sm, inverted);
+  if (inverted && (e0 + (threadIdx.x & 31)) < A.real_end) atomicOr(A.flags, kFlagInverted);
+  cp_async_wait_all();
+  bar_compute<true>();
+  if (e0_next >= 0) prefetch_stage2(A, *P);
+  if (DO_FORCE) force_phase(A, sm, e0);
+  const int w = threadIdx.x >> 5;
+  const int p = w / 3, i = w % 3;
+  switch (p) {                                       // warp-uniform
+    case 0: tangent_xchg_accumulate<0>(A, sm, X, i, wait_empty); break;
+    case 1: tangent_xchg_accumulate<1>(A, sm, X, i, wait_empty); break;
+    case 2: tangent_xchg_accumulate<2>(A, sm, X, i, wait_empty); break;
+    case 3: tangent_xchg_accumulate<3>(A, sm, X, i, wait_empty); break;
+    default: tangent_xchg_accumulate<4>(A, sm, X, i, wait_empty); break;
+  }
+}
+
+template <int COMBO, bool DO_FORCE>
+__device__ __forceinline__ void ws_dispatch(const Args<float>& a, unsigned char* smem_raw, float* X,
+                                            Prefetch<float>* P, int64_t e0, int64_t e0_next, bool wait_empty,
+                                            int combo) {
+  if constexpr (COMBO < 4) {
+    ws_tile<COMBO / 2, (COMBO % 2) != 0, DO_FORCE>(a, smem_raw, X, P, e0, e0_next, wait_empty);
+  } else {
+    switch (combo) {                                 // block-uniform
+      case 0: ws_tile<TL_SVK, false, DO_FORCE>(a, smem_raw, X, P, e0, e0_next, wait_empty); break;
+      case 1: ws_tile<TL_SVK, true, DO_FORCE>(a, smem_raw, X, P, e0, e0_next, wait_empty); break;
+      case 2: ws_tile<TL_MOONEY_RIVLIN, false, DO_FORCE>(a, smem_raw, X, P, e0, e0_next, wait_empty); break;
+      default: ws_tile<TL_MOONEY_RIVLIN, true, DO_FORCE>(a, smem_raw, X, P, e0, e0_next, wait_empty); break;
+    }
+  }
+}
+
+template <int COMBO, bool DO_FORCE>
+__global__ void __launch_bounds__(NTW, 1) elem_kernel_ws(Args<float> A, SegTable<float> S, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_next;
+  __shared__ long long s_e0[2], s_end[2];
+  Smem<float>& sm = *reinterpret_cast<Smem<float>*>(smem_raw);
+  float* X = reinterpret_cast<float*>(smem_raw + sizeof(Smem<float>));
+  Prefetch<float>* P = reinterpret_cast<Prefetch<float>*>(smem_raw + A.pf_off);
+  TileMeta* meta1 = reinterpret_cast<TileMeta*>(smem_raw + A.meta_off);
+  int t = blockIdx.x;
+  if (t >= S.ntiles) return;                         // uniform over the block
+  const int warp = threadIdx.x >> 5;
+  if (warp >= NWARP) {                               // scatter warps: block-row pair warp - 15
+    const int sp = warp - NWARP;
+    for (int k = 0;; ++k) {
+      bar_sync_all(kBarFull);
+      const int par = k & 1;
+      const long long e0 = s_e0[par];
+      if (e0 < 0) break;
+      const TileMeta& mt = par ? *meta1 : sm.meta;
+      const long long end = s_end[par];
+      for (int i = 0; i < 3; ++i) tangent_xchg_scatter(A, mt, X, e0, end, sp, i);
+      bar_arrive_all(kBarEmpty);
+    }
+    return;
+  }
+  SegWalk cur, nxt;
+  int64_t e0 = cur.e0(S, t);
+  load_tile<float, true, true>(A, sm, e0, sm.meta);
+  if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t + (int)gridDim.x;
+  bar_compute<true>();
+  int k = 0;
+  for (;; ++k) {
+    const int par = k & 1;
+    const int t_next = s_next;
+    Args<float> a = A;
+    a.mat = S.s[cur.sg].mat;
+    a.real_end = S.s[cur.sg].real_end;
+    nxt = cur;
+    const int64_t e0_next = t_next < S.ntiles ? nxt.e0(S, t_next) : -1;
+    ws_dispatch<COMBO, DO_FORCE>(a, smem_raw, X, P, e0, e0_next, k > 0, S.s[cur.sg].combo);
+    if (threadIdx.x == 0) {
+      s_e0[par] = e0;
+      s_end[par] = a.real_end;
+    }
+    bar_arrive_all(kBarFull);                        // X and the tile's scatter data are ready
+    cp_async_wait_all();
+    bar_compute<true>();                             // the next tile's prefetch has landed
+    if (t_next >= S.ntiles) break;
+    if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t_next + (int)gridDim.x;
+    t = t_next;
+    cur = nxt;
+    e0 = e0_next;
+    unpack_tile<float, true, true>(A, sm, *P, par ? sm.meta : *meta1);   // ends with a compute barrier
+  }
+  bar_sync_all(kBarEmpty);                           // the last tile has been issued
+  if (threadIdx.x == 0) s_e0[(k + 1) & 1] = -1;
+  bar_arrive_all(kBarFull);
 }
 
 template <typename T, bool DO_FORCE, bool DO_TANGENT>
@@ -787,8 +933,16 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   const bool xchg = std::is_same<T, float>::value && DO_TANGENT && values && !K_elem && m->tune.elem_xchg;
   size_t smem = DO_TANGENT ? sizeof(Smem<T>) + (xchg ? sizeof(float) * kXFloats : 0)
                            : offsetof(Smem<T>, A);
-  // the float32 kernels prefetch the next tile into a buffer after the rest
-  int pf_off = -1;
+  // the warp-specialised float32 assembly keeps a second scatter-metadata
+  // buffer; the float32 kernels prefetch the next tile into a buffer after
+  // the rest
+  const bool ws = xchg && m->tune.elem_prefetch && m->tune.elem_ws && !m->tune.elem_full_grid;
+  int meta_off = -1, pf_off = -1;
+  if (ws) {
+    smem = (smem + 15) / 16 * 16;
+    meta_off = (int)smem;
+    smem += sizeof(TileMeta);
+  }
   if (std::is_same<T, float>::value && m->tune.elem_prefetch) {
     smem = (smem + 15) / 16 * 16;
     pf_off = (int)smem;
@@ -818,6 +972,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   A.v4_ok = ((reinterpret_cast<uintptr_t>(values) & 15u) == 0) ? 1 : 0;
   A.xchg = xchg ? 1 : 0;
   A.pf_off = pf_off;
+  A.meta_off = meta_off;
   cudaEvent_t t0 = timer_open(m);
   // Segments in groups of at most kMaxSeg, one persistent launch per group.
   // The float32 kernels include an all-materials variant; the float64 ones
@@ -870,7 +1025,20 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       continue;
     }
     void (*kern)(Args<T>, SegTable<T>, int*) = nullptr;
-    switch (mixed ? 4 : combo0) {
+    int threads = NT;
+    if constexpr (std::is_same<T, float>::value && DO_TANGENT) {
+      if (ws) {
+        threads = NTW;
+        switch (mixed ? 4 : combo0) {
+          case 0: kern = elem_kernel_ws<0, DO_FORCE>; break;
+          case 1: kern = elem_kernel_ws<1, DO_FORCE>; break;
+          case 2: kern = elem_kernel_ws<2, DO_FORCE>; break;
+          case 3: kern = elem_kernel_ws<3, DO_FORCE>; break;
+          default: kern = elem_kernel_ws<4, DO_FORCE>; break;
+        }
+      }
+    }
+    if (!kern) switch (mixed ? 4 : combo0) {
       case 0: kern = elem_kernel<T, 0, DO_FORCE, DO_TANGENT>; break;
       case 1: kern = elem_kernel<T, 1, DO_FORCE, DO_TANGENT>; break;
       case 2: kern = elem_kernel<T, 2, DO_FORCE, DO_TANGENT>; break;
@@ -882,7 +1050,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     if (!kern) return fail(m, TL_ERR_UNSUPPORTED, "element kernel selection");
     TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 1;
-    TL_CUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+    TL_CUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
     const bool full = m->tune.elem_full_grid != 0;
     const int grid = full ? S.ntiles : (int)std::min<int64_t>(S.ntiles, (int64_t)m->num_sms * std::max(occ, 1));
     int* counter = nullptr;
@@ -891,7 +1059,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       TL_CUDA(m, cudaMemsetAsync(counter, 0, sizeof(int), m->stream));
     }
     ++nlaunch;
-    kern<<<(unsigned)grid, NT, smem, m->stream>>>(A, S, counter);
+    kern<<<(unsigned)grid, (unsigned)threads, smem, m->stream>>>(A, S, counter);
     TL_CUDA(m, cudaGetLastError());
     ++m->launches;
   }

@@ -45,10 +45,12 @@ struct NewtonGraph;  // captured Newton step (tl_newton.cu)
 
 // Launch shapes picked per handle by the autotuner (tl_tune.cu).
 struct Tune {
-  int spmv_group = 8;     // lanes per node in the PCG product H p (4, 8, 16)
+  int spmv_group = 4;     // lanes per node in the PCG product H p (4, 8, 16)
   int elem_xchg = 1;      // FP32 assembly: 1 = exchanged vector runs, 0 = scalar scatter
   int elem_full_grid = 0; // element kernels: 0 = persistent grid (SMs x occupancy), 1 = one CTA per tile
   int elem_prefetch = 1;  // float32 element kernels: 1 = prefetch the next tile with cp.async
+  int elem_ws = 0;        // float32 CSR assembly: 1 = warp-specialised scatter (needs prefetch, persistent grid)
+  int residual_lanes = 1; // lanes per node in the residual (1 or 4)
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };
@@ -90,6 +92,7 @@ struct tl_mesh {
   uint32_t* d_flags = nullptr;    // sticky device status
   int* d_tile_counters = nullptr; // kTileCounters dynamic tile queues
   double* d_partials = nullptr;   // reduction partials
+  double* d_dv = nullptr;         // v - v_n of the last residual (3 nn)
   int partials_cap = 0;
 
   tl::Solver* solver = nullptr;

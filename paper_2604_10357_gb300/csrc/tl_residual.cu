@@ -7,10 +7,10 @@
 //   Sec. 4.4 (gradient): one thread per coefficient row of M, no atomics;
 //   eq. hessian: the h^2 rho C_q^T C_q term (identity rows for clamps).
 //
-// A group of four lanes per node handles its three DOFs (the mass CSR row is
-// shared by the three components); ||g||^2 is reduced per block into a
-// partials array and summed by a second one-block kernel, so the norm is
-// deterministic.
+// One thread (or a group of lanes) per node handles its three DOFs (the mass
+// CSR row is shared by the three components); ||g||^2 is reduced per block
+// into a partials array and summed by a second one-block kernel, so the norm
+// is deterministic.
 #include <mutex>
 
 #include "tl_internal.cuh"
@@ -28,35 +28,46 @@ constexpr int kResBlock = 256;
 constexpr int kNoAllocMaxBlocks = 16384;                    // nn <= 4,194,304
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 
-// kResLanes lanes per node: lane l sums the mass row entries l, l + kResLanes,
-// ... (the rows have ~28 entries), the group combines the three sums and its
-// first lane forms the node's three residual components.  A block holds
-// kResBlock nodes, so the partial count is the same as with one thread per
-// node.
-constexpr int kResLanes = 4;
-
-__global__ void __launch_bounds__(kResBlock * kResLanes)
+// LANES lanes per node: lane l sums the mass row entries l, l + LANES, ...
+// (rows have ~28 entries), the group combines the three sums and its first
+// lane forms the node's three residual components.  A block holds kResBlock
+// nodes, so the partial count does not depend on LANES.  dv = v - v_n is read
+// precomputed when given (one subtraction per DOF instead of one per mass
+// entry: on GB300 the float64 subtractions and multiply-adds bound this
+// kernel), else formed inline.
+template <int LANES>
+__global__ void __launch_bounds__(kResBlock * LANES)
     residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass, const double* mrow,
                     const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double rho, double gx,
-                    double gy, double gz, const double* q_n, const double* v_n, const double* v,
+                    double gy, double gz, const double* q_n, const double* v_n, const double* v, const double* dv,
                     const double* f_int, const double* f_ext, const double* lambda, double* g,
                     double* partials) {
-  __shared__ double red[kResBlock * kResLanes / 32];
-  const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kResLanes;
-  const int l = threadIdx.x & (kResLanes - 1);
+  __shared__ double red[kResBlock * LANES / 32];
+  const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LANES;
+  const int l = threadIdx.x & (LANES - 1);
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, sq = 0.0;
   if (I < nn) {
     const int p0 = node_ptr[I], p1 = node_ptr[I + 1];
-    for (int p = p0 + l; p < p1; p += kResLanes) {
-      const int64_t J = node_col[p];
-      const double mij = mass[p];
-      acc0 += mij * (v[3 * J] - v_n[3 * J]);
-      acc1 += mij * (v[3 * J + 1] - v_n[3 * J + 1]);
-      acc2 += mij * (v[3 * J + 2] - v_n[3 * J + 2]);
+    if (dv) {
+      for (int p = p0 + l; p < p1; p += LANES) {
+        const int64_t J = node_col[p];
+        const double mij = mass[p];
+        acc0 += mij * dv[3 * J];
+        acc1 += mij * dv[3 * J + 1];
+        acc2 += mij * dv[3 * J + 2];
+      }
+    } else {
+      for (int p = p0 + l; p < p1; p += LANES) {
+        const int64_t J = node_col[p];
+        const double mij = mass[p];
+        acc0 += mij * (v[3 * J] - v_n[3 * J]);
+        acc1 += mij * (v[3 * J + 1] - v_n[3 * J + 1]);
+        acc2 += mij * (v[3 * J + 2] - v_n[3 * J + 2]);
+      }
     }
   }
 #pragma unroll
-  for (int o = kResLanes / 2; o > 0; o >>= 1) {
+  for (int o = LANES / 2; o > 0; o >>= 1) {
     acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
     acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
     acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
@@ -89,6 +100,11 @@ __global__ void __launch_bounds__(kResBlock * kResLanes)
   }
 }
 
+__global__ void velocity_change(const double* v, const double* v_n, int64_t n, double* dv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dv[i] = v[i] - v_n[i];
+}
+
 __global__ void finish_norm(const double* partials, int n, double* out, uint32_t* flags) {
   __shared__ double red[32];
   double t = 0.0;
@@ -116,6 +132,7 @@ __global__ void add_diag(const int32_t* diag, int64_t n, T value, T* values) {
 
 // Norm partials owned by the handle (one per block of kResBlock nodes).
 tl_status residual_ensure(tl_mesh* m) {
+  if (!m->d_dv) TL_CUDA(m, cudaMalloc(&m->d_dv, sizeof(double) * 3 * m->nn));
   const int nb = (int)((m->nn + kResBlock - 1) / kResBlock);
   if (nb > m->partials_cap) {
     if (m->d_partials) cudaFree(m->d_partials);
@@ -134,14 +151,20 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   TL_TRY(residual_ensure(m));
   cudaEvent_t t0 = timer_open(m);
   // f_int may alias g: each thread reads its own entries before writing them
-  residual_kernel<<<nb, kResBlock * kResLanes, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow,
-                                                    m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
-                                                    p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_int,
-                                                    f_ext, lambda, g, m->d_partials);
+  const int64_t n3 = 3 * m->nn;
+  velocity_change<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv);
+  if (m->tune.residual_lanes == 4)
+    residual_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
+        m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
+        p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials);
+  else
+    residual_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
+        m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
+        p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials);
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(m->d_partials, nb, g_norm, m->d_flags);
   TL_CUDA(m, cudaGetLastError());
-  m->launches += 2;
+  m->launches += 3;
   timer_close(m, t0, kTimeResidual);
   return TL_OK;
 }
@@ -202,9 +225,9 @@ extern "C" tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, co
   double* partials = nullptr;
   tl_status s = noalloc_scratch(m, dev, &partials);
   if (s != TL_OK) return s;
-  residual_kernel<<<(unsigned)nb, kResBlock * kResLanes, 0, m->stream>>>(
+  residual_kernel<1><<<(unsigned)nb, kResBlock, 0, m->stream>>>(
       m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
-      p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, f_int, f_ext, lambda, g, partials);
+      p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, nullptr, f_int, f_ext, lambda, g, partials);
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(partials, (int)nb, g_norm, m->d_flags);
   TL_CUDA(m, cudaGetLastError());

@@ -8,8 +8,11 @@
 //     (SMs x resident CTAs, tiles from a device counter) or one CTA per tile;
 //     for the float32 form also the scatter strategy (exchanged 3-entry runs
 //     as vector reductions, or one scalar reduction per entry) and the
-//     cp.async prefetch of the next tile (or none);
-//   * PCG product H p: 4, 8 or 16 lanes per node.
+//     cp.async prefetch of the next tile (or none), and warp specialisation
+//     (scatter warps issue a tile's reductions while the compute warps
+//     evaluate the next tile);
+//   * PCG product H p: 4, 8 or 16 lanes per node;
+//   * residual: 1 or 4 lanes per node.
 // Each variant is warmed up once and timed over `reps` launches with CUDA
 // events on the handle's stream; the fastest is kept in the handle and used by
 // every later call (a captured Newton graph is rebuilt on its next use).
@@ -66,30 +69,35 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   tl_status st = TL_OK;
   // element pass: (prefetch, xchg, full grid) variants; the float64 kernels
   // have neither the exchange nor the prefetch
-  struct V { int pf, xchg, full; };
+  struct V { int pf, xchg, full, ws; };
   std::vector<V> variants;
+  if (fp32) variants.push_back({1, 1, 0, 1});       // warp-specialised
   for (int pf = fp32 ? 1 : 0; pf >= 0; --pf)
     for (int xchg = fp32 ? 1 : 0; xchg >= 0; --xchg)
-      for (int full = 0; full <= 1; ++full) variants.push_back({pf, xchg, full});
+      for (int full = 0; full <= 1; ++full) variants.push_back({pf, xchg, full, 0});
   float best = 1e30f;
   Tune chosen = saved;
   for (size_t k = 0; k < variants.size() && st == TL_OK; ++k) {
     m->tune.elem_prefetch = variants[k].pf;
     m->tune.elem_xchg = variants[k].xchg;
     m->tune.elem_full_grid = variants[k].full;
+    m->tune.elem_ws = variants[k].ws;
     float ms = 0.f;
     st = time_reps(m, reps, [&]() {
       tl_status s2 = launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
       return s2;
     }, &ms);
     if (st != TL_OK) break;
-    const int slot = 4 * (1 - variants[k].pf) + 2 * (1 - variants[k].xchg) + variants[k].full;
-    r.ms_element[slot] = ms;
+    if (variants[k].ws)
+      r.ms_ws = ms;
+    else
+      r.ms_element[4 * (1 - variants[k].pf) + 2 * (1 - variants[k].xchg) + variants[k].full] = ms;
     if (ms < best) {
       best = ms;
       chosen.elem_prefetch = variants[k].pf;
       chosen.elem_xchg = variants[k].xchg;
       chosen.elem_full_grid = variants[k].full;
+      chosen.elem_ws = variants[k].ws;
     }
   }
   // PCG product: lanes per node
@@ -106,9 +114,35 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
       chosen.spmv_group = groups[k];
     }
   }
+  // residual: lanes per node (zero force, the handle's current lambda-free state)
+  double* g = nullptr;
+  if (st == TL_OK && cudaMalloc(&g, sizeof(double) * (3 * m->nn + 1)) != cudaSuccess)
+    st = fail(m, TL_ERR_OOM, "autotune buffers");
+  if (st == TL_OK) st = residual_ensure(m);
+  if (st == TL_OK && cudaMemsetAsync(f, 0, sizeof(double) * 3 * m->nn, m->stream) != cudaSuccess)
+    st = fail(m, TL_ERR_CUDA, "memset");
+  best = 1e30f;
+  const int lanes[2] = {1, 4};
+  tl_params prm = {};
+  prm.h = h;
+  prm.rho_alm = 1e12;
+  for (int k = 0; k < 2 && st == TL_OK; ++k) {
+    m->tune.residual_lanes = lanes[k];
+    float ms = 0.f;
+    st = time_reps(m, reps, [&]() {
+      return launch_residual(m, &prm, q_n, v, v, f, nullptr, nullptr, g, g + 3 * m->nn);
+    }, &ms);
+    if (st != TL_OK) break;
+    r.ms_residual[k] = ms;
+    if (ms < best) {
+      best = ms;
+      chosen.residual_lanes = lanes[k];
+    }
+  }
   cudaStreamSynchronize(m->stream);
   cudaFree(values);
   cudaFree(f);
+  if (g) cudaFree(g);
   if (st != TL_OK) {
     m->tune = saved;
     return st;
@@ -120,6 +154,8 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.elem_xchg = chosen.elem_xchg;
   r.elem_full_grid = chosen.elem_full_grid;
   r.elem_prefetch = chosen.elem_prefetch;
+  r.elem_ws = chosen.elem_ws;
+  r.residual_lanes = chosen.residual_lanes;
   if (out) *out = r;
   return TL_OK;
 }
@@ -131,6 +167,8 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.elem_xchg = m->tune.elem_xchg;
   r.elem_full_grid = m->tune.elem_full_grid;
   r.elem_prefetch = m->tune.elem_prefetch;
+  r.elem_ws = m->tune.elem_ws;
+  r.residual_lanes = m->tune.residual_lanes;
   *out = r;
   return TL_OK;
 }
@@ -139,10 +177,13 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   if (!m || !in) return TL_ERR_INVALID_ARG;
   if (in->spmv_group != 4 && in->spmv_group != 8 && in->spmv_group != 16) return TL_ERR_INVALID_ARG;
   if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1) ||
-      (in->elem_prefetch != 0 && in->elem_prefetch != 1))
+      (in->elem_prefetch != 0 && in->elem_prefetch != 1) || (in->elem_ws != 0 && in->elem_ws != 1) ||
+      (in->residual_lanes != 1 && in->residual_lanes != 4))
     return TL_ERR_INVALID_ARG;
   m->tune.spmv_group = in->spmv_group;
   m->tune.elem_prefetch = in->elem_prefetch;
+  m->tune.elem_ws = in->elem_ws;
+  m->tune.residual_lanes = in->residual_lanes;
   m->tune.elem_xchg = in->elem_xchg;
   m->tune.elem_full_grid = in->elem_full_grid;
   m->tune.generation += 1;
