@@ -283,9 +283,10 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *     (SMs x resident CTAs) or one CTA per 32-element tile; for
  *     TL_FP32_ELEM also the scatter (exchanged 3-entry runs issued as vector
  *     reductions, or one scalar reduction per entry), the prefetch of the
- *     next tile (cp.async into shared memory, or none) and warp
+ *     next tile (cp.async into shared memory, or none), warp
  *     specialisation (5 extra warps issue a tile's reductions while the
- *     compute warps evaluate the next tile);
+ *     compute warps evaluate the next tile) and two CTAs per SM (registers
+ *     capped at 64, no prefetch buffer);
  *   PCG product H p: 4, 8 or 16 lanes per node;
  *   residual: 1 or 4 lanes per node.
  * reps timed launches per variant after one warm-up.  Needs the pattern;
@@ -300,11 +301,13 @@ typedef struct tl_tune_result {
   int32_t elem_prefetch;      /* 1: cp.async prefetch of the next tile (FP32) */
   int32_t elem_ws;            /* 1: warp-specialised scatter (FP32; with xchg, prefetch, persistent grid) */
   int32_t residual_lanes;     /* lanes per node in the residual: 1 or 4 */
+  int32_t elem_occ2;          /* 1: two CTAs per SM (FP32 exchanged assembly, one material kind) */
+  int32_t _pad;
   float ms_element[8];        /* measured element-pass times without warp specialisation (0: not measured) */
   float ms_ws;                /* measured time of the warp-specialised variant (0: not measured) */
   float ms_spmv[3];
   float ms_residual[2];       /* residual with 1 and 4 lanes per node */
-  float _pad;
+  float ms_occ2;              /* measured time of the two-CTA variant (0: not measured) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

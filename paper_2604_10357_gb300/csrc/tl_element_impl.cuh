@@ -82,6 +82,7 @@ struct Args {
   int32_t xchg;        // FP32 CSR assembly through the exchange buffer
   int32_t pf_off;      // byte offset of the prefetch buffer in shared memory (-1: none)
   int32_t meta_off;    // byte offset of the second scatter-metadata buffer (warp-specialised kernel)
+  int32_t x_alias;     // 1: the exchange buffer overlays the force and tangent arrays (two CTAs per SM)
 };
 
 // Per-element shared-memory strides padded to odd word counts so that lanes
@@ -501,7 +502,7 @@ __device__ __forceinline__ void red_run(const Args<float>& A, int s, float x0, f
 // block-row pair made the kernel miss in the instruction cache).
 template <int P>
 __device__ __forceinline__ void tangent_xchg_accumulate(const Args<float>& A, const Smem<float>& sm, float* X,
-                                                        int i, bool wait_empty = false) {
+                                                        int i, bool wait_empty = false, bool block_sync = false) {
   constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
   const int e = threadIdx.x & 31;
   float acc0[n0][3], acc1[n1][3];
@@ -510,6 +511,9 @@ __device__ __forceinline__ void tangent_xchg_accumulate(const Args<float>& A, co
   // warp-specialised kernel: the scatter warps must have finished issuing the
   // previous tile from X (every compute warp takes this branch alike)
   if (wait_empty) bar_sync_all(kBarEmpty);
+  // two-CTA variant: X overlays the force and tangent arrays, which every
+  // warp must have finished reading (uniform over the block)
+  if (block_sync) __syncthreads();
   const int base = e * 495 + P * 99 + i * 3;
 #pragma unroll
   for (int j = 0; j < n0; ++j)
@@ -570,13 +574,15 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
     const int p = w / 3, i = w % 3;
     if constexpr (std::is_same<T, float>::value) {
       if (A.xchg) {                    // kernel-argument test: uniform over the block
-        float* X = reinterpret_cast<float*>(smem_raw + sizeof(Smem<float>));
+        const bool alias = A.x_alias != 0;
+        float* X = reinterpret_cast<float*>(alias ? smem_raw + offsetof(Smem<float>, fq)
+                                                  : smem_raw + sizeof(Smem<float>));
         switch (p) {                   // warp-uniform
-          case 0: tangent_xchg_accumulate<0>(A, sm, X, i); break;
-          case 1: tangent_xchg_accumulate<1>(A, sm, X, i); break;
-          case 2: tangent_xchg_accumulate<2>(A, sm, X, i); break;
-          case 3: tangent_xchg_accumulate<3>(A, sm, X, i); break;
-          default: tangent_xchg_accumulate<4>(A, sm, X, i); break;
+          case 0: tangent_xchg_accumulate<0>(A, sm, X, i, false, alias); break;
+          case 1: tangent_xchg_accumulate<1>(A, sm, X, i, false, alias); break;
+          case 2: tangent_xchg_accumulate<2>(A, sm, X, i, false, alias); break;
+          case 3: tangent_xchg_accumulate<3>(A, sm, X, i, false, alias); break;
+          default: tangent_xchg_accumulate<4>(A, sm, X, i, false, alias); break;
         }
         __syncthreads();               // reached by every thread of the block
         tangent_xchg_scatter(A, sm.meta, X, e0, A.real_end, p, i);
@@ -771,9 +777,12 @@ __global__ void __launch_bounds__(NTF) force_kernel(Args<T> A, SegTable<T> S) {
 // segment of a tile is found by walking the table forward.  COMBO < 4
 // compiles one (material, Kelvin-Voigt) pair, COMBO = 4 all four with a
 // block-uniform dispatch per tile (multi-material meshes and batches).  The
-// float32 kernels prefetch the next tile (A.pf_off >= 0).
-template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT>
-__global__ void __launch_bounds__(NT, 1) elem_kernel(Args<T> A, SegTable<T> S, int* counter) {
+// float32 kernels prefetch the next tile (A.pf_off >= 0).  MINB = 2 caps the
+// registers at 64 so that two CTAs share an SM (with the exchange buffer
+// overlaid on the force and tangent arrays and no prefetch, 105 KB each): the
+// latency of one CTA's staging hides behind the other's arithmetic.
+template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) elem_kernel(Args<T> A, SegTable<T> S, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next;
   Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
@@ -973,6 +982,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   A.xchg = xchg ? 1 : 0;
   A.pf_off = pf_off;
   A.meta_off = meta_off;
+  A.x_alias = 0;
   cudaEvent_t t0 = timer_open(m);
   // Segments in groups of at most kMaxSeg, one persistent launch per group.
   // The float32 kernels include an all-materials variant; the float64 ones
@@ -1038,6 +1048,24 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
         }
       }
     }
+    // two CTAs per SM (registers capped at 64; the exchange buffer overlays
+    // the force and tangent arrays; no prefetch buffer): one material kind only
+    Args<T> Al = A;
+    size_t smem_l = smem;
+    if constexpr (std::is_same<T, float>::value && DO_TANGENT) {
+      if (!kern && xchg && m->tune.elem_occ2 && !mixed) {
+        Al.x_alias = 1;
+        Al.pf_off = -1;
+        Al.meta_off = -1;
+        smem_l = sizeof(Smem<T>);
+        switch (combo0) {
+          case 0: kern = elem_kernel<T, 0, DO_FORCE, DO_TANGENT, 2>; break;
+          case 1: kern = elem_kernel<T, 1, DO_FORCE, DO_TANGENT, 2>; break;
+          case 2: kern = elem_kernel<T, 2, DO_FORCE, DO_TANGENT, 2>; break;
+          default: kern = elem_kernel<T, 3, DO_FORCE, DO_TANGENT, 2>; break;
+        }
+      }
+    }
     if (!kern) switch (mixed ? 4 : combo0) {
       case 0: kern = elem_kernel<T, 0, DO_FORCE, DO_TANGENT>; break;
       case 1: kern = elem_kernel<T, 1, DO_FORCE, DO_TANGENT>; break;
@@ -1048,9 +1076,9 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
         break;
     }
     if (!kern) return fail(m, TL_ERR_UNSUPPORTED, "element kernel selection");
-    TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
     int occ = 1;
-    TL_CUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+    TL_CUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem_l));
     const bool full = m->tune.elem_full_grid != 0;
     const int grid = full ? S.ntiles : (int)std::min<int64_t>(S.ntiles, (int64_t)m->num_sms * std::max(occ, 1));
     int* counter = nullptr;
@@ -1059,7 +1087,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       TL_CUDA(m, cudaMemsetAsync(counter, 0, sizeof(int), m->stream));
     }
     ++nlaunch;
-    kern<<<(unsigned)grid, (unsigned)threads, smem, m->stream>>>(A, S, counter);
+    kern<<<(unsigned)grid, (unsigned)threads, smem_l, m->stream>>>(Al, S, counter);
     TL_CUDA(m, cudaGetLastError());
     ++m->launches;
   }

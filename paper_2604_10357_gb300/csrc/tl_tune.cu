@@ -10,7 +10,7 @@
 //     as vector reductions, or one scalar reduction per entry) and the
 //     cp.async prefetch of the next tile (or none), and warp specialisation
 //     (scatter warps issue a tile's reductions while the compute warps
-//     evaluate the next tile);
+//     evaluate the next tile) and two CTAs per SM (64 registers, no prefetch);
 //   * PCG product H p: 4, 8 or 16 lanes per node;
 //   * residual: 1 or 4 lanes per node.
 // Each variant is warmed up once and timed over `reps` launches with CUDA
@@ -69,12 +69,15 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   tl_status st = TL_OK;
   // element pass: (prefetch, xchg, full grid) variants; the float64 kernels
   // have neither the exchange nor the prefetch
-  struct V { int pf, xchg, full, ws; };
+  struct V { int pf, xchg, full, ws, occ2; };
   std::vector<V> variants;
-  if (fp32) variants.push_back({1, 1, 0, 1});       // warp-specialised
+  if (fp32) {
+    variants.push_back({1, 1, 0, 1, 0});             // warp-specialised
+    variants.push_back({0, 1, 0, 0, 1});             // two CTAs per SM
+  }
   for (int pf = fp32 ? 1 : 0; pf >= 0; --pf)
     for (int xchg = fp32 ? 1 : 0; xchg >= 0; --xchg)
-      for (int full = 0; full <= 1; ++full) variants.push_back({pf, xchg, full, 0});
+      for (int full = 0; full <= 1; ++full) variants.push_back({pf, xchg, full, 0, 0});
   float best = 1e30f;
   Tune chosen = saved;
   for (size_t k = 0; k < variants.size() && st == TL_OK; ++k) {
@@ -82,6 +85,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     m->tune.elem_xchg = variants[k].xchg;
     m->tune.elem_full_grid = variants[k].full;
     m->tune.elem_ws = variants[k].ws;
+    m->tune.elem_occ2 = variants[k].occ2;
     float ms = 0.f;
     st = time_reps(m, reps, [&]() {
       tl_status s2 = launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
@@ -90,6 +94,8 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     if (st != TL_OK) break;
     if (variants[k].ws)
       r.ms_ws = ms;
+    else if (variants[k].occ2)
+      r.ms_occ2 = ms;
     else
       r.ms_element[4 * (1 - variants[k].pf) + 2 * (1 - variants[k].xchg) + variants[k].full] = ms;
     if (ms < best) {
@@ -98,6 +104,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
       chosen.elem_xchg = variants[k].xchg;
       chosen.elem_full_grid = variants[k].full;
       chosen.elem_ws = variants[k].ws;
+      chosen.elem_occ2 = variants[k].occ2;
     }
   }
   // PCG product: lanes per node
@@ -156,6 +163,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.elem_prefetch = chosen.elem_prefetch;
   r.elem_ws = chosen.elem_ws;
   r.residual_lanes = chosen.residual_lanes;
+  r.elem_occ2 = chosen.elem_occ2;
   if (out) *out = r;
   return TL_OK;
 }
@@ -169,6 +177,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.elem_prefetch = m->tune.elem_prefetch;
   r.elem_ws = m->tune.elem_ws;
   r.residual_lanes = m->tune.residual_lanes;
+  r.elem_occ2 = m->tune.elem_occ2;
   *out = r;
   return TL_OK;
 }
@@ -178,12 +187,13 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   if (in->spmv_group != 4 && in->spmv_group != 8 && in->spmv_group != 16) return TL_ERR_INVALID_ARG;
   if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1) ||
       (in->elem_prefetch != 0 && in->elem_prefetch != 1) || (in->elem_ws != 0 && in->elem_ws != 1) ||
-      (in->residual_lanes != 1 && in->residual_lanes != 4))
+      (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1))
     return TL_ERR_INVALID_ARG;
   m->tune.spmv_group = in->spmv_group;
   m->tune.elem_prefetch = in->elem_prefetch;
   m->tune.elem_ws = in->elem_ws;
   m->tune.residual_lanes = in->residual_lanes;
+  m->tune.elem_occ2 = in->elem_occ2;
   m->tune.elem_xchg = in->elem_xchg;
   m->tune.elem_full_grid = in->elem_full_grid;
   m->tune.generation += 1;

@@ -35,31 +35,36 @@ def test_autotune_reports_and_keeps_a_choice():
     assert rep["spmv_group"] in (4, 8, 16)
     assert rep["elem_xchg"] in (0, 1) and rep["elem_full_grid"] in (0, 1)
     assert all(t > 0 for t in rep["ms_element"]) and all(t > 0 for t in rep["ms_spmv"]) and rep["ms_ws"] > 0
-    best = min(min(rep["ms_element"]), rep["ms_ws"])
+    assert rep["ms_occ2"] > 0
+    best = min(min(rep["ms_element"]), rep["ms_ws"], rep["ms_occ2"])
     if rep["elem_ws"]:
         assert rep["ms_ws"] == best
+    elif rep["elem_occ2"]:
+        assert rep["ms_occ2"] == best
     else:
         k = 4 * (1 - rep["elem_prefetch"]) + 2 * (1 - rep["elem_xchg"]) + rep["elem_full_grid"]
         assert rep["ms_element"][k] == best
     assert rep["ms_spmv"][(4, 8, 16).index(rep["spmv_group"])] == min(rep["ms_spmv"])
     assert rep["ms_residual"][(1, 4).index(rep["residual_lanes"])] == min(rep["ms_residual"])
     cur = g.tune_get()
-    keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes")
+    keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes", "elem_occ2")
     assert all(cur[k] == rep[k] for k in keys)
     with pytest.raises(tl.TLError):
         g.tune_set(spmv_group=5)
 
 
-@pytest.mark.parametrize("prefetch,xchg,full_grid,ws",
-                         [(pf, x, f, 0) for pf in (0, 1) for x in (0, 1) for f in (0, 1)] + [(1, 1, 0, 1)])
-def test_every_element_variant_matches_oracle(xchg, full_grid, prefetch, ws):
+@pytest.mark.parametrize("prefetch,xchg,full_grid,ws,occ2",
+                         [(pf, x, f, 0, 0) for pf in (0, 1) for x in (0, 1) for f in (0, 1)]
+                         + [(1, 1, 0, 1, 0), (0, 1, 0, 0, 1)])
+def test_every_element_variant_matches_oracle(xchg, full_grid, prefetch, ws, occ2):
     tl = _tl()
     w = inputs.workload_small_svk()
     m = w["mesh"]
     om = asm.OracleMesh(m.X, m.conn, [w["material"]], fixed_nodes=m.fixed_nodes)
     g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
     g.build_pattern(m.fixed_nodes)
-    g.tune_set(spmv_group=8, elem_xchg=xchg, elem_full_grid=full_grid, elem_prefetch=prefetch, elem_ws=ws)
+    g.tune_set(spmv_group=8, elem_xchg=xchg, elem_full_grid=full_grid, elem_prefetch=prefetch, elem_ws=ws,
+               elem_occ2=occ2)
     h, rho = w["h"], 1e12
     vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho).cpu().numpy().astype(np.float64)
     ref = om.hessian_values(w["q_n"], w["v"], h, rho)
