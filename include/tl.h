@@ -97,8 +97,9 @@ typedef struct tl_params {
   int32_t max_outer;          /* K_max */
   int32_t linear_solver;      /* tl_linear_solver */
   int32_t lin_max_iter;       /* PCG iteration cap (0: 5000) */
-  double lin_rtol;            /* PCG: ||H dv + g|| <= eta ||g|| with eta = lin_rtol (0: 1e-10), */
-                              /* or, if lin_adaptive, eta = max(lin_rtol, 0.1 target / ||g||)   */
+  double lin_rtol;            /* PCG: ||H dv + g|| <= eta ||g|| with eta = lin_rtol (0: 1e-10,    */
+                              /* 1e-6 for TL_FP32_ELEM), or, if lin_adaptive,                   */
+                              /* eta = max(lin_rtol, min(0.5, 0.1 target / ||g||))              */
   int32_t lin_adaptive;       /* 1: inexact Newton (solve only as tightly as the target needs) */
   int32_t use_graph;          /* 1: run the step as one captured CUDA graph with device-side */
                               /* convergence control (PCG only; see tl_newton_step)           */
@@ -259,7 +260,7 @@ tl_status tl_timing_read(tl_mesh* m, tl_timing* out);
  *   Inner solver (p->linear_solver): TL_SOLVER_DIRECT = vendor sparse
  * Cholesky; TL_SOLVER_PCG = block-Jacobi conjugate gradients on the device to
  * ||H dv + g|| <= eta ||g|| (eta from lin_rtol / lin_adaptive; with
- * TL_FP32_ELEM eta is at least 1e-6, the resolution of a float32 H).  PCG
+ * TL_FP32_ELEM and lin_rtol = 0 eta is at least 1e-6).  PCG
  * stops early when p.Hp <= 0 (H not positive definite along p).
  *   p->use_graph = 1 (PCG only) runs the whole step as one captured CUDA
  * graph: the loops are conditional graph nodes, the tests on ||g||, ||c||

@@ -170,9 +170,13 @@ __global__ void ctl_outer(NewtonCtl* c, const double* cnorm, double eps_out, int
 
 constexpr int kPcgChunk = 8;   // PCG iterations between two device-side checks
 
-// A float32 Hessian (TL_FP32_ELEM) is symmetric only to rounding and defines
-// the Newton direction to about 1e-7 relative: PCG is not asked for more.
-double pcg_eta_min(const tl_mesh* m) { return m->precision == TL_FP32_ELEM ? 1e-6 : 0.0; }
+// PCG tolerance floor: lin_rtol when the caller sets it, else 1e-10 for the
+// float64 element path and 1e-6 for a float32 Hessian (symmetric only to
+// rounding; its products carry float32 sums, so tighter solves gain little).
+double pcg_rtol_floor(const tl_mesh* m, const tl_params* p) {
+  if (p->lin_rtol > 0.0) return p->lin_rtol;
+  return m->precision == TL_FP32_ELEM ? 1e-6 : 1e-10;
+}
 
 }  // namespace
 
@@ -239,7 +243,7 @@ tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
   const int64_t ndof = 3 * m->nn;
   const unsigned nb = (unsigned)((ndof + 255) / 256);
   const size_t vb = (m->precision == TL_FP32_ELEM ? sizeof(float) : sizeof(double));
-  const double lin_rtol = p->lin_rtol > 0.0 ? p->lin_rtol : 1e-10;
+  const double lin_rtol = pcg_rtol_floor(m, p);
   const int lin_max = p->lin_max_iter > 0 ? p->lin_max_iter : 5000;
   double *g = m->nw_g, *f = m->nw_f, *dv = m->nw_dv, *scal = m->nw_scal;
   void* values = m->nw_values;
@@ -295,7 +299,7 @@ tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
       st = launch_force_prec(m, G->q_n, G->v, p->h, f, true);
       if (st == TL_OK) st = launch_residual(m, p, G->q_n, G->v_n, G->v, f, G->f_ext, G->lam, g, scal);
       if (st == TL_OK) {
-        ctl_inner<<<1, 1, 0, s>>>(c, scal, p->max_inner, lin_rtol, p->lin_adaptive, pcg_eta_min(m), h_in,
+        ctl_inner<<<1, 1, 0, s>>>(c, scal, p->max_inner, lin_rtol, p->lin_adaptive, 0.0, h_in,
                                   h_step);
         e = capture_conditional(s, h_step, cudaGraphCondTypeIf, &b_step);
       }
@@ -452,7 +456,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
     tl_status st = solver_setup(m);
     if (st != TL_OK) return st;
   }
-  const double lin_rtol = p->lin_rtol > 0.0 ? p->lin_rtol : 1e-10;
+  const double lin_rtol = pcg_rtol_floor(m, p);
   const int lin_max = p->lin_max_iter > 0 ? p->lin_max_iter : 5000;
   int lin_total = 0;
   const int64_t ndof = 3 * m->nn;
@@ -541,7 +545,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
         // inexact Newton: the linear residual only needs to be well below the
         // Newton target (g_{k+1} ~ linear residual + O(|dv|^2))
         const double eta = std::max(
-            pcg_eta_min(m), p->lin_adaptive ? std::min(0.5, std::max(lin_rtol, 0.1 * target / gn)) : lin_rtol);
+            0.0, p->lin_adaptive ? std::min(0.5, std::max(lin_rtol, 0.1 * target / gn)) : lin_rtol);
         NTRY(pcg_solve(m, w.values, w.g, w.dv, eta, lin_max, &it));
         lin_total += it;
       } else {
