@@ -331,10 +331,11 @@ def run_ours(args, rank, world):
                    "material": "SVK E=1e7 nu=0.3 + Kelvin-Voigt 1e3", "h": h,
                    "l2": "no flush: the H values written every step (%.2f GB) exceed L2" % (nnz * vbytes / 1e9),
                    "parallelism": f"replicas x{world}", "pattern_build_s": t_pat,
-                   "launch_shapes": {k: tune[k] for k in ("elem_ws", "elem_occ2", "elem_prefetch", "elem_xchg",
-                                                          "elem_full_grid", "spmv_group", "residual_lanes")},
-                   "launch_shape_ms": {k: tune[k] for k in ("ms_ws", "ms_occ2", "ms_element", "ms_spmv",
-                                                            "ms_residual")}},
+                   "launch_shapes": {k: tune[k] for k in ("elem_ws", "elem_occ2", "elem_spread", "elem_prefetch",
+                                                          "elem_xchg", "elem_full_grid", "spmv_group",
+                                                          "residual_lanes")},
+                   "launch_shape_ms": {k: tune[k] for k in ("ms_ws", "ms_occ2", "ms_spread", "ms_element",
+                                                            "ms_spmv", "ms_residual")}},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(tim["launches"]),

@@ -64,8 +64,8 @@ typedef enum tl_material_kind { TL_SVK = 0, TL_MOONEY_RIVLIN = 1 } tl_material_k
 typedef enum tl_precision { TL_FP64 = 0, TL_FP32_ELEM = 1 } tl_precision;
 
 /* Material of a set of elements (Sec. 4.3 Stage 1: SVK or compressible
- * Mooney-Rivlin, plus optional Kelvin-Voigt damping; constitutive forms as in
- * the project notes because the paper defers them to its Part I):
+ * Mooney-Rivlin, plus optional Kelvin-Voigt damping; the paper defers the
+ * constitutive forms to its Part I, so they are stated here):
  *   SVK  : S = lambda tr(E) I + 2 mu E, lambda/mu from (E, nu)
  *   MR   : W = C10(J^-2/3 I1 - 3) + C01(J^-4/3 I2 - 3) + kappa/2 (J-1)^2
  *   KV   : S_v = lambda_d tr(Edot) I + 2 eta_d Edot, Edot = sym(F^T Fdot);
@@ -286,8 +286,9 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *     reductions, or one scalar reduction per entry), the prefetch of the
  *     next tile (cp.async into shared memory, or none), warp
  *     specialisation (5 extra warps issue a tile's reductions while the
- *     compute warps evaluate the next tile) and two CTAs per SM (registers
- *     capped at 64, no prefetch buffer);
+ *     compute warps evaluate the next tile), two CTAs per SM (registers
+ *     capped at 64, no prefetch buffer), and, for the fastest of these, the
+ *     tile order (in order, or permuted so that tiles in flight are far apart);
  *   PCG product H p: 4, 8 or 16 lanes per node;
  *   residual: 1 or 4 lanes per node.
  * reps timed launches per variant after one warm-up.  Needs the pattern;
@@ -303,12 +304,14 @@ typedef struct tl_tune_result {
   int32_t elem_ws;            /* 1: warp-specialised scatter (FP32; with xchg, prefetch, persistent grid) */
   int32_t residual_lanes;     /* lanes per node in the residual: 1 or 4 */
   int32_t elem_occ2;          /* 1: two CTAs per SM (FP32 exchanged assembly, one material kind) */
-  int32_t _pad;
+  int32_t elem_spread;        /* 1: tiles in flight spread over the mesh (permuted launch order) */
   float ms_element[8];        /* measured element-pass times without warp specialisation (0: not measured) */
   float ms_ws;                /* measured time of the warp-specialised variant (0: not measured) */
   float ms_spmv[3];
   float ms_residual[2];       /* residual with 1 and 4 lanes per node */
   float ms_occ2;              /* measured time of the two-CTA variant (0: not measured) */
+  float ms_spread;            /* the chosen element variant with the permuted tile order */
+  float _pad;
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

@@ -714,7 +714,14 @@ struct SegTable {
   SegEntry<T> s[kMaxSeg];
   int32_t nseg;
   int32_t ntiles;
+  int32_t perm_mul;    // tile k of the launch order is tile (k * perm_mul) mod ntiles (1: in order)
 };
+
+// Tile of launch-order position k (a bijection when gcd(perm_mul, ntiles) = 1).
+template <typename T>
+__device__ __forceinline__ int tile_at(const SegTable<T>& S, int k) {
+  return S.perm_mul == 1 ? k : (int)(((int64_t)k * S.perm_mul) % S.ntiles);
+}
 
 // One tile through the kernel of its (material, Kelvin-Voigt) pair.
 template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT>
@@ -787,32 +794,37 @@ __global__ void __launch_bounds__(NT, MINB) elem_kernel(Args<T> A, SegTable<T> S
   __shared__ int s_next;
   Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
   Prefetch<T>* P = A.pf_off >= 0 ? reinterpret_cast<Prefetch<T>*>(smem_raw + A.pf_off) : nullptr;
+  // k counts positions of the launch order; tile_at maps them to tiles.  In
+  // order (perm_mul = 1) the segment walk only moves forward; with a
+  // permutation every tile's segment is walked from the start (<= 64 entries).
+  const bool in_order = S.perm_mul == 1;
   SegWalk cur, nxt;
-  int t = blockIdx.x;
-  if (t >= S.ntiles) return;                         // uniform over the block
-  int64_t e0 = cur.e0(S, t);
+  int k = blockIdx.x;
+  if (k >= S.ntiles) return;                         // uniform over the block
+  int64_t e0 = cur.e0(S, tile_at(S, k));
   load_tile<T, DO_TANGENT>(A, sm, e0, sm.meta);
-  if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t + (int)gridDim.x;
+  if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : k + (int)gridDim.x;
   __syncthreads();
   while (true) {
-    const int t_next = s_next;
+    const int k_next = s_next;
     Args<T> a = A;
     a.mat = S.s[cur.sg].mat;
     a.real_end = S.s[cur.sg].real_end;
-    nxt = cur;
-    const int64_t e0_next = (P && t_next < S.ntiles) ? nxt.e0(S, t_next) : -1;
+    nxt = in_order ? cur : SegWalk();
+    const int64_t e0_next = (P && k_next < S.ntiles) ? nxt.e0(S, tile_at(S, k_next)) : -1;
     dispatch_tile<T, COMBO, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, S.s[cur.sg].combo, P, e0_next);
     if (P) cp_async_wait_all();
     __syncthreads();                                 // this tile's shared data is consumed
-    if (t_next >= S.ntiles) break;
-    if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : t_next + (int)gridDim.x;
-    t = t_next;
+    if (k_next >= S.ntiles) break;
+    if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : k_next + (int)gridDim.x;
+    k = k_next;
     if (P) {
       cur = nxt;
       e0 = e0_next;
       unpack_tile<T, DO_TANGENT>(A, sm, *P, sm.meta);  // ends with a barrier (also publishes s_next)
     } else {
-      e0 = cur.e0(S, t);
+      if (!in_order) cur = SegWalk();
+      e0 = cur.e0(S, tile_at(S, k));
       load_tile<T, DO_TANGENT>(A, sm, e0, sm.meta);    // ends with a barrier (also publishes s_next)
     }
   }
@@ -995,6 +1007,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     SegTable<T> S;
     S.nseg = 0;
     S.ntiles = 0;
+    S.perm_mul = 1;
     int combo0 = -1;
     bool mixed = false;
     for (; k < m->segs.size() && S.nseg < kMaxSeg; ++k) {
@@ -1081,6 +1094,14 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     TL_CUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem_l));
     const bool full = m->tune.elem_full_grid != 0;
     const int grid = full ? S.ntiles : (int)std::min<int64_t>(S.ntiles, (int64_t)m->num_sms * std::max(occ, 1));
+    // spread: tiles in flight at the same time lie ~ntiles/grid apart, so their
+    // reductions go to distant CSR rows (the warp-specialised kernel keeps order)
+    if (m->tune.elem_spread && !full && threads == NT && S.ntiles > 2 * grid) {
+      int mul = (S.ntiles + grid - 1) / grid;
+      auto gcd = [](int a, int b) { while (b) { const int r = a % b; a = b; b = r; } return a; };
+      while (gcd(mul, S.ntiles) != 1) ++mul;
+      S.perm_mul = mul;
+    }
     int* counter = nullptr;
     if (!full && nlaunch < kTileCounters) {
       counter = m->d_tile_counters + nlaunch;

@@ -52,6 +52,7 @@ struct Tune {
   int elem_ws = 0;        // float32 CSR assembly: 1 = warp-specialised scatter (needs prefetch, persistent grid)
   int residual_lanes = 1; // lanes per node in the residual (1 or 4)
   int elem_occ2 = 1;      // float32 CSR assembly: 1 = two CTAs per SM (64 registers, overlaid exchange buffer)
+  int elem_spread = 0;    // element kernels: 1 = tiles in flight spread over the mesh (permuted launch order)
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };

@@ -107,6 +107,20 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
       chosen.elem_occ2 = variants[k].occ2;
     }
   }
+  // tile order of the fastest element variant: in order or spread
+  if (st == TL_OK && !chosen.elem_full_grid && !chosen.elem_ws) {
+    m->tune = chosen;
+    m->tune.elem_spread = 1;
+    float ms = 0.f;
+    st = time_reps(m, reps, [&]() {
+      return launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
+    }, &ms);
+    if (st == TL_OK) {
+      r.ms_spread = ms;
+      chosen.elem_spread = ms < best ? 1 : 0;
+    }
+    m->tune = saved;
+  }
   // PCG product: lanes per node
   if (st == TL_OK) st = pcg_ensure(m);
   best = 1e30f;
@@ -164,6 +178,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.elem_ws = chosen.elem_ws;
   r.residual_lanes = chosen.residual_lanes;
   r.elem_occ2 = chosen.elem_occ2;
+  r.elem_spread = chosen.elem_spread;
   if (out) *out = r;
   return TL_OK;
 }
@@ -178,6 +193,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.elem_ws = m->tune.elem_ws;
   r.residual_lanes = m->tune.residual_lanes;
   r.elem_occ2 = m->tune.elem_occ2;
+  r.elem_spread = m->tune.elem_spread;
   *out = r;
   return TL_OK;
 }
@@ -187,13 +203,15 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   if (in->spmv_group != 4 && in->spmv_group != 8 && in->spmv_group != 16) return TL_ERR_INVALID_ARG;
   if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1) ||
       (in->elem_prefetch != 0 && in->elem_prefetch != 1) || (in->elem_ws != 0 && in->elem_ws != 1) ||
-      (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1))
+      (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1) ||
+      (in->elem_spread != 0 && in->elem_spread != 1))
     return TL_ERR_INVALID_ARG;
   m->tune.spmv_group = in->spmv_group;
   m->tune.elem_prefetch = in->elem_prefetch;
   m->tune.elem_ws = in->elem_ws;
   m->tune.residual_lanes = in->residual_lanes;
   m->tune.elem_occ2 = in->elem_occ2;
+  m->tune.elem_spread = in->elem_spread;
   m->tune.elem_xchg = in->elem_xchg;
   m->tune.elem_full_grid = in->elem_full_grid;
   m->tune.generation += 1;
