@@ -34,8 +34,11 @@ UNIT = "elems/s"
 
 # Algorithmic FP32 flops per element of the fused pass (force + tangent +
 # assembly), counted from the formulas the kernel evaluates (FMA = 2), once
-# per element, without the kernel's own redundancy; see the project design
-# notes for the line-by-line count.
+# per element, without the kernel's own redundancy.  Per quadrature point
+# (SVK + KV): grad N 92, H 180, Fdot 180, J - 1 37, E 54, S 11, Edot 72,
+# S_v 11, S_tot 6, B 36, P 64, f 180, tangent entries 278 (45 unique),
+# A n per node 1,620, 55 blocks x 9 x 3 FMA 2,970 = 5,791; x 5 plus the
+# force and tangent reductions and the mass term (457) = 29,412.
 FLOPS_PER_ELEM = {("svk", False): 28_067, ("svk", True): 29_412,
                   ("mr", False): 33_782, ("mr", True): 36_477}
 
@@ -184,6 +187,17 @@ def oracle_step_rate(budget_s=12.0, min_reps=1, nx=10, ny=4, nz=4):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def replica_aggregate(ms, ne, steps, world, device="cuda"):
+    """Max over ranks of the timed region (ms) and the whole-job rate: every
+    rank assembles its own replica of ne elements per step (weak scaling)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * ne * steps / (ms_max * 1e-3)
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -284,13 +298,8 @@ def run_ours(args, rank, world):
     if rank == 0:
         sampler.stop()
 
-    # max over ranks of the timed region
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = replica_aggregate(ms, m.ne, args.steps, world)
     ms_step = ms_max / args.steps
-    value = world * m.ne * args.steps / (ms_max * 1e-3)
 
     if rank != 0:
         return None

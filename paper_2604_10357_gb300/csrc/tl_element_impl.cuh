@@ -88,7 +88,13 @@ struct Args {
 // Per-element shared-memory strides padded to odd word counts so that lanes
 // (= elements) reading the same offset hit distinct banks.
 constexpr int kNStride = 151;    // 5 qp x 30 grad N, + 1
-constexpr int kAStride = 407;    // 5 qp x 81 tangent entries, + 2
+// Tangent rows: 27 entries padded to 28 and 84 per quadrature point, so every
+// row starts on a 16-byte boundary (vector shared-memory accesses); the
+// per-element stride 420 = 4 (mod 32) keeps eight lanes of a 16-byte access
+// on distinct banks.
+constexpr int kARow = 28;
+constexpr int kAQp = 3 * kARow;           // 84
+constexpr int kAStride = 5 * kAQp;        // 420
 constexpr int kFStride = 151;    // 5 qp x 30 force entries, + 1
 constexpr int kUStride = 31;
 
@@ -293,7 +299,7 @@ __device__ __forceinline__ void qp_rows(const Args<T>& A, Smem<T>& sm, const QP<
 #pragma unroll
   for (int a = 0; a < 10; ++a)
     sm.fq[e * kFStride + q * 30 + a * 3 + i] = Pi[0] * n[a][0] + Pi[1] * n[a][1] + Pi[2] * n[a][2];
-  if (WANT_A) tangent_row<T, MAT, KV, i>(s, A.mat, A.alpha, A.beta, wJ, &sm.A[e * kAStride + q * 81 + i * 27]);
+  if (WANT_A) tangent_row<T, MAT, KV, i>(s, A.mat, A.alpha, A.beta, wJ, &sm.A[e * kAStride + q * kAQp + i * kARow]);
 }
 
 // qp phase: warp w -> (q = w / 3, row i = w % 3), lane = element.  The
@@ -374,7 +380,7 @@ __device__ __forceinline__ void tangent_blockrow(const Args<T>& A, const Smem<T>
 #pragma unroll 1
   for (int q = 0; q < 5; ++q) {
     const T* nq = &sm.n[e * kNStride + q * 30];
-    const T* Aq = &sm.A[e * kAStride + q * 81 + i * 27];
+    const T* Aq = &sm.A[e * kAStride + q * kAQp + i * kARow];
     const T na[3] = {nq[A0 * 3], nq[A0 * 3 + 1], nq[A0 * 3 + 2]};
     T An[3][3];
 #pragma unroll
@@ -433,14 +439,17 @@ __device__ __forceinline__ void accumulate_blockrow(const Args<T>& A, const Smem
 #pragma unroll 1
   for (int q = 0; q < 5; ++q) {
     const T* nq = &sm.n[e * kNStride + q * 30];
-    const T* Aq = &sm.A[e * kAStride + q * 81 + i * 27];
+    const T* Aq = &sm.A[e * kAStride + q * kAQp + i * kARow];
     const T na[3] = {nq[A0 * 3], nq[A0 * 3 + 1], nq[A0 * 3 + 2]};
+    T av[27];
+#pragma unroll
+    for (int c = 0; c < 27; ++c) av[c] = Aq[c];
     T An[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int L = 0; L < 3; ++L)
-        An[k][L] = na[0] * Aq[0 * 9 + k * 3 + L] + na[1] * Aq[1 * 9 + k * 3 + L] + na[2] * Aq[2 * 9 + k * 3 + L];
+        An[k][L] = na[0] * av[0 * 9 + k * 3 + L] + na[1] * av[1 * 9 + k * 3 + L] + na[2] * av[2 * 9 + k * 3 + L];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       const int b = A0 + j;
