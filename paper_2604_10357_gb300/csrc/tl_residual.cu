@@ -38,7 +38,8 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 template <int LANES>
 __global__ void __launch_bounds__(kResBlock * LANES)
     residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass, const double* mrow,
-                    const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double rho, double gx,
+                    const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double inv_h, double rho,
+                    double gx,
                     double gy, double gz, const double* q_n, const double* v_n, const double* v, const double* dv,
                     const double* f_int, const double* f_ext, const double* lambda, double* g,
                     double* partials) {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kResBlock * LANES)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int64_t r = 3 * I + d;
-      double gd = acc[d] / h + f_int[r] - mr * grav[d];
+      double gd = acc[d] * inv_h + f_int[r] - mr * grav[d];
       if (f_ext) gd -= f_ext[r];
       if (j >= 0) {
         const double c = (q_n[r] + h * v[r]) - X[r];
@@ -155,11 +156,11 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   velocity_change<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv);
   if (m->tune.residual_lanes == 4)
     residual_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
-        m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
+        m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
         p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials);
   else
     residual_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
-        m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
+        m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
         p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials);
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(m->d_partials, nb, g_norm, m->d_flags);
@@ -226,7 +227,7 @@ extern "C" tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, co
   tl_status s = noalloc_scratch(m, dev, &partials);
   if (s != TL_OK) return s;
   residual_kernel<1><<<(unsigned)nb, kResBlock, 0, m->stream>>>(
-      m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, p->rho_alm,
+      m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
       p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, nullptr, f_int, f_ext, lambda, g, partials);
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(partials, (int)nb, g_norm, m->d_flags);
