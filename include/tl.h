@@ -311,7 +311,9 @@ typedef struct tl_tune_result {
   float ms_residual[2];       /* residual with 1 and 4 lanes per node */
   float ms_occ2;              /* measured time of the two-CTA variant (0: not measured) */
   float ms_spread;            /* the chosen element variant with the permuted tile order */
-  float _pad;
+  int32_t pcg_f32;            /* FP32 Hessian: 1 = PCG vectors in float32 (dot products accumulated in
+                                 float64), 0 = float64 vectors; not timed by tl_autotune (it changes
+                                 the rounding of the iterates, not only their order); default 1 */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

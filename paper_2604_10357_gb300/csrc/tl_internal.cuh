@@ -53,6 +53,7 @@ struct Tune {
   int residual_lanes = 1; // lanes per node in the residual (1 or 4)
   int elem_occ2 = 1;      // float32 CSR assembly: 1 = two CTAs per SM (64 registers, overlaid exchange buffer)
   int elem_spread = 0;    // element kernels: 1 = tiles in flight spread over the mesh (permuted launch order)
+  int pcg_f32 = 1;        // float32 Hessian: 1 = PCG vectors in float32 (dot products float64)
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };
@@ -142,6 +143,8 @@ tl_status pcg_ensure(tl_mesh* m);
 double* pcg_scalars(tl_mesh* m);   // slot 3: r.r of the current PCG iterate
 tl_status pcg_prepare(tl_mesh* m, const void* values, const double* g, double* dv);
 tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count);
+tl_status pcg_result(tl_mesh* m, double* dv);   // dv from the float32 iterate (after the iterations)
+bool pcg_float32(const tl_mesh* m);
 tl_status pcg_spmv_only(tl_mesh* m, const void* values, int group);   // Ap = H p, for the autotuner
 tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv, double rtol, int max_iter,
                     int* iters_out);

@@ -324,7 +324,8 @@ tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
         e = capture_conditional(s, h_pcg, cudaGraphCondTypeWhile, &b_pcg);
         if (e == cudaSuccess) {
           ctl_pcg_done<<<1, 1, 0, s>>>(c);
-          axpy_kernel<<<nb, 256, 0, s>>>(G->v, dv, 1.0, ndof);
+          st = pcg_result(m, dv);
+          if (st == TL_OK) axpy_kernel<<<nb, 256, 0, s>>>(G->v, dv, 1.0, ndof);
         }
       }
     }

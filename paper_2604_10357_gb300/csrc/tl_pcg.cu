@@ -28,6 +28,8 @@ struct PcgWork {
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *binv = nullptr, *part = nullptr,
          *scal = nullptr;
   float* p32 = nullptr;        // float32 copy of p (float32 element form)
+  // float32 iteration (float32 Hessian): x, r, z, Hp and the Jacobi blocks in float32
+  float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *Ap32 = nullptr, *binv32 = nullptr;
   unsigned* tickets = nullptr; // last-block counters of the two fused reductions
   int32_t* diag_k = nullptr;   // per node: position of I in its own adjacency
   int nparts = 0;
@@ -284,11 +286,163 @@ __global__ void pcg_start(const double* g, double* x, double* r, double* z, doub
   }
 }
 
+// ---------------------------------------------------------------------------
+// Float32 iteration for a float32 Hessian: the vectors x, r, z, p, Hp and the
+// Jacobi blocks are float32 (a float32 H defines the Newton direction to
+// ~1e-6, the tolerance floor of this solve), halving the vector traffic and
+// keeping the arithmetic off GB300's float64 pipe; dot products are summed in
+// float64; the input -g and the output dv stay float64.
+// ---------------------------------------------------------------------------
+__global__ void jacobi_to_f32(const double* binv, int64_t n, float* binv32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) binv32[i] = float(binv[i]);
+}
+
+__global__ void pcg_start32(const double* g, float* x, float* r, float* z, float* p, const float* binv,
+                            int64_t nn, double* part_rz, double* part_rr, double* scal) {
+  __shared__ double red[kBlock / 32];
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I == 0) scal[6] = 0.0;
+  double rz = 0.0, rr = 0.0;
+  if (I < nn) {
+    float rv[3];
+    for (int d = 0; d < 3; ++d) {
+      rv[d] = float(-g[3 * I + d]);
+      r[3 * I + d] = rv[d];
+      x[3 * I + d] = 0.0f;
+    }
+    const float* B = binv + 9 * I;
+    for (int d = 0; d < 3; ++d) {
+      const float zd = B[3 * d] * rv[0] + B[3 * d + 1] * rv[1] + B[3 * d + 2] * rv[2];
+      z[3 * I + d] = zd;
+      p[3 * I + d] = zd;
+      rz += double(rv[d]) * double(zd);
+      rr += double(rv[d]) * double(rv[d]);
+    }
+  }
+  const double a = block_sum(rz, red);
+  __syncthreads();
+  const double b = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = a;
+    part_rr[blockIdx.x] = b;
+  }
+}
+
+template <int G>
+__global__ void spmv_node32(const float* __restrict__ vals, const int32_t* __restrict__ node_ptr,
+                            const int32_t* __restrict__ node_col, int64_t nn, const float* __restrict__ p,
+                            float* __restrict__ Ap, double* part, double* scal, unsigned* ticket) {
+  __shared__ double red[kBlock / 32];
+  const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int l = threadIdx.x & (G - 1);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  double dot = 0.0;
+  if (I < nn) {
+    const int p0 = node_ptr[I], deg = node_ptr[I + 1] - p0;
+    const float* v0 = vals + 9 * (int64_t)p0;
+    const float* v1 = v0 + 3 * deg;
+    const float* v2 = v1 + 3 * deg;
+    for (int j = l; j < deg; j += G) {
+      const int J = node_col[p0 + j];
+      const float x0 = p[3 * J], x1 = p[3 * J + 1], x2 = p[3 * J + 2];
+      s0 += v0[3 * j] * x0 + v0[3 * j + 1] * x1 + v0[3 * j + 2] * x2;
+      s1 += v1[3 * j] * x0 + v1[3 * j + 1] * x1 + v1[3 * j + 2] * x2;
+      s2 += v2[3 * j] * x0 + v2[3 * j + 1] * x1 + v2[3 * j + 2] * x2;
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (I < nn && l == 0) {
+    Ap[3 * I] = s0;
+    Ap[3 * I + 1] = s1;
+    Ap[3 * I + 2] = s2;
+    dot = double(s0) * double(p[3 * I]) + double(s1) * double(p[3 * I + 1]) + double(s2) * double(p[3 * I + 2]);
+  }
+  const double t = block_sum(dot, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (last_block(ticket)) {
+    __syncthreads();
+    const double tot = sum_partials(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      scal[1] = tot;
+      *ticket = 0u;
+    }
+  }
+}
+
+__global__ void update_xr32(float* x, float* r, float* z, const float* p, const float* Ap, const float* binv,
+                            double* scal, int64_t nn, double* part_rz, double* part_rr, int parity,
+                            unsigned* ticket) {
+  __shared__ double red[kBlock / 32];
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int rz_old = 2 * parity, rz_new = 2 - 2 * parity;
+  const bool ok = scal[1] > 0.0;
+  const float alpha = ok ? float(scal[rz_old] / scal[1]) : 0.0f;
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) scal[6] = 1.0;
+  double rz = 0.0, rr = 0.0;
+  if (I < nn) {
+    float rv[3];
+    for (int d = 0; d < 3; ++d) {
+      const int64_t i = 3 * I + d;
+      x[i] += alpha * p[i];
+      rv[d] = r[i] - alpha * Ap[i];
+      r[i] = rv[d];
+    }
+    const float* B = binv + 9 * I;
+    for (int d = 0; d < 3; ++d) {
+      const float zd = B[3 * d] * rv[0] + B[3 * d + 1] * rv[1] + B[3 * d + 2] * rv[2];
+      z[3 * I + d] = zd;
+      rz += double(rv[d]) * double(zd);
+      rr += double(rv[d]) * double(rv[d]);
+    }
+  }
+  const double a = block_sum(rz, red);
+  __syncthreads();
+  const double b = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = a;
+    part_rr[blockIdx.x] = b;
+  }
+  if (last_block(ticket)) {
+    __syncthreads();
+    const double trz = sum_partials(part_rz, gridDim.x, red);
+    __syncthreads();
+    const double trr = sum_partials(part_rr, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      scal[rz_new] = trz;
+      scal[3] = trr;
+      *ticket = 0u;
+    }
+  }
+}
+
+__global__ void update_p32(float* p, const float* z, int64_t n, const double* scal, int parity) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const double rz_old = scal[2 * parity], rz_new = scal[2 - 2 * parity];
+  const float beta = rz_old != 0.0 ? float(rz_new / rz_old) : 0.0f;
+  if (i < n) p[i] = z[i] + beta * p[i];
+}
+
+__global__ void widen(const float* x, int64_t n, double* y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = double(x[i]);
+}
+
 }  // namespace
+
+// The float32 iteration runs for a float32 Hessian unless the autotuner or the
+// caller turned it off.
+bool pcg_float32(const tl_mesh* m) { return m->precision == TL_FP32_ELEM && m->tune.pcg_f32; }
 
 void pcg_destroy(PcgWork* w) {
   if (!w) return;
-  void* ptrs[] = {w->r, w->z, w->p, w->Ap, w->binv, w->part, w->scal, w->diag_k, w->p32, w->tickets};
+  void* ptrs[] = {w->r, w->z, w->p, w->Ap, w->binv, w->part, w->scal, w->diag_k, w->p32, w->tickets,
+                  w->x32, w->r32, w->z32, w->Ap32, w->binv32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete w;
@@ -315,6 +469,11 @@ tl_status pcg_ensure(tl_mesh* m) {
   if (m->precision == TL_FP32_ELEM) {
     TL_CUDA(m, cudaMalloc(&w->p32, sizeof(float) * n));
     TL_CUDA(m, cudaMemsetAsync(w->p32, 0, sizeof(float) * n, m->stream));
+    TL_CUDA(m, cudaMalloc(&w->x32, sizeof(float) * n));
+    TL_CUDA(m, cudaMalloc(&w->r32, sizeof(float) * n));
+    TL_CUDA(m, cudaMalloc(&w->z32, sizeof(float) * n));
+    TL_CUDA(m, cudaMalloc(&w->Ap32, sizeof(float) * n));
+    TL_CUDA(m, cudaMalloc(&w->binv32, sizeof(float) * 9 * nn));
   }
   node_diag_pos<<<(unsigned)((nn + 255) / 256), 256, 0, m->stream>>>(m->d_node_ptr, m->d_node_col, nn, w->diag_k);
   TL_CUDA(m, cudaGetLastError());
@@ -338,8 +497,14 @@ tl_status pcg_prepare(tl_mesh* m, const void* values, const double* g, double* d
     block_jacobi<double><<<nbn, kBlock, 0, s>>>((const double*)values, m->d_node_ptr, w->diag_k, nn, w->binv);
   double* part_rz = w->part;
   double* part_rr = w->part + w->nparts;
-  float* p32 = m->precision == TL_FP32_ELEM ? w->p32 : nullptr;
-  pcg_start<<<nbn, kBlock, 0, s>>>(g, dv, w->r, w->z, w->p, p32, w->binv, nn, part_rz, part_rr, w->scal);
+  if (pcg_float32(m)) {
+    jacobi_to_f32<<<(unsigned)((9 * nn + kBlock - 1) / kBlock), kBlock, 0, s>>>(w->binv, 9 * nn, w->binv32);
+    pcg_start32<<<nbn, kBlock, 0, s>>>(g, w->x32, w->r32, w->z32, w->p32, w->binv32, nn, part_rz, part_rr, w->scal);
+    m->launches += 1;
+  } else {
+    float* p32 = m->precision == TL_FP32_ELEM ? w->p32 : nullptr;
+    pcg_start<<<nbn, kBlock, 0, s>>>(g, dv, w->r, w->z, w->p, p32, w->binv, nn, part_rz, part_rr, w->scal);
+  }
   finish_sum<<<1, 1024, 0, s>>>(part_rz, nbn, w->scal, 0);
   finish_sum<<<1, 1024, 0, s>>>(part_rr, nbn, w->scal, 3);
   TL_CUDA(m, cudaGetLastError());
@@ -351,8 +516,12 @@ template <typename T, int G>
 void launch_spmv(tl_mesh* m, const void* values, PcgWork* w, unsigned* nblocks) {
   const int64_t nn = m->nn;
   const unsigned nb = (unsigned)((G * nn + kBlock - 1) / kBlock);
-  spmv_node<T, G><<<nb, kBlock, 0, m->stream>>>((const T*)values, m->d_node_ptr, m->d_node_col, nn, w->p, w->p32,
-                                                w->Ap, w->part, w->scal, w->tickets);
+  if (std::is_same<T, float>::value && pcg_float32(m))
+    spmv_node32<G><<<nb, kBlock, 0, m->stream>>>((const float*)values, m->d_node_ptr, m->d_node_col, nn, w->p32,
+                                                 w->Ap32, w->part, w->scal, w->tickets);
+  else
+    spmv_node<T, G><<<nb, kBlock, 0, m->stream>>>((const T*)values, m->d_node_ptr, m->d_node_col, nn, w->p,
+                                                  w->p32, w->Ap, w->part, w->scal, w->tickets);
   *nblocks = nb;
 }
 
@@ -393,9 +562,15 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
     }
     (void)nbs;
     const int parity = k & 1;            // chunks start at even iterations (count is 8 except the last)
-    update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr,
-                                     parity, w->tickets + 1);
-    update_p<<<nbv, kBlock, 0, s>>>(w->p, fp32 ? w->p32 : nullptr, w->z, n, w->scal, parity);
+    if (pcg_float32(m)) {
+      update_xr32<<<nbn, kBlock, 0, s>>>(w->x32, w->r32, w->z32, w->p32, w->Ap32, w->binv32, w->scal, nn, part_rz,
+                                         part_rr, parity, w->tickets + 1);
+      update_p32<<<nbv, kBlock, 0, s>>>(w->p32, w->z32, n, w->scal, parity);
+    } else {
+      update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr,
+                                       parity, w->tickets + 1);
+      update_p<<<nbv, kBlock, 0, s>>>(w->p, fp32 ? w->p32 : nullptr, w->z, n, w->scal, parity);
+    }
     m->launches += 3;
   }
   TL_CUDA(m, cudaGetLastError());
@@ -425,7 +600,18 @@ tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv,
     if (!std::isfinite(rr)) return fail(m, TL_ERR_NONFINITE, "PCG residual not finite");
     if (rr <= tol2 || sc[3] != 0.0) break;
   }
+  TL_TRY(pcg_result(m, dv));
   if (iters_out) *iters_out = it;
+  return TL_OK;
+}
+
+// dv from the float32 iterate (no-op for the float64 iteration, which updates dv in place).
+tl_status pcg_result(tl_mesh* m, double* dv) {
+  if (!pcg_float32(m)) return TL_OK;
+  const int64_t n = 3 * m->nn;
+  widen<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, m->stream>>>(m->pcg->x32, n, dv);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
   return TL_OK;
 }
 

@@ -179,6 +179,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.residual_lanes = chosen.residual_lanes;
   r.elem_occ2 = chosen.elem_occ2;
   r.elem_spread = chosen.elem_spread;
+  r.pcg_f32 = chosen.pcg_f32;
   if (out) *out = r;
   return TL_OK;
 }
@@ -194,6 +195,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.residual_lanes = m->tune.residual_lanes;
   r.elem_occ2 = m->tune.elem_occ2;
   r.elem_spread = m->tune.elem_spread;
+  r.pcg_f32 = m->tune.pcg_f32;
   *out = r;
   return TL_OK;
 }
@@ -204,7 +206,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1) ||
       (in->elem_prefetch != 0 && in->elem_prefetch != 1) || (in->elem_ws != 0 && in->elem_ws != 1) ||
       (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1) ||
-      (in->elem_spread != 0 && in->elem_spread != 1))
+      (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1))
     return TL_ERR_INVALID_ARG;
   m->tune.spmv_group = in->spmv_group;
   m->tune.elem_prefetch = in->elem_prefetch;
@@ -214,6 +216,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   m->tune.elem_spread = in->elem_spread;
   m->tune.elem_xchg = in->elem_xchg;
   m->tune.elem_full_grid = in->elem_full_grid;
+  m->tune.pcg_f32 = in->pcg_f32;
   m->tune.generation += 1;
   return TL_OK;
 }

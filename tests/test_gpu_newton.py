@@ -152,6 +152,34 @@ def test_newton_graph_equals_host_loop(prec, adaptive):
     assert np.abs(l1 - l0).max() <= 1e-6 * np.abs(l0).max()
 
 
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_pcg_vector_precisions_reach_same_state(use_graph):
+    """With a float32 Hessian the PCG vectors may be float32 (dot products in
+    float64) or float64: each Newton solve is inexact either way, and both
+    converge the float64 residual to 1e-8, so the velocities agree to the
+    residual's tolerance and the Newton counts are the same."""
+    tl = _tl()
+    w = inputs.workload_mid_mr_kv()
+    X = w["mesh"].X
+    w = dict(w, q_n=X + 0.05 * (w["q_n"] - X), v=0.2 * w["v"])
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
+    g.build_pattern(m.fixed_nodes)
+    p = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, use_graph=use_graph)
+    out = {}
+    for f32 in (0, 1):
+        g.tune_set(pcg_f32=f32)
+        assert g.tune_get()["pcg_f32"] == f32
+        lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+        v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+        assert st["converged"] == 1 and st["g_norm"] <= 1e-8 * st["g_ref"]
+        out[f32] = (v.cpu().numpy(), st)
+    (v0, s0), (v1, s1) = out[0], out[1]
+    assert s1["outer_iters"] == s0["outer_iters"]
+    assert abs(s1["inner_iters"] - s0["inner_iters"]) <= 1
+    assert np.linalg.norm(v1 - v0) <= 1e-7 * np.linalg.norm(v0)
+
+
 def test_newton_graph_caps_and_rebuild():
     """Iteration caps end the captured loops with NOT_CONVERGED and the same
     statistics as the host loop; a parameter change rebuilds the graph and a
