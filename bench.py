@@ -341,10 +341,10 @@ def run_ours(args, rank, world):
                    "l2": "no flush: the H values written every step (%.2f GB) exceed L2" % (nnz * vbytes / 1e9),
                    "parallelism": f"replicas x{world}", "pattern_build_s": t_pat,
                    "launch_shapes": {k: tune[k] for k in ("elem_ws", "elem_occ2", "elem_spread", "elem_prefetch",
-                                                          "elem_xchg", "elem_full_grid", "spmv_group",
+                                                          "elem_xchg", "elem_full_grid", "spmv_group", "spmv_row",
                                                           "residual_lanes")},
                    "launch_shape_ms": {k: tune[k] for k in ("ms_ws", "ms_occ2", "ms_spread", "ms_element",
-                                                            "ms_spmv", "ms_residual")}},
+                                                            "ms_spmv", "ms_spmv_row", "ms_residual")}},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(tim["launches"]),
@@ -385,6 +385,12 @@ def run_newton(args):
     model_path = os.path.join(ROOT, "paper_2604_10357_gb300", "data", "warmstart_box120x12x12.npz")
     model = warmstart.WarmStartModel.from_npz(model_path) if os.path.exists(model_path) else None
     c_mode = "mlp" if model is not None else "extrapolation"
+    # launch shapes of both arms picked by the autotuner on the first held-out state (untimed)
+    shape_keys = ("elem_occ2", "elem_prefetch", "elem_xchg", "elem_full_grid", "spmv_group", "spmv_row", "pcg_f32")
+    shapes = {}
+    for name, g in (("plain", g64), ("chosen", g32)):
+        t = g.tune_get() if args.no_autotune else g.autotune(tr.q[test_idx[0]], tr.v[test_idx[0]], w["h"], reps=3)
+        shapes[name] = {k: t[k] for k in shape_keys}
     # one untimed pass of each arm first (graph capture, first-use allocations)
     warmstart.evaluate(g64, tr, test_idx[:1], plain, modes=["v_n"])
     warmstart.evaluate(g32, tr, test_idx[:1], chosen, model, modes=[c_mode])
@@ -396,6 +402,7 @@ def run_newton(args):
            "chosen": dict(c_sum[c_mode], desc=f"FP32 element form, start {c_mode}, inexact-Newton PCG, "
                                                 + ("host loop" if args.newton_no_graph else "captured graph")),
            "speedup": p_sum["v_n"]["mean_ms"] / c_sum[c_mode]["mean_ms"],
+           "launch_shapes": shapes,
            "model": os.path.relpath(model_path, ROOT) if model is not None else None}
     if args.newton_direct:
         direct = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_DIRECT)

@@ -289,7 +289,8 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *     compute warps evaluate the next tile), two CTAs per SM (registers
  *     capped at 64, no prefetch buffer), and, for the fastest of these, the
  *     tile order (in order, or permuted so that tiles in flight are far apart);
- *   PCG product H p: 4, 8 or 16 lanes per node;
+ *   PCG product H p: 4, 8 or 16 lanes per node (one neighbour per lane), and for the
+ *     float32 iteration 8, 16 or 32 lanes per node along the contiguous rows;
  *   residual: 1 or 4 lanes per node.
  * reps timed launches per variant after one warm-up.  Needs the pattern;
  * allocates and frees one CSR values array and one force array.  Synchronous.
@@ -297,7 +298,7 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  * the reductions.  ms_element[k]: k = 4*(1-prefetch) + 2*(1-xchg) + full_grid;
  * ms_spmv[k]: 4, 8, 16 lanes. */
 typedef struct tl_tune_result {
-  int32_t spmv_group;         /* lanes per node in H p */
+  int32_t spmv_group;         /* lanes per node in H p: 4, 8, 16 or 32 */
   int32_t elem_xchg;          /* 1: exchanged vector runs (FP32 assembly) */
   int32_t elem_full_grid;     /* 1: one CTA per tile; 0: persistent grid */
   int32_t elem_prefetch;      /* 1: cp.async prefetch of the next tile (FP32) */
@@ -314,6 +315,9 @@ typedef struct tl_tune_result {
   int32_t pcg_f32;            /* FP32 Hessian: 1 = PCG vectors in float32 (dot products accumulated in
                                  float64), 0 = float64 vectors; not timed by tl_autotune (it changes
                                  the rounding of the iterates, not only their order); default 1 */
+  int32_t spmv_row;           /* float32 PCG iteration: 1 = row-contiguous H p (the group's lanes read
+                                 contiguous runs of the three rows), 0 = one neighbour per lane */
+  float ms_spmv_row[3];       /* measured row-contiguous H p with 8, 16, 32 lanes per node (0: not measured) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

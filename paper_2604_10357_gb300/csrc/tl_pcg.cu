@@ -375,6 +375,73 @@ __global__ void spmv_node32(const float* __restrict__ vals, const int32_t* __res
   }
 }
 
+// Ap = H p, row-contiguous form (float32 iteration): a group of G lanes per
+// node walks the three rows of node I together, lane l taking the positions
+// t = l, l+G, ... of each row (neighbour j = t / 3, component k = t % 3), so
+// every value load of the group is one contiguous run; the neighbour index
+// and p[3J+k] are read once for the three rows.  Grid-stride over the nodes
+// with at most `nparts` blocks (the partials of p.Ap).
+template <int G>
+__global__ void spmv_row32(const float* __restrict__ vals, const int32_t* __restrict__ node_ptr,
+                           const int32_t* __restrict__ node_col, int64_t nn, const float* __restrict__ p,
+                           float* __restrict__ Ap, double* part, double* scal, unsigned* ticket) {
+  static_assert(G >= 4 && G <= 32 && (G & (G - 1)) == 0, "G: power of two in [4, 32]");
+  __shared__ double red[kBlock / 32];
+  const int l = threadIdx.x & (G - 1);
+  const int64_t groups = (int64_t)gridDim.x * (kBlock / G);
+  // the loop bound is tested on the warp's first group, so every lane of a
+  // warp runs the same trips and reaches the shuffles together
+  const int64_t warp_first = (blockIdx.x * (int64_t)kBlock + (threadIdx.x & ~31)) / G;
+  const int sub = (threadIdx.x & 31) / G;
+  double dot = 0.0;
+  for (int64_t I0 = warp_first; I0 < nn; I0 += groups) {
+    const int64_t I = I0 + sub;
+    const bool act = I < nn;
+    const int p0 = act ? node_ptr[I] : 0, n3 = act ? 3 * (node_ptr[I + 1] - p0) : 0;
+    const float* v0 = vals + 9 * (int64_t)p0;
+    const float* v1 = v0 + n3;
+    const float* v2 = v1 + n3;
+    const int32_t* c = node_col + p0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    int j = l / 3, k = l - 3 * (l / 3);
+#pragma unroll 2
+    for (int t = l; t < n3; t += G) {
+      const float x = p[3 * c[j] + k];
+      s0 += v0[t] * x;
+      s1 += v1[t] * x;
+      s2 += v2[t] * x;
+      j += G / 3;
+      k += G % 3;
+      if (k >= 3) {
+        k -= 3;
+        ++j;
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (act && l == 0) {
+      Ap[3 * I] = s0;
+      Ap[3 * I + 1] = s1;
+      Ap[3 * I + 2] = s2;
+      dot += double(s0) * double(p[3 * I]) + double(s1) * double(p[3 * I + 1]) + double(s2) * double(p[3 * I + 2]);
+    }
+  }
+  const double t = block_sum(dot, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (last_block(ticket)) {
+    __syncthreads();
+    const double tot = sum_partials(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      scal[1] = tot;
+      *ticket = 0u;
+    }
+  }
+}
+
 __global__ void update_xr32(float* x, float* r, float* z, const float* p, const float* Ap, const float* binv,
                             double* scal, int64_t nn, double* part_rz, double* part_rr, int parity,
                             unsigned* ticket) {
@@ -454,7 +521,7 @@ tl_status pcg_ensure(tl_mesh* m) {
   const int64_t nn = m->nn, n = 3 * nn;
   PcgWork* w = new PcgWork();
   m->pcg = w;
-  w->nparts = (int)std::max<int64_t>((nn + kBlock - 1) / kBlock, (16 * nn + kBlock - 1) / kBlock);
+  w->nparts = (int)std::max<int64_t>((nn + kBlock - 1) / kBlock, (32 * nn + kBlock - 1) / kBlock);
   TL_CUDA(m, cudaMalloc(&w->r, sizeof(double) * n));
   TL_CUDA(m, cudaMalloc(&w->z, sizeof(double) * n));
   TL_CUDA(m, cudaMalloc(&w->p, sizeof(double) * n));
@@ -515,8 +582,13 @@ tl_status pcg_prepare(tl_mesh* m, const void* values, const double* g, double* d
 template <typename T, int G>
 void launch_spmv(tl_mesh* m, const void* values, PcgWork* w, unsigned* nblocks) {
   const int64_t nn = m->nn;
-  const unsigned nb = (unsigned)((G * nn + kBlock - 1) / kBlock);
-  if (std::is_same<T, float>::value && pcg_float32(m))
+  unsigned nb = (unsigned)((G * nn + kBlock - 1) / kBlock);
+  if (std::is_same<T, float>::value && pcg_float32(m) && m->tune.spmv_row) {
+    // a grid of at most 8 blocks per SM (one resident wave) and nparts blocks
+    nb = (unsigned)std::min(std::min((int64_t)nb, (int64_t)8 * m->num_sms), (int64_t)w->nparts);
+    spmv_row32<G><<<nb, kBlock, 0, m->stream>>>((const float*)values, m->d_node_ptr, m->d_node_col, nn, w->p32,
+                                                w->Ap32, w->part, w->scal, w->tickets);
+  } else if (std::is_same<T, float>::value && pcg_float32(m))
     spmv_node32<G><<<nb, kBlock, 0, m->stream>>>((const float*)values, m->d_node_ptr, m->d_node_col, nn, w->p32,
                                                  w->Ap32, w->part, w->scal, w->tickets);
   else
@@ -532,6 +604,7 @@ tl_status pcg_spmv_only(tl_mesh* m, const void* values, int group) {
   const bool fp32 = m->precision == TL_FP32_ELEM;
   if (group == 4) fp32 ? launch_spmv<float, 4>(m, values, w, &nbs) : launch_spmv<double, 4>(m, values, w, &nbs);
   else if (group == 16) fp32 ? launch_spmv<float, 16>(m, values, w, &nbs) : launch_spmv<double, 16>(m, values, w, &nbs);
+  else if (group == 32) fp32 ? launch_spmv<float, 32>(m, values, w, &nbs) : launch_spmv<double, 32>(m, values, w, &nbs);
   else fp32 ? launch_spmv<float, 8>(m, values, w, &nbs) : launch_spmv<double, 8>(m, values, w, &nbs);
   TL_CUDA(m, cudaGetLastError());
   ++m->launches;
@@ -554,10 +627,12 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
     if (fp32) {
       if (G == 4) launch_spmv<float, 4>(m, values, w, &nbs);
       else if (G == 16) launch_spmv<float, 16>(m, values, w, &nbs);
+      else if (G == 32) launch_spmv<float, 32>(m, values, w, &nbs);
       else launch_spmv<float, 8>(m, values, w, &nbs);
     } else {
       if (G == 4) launch_spmv<double, 4>(m, values, w, &nbs);
       else if (G == 16) launch_spmv<double, 16>(m, values, w, &nbs);
+      else if (G == 32) launch_spmv<double, 32>(m, values, w, &nbs);
       else launch_spmv<double, 8>(m, values, w, &nbs);
     }
     (void)nbs;

@@ -11,7 +11,9 @@
 //     cp.async prefetch of the next tile (or none), and warp specialisation
 //     (scatter warps issue a tile's reductions while the compute warps
 //     evaluate the next tile) and two CTAs per SM (64 registers, no prefetch);
-//   * PCG product H p: 4, 8 or 16 lanes per node;
+//   * PCG product H p: 4, 8 or 16 lanes per node, one neighbour per lane;
+//     for the float32 iteration also 8, 16 or 32 lanes per node along the
+//     contiguous rows;
 //   * residual: 1 or 4 lanes per node.
 // Each variant is warmed up once and timed over `reps` launches with CUDA
 // events on the handle's stream; the fastest is kept in the handle and used by
@@ -123,6 +125,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   }
   // PCG product: lanes per node
   if (st == TL_OK) st = pcg_ensure(m);
+  m->tune.spmv_row = 0;
   best = 1e30f;
   const int groups[3] = {4, 8, 16};
   for (int k = 0; k < 3 && st == TL_OK; ++k) {
@@ -133,7 +136,25 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     if (ms < best) {
       best = ms;
       chosen.spmv_group = groups[k];
+      chosen.spmv_row = 0;
     }
+  }
+  // float32 iteration: the row-contiguous product with 8, 16, 32 lanes per node
+  if (st == TL_OK && pcg_float32(m)) {
+    const int rgroups[3] = {8, 16, 32};
+    m->tune.spmv_row = 1;
+    for (int k = 0; k < 3 && st == TL_OK; ++k) {
+      float ms = 0.f;
+      st = time_reps(m, reps, [&]() { return pcg_spmv_only(m, values, rgroups[k]); }, &ms);
+      if (st != TL_OK) break;
+      r.ms_spmv_row[k] = ms;
+      if (ms < best) {
+        best = ms;
+        chosen.spmv_group = rgroups[k];
+        chosen.spmv_row = 1;
+      }
+    }
+    m->tune.spmv_row = saved.spmv_row;
   }
   // residual: lanes per node (zero force, the handle's current lambda-free state)
   double* g = nullptr;
@@ -180,6 +201,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.elem_occ2 = chosen.elem_occ2;
   r.elem_spread = chosen.elem_spread;
   r.pcg_f32 = chosen.pcg_f32;
+  r.spmv_row = chosen.spmv_row;
   if (out) *out = r;
   return TL_OK;
 }
@@ -196,17 +218,20 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.elem_occ2 = m->tune.elem_occ2;
   r.elem_spread = m->tune.elem_spread;
   r.pcg_f32 = m->tune.pcg_f32;
+  r.spmv_row = m->tune.spmv_row;
   *out = r;
   return TL_OK;
 }
 
 extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   if (!m || !in) return TL_ERR_INVALID_ARG;
-  if (in->spmv_group != 4 && in->spmv_group != 8 && in->spmv_group != 16) return TL_ERR_INVALID_ARG;
+  if (in->spmv_group != 4 && in->spmv_group != 8 && in->spmv_group != 16 && in->spmv_group != 32)
+    return TL_ERR_INVALID_ARG;
   if ((in->elem_xchg != 0 && in->elem_xchg != 1) || (in->elem_full_grid != 0 && in->elem_full_grid != 1) ||
       (in->elem_prefetch != 0 && in->elem_prefetch != 1) || (in->elem_ws != 0 && in->elem_ws != 1) ||
       (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1) ||
-      (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1))
+      (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1) ||
+      (in->spmv_row != 0 && in->spmv_row != 1))
     return TL_ERR_INVALID_ARG;
   m->tune.spmv_group = in->spmv_group;
   m->tune.elem_prefetch = in->elem_prefetch;
@@ -217,6 +242,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   m->tune.elem_xchg = in->elem_xchg;
   m->tune.elem_full_grid = in->elem_full_grid;
   m->tune.pcg_f32 = in->pcg_f32;
+  m->tune.spmv_row = in->spmv_row;
   m->tune.generation += 1;
   return TL_OK;
 }

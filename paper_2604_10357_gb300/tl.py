@@ -69,7 +69,7 @@ class tl_tune_result(C.Structure):
                 ("elem_occ2", C.c_int32), ("elem_spread", C.c_int32),
                 ("ms_element", C.c_float * 8), ("ms_ws", C.c_float), ("ms_spmv", C.c_float * 3),
                 ("ms_residual", C.c_float * 2), ("ms_occ2", C.c_float), ("ms_spread", C.c_float),
-                ("pcg_f32", C.c_int32)]
+                ("pcg_f32", C.c_int32), ("spmv_row", C.c_int32), ("ms_spmv_row", C.c_float * 3)]
 
 
 # every symbol declared in include/tl.h, with (restype, argtypes)
@@ -161,7 +161,8 @@ def _tune_dict(r):
                 elem_prefetch=r.elem_prefetch, elem_ws=r.elem_ws, residual_lanes=r.residual_lanes,
                 elem_occ2=r.elem_occ2, elem_spread=r.elem_spread, ms_element=list(r.ms_element),
                 ms_ws=r.ms_ws, ms_spmv=list(r.ms_spmv), ms_residual=list(r.ms_residual), ms_occ2=r.ms_occ2,
-                ms_spread=r.ms_spread, pcg_f32=r.pcg_f32)
+                ms_spread=r.ms_spread, pcg_f32=r.pcg_f32,
+                spmv_row=r.spmv_row, ms_spmv_row=list(r.ms_spmv_row))
 
 
 def _stream_ptr():
@@ -318,11 +319,11 @@ class Mesh:
         return _tune_dict(r)
 
     def tune_set(self, spmv_group=4, elem_xchg=1, elem_full_grid=0, elem_prefetch=1, elem_ws=0, residual_lanes=1,
-                 elem_occ2=1, elem_spread=0, pcg_f32=1):
+                 elem_occ2=1, elem_spread=0, pcg_f32=1, spmv_row=0):
         r = tl_tune_result()
         r.spmv_group, r.elem_xchg, r.elem_full_grid = spmv_group, elem_xchg, elem_full_grid
         r.elem_prefetch, r.elem_ws, r.residual_lanes = elem_prefetch, elem_ws, residual_lanes
-        r.elem_occ2, r.elem_spread, r.pcg_f32 = elem_occ2, elem_spread, pcg_f32
+        r.elem_occ2, r.elem_spread, r.pcg_f32, r.spmv_row = elem_occ2, elem_spread, pcg_f32, spmv_row
         self._check(self.lib.tl_tune_set(self.h, C.byref(r)))
 
     def timing_enable(self, on=True):

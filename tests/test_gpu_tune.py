@@ -32,7 +32,7 @@ def test_autotune_reports_and_keeps_a_choice():
     g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
     g.build_pattern(m.fixed_nodes)
     rep = g.autotune(_dev(w["q_n"]), _dev(w["v"]), w["h"], reps=3)
-    assert rep["spmv_group"] in (4, 8, 16)
+    assert rep["spmv_group"] in (4, 8, 16, 32) and rep["spmv_row"] in (0, 1)
     assert rep["elem_xchg"] in (0, 1) and rep["elem_full_grid"] in (0, 1)
     assert all(t > 0 for t in rep["ms_element"]) and all(t > 0 for t in rep["ms_spmv"]) and rep["ms_ws"] > 0
     assert rep["ms_occ2"] > 0
@@ -44,11 +44,16 @@ def test_autotune_reports_and_keeps_a_choice():
     else:
         k = 4 * (1 - rep["elem_prefetch"]) + 2 * (1 - rep["elem_xchg"]) + rep["elem_full_grid"]
         assert rep["ms_element"][k] == best
-    assert rep["ms_spmv"][(4, 8, 16).index(rep["spmv_group"])] == min(rep["ms_spmv"])
+    assert all(t > 0 for t in rep["ms_spmv_row"])          # the float32 iteration times the row form too
+    spmv_best = min(rep["ms_spmv"] + rep["ms_spmv_row"])
+    if rep["spmv_row"]:
+        assert rep["ms_spmv_row"][(8, 16, 32).index(rep["spmv_group"])] == spmv_best
+    else:
+        assert rep["ms_spmv"][(4, 8, 16).index(rep["spmv_group"])] == spmv_best
     assert rep["ms_residual"][(1, 4).index(rep["residual_lanes"])] == min(rep["ms_residual"])
     cur = g.tune_get()
     keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes", "elem_occ2",
-            "elem_spread")
+            "elem_spread", "spmv_row", "pcg_f32")
     assert all(cur[k] == rep[k] for k in keys)
     with pytest.raises(tl.TLError):
         g.tune_set(spmv_group=5)
@@ -94,3 +99,27 @@ def test_every_spmv_shape_converges_to_the_same_state(group):
         assert st["converged"] == 1
         out[gr] = v.cpu().numpy()
     assert np.linalg.norm(out[group] - out[8]) <= 1e-9 * np.linalg.norm(out[8])
+
+
+@pytest.mark.parametrize("row,group", [(0, 4), (0, 16), (1, 8), (1, 16), (1, 32)])
+def test_every_float32_spmv_shape_converges_to_the_same_state(row, group):
+    """Float32 Hessian, float32 PCG iteration: each product shape (one
+    neighbour per lane, or lanes along the contiguous rows) gives the same
+    converged Newton step as the 8-lane neighbour form, to the residual's
+    tolerance, with the same Newton count."""
+    tl = _tl()
+    w = inputs.workload_small_svk()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
+    g.build_pattern(m.fixed_nodes)
+    p = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG)
+    out = {}
+    for key, (r, gr) in (("ref", (0, 8)), ("test", (row, group))):
+        g.tune_set(spmv_group=gr, spmv_row=r)
+        lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+        v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+        assert st["converged"] == 1 and st["g_norm"] <= 1e-8 * st["g_ref"]
+        out[key] = (v.cpu().numpy(), st)
+    (v0, s0), (v1, s1) = out["ref"], out["test"]
+    assert s1["inner_iters"] == s0["inner_iters"]
+    assert np.linalg.norm(v1 - v0) <= 1e-7 * np.linalg.norm(v0)
