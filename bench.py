@@ -341,10 +341,10 @@ def run_ours(args, rank, world):
                    "l2": "no flush: the H values written every step (%.2f GB) exceed L2" % (nnz * vbytes / 1e9),
                    "parallelism": f"replicas x{world}", "pattern_build_s": t_pat,
                    "launch_shapes": {k: tune[k] for k in ("elem_ws", "elem_occ2", "elem_spread", "elem_prefetch",
-                                                          "elem_xchg", "elem_full_grid", "spmv_group", "spmv_row",
+                                                          "elem_xchg", "elem_full_grid", "elem_agg", "spmv_group", "spmv_row",
                                                           "residual_lanes")},
                    "launch_shape_ms": {k: tune[k] for k in ("ms_ws", "ms_occ2", "ms_spread", "ms_element",
-                                                            "ms_spmv", "ms_spmv_row", "ms_residual")}},
+                                                            "ms_agg", "ms_spmv", "ms_spmv_row", "ms_residual")}},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(tim["launches"]),
@@ -386,7 +386,8 @@ def run_newton(args):
     model = warmstart.WarmStartModel.from_npz(model_path) if os.path.exists(model_path) else None
     c_mode = "mlp" if model is not None else "extrapolation"
     # launch shapes of both arms picked by the autotuner on the first held-out state (untimed)
-    shape_keys = ("elem_occ2", "elem_prefetch", "elem_xchg", "elem_full_grid", "spmv_group", "spmv_row", "pcg_f32")
+    shape_keys = ("elem_occ2", "elem_prefetch", "elem_xchg", "elem_full_grid", "elem_agg", "spmv_group", "spmv_row",
+                  "pcg_f32")
     shapes = {}
     for name, g in (("plain", g64), ("chosen", g32)):
         t = g.tune_get() if args.no_autotune else g.autotune(tr.q[test_idx[0]], tr.v[test_idx[0]], w["h"], reps=3)

@@ -291,6 +291,7 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *     tile order (in order, or permuted so that tiles in flight are far apart);
  *   PCG product H p: 4, 8 or 16 lanes per node (one neighbour per lane), and for the
  *     float32 iteration 8, 16 or 32 lanes per node along the contiguous rows;
+ *   the fastest exchanged FP32 variant with per-tile aggregation of shared node pairs;
  *   residual: 1 or 4 lanes per node.
  * reps timed launches per variant after one warm-up.  Needs the pattern;
  * allocates and frees one CSR values array and one force array.  Synchronous.
@@ -318,6 +319,10 @@ typedef struct tl_tune_result {
   int32_t spmv_row;           /* float32 PCG iteration: 1 = row-contiguous H p (the group's lanes read
                                  contiguous runs of the three rows), 0 = one neighbour per lane */
   float ms_spmv_row[3];       /* measured row-contiguous H p with 8, 16, 32 lanes per node (0: not measured) */
+  int32_t elem_agg;           /* 1: FP32 exchanged assembly sums the node-pair blocks that several elements
+                                 of a 32-element tile share before the reductions (per-tile maps built on
+                                 the device on first use: about 38 KB per tile; needs < 2^24 nodes) */
+  float ms_agg;               /* measured time of the fastest exchanged variant with aggregation (0: not measured) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

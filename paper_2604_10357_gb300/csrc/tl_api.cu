@@ -65,6 +65,7 @@ void free_mesh(tl_mesh* m) {
                   m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_values};
   solver_destroy(m->solver);
   pcg_destroy(m->pcg);
+  tile_maps_free(m);
   newton_graph_destroy(m->ngraph);
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -83,6 +83,11 @@ struct Args {
   int32_t pf_off;      // byte offset of the prefetch buffer in shared memory (-1: none)
   int32_t meta_off;    // byte offset of the second scatter-metadata buffer (warp-specialised kernel)
   int32_t x_alias;     // 1: the exchange buffer overlays the force and tangent arrays (two CTAs per SM)
+  int32_t agg;         // 1: per-tile aggregation of shared node pairs (maps below)
+  const int2* agg_slot;        // per tile: CSR position of row 3I and row stride of each distinct pair
+  const uint16_t* agg_cptr;    // per tile: first contribution of each pair
+  const uint16_t* agg_code;    // per tile: exchange-buffer block (+ transposed flag) of each contribution
+  const int32_t* agg_nu;       // per tile: number of distinct pairs
 };
 
 // Per-element shared-memory strides padded to odd word counts so that lanes
@@ -553,6 +558,40 @@ __device__ __forceinline__ void tangent_xchg_scatter(const Args<float>& A, const
   }
 }
 
+// Aggregated scatter of one tile from the exchange buffer: thread -> distinct
+// node pair u of the tile (consecutive threads, consecutive CSR blocks), the
+// 3x3 block summed over the elements that contribute to it (an upper-triangle
+// block of X, or its transpose for a lower one), then one run of three
+// reductions per row.  Replaces one reduction per element entry by one per
+// entry of the tile.
+__device__ __forceinline__ void tangent_agg_scatter(const Args<float>& A, const float* X, int64_t tile) {
+  const int nu = A.agg_nu[tile];
+  const int2* slot = A.agg_slot + tile * kAggCap;
+  const uint16_t* cptr = A.agg_cptr + tile * (kAggCap + 1);
+  const uint16_t* code = A.agg_code + tile * kAggCap;
+#pragma unroll 1
+  for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+    const int2 s = slot[u];
+    const int c0 = cptr[u], c1 = cptr[u + 1];
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = 0.0f;
+#pragma unroll 1
+    for (int c = c0; c < c1; ++c) {
+      const int cd = code[c];
+      const float* xb = X + (cd & 0x7fff);
+      const int sd = (cd & 0x8000) ? 1 : 3, sk = (cd & 0x8000) ? 3 : 1;   // row / column strides
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[3 * d + k] += xb[d * sd + k * sk];
+    }
+    red_run(A, s.x, v[0], v[1], v[2]);
+    red_run(A, s.x + s.y, v[3], v[4], v[5]);
+    red_run(A, s.x + 2 * s.y, v[6], v[7], v[8]);
+  }
+}
+
 constexpr int kXFloats = 32 * 55 * 9;   // exchange buffer of the FP32 assembly
 
 // Block rows a0 = P (b = P..9) and a1 = 9 - P (b = 9-P..9): 11 blocks, so the
@@ -594,7 +633,10 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
           default: tangent_xchg_accumulate<4>(A, sm, X, i, false, alias); break;
         }
         __syncthreads();               // reached by every thread of the block
-        tangent_xchg_scatter(A, sm.meta, X, e0, A.real_end, p, i);
+        if (A.agg)
+          tangent_agg_scatter(A, X, e0 / E);
+        else
+          tangent_xchg_scatter(A, sm.meta, X, e0, A.real_end, p, i);
         return;
       }
     }
@@ -1004,6 +1046,13 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   A.pf_off = pf_off;
   A.meta_off = meta_off;
   A.x_alias = 0;
+  // per-tile aggregation: exchanged float32 assembly without warp
+  // specialisation, once the maps exist (built by the autotuner or tl_tune_set)
+  A.agg = (xchg && !ws && m->tune.elem_agg && m->agg_nu) ? 1 : 0;
+  A.agg_slot = m->agg_slot;
+  A.agg_cptr = m->agg_cptr;
+  A.agg_code = m->agg_code;
+  A.agg_nu = m->agg_nu;
   cudaEvent_t t0 = timer_open(m);
   // Segments in groups of at most kMaxSeg, one persistent launch per group.
   // The float32 kernels include an all-materials variant; the float64 ones

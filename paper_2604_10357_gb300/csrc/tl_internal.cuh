@@ -17,6 +17,10 @@ namespace tl {
 // segment of the internal element order is padded to a multiple of this.
 constexpr int kTile = 32;
 
+// Capacity of a tile's aggregation map (distinct node-pair blocks and
+// contributions): 32 elements x 100 ordered pairs.
+constexpr int kAggCap = kTile * 100;
+
 // Tile counters of the persistent element launches (one per launch of a pass).
 constexpr int kTileCounters = 256;
 
@@ -55,6 +59,7 @@ struct Tune {
   int elem_occ2 = 1;      // float32 CSR assembly: 1 = two CTAs per SM (64 registers, overlaid exchange buffer)
   int elem_spread = 0;    // element kernels: 1 = tiles in flight spread over the mesh (permuted launch order)
   int pcg_f32 = 1;        // float32 Hessian: 1 = PCG vectors in float32 (dot products float64)
+  int elem_agg = 0;       // float32 exchanged assembly: 1 = per-tile aggregation of shared node pairs
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };
@@ -91,6 +96,12 @@ struct tl_mesh {
   int64_t nfixed = 0;
   int32_t* d_fixed_of_node = nullptr;  // nn: j (index in sorted fixed list) or -1
   int32_t* d_fixed_diag = nullptr;     // 3 nfixed: CSR position of (r, r)
+
+  // per-tile aggregation maps of the float32 assembly (tl_tilemap.cu), built on demand
+  int2* agg_slot = nullptr;       // ntiles x kAggCap
+  uint16_t* agg_cptr = nullptr;   // ntiles x (kAggCap + 1)
+  uint16_t* agg_code = nullptr;   // ntiles x kAggCap
+  int32_t* agg_nu = nullptr;      // ntiles
 
   // scratch
   uint32_t* d_flags = nullptr;    // sticky device status
@@ -138,6 +149,9 @@ tl_status launch_force_prec(tl_mesh* m, const double* q_n, const double* v, doub
 
 // sparse direct solver (tl_solver.cu) and PCG (tl_pcg.cu)
 void solver_destroy(Solver* s);
+// per-tile aggregation maps of the float32 assembly (tl_tilemap.cu)
+tl_status tile_maps_ensure(tl_mesh* m);
+void tile_maps_free(tl_mesh* m);
 void pcg_destroy(PcgWork* w);
 void newton_graph_destroy(NewtonGraph* g);
 tl_status pcg_ensure(tl_mesh* m);

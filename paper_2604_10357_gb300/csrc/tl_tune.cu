@@ -11,6 +11,8 @@
 //     cp.async prefetch of the next tile (or none), and warp specialisation
 //     (scatter warps issue a tile's reductions while the compute warps
 //     evaluate the next tile) and two CTAs per SM (64 registers, no prefetch);
+//     for the fastest exchanged variant also the per-tile aggregation of the
+//     node pairs that several elements of a tile share;
 //   * PCG product H p: 4, 8 or 16 lanes per node, one neighbour per lane;
 //     for the float32 iteration also 8, 16 or 32 lanes per node along the
 //     contiguous rows;
@@ -18,6 +20,7 @@
 // Each variant is warmed up once and timed over `reps` launches with CUDA
 // events on the handle's stream; the fastest is kept in the handle and used by
 // every later call (a captured Newton graph is rebuilt on its next use).
+#include <algorithm>
 #include <vector>
 
 #include "tl_internal.cuh"
@@ -120,8 +123,27 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     if (st == TL_OK) {
       r.ms_spread = ms;
       chosen.elem_spread = ms < best ? 1 : 0;
+      best = std::min(best, ms);
     }
     m->tune = saved;
+  }
+  // per-tile aggregation of shared node pairs on the fastest exchanged
+  // float32 variant (needs the tile maps; meshes they do not fit skip it)
+  if (st == TL_OK && fp32 && chosen.elem_xchg && !chosen.elem_ws && m->nn < (int64_t(1) << 24)) {
+    st = tile_maps_ensure(m);
+    if (st == TL_OK) {
+      m->tune = chosen;
+      m->tune.elem_agg = 1;
+      float ms = 0.f;
+      st = time_reps(m, reps, [&]() {
+        return launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
+      }, &ms);
+      if (st == TL_OK) {
+        r.ms_agg = ms;
+        chosen.elem_agg = ms < best ? 1 : 0;
+      }
+      m->tune = saved;
+    }
   }
   // PCG product: lanes per node
   if (st == TL_OK) st = pcg_ensure(m);
@@ -202,6 +224,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.elem_spread = chosen.elem_spread;
   r.pcg_f32 = chosen.pcg_f32;
   r.spmv_row = chosen.spmv_row;
+  r.elem_agg = chosen.elem_agg;
   if (out) *out = r;
   return TL_OK;
 }
@@ -219,6 +242,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.elem_spread = m->tune.elem_spread;
   r.pcg_f32 = m->tune.pcg_f32;
   r.spmv_row = m->tune.spmv_row;
+  r.elem_agg = m->tune.elem_agg;
   *out = r;
   return TL_OK;
 }
@@ -231,8 +255,9 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
       (in->elem_prefetch != 0 && in->elem_prefetch != 1) || (in->elem_ws != 0 && in->elem_ws != 1) ||
       (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1) ||
       (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1) ||
-      (in->spmv_row != 0 && in->spmv_row != 1))
+      (in->spmv_row != 0 && in->spmv_row != 1) || (in->elem_agg != 0 && in->elem_agg != 1))
     return TL_ERR_INVALID_ARG;
+  if (in->elem_agg && m->precision == TL_FP32_ELEM) TL_TRY(tile_maps_ensure(m));
   m->tune.spmv_group = in->spmv_group;
   m->tune.elem_prefetch = in->elem_prefetch;
   m->tune.elem_ws = in->elem_ws;
@@ -243,6 +268,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   m->tune.elem_full_grid = in->elem_full_grid;
   m->tune.pcg_f32 = in->pcg_f32;
   m->tune.spmv_row = in->spmv_row;
+  m->tune.elem_agg = in->elem_agg;
   m->tune.generation += 1;
   return TL_OK;
 }

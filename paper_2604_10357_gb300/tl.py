@@ -69,7 +69,8 @@ class tl_tune_result(C.Structure):
                 ("elem_occ2", C.c_int32), ("elem_spread", C.c_int32),
                 ("ms_element", C.c_float * 8), ("ms_ws", C.c_float), ("ms_spmv", C.c_float * 3),
                 ("ms_residual", C.c_float * 2), ("ms_occ2", C.c_float), ("ms_spread", C.c_float),
-                ("pcg_f32", C.c_int32), ("spmv_row", C.c_int32), ("ms_spmv_row", C.c_float * 3)]
+                ("pcg_f32", C.c_int32), ("spmv_row", C.c_int32), ("ms_spmv_row", C.c_float * 3),
+                ("elem_agg", C.c_int32), ("ms_agg", C.c_float)]
 
 
 # every symbol declared in include/tl.h, with (restype, argtypes)
@@ -162,7 +163,7 @@ def _tune_dict(r):
                 elem_occ2=r.elem_occ2, elem_spread=r.elem_spread, ms_element=list(r.ms_element),
                 ms_ws=r.ms_ws, ms_spmv=list(r.ms_spmv), ms_residual=list(r.ms_residual), ms_occ2=r.ms_occ2,
                 ms_spread=r.ms_spread, pcg_f32=r.pcg_f32,
-                spmv_row=r.spmv_row, ms_spmv_row=list(r.ms_spmv_row))
+                spmv_row=r.spmv_row, ms_spmv_row=list(r.ms_spmv_row), elem_agg=r.elem_agg, ms_agg=r.ms_agg)
 
 
 def _stream_ptr():
@@ -319,11 +320,12 @@ class Mesh:
         return _tune_dict(r)
 
     def tune_set(self, spmv_group=4, elem_xchg=1, elem_full_grid=0, elem_prefetch=1, elem_ws=0, residual_lanes=1,
-                 elem_occ2=1, elem_spread=0, pcg_f32=1, spmv_row=0):
+                 elem_occ2=1, elem_spread=0, pcg_f32=1, spmv_row=0, elem_agg=0):
         r = tl_tune_result()
         r.spmv_group, r.elem_xchg, r.elem_full_grid = spmv_group, elem_xchg, elem_full_grid
         r.elem_prefetch, r.elem_ws, r.residual_lanes = elem_prefetch, elem_ws, residual_lanes
         r.elem_occ2, r.elem_spread, r.pcg_f32, r.spmv_row = elem_occ2, elem_spread, pcg_f32, spmv_row
+        r.elem_agg = elem_agg
         self._check(self.lib.tl_tune_set(self.h, C.byref(r)))
 
     def timing_enable(self, on=True):

@@ -89,15 +89,21 @@ def test_one_persistent_launch_and_sampled_element_parity(batched):
     assert np.all(np.linalg.norm(tot, axis=1) <= 1e-6 * mag)
 
 
-def test_sampled_hessian_rows(batched):
+@pytest.mark.parametrize("agg", [0, 1])
+def test_sampled_hessian_rows(batched, agg):
     """CSR rows of a few nodes per body: every entry against the oracle's
     element matrices (mass / h + h K_t + D) summed over the elements at the
-    node, plus the clamp penalty."""
+    node, plus the clamp penalty; with the per-element scatter and with the
+    per-tile aggregation of shared node pairs (tiles of both materials, both
+    body shapes, and tiles that straddle two bodies)."""
     tl, w, g, _ = batched
     m = w["mesh"]
     h, rho = w["h"], 1e12
     rng = np.random.default_rng(32)
+    g.tune_set(elem_agg=agg)
+    assert g.tune_get()["elem_agg"] == agg
     vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho)
+    g.tune_set()
     row_ptr, col = (a.cpu().numpy() for a in g.get_pattern()[:2])
     starts = np.concatenate([[0], np.cumsum([b.nn for b in w["meshes"]])])
     nodes = np.unique(np.concatenate([rng.integers(starts[b], starts[b + 1], size=2)

@@ -53,17 +53,24 @@ def test_autotune_reports_and_keeps_a_choice():
     assert rep["ms_residual"][(1, 4).index(rep["residual_lanes"])] == min(rep["ms_residual"])
     cur = g.tune_get()
     keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes", "elem_occ2",
-            "elem_spread", "spmv_row", "pcg_f32")
+            "elem_spread", "spmv_row", "pcg_f32", "elem_agg")
     assert all(cur[k] == rep[k] for k in keys)
+    # refinements of the fastest exchanged variant: tile order, then aggregation
+    if not rep["elem_ws"] and (rep["elem_occ2"] or rep["elem_xchg"]):
+        assert rep["ms_agg"] > 0
+        others = [best] + ([rep["ms_spread"]] if rep["ms_spread"] > 0 else [])
+        assert (rep["ms_agg"] < min(others)) == bool(rep["elem_agg"])
     with pytest.raises(tl.TLError):
         g.tune_set(spmv_group=5)
 
 
-@pytest.mark.parametrize("prefetch,xchg,full_grid,ws,occ2,spread",
-                         [(pf, x, f, 0, 0, 0) for pf in (0, 1) for x in (0, 1) for f in (0, 1)]
-                         + [(1, 1, 0, 1, 0, 0), (0, 1, 0, 0, 1, 0), (0, 1, 0, 0, 1, 1), (1, 1, 0, 0, 0, 1),
-                            (1, 0, 0, 0, 0, 1)])
-def test_every_element_variant_matches_oracle(xchg, full_grid, prefetch, ws, occ2, spread):
+@pytest.mark.parametrize("prefetch,xchg,full_grid,ws,occ2,spread,agg",
+                         [(pf, x, f, 0, 0, 0, 0) for pf in (0, 1) for x in (0, 1) for f in (0, 1)]
+                         + [(1, 1, 0, 1, 0, 0, 0), (0, 1, 0, 0, 1, 0, 0), (0, 1, 0, 0, 1, 1, 0), (1, 1, 0, 0, 0, 1, 0),
+                            (1, 0, 0, 0, 0, 1, 0),
+                            (0, 1, 0, 0, 1, 0, 1), (0, 1, 0, 0, 1, 1, 1), (1, 1, 0, 0, 0, 0, 1), (0, 1, 1, 0, 0, 0, 1),
+                            (0, 1, 0, 0, 0, 0, 1)])
+def test_every_element_variant_matches_oracle(xchg, full_grid, prefetch, ws, occ2, spread, agg):
     tl = _tl()
     w = inputs.workload_small_svk()
     m = w["mesh"]
@@ -71,7 +78,7 @@ def test_every_element_variant_matches_oracle(xchg, full_grid, prefetch, ws, occ
     g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
     g.build_pattern(m.fixed_nodes)
     g.tune_set(spmv_group=8, elem_xchg=xchg, elem_full_grid=full_grid, elem_prefetch=prefetch, elem_ws=ws,
-               elem_occ2=occ2, elem_spread=spread)
+               elem_occ2=occ2, elem_spread=spread, elem_agg=agg)
     h, rho = w["h"], 1e12
     vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho).cpu().numpy().astype(np.float64)
     ref = om.hessian_values(w["q_n"], w["v"], h, rho)
