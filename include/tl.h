@@ -147,7 +147,10 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
  * CSR pattern of H (3x3 blocks per adjacent node pair, rows and columns
  * ascending, full symmetric storage), the per-element slot map, the
  * consistent mass (Sec. 4.1, integrated exactly) and the clamp constraint
- * rows (identity rows of C_q, one per DOF of each fixed node).
+ * rows (identity rows of C_q, one per DOF of each fixed node).  For a
+ * TL_FP32_ELEM handle with fewer than 2^24 nodes also the per-tile
+ * aggregation maps of the assembly (distinct node pairs of each 32-element
+ * tile and the element blocks that add to them; about 38 KB per tile).
  *   fixed_nodes  HOST, nfixed int32 node ids (any order, no duplicates)
  *   nnz_out      HOST, receives nnz of H
  * Synchronous.  TL_ERR_OVERFLOW if nnz >= 2^31. */
@@ -321,7 +324,8 @@ typedef struct tl_tune_result {
   float ms_spmv_row[3];       /* measured row-contiguous H p with 8, 16, 32 lanes per node (0: not measured) */
   int32_t elem_agg;           /* 1: FP32 exchanged assembly sums the node-pair blocks that several elements
                                  of a 32-element tile share before the reductions (per-tile maps built on
-                                 the device on first use: about 38 KB per tile; needs < 2^24 nodes) */
+                                 the device by tl_build_pattern for FP32 handles with < 2^24 nodes: about
+                                 38 KB per tile of 32 elements); default 1 */
   float ms_agg;               /* measured time of the fastest exchanged variant with aggregation (0: not measured) */
 } tl_tune_result;
 

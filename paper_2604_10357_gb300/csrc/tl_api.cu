@@ -287,6 +287,12 @@ tl_status tl_build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixe
   if (m->have_pattern) return fail(m, TL_ERR_STATE, "pattern already built");
   tl_status s = build_pattern(m, fixed_nodes, nfixed);
   if (s != TL_OK) return s;
+  // float32 handles: the per-tile aggregation maps of the assembly, built
+  // with the pattern so that the default launch shape can use them
+  if (m->precision == TL_FP32_ELEM && m->nn < (int64_t(1) << 24)) {
+    s = tile_maps_ensure(m);
+    if (s != TL_OK) return s;
+  }
   if (nnz_out) *nnz_out = m->nnz;
   return TL_OK;
 }

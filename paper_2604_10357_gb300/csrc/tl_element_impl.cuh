@@ -134,13 +134,13 @@ __device__ __forceinline__ void load_tile(const Args<T>& A, Smem<T>& sm, int64_t
     const int e = t / 10, a = t % 10;
     const int node = A.conn[(e0 + e) * 10 + a];
     sm.node[a][e] = node;
-    if (NEED_PATTERN) {
+    if (NEED_PATTERN && !A.agg) {     // the aggregated scatter reads the tile maps instead
       const int p0 = A.node_ptr[node], p1 = A.node_ptr[node + 1];
       mt.rbase[a][e] = 9 * p0;
       mt.rstr[a][e] = 3 * (p1 - p0);
     }
   }
-  if (NEED_PATTERN) {
+  if (NEED_PATTERN && !A.agg) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(A.blk + e0 * 100);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&mt.blk[0][0]);
     for (int t = tid; t < E * 25; t += NT) dst[t] = src[t];
@@ -204,7 +204,8 @@ __device__ __forceinline__ void prefetch_stage1(const Args<T>& A, Prefetch<T>& P
   const unsigned char* c = reinterpret_cast<const unsigned char*>(A.conn + e0 * 10);
   const unsigned char* g = reinterpret_cast<const unsigned char*>(A.geo + e0 * 16);
   const unsigned char* b = A.blk + e0 * 100;
-  constexpr int nc = E * 10 * 4 / 16, ng = E * 16 * (int)sizeof(T) / 16, nb = E * 100 / 16;
+  constexpr int nc = E * 10 * 4 / 16, ng = E * 16 * (int)sizeof(T) / 16;
+  const int nb = A.agg ? 0 : E * 100 / 16;       // slot blocks: not read by the aggregated scatter
   for (int k = tid; k < nc + ng + nb; k += NT) {
     if (k < nc) cp_async16(reinterpret_cast<unsigned char*>(P.conn) + 16 * k, c + 16 * k);
     else if (k < nc + ng) cp_async16(reinterpret_cast<unsigned char*>(P.geo) + 16 * (k - nc), g + 16 * (k - nc));
@@ -220,6 +221,7 @@ __device__ __forceinline__ void prefetch_stage2(const Args<T>& A, Prefetch<T>& P
   // element index fastest: consecutive threads write consecutive words
   for (int t = tid; t < E * 10; t += NT) {
     const int a = t / E, e = t % E;
+    if (A.agg) break;                              // row pointers: only for the per-element scatter
     const int node = P.conn[e * 10 + a];
     cp_async4(&P.nptr[0][a][e], A.node_ptr + node);
     cp_async4(&P.nptr[1][a][e], A.node_ptr + node + 1);
@@ -241,13 +243,13 @@ __device__ __forceinline__ void unpack_tile(const Args<T>& A, Smem<T>& sm, const
   for (int t = tid; t < E * 10; t += NT) {
     const int a = t / E, e = t % E;
     sm.node[a][e] = P.conn[e * 10 + a];
-    if (NEED_PATTERN) {
+    if (NEED_PATTERN && !A.agg) {
       const int p0 = P.nptr[0][a][e], p1 = P.nptr[1][a][e];
       mt.rbase[a][e] = 9 * p0;
       mt.rstr[a][e] = 3 * (p1 - p0);
     }
   }
-  if (NEED_PATTERN) {
+  if (NEED_PATTERN && !A.agg) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(P.blk);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&mt.blk[0][0]);
     for (int t = tid; t < E * 25; t += NT) dst[t] = src[t];
@@ -569,26 +571,48 @@ __device__ __forceinline__ void tangent_agg_scatter(const Args<float>& A, const 
   const int2* slot = A.agg_slot + tile * kAggCap;
   const uint16_t* cptr = A.agg_cptr + tile * (kAggCap + 1);
   const uint16_t* code = A.agg_code + tile * kAggCap;
+  // the map entries of a thread's next pair are loaded before its current
+  // pair is summed (their global-load latency overlaps the shared-memory sums)
+  int u = threadIdx.x;
+  int2 s = make_int2(0, 0);
+  int c0 = 0, c1 = 0;
+  if (u < nu) {
+    s = slot[u];
+    c0 = cptr[u];
+    c1 = cptr[u + 1];
+  }
 #pragma unroll 1
-  for (int u = threadIdx.x; u < nu; u += blockDim.x) {
-    const int2 s = slot[u];
-    const int c0 = cptr[u], c1 = cptr[u + 1];
+  while (u < nu) {
+    const int un = u + (int)blockDim.x;
+    int2 sn = make_int2(0, 0);
+    int c0n = 0, c1n = 0;
+    if (un < nu) {
+      sn = slot[un];
+      c0n = cptr[un];
+      c1n = cptr[un + 1];
+    }
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = 0.0f;
+    int cd = code[c0];                           // c0 < c1: every pair has a contribution
 #pragma unroll 1
     for (int c = c0; c < c1; ++c) {
-      const int cd = code[c];
+      const int cdn = c + 1 < c1 ? (int)code[c + 1] : 0;
       const float* xb = X + (cd & 0x7fff);
       const int sd = (cd & 0x8000) ? 1 : 3, sk = (cd & 0x8000) ? 3 : 1;   // row / column strides
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int k = 0; k < 3; ++k) v[3 * d + k] += xb[d * sd + k * sk];
+      cd = cdn;
     }
     red_run(A, s.x, v[0], v[1], v[2]);
     red_run(A, s.x + s.y, v[3], v[4], v[5]);
     red_run(A, s.x + 2 * s.y, v[6], v[7], v[8]);
+    u = un;
+    s = sn;
+    c0 = c0n;
+    c1 = c1n;
   }
 }
 

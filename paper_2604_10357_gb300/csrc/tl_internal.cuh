@@ -59,7 +59,7 @@ struct Tune {
   int elem_occ2 = 1;      // float32 CSR assembly: 1 = two CTAs per SM (64 registers, overlaid exchange buffer)
   int elem_spread = 0;    // element kernels: 1 = tiles in flight spread over the mesh (permuted launch order)
   int pcg_f32 = 1;        // float32 Hessian: 1 = PCG vectors in float32 (dot products float64)
-  int elem_agg = 0;       // float32 exchanged assembly: 1 = per-tile aggregation of shared node pairs
+  int elem_agg = 1;       // float32 exchanged assembly: 1 = per-tile aggregation of shared node pairs
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };

@@ -85,6 +85,8 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
       for (int full = 0; full <= 1; ++full) variants.push_back({pf, xchg, full, 0, 0});
   float best = 1e30f;
   Tune chosen = saved;
+  chosen.elem_agg = 0;                 // the base variants are timed without aggregation
+  m->tune.elem_agg = 0;
   for (size_t k = 0; k < variants.size() && st == TL_OK; ++k) {
     m->tune.elem_prefetch = variants[k].pf;
     m->tune.elem_xchg = variants[k].xchg;
@@ -130,7 +132,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   // per-tile aggregation of shared node pairs on the fastest exchanged
   // float32 variant (needs the tile maps; meshes they do not fit skip it)
   if (st == TL_OK && fp32 && chosen.elem_xchg && !chosen.elem_ws && m->nn < (int64_t(1) << 24)) {
-    st = tile_maps_ensure(m);
+    st = tile_maps_ensure(m);            // built with the pattern already (no-op)
     if (st == TL_OK) {
       m->tune = chosen;
       m->tune.elem_agg = 1;

@@ -320,7 +320,7 @@ class Mesh:
         return _tune_dict(r)
 
     def tune_set(self, spmv_group=4, elem_xchg=1, elem_full_grid=0, elem_prefetch=1, elem_ws=0, residual_lanes=1,
-                 elem_occ2=1, elem_spread=0, pcg_f32=1, spmv_row=0, elem_agg=0):
+                 elem_occ2=1, elem_spread=0, pcg_f32=1, spmv_row=0, elem_agg=1):
         r = tl_tune_result()
         r.spmv_group, r.elem_xchg, r.elem_full_grid = spmv_group, elem_xchg, elem_full_grid
         r.elem_prefetch, r.elem_ws, r.residual_lanes = elem_prefetch, elem_ws, residual_lanes
