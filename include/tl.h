@@ -326,7 +326,7 @@ typedef struct tl_tune_result {
                                  of a 32-element tile share before the reductions (per-tile maps built on
                                  the device by tl_build_pattern for FP32 handles with < 2^24 nodes: about
                                  38 KB per tile of 32 elements); default 1 */
-  float ms_agg;               /* measured time of the fastest exchanged variant with aggregation (0: not measured) */
+  float ms_agg;               /* fastest measured exchanged variant with aggregation (0: not measured) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

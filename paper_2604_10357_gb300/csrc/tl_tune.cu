@@ -72,46 +72,57 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   const Tune saved = m->tune;
   tl_tune_result r = {};
   tl_status st = TL_OK;
-  // element pass: (prefetch, xchg, full grid) variants; the float64 kernels
-  // have neither the exchange nor the prefetch
-  struct V { int pf, xchg, full, ws, occ2; };
+  // element pass: (prefetch, xchg, full grid) variants, and for float32 the
+  // warp-specialised and two-CTA kernels; every exchanged float32 variant is
+  // timed with and without the per-tile aggregation (the float64 kernels
+  // have neither the exchange nor the prefetch)
+  const bool agg_ok = fp32 && m->nn < (int64_t(1) << 24) && tile_maps_ensure(m) == TL_OK;
+  struct V { int pf, xchg, full, ws, occ2, agg; };
   std::vector<V> variants;
   if (fp32) {
-    variants.push_back({1, 1, 0, 1, 0});             // warp-specialised
-    variants.push_back({0, 1, 0, 0, 1});             // two CTAs per SM
+    variants.push_back({1, 1, 0, 1, 0, 0});          // warp-specialised
+    variants.push_back({0, 1, 0, 0, 1, 0});          // two CTAs per SM
+    if (agg_ok) variants.push_back({0, 1, 0, 0, 1, 1});
   }
   for (int pf = fp32 ? 1 : 0; pf >= 0; --pf)
     for (int xchg = fp32 ? 1 : 0; xchg >= 0; --xchg)
-      for (int full = 0; full <= 1; ++full) variants.push_back({pf, xchg, full, 0, 0});
+      for (int full = 0; full <= 1; ++full) {
+        variants.push_back({pf, xchg, full, 0, 0, 0});
+        if (xchg && agg_ok) variants.push_back({pf, xchg, full, 0, 0, 1});
+      }
   float best = 1e30f;
   Tune chosen = saved;
-  chosen.elem_agg = 0;                 // the base variants are timed without aggregation
-  m->tune.elem_agg = 0;
+  m->tune.elem_spread = 0;
+  chosen.elem_spread = 0;
   for (size_t k = 0; k < variants.size() && st == TL_OK; ++k) {
-    m->tune.elem_prefetch = variants[k].pf;
-    m->tune.elem_xchg = variants[k].xchg;
-    m->tune.elem_full_grid = variants[k].full;
-    m->tune.elem_ws = variants[k].ws;
-    m->tune.elem_occ2 = variants[k].occ2;
+    const V& vk = variants[k];
+    m->tune.elem_prefetch = vk.pf;
+    m->tune.elem_xchg = vk.xchg;
+    m->tune.elem_full_grid = vk.full;
+    m->tune.elem_ws = vk.ws;
+    m->tune.elem_occ2 = vk.occ2;
+    m->tune.elem_agg = vk.agg;
     float ms = 0.f;
     st = time_reps(m, reps, [&]() {
-      tl_status s2 = launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
-      return s2;
+      return launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
     }, &ms);
     if (st != TL_OK) break;
-    if (variants[k].ws)
+    if (vk.agg)
+      r.ms_agg = r.ms_agg > 0.f ? std::min(r.ms_agg, ms) : ms;
+    else if (vk.ws)
       r.ms_ws = ms;
-    else if (variants[k].occ2)
+    else if (vk.occ2)
       r.ms_occ2 = ms;
     else
-      r.ms_element[4 * (1 - variants[k].pf) + 2 * (1 - variants[k].xchg) + variants[k].full] = ms;
+      r.ms_element[4 * (1 - vk.pf) + 2 * (1 - vk.xchg) + vk.full] = ms;
     if (ms < best) {
       best = ms;
-      chosen.elem_prefetch = variants[k].pf;
-      chosen.elem_xchg = variants[k].xchg;
-      chosen.elem_full_grid = variants[k].full;
-      chosen.elem_ws = variants[k].ws;
-      chosen.elem_occ2 = variants[k].occ2;
+      chosen.elem_prefetch = vk.pf;
+      chosen.elem_xchg = vk.xchg;
+      chosen.elem_full_grid = vk.full;
+      chosen.elem_ws = vk.ws;
+      chosen.elem_occ2 = vk.occ2;
+      chosen.elem_agg = vk.agg;
     }
   }
   // tile order of the fastest element variant: in order or spread
@@ -125,28 +136,9 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     if (st == TL_OK) {
       r.ms_spread = ms;
       chosen.elem_spread = ms < best ? 1 : 0;
-      best = std::min(best, ms);
-    }
-    m->tune = saved;
-  }
-  // per-tile aggregation of shared node pairs on the fastest exchanged
-  // float32 variant (needs the tile maps; meshes they do not fit skip it)
-  if (st == TL_OK && fp32 && chosen.elem_xchg && !chosen.elem_ws && m->nn < (int64_t(1) << 24)) {
-    st = tile_maps_ensure(m);            // built with the pattern already (no-op)
-    if (st == TL_OK) {
-      m->tune = chosen;
-      m->tune.elem_agg = 1;
-      float ms = 0.f;
-      st = time_reps(m, reps, [&]() {
-        return launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
-      }, &ms);
-      if (st == TL_OK) {
-        r.ms_agg = ms;
-        chosen.elem_agg = ms < best ? 1 : 0;
-      }
-      m->tune = saved;
     }
   }
+  m->tune = saved;
   // PCG product: lanes per node
   if (st == TL_OK) st = pcg_ensure(m);
   m->tune.spmv_row = 0;

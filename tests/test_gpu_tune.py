@@ -36,14 +36,20 @@ def test_autotune_reports_and_keeps_a_choice():
     assert rep["elem_xchg"] in (0, 1) and rep["elem_full_grid"] in (0, 1)
     assert all(t > 0 for t in rep["ms_element"]) and all(t > 0 for t in rep["ms_spmv"]) and rep["ms_ws"] > 0
     assert rep["ms_occ2"] > 0
-    best = min(min(rep["ms_element"]), rep["ms_ws"], rep["ms_occ2"])
-    if rep["elem_ws"]:
+    assert rep["ms_agg"] > 0                                 # aggregation timed on the exchanged variants
+    best = min(min(rep["ms_element"]), rep["ms_ws"], rep["ms_occ2"], rep["ms_agg"])
+    if rep["elem_agg"]:
+        assert rep["ms_agg"] == best
+    elif rep["elem_ws"]:
         assert rep["ms_ws"] == best
     elif rep["elem_occ2"]:
         assert rep["ms_occ2"] == best
     else:
         k = 4 * (1 - rep["elem_prefetch"]) + 2 * (1 - rep["elem_xchg"]) + rep["elem_full_grid"]
         assert rep["ms_element"][k] == best
+    # then the tile order of that variant
+    if rep["ms_spread"] > 0:
+        assert (rep["ms_spread"] < best) == bool(rep["elem_spread"])
     assert all(t > 0 for t in rep["ms_spmv_row"])          # the float32 iteration times the row form too
     spmv_best = min(rep["ms_spmv"] + rep["ms_spmv_row"])
     if rep["spmv_row"]:
@@ -55,11 +61,6 @@ def test_autotune_reports_and_keeps_a_choice():
     keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes", "elem_occ2",
             "elem_spread", "spmv_row", "pcg_f32", "elem_agg")
     assert all(cur[k] == rep[k] for k in keys)
-    # refinements of the fastest exchanged variant: tile order, then aggregation
-    if not rep["elem_ws"] and (rep["elem_occ2"] or rep["elem_xchg"]):
-        assert rep["ms_agg"] > 0
-        others = [best] + ([rep["ms_spread"]] if rep["ms_spread"] > 0 else [])
-        assert (rep["ms_agg"] < min(others)) == bool(rep["elem_agg"])
     with pytest.raises(tl.TLError):
         g.tune_set(spmv_group=5)
 
