@@ -123,7 +123,7 @@ class ClockSampler:
 
 
 ELEM_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2604_10357_gb300", "csrc", f)
-                       for f in ("tl_element_impl.cuh", "tl_element_common.cuh")]
+                       for f in ("tl_element_impl.cuh", "tl_element_common.cuh", "tl_tilemap.cu")]
 
 
 def kernel_source_hash(files=ELEM_KERNEL_SOURCES):
