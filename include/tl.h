@@ -302,7 +302,7 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  * the reductions.  ms_element[k]: k = 4*(1-prefetch) + 2*(1-xchg) + full_grid;
  * ms_spmv[k]: 4, 8, 16 lanes. */
 typedef struct tl_tune_result {
-  int32_t spmv_group;         /* lanes per node in H p: 4, 8, 16 or 32 */
+  int32_t spmv_group;         /* lanes per node in H p: 4, 8, 16 or 32 (default 4; 8 for TL_FP32_ELEM) */
   int32_t elem_xchg;          /* 1: exchanged vector runs (FP32 assembly) */
   int32_t elem_full_grid;     /* 1: one CTA per tile; 0: persistent grid */
   int32_t elem_prefetch;      /* 1: cp.async prefetch of the next tile (FP32) */
@@ -320,7 +320,8 @@ typedef struct tl_tune_result {
                                  float64), 0 = float64 vectors; not timed by tl_autotune (it changes
                                  the rounding of the iterates, not only their order); default 1 */
   int32_t spmv_row;           /* float32 PCG iteration: 1 = row-contiguous H p (the group's lanes read
-                                 contiguous runs of the three rows), 0 = one neighbour per lane */
+                                 contiguous runs of the three rows), 0 = one neighbour per lane
+                                 (default 0; 1 for TL_FP32_ELEM) */
   float ms_spmv_row[3];       /* measured row-contiguous H p with 8, 16, 32 lanes per node (0: not measured) */
   int32_t elem_agg;           /* 1: FP32 exchanged assembly sums the node-pair blocks that several elements
                                  of a 32-element tile share before the reductions (per-tile maps built on

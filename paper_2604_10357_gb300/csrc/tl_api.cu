@@ -164,6 +164,10 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
     m->num_sms = 1;
   m->stream = (cudaStream_t)stream;
   m->precision = precision;
+  if (precision == TL_FP32_ELEM) {     // float32 PCG iteration: the row-contiguous product, 8 lanes per node
+    m->tune.spmv_group = 8;
+    m->tune.spmv_row = 1;
+  }
   m->nn = nn;
   m->ne = ne;
   // ---- materials ----------------------------------------------------------

@@ -49,8 +49,8 @@ struct NewtonGraph;  // captured Newton step (tl_newton.cu)
 
 // Launch shapes picked per handle by the autotuner (tl_tune.cu).
 struct Tune {
-  int spmv_group = 4;     // lanes per node in the PCG product H p (4, 8, 16, 32)
-  int spmv_row = 0;       // float32 iteration: 1 = row-contiguous product (lanes along the rows)
+  int spmv_group = 4;     // lanes per node in the PCG product H p (4, 8, 16, 32); 8 for float32 handles
+  int spmv_row = 0;       // float32 iteration: 1 = row-contiguous product (lanes along the rows); 1 for float32 handles
   int elem_xchg = 1;      // FP32 assembly: 1 = exchanged vector runs, 0 = scalar scatter
   int elem_full_grid = 0; // element kernels: 0 = persistent grid (SMs x occupancy), 1 = one CTA per tile
   int elem_prefetch = 1;  // float32 element kernels: 1 = prefetch the next tile with cp.async

@@ -319,13 +319,19 @@ class Mesh:
         self._check(self.lib.tl_tune_get(self.h, C.byref(r)))
         return _tune_dict(r)
 
-    def tune_set(self, spmv_group=4, elem_xchg=1, elem_full_grid=0, elem_prefetch=1, elem_ws=0, residual_lanes=1,
-                 elem_occ2=1, elem_spread=0, pcg_f32=1, spmv_row=0, elem_agg=1):
+    TUNE_KEYS = ("spmv_group", "spmv_row", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws",
+                 "residual_lanes", "elem_occ2", "elem_spread", "pcg_f32", "elem_agg")
+
+    def tune_set(self, **choice):
+        """Set launch shapes by name (see tl_tune_result); the others keep
+        their current values."""
+        unknown = set(choice) - set(self.TUNE_KEYS)
+        if unknown:
+            raise TypeError(f"unknown launch-shape keys: {sorted(unknown)}")
         r = tl_tune_result()
-        r.spmv_group, r.elem_xchg, r.elem_full_grid = spmv_group, elem_xchg, elem_full_grid
-        r.elem_prefetch, r.elem_ws, r.residual_lanes = elem_prefetch, elem_ws, residual_lanes
-        r.elem_occ2, r.elem_spread, r.pcg_f32, r.spmv_row = elem_occ2, elem_spread, pcg_f32, spmv_row
-        r.elem_agg = elem_agg
+        self._check(self.lib.tl_tune_get(self.h, C.byref(r)))
+        for k, val in choice.items():
+            setattr(r, k, int(val))
         self._check(self.lib.tl_tune_set(self.h, C.byref(r)))
 
     def timing_enable(self, on=True):

@@ -103,7 +103,7 @@ def test_sampled_hessian_rows(batched, agg):
     g.tune_set(elem_agg=agg)
     assert g.tune_get()["elem_agg"] == agg
     vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho)
-    g.tune_set()
+    g.tune_set(elem_agg=1)
     row_ptr, col = (a.cpu().numpy() for a in g.get_pattern()[:2])
     starts = np.concatenate([[0], np.cumsum([b.nn for b in w["meshes"]])])
     nodes = np.unique(np.concatenate([rng.integers(starts[b], starts[b + 1], size=2)
