@@ -362,9 +362,10 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world}", "pattern_build_s": t_pat,
                    "launch_shapes": {k: tune[k] for k in ("elem_ws", "elem_occ2", "elem_spread", "elem_prefetch",
                                                           "elem_xchg", "elem_full_grid", "elem_agg", "spmv_group", "spmv_row",
-                                                          "residual_lanes")},
+                                                          "residual_lanes", "residual_split")},
                    "launch_shape_ms": {k: tune[k] for k in ("ms_ws", "ms_occ2", "ms_spread", "ms_element",
-                                                            "ms_agg", "ms_spmv", "ms_spmv_row", "ms_residual")}},
+                                                            "ms_agg", "ms_spmv", "ms_spmv_row", "ms_residual",
+                                                            "ms_residual_split")}},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(tim["launches"]),
@@ -407,7 +408,7 @@ def run_newton(args):
     c_mode = "mlp" if model is not None else "extrapolation"
     # launch shapes of both arms picked by the autotuner on the first held-out state (untimed)
     shape_keys = ("elem_occ2", "elem_prefetch", "elem_xchg", "elem_full_grid", "elem_agg", "spmv_group", "spmv_row",
-                  "pcg_f32")
+                  "pcg_f32", "residual_split")
     shapes = {}
     for name, g in (("plain", g64), ("chosen", g32)):
         t = g.tune_get() if args.no_autotune else g.autotune(tr.q[test_idx[0]], tr.v[test_idx[0]], w["h"], reps=3)

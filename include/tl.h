@@ -295,7 +295,7 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *   PCG product H p: 4, 8 or 16 lanes per node (one neighbour per lane), and for the
  *     float32 iteration 8, 16 or 32 lanes per node along the contiguous rows;
  *   the fastest exchanged FP32 variant with per-tile aggregation of shared node pairs;
- *   residual: 1 or 4 lanes per node.
+ *   residual: 1 or 4 lanes per node, or the double-float mass product;
  * reps timed launches per variant after one warm-up.  Needs the pattern;
  * allocates and frees one CSR values array and one force array.  Synchronous.
  * The result does not change any computed value beyond the rounding order of
@@ -328,6 +328,10 @@ typedef struct tl_tune_result {
                                  the device by tl_build_pattern for FP32 handles with < 2^24 nodes: about
                                  38 KB per tile of 32 elements); default 1 */
   float ms_agg;               /* fastest measured exchanged variant with aggregation (0: not measured) */
+  int32_t residual_split;     /* 1: the residual's mass product M (v - v_n) in double-float arithmetic
+                                 (float32 pairs with 48-bit significands, error-free products and sums;
+                                 the rest of the residual float64); 0: float64 (default 1) */
+  float ms_residual_split;    /* measured time of the double-float residual (0: not measured) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

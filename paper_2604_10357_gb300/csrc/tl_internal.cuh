@@ -56,6 +56,7 @@ struct Tune {
   int elem_prefetch = 1;  // float32 element kernels: 1 = prefetch the next tile with cp.async
   int elem_ws = 0;        // float32 CSR assembly: 1 = warp-specialised scatter (needs prefetch, persistent grid)
   int residual_lanes = 1; // lanes per node in the residual (1 or 4)
+  int residual_split = 1; // residual: 1 = mass product in double-float (float32 pairs, 48-bit significands)
   int elem_occ2 = 1;      // float32 CSR assembly: 1 = two CTAs per SM (64 registers, overlaid exchange buffer)
   int elem_spread = 0;    // element kernels: 1 = tiles in flight spread over the mesh (permuted launch order)
   int pcg_f32 = 1;        // float32 Hessian: 1 = PCG vectors in float32 (dot products float64)
@@ -108,6 +109,8 @@ struct tl_mesh {
   int* d_tile_counters = nullptr; // kTileCounters dynamic tile queues
   double* d_partials = nullptr;   // reduction partials
   double* d_dv = nullptr;         // v - v_n of the last residual (3 nn)
+  float2* d_dv2 = nullptr;        // the same as float32 pairs (double-float mass product)
+  float2* d_mass2 = nullptr;      // node-level mass as float32 pairs (nnz_node)
   int partials_cap = 0;
 
   tl::Solver* solver = nullptr;
@@ -177,6 +180,7 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
                           const double* lambda, double* g, double* g_norm);
 tl_status launch_add_penalty(tl_mesh* m, double value, void* values);
 tl_status residual_ensure(tl_mesh* m);
+tl_status mass_split_build(tl_mesh* m, cudaStream_t s);
 
 // instrumentation helpers (tl_api.cu): a category's event pair is opened
 // before and closed after the launches it brackets.

@@ -312,6 +312,13 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
                                                    sg.end, m->mats[sg.mat].rho, m->d_mass, m->d_mrow);
     TRY(cudaGetLastError());
   }
+  {
+    const tl_status ms = mass_split_build(m, s);     // float32 pairs of the mass (double-float residual)
+    if (ms != TL_OK) {
+      cleanup();
+      return ms;
+    }
+  }
   // ---- clamp rows --------------------------------------------------------
   m->nfixed = nfixed;
   TRY(cudaMalloc(&m->d_fixed_of_node, sizeof(int32_t) * nn));

@@ -106,6 +106,92 @@ __global__ void velocity_change(const double* v, const double* v_n, int64_t n, d
   if (i < n) dv[i] = v[i] - v_n[i];
 }
 
+// ---------------------------------------------------------------------------
+// Mass product in double-float arithmetic.  GB300 runs float64 arithmetic at
+// 1/64 of the float32 rate, and the float64 multiply-adds of the mass product
+// bound the residual kernel above.  Here every float64 operand x is held as
+// an unevaluated float32 pair x = x.hi + x.lo (|x.lo| <= ulp(x.hi) / 2, 48
+// significant bits), and the row sum of m_IJ dv_J runs in float32 with
+// error-free transformations (Dekker's product via FMA, Knuth's two-sum):
+//   p = a.hi b.hi exactly as p.hi + p.e (p.e = fma(a.hi, b.hi, -p.hi)),
+//   plus the cross terms a.hi b.lo + a.lo b.hi (a.lo b.lo ~ 2^-48 dropped);
+//   s = s + p with the rounding error of the high part kept exactly.
+// The sum is accurate to a few units of 2^-48 relative to the largest terms
+// (float64: 2^-53); it is converted to float64 once per node, and the rest of
+// the residual stays float64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 split_f64(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+__device__ __forceinline__ void df_mac(float& s_hi, float& s_lo, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = __fmaf_rn(a.x, b.x, -p);                      // exact error of the high product
+  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));        // cross terms
+  const float s = s_hi + p;                               // two-sum of s_hi and p
+  const float bb = s - s_hi;
+  const float err = (s_hi - (s - bb)) + (p - bb);
+  s_hi = s;
+  s_lo += err + e;
+}
+
+__global__ void split_array(const double* x, int64_t n, float2* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = split_f64(x[i]);
+}
+
+__global__ void velocity_change_split(const double* v, const double* v_n, int64_t n, float2* dv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dv[i] = split_f64(v[i] - v_n[i]);
+}
+
+__global__ void __launch_bounds__(kResBlock)
+    residual_split_kernel(const int32_t* node_ptr, const int32_t* node_col, const float2* mass2, const double* mrow,
+                          const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double inv_h,
+                          double rho, double gx, double gy, double gz, const double* q_n, const double* v,
+                          const float2* dv2, const double* f_int, const double* f_ext, const double* lambda,
+                          double* g, double* partials) {
+  __shared__ double red[kResBlock / 32];
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (I < nn) {
+    const int p0 = node_ptr[I], p1 = node_ptr[I + 1];
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    for (int p = p0; p < p1; ++p) {
+      const int64_t J = node_col[p];
+      const float2 mij = mass2[p];
+      df_mac(h0, l0, mij, dv2[3 * J]);
+      df_mac(h1, l1, mij, dv2[3 * J + 1]);
+      df_mac(h2, l2, mij, dv2[3 * J + 2]);
+    }
+    const double acc[3] = {(double)h0 + (double)l0, (double)h1 + (double)l1, (double)h2 + (double)l2};
+    const double grav[3] = {gx, gy, gz};
+    const int j = fixed_of_node[I];
+    const double mr = mrow[I];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int64_t r = 3 * I + d;
+      double gd = acc[d] * inv_h + f_int[r] - mr * grav[d];
+      if (f_ext) gd -= f_ext[r];
+      if (j >= 0) {
+        const double c = (q_n[r] + h * v[r]) - X[r];
+        gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
+      }
+      g[r] = gd;
+      sq += gd * gd;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
 __global__ void finish_norm(const double* partials, int n, double* out, uint32_t* flags) {
   __shared__ double red[32];
   double t = 0.0;
@@ -131,9 +217,21 @@ __global__ void add_diag(const int32_t* diag, int64_t n, T value, T* values) {
 
 }  // namespace
 
+// float32 pairs of the node-level mass (double-float mass product); once per
+// handle, after the mass is assembled.
+tl_status mass_split_build(tl_mesh* m, cudaStream_t s) {
+  const int64_t n = std::max<int64_t>(m->nnz_node, 1);
+  if (!m->d_mass2) TL_CUDA(m, cudaMalloc(&m->d_mass2, sizeof(float2) * n));
+  split_array<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->d_mass, n, m->d_mass2);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
+  return TL_OK;
+}
+
 // Norm partials owned by the handle (one per block of kResBlock nodes).
 tl_status residual_ensure(tl_mesh* m) {
   if (!m->d_dv) TL_CUDA(m, cudaMalloc(&m->d_dv, sizeof(double) * 3 * m->nn));
+  if (!m->d_dv2) TL_CUDA(m, cudaMalloc(&m->d_dv2, sizeof(float2) * 3 * m->nn));
   const int nb = (int)((m->nn + kResBlock - 1) / kResBlock);
   if (nb > m->partials_cap) {
     if (m->d_partials) cudaFree(m->d_partials);
@@ -153,6 +251,13 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   cudaEvent_t t0 = timer_open(m);
   // f_int may alias g: each thread reads its own entries before writing them
   const int64_t n3 = 3 * m->nn;
+  if (m->tune.residual_split && m->d_mass2) {
+    velocity_change_split<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv2);
+    residual_split_kernel<<<nb, kResBlock, 0, m->stream>>>(
+        m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
+        p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
+        m->d_partials);
+  } else {
   velocity_change<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv);
   if (m->tune.residual_lanes == 4)
     residual_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
@@ -162,6 +267,7 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
     residual_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
         m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
         p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials);
+  }
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(m->d_partials, nb, g_norm, m->d_flags);
   TL_CUDA(m, cudaGetLastError());

@@ -16,7 +16,7 @@
 //   * PCG product H p: 4, 8 or 16 lanes per node, one neighbour per lane;
 //     for the float32 iteration also 8, 16 or 32 lanes per node along the
 //     contiguous rows;
-//   * residual: 1 or 4 lanes per node.
+//   * residual: 1 or 4 lanes per node, or the double-float mass product.
 // Each variant is warmed up once and timed over `reps` launches with CUDA
 // events on the handle's stream; the fastest is kept in the handle and used by
 // every later call (a captured Newton graph is rebuilt on its next use).
@@ -184,6 +184,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   tl_params prm = {};
   prm.h = h;
   prm.rho_alm = 1e12;
+  m->tune.residual_split = 0;
   for (int k = 0; k < 2 && st == TL_OK; ++k) {
     m->tune.residual_lanes = lanes[k];
     float ms = 0.f;
@@ -195,6 +196,20 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     if (ms < best) {
       best = ms;
       chosen.residual_lanes = lanes[k];
+      chosen.residual_split = 0;
+    }
+  }
+  // residual with the double-float mass product
+  if (st == TL_OK && m->d_mass2) {
+    m->tune.residual_split = 1;
+    float ms = 0.f;
+    st = time_reps(m, reps, [&]() {
+      return launch_residual(m, &prm, q_n, v, v, f, nullptr, nullptr, g, g + 3 * m->nn);
+    }, &ms);
+    m->tune.residual_split = saved.residual_split;
+    if (st == TL_OK) {
+      r.ms_residual_split = ms;
+      if (ms < best) chosen.residual_split = 1;
     }
   }
   cudaStreamSynchronize(m->stream);
@@ -219,6 +234,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.pcg_f32 = chosen.pcg_f32;
   r.spmv_row = chosen.spmv_row;
   r.elem_agg = chosen.elem_agg;
+  r.residual_split = chosen.residual_split;
   if (out) *out = r;
   return TL_OK;
 }
@@ -237,6 +253,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.pcg_f32 = m->tune.pcg_f32;
   r.spmv_row = m->tune.spmv_row;
   r.elem_agg = m->tune.elem_agg;
+  r.residual_split = m->tune.residual_split;
   *out = r;
   return TL_OK;
 }
@@ -249,7 +266,8 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
       (in->elem_prefetch != 0 && in->elem_prefetch != 1) || (in->elem_ws != 0 && in->elem_ws != 1) ||
       (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1) ||
       (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1) ||
-      (in->spmv_row != 0 && in->spmv_row != 1) || (in->elem_agg != 0 && in->elem_agg != 1))
+      (in->spmv_row != 0 && in->spmv_row != 1) || (in->elem_agg != 0 && in->elem_agg != 1) ||
+      (in->residual_split != 0 && in->residual_split != 1))
     return TL_ERR_INVALID_ARG;
   if (in->elem_agg && m->precision == TL_FP32_ELEM) TL_TRY(tile_maps_ensure(m));
   m->tune.spmv_group = in->spmv_group;
@@ -263,6 +281,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   m->tune.pcg_f32 = in->pcg_f32;
   m->tune.spmv_row = in->spmv_row;
   m->tune.elem_agg = in->elem_agg;
+  m->tune.residual_split = in->residual_split;
   m->tune.generation += 1;
   return TL_OK;
 }

@@ -152,10 +152,15 @@ def test_hessian_values_and_fused_force_parity(case, prec):
     assert force_error(f.cpu().numpy(), om.internal_force(w["q_n"], w["v"], h), fe) < tol
 
 
-def test_residual_parity(case):
+@pytest.mark.parametrize("split", [0, 1])
+def test_residual_parity(case, split):
+    """float64 residual, and the residual whose mass product runs in
+    double-float arithmetic (48-bit significands): both within the float64
+    bar of the oracle."""
     tl = _tl()
     name, w, om = case
     g = _gpu_mesh(tl, w, tl.TL_FP64)
+    g.tune_set(residual_split=split)
     m = w["mesh"]
     rng = np.random.default_rng(5)
     v_n = w["v"] + 0.01 * rng.normal(size=w["v"].shape)
