@@ -189,7 +189,9 @@ tl_status tl_assemble_hessian(tl_mesh* m, const double* q_n, const double* v, do
  *   g = M (v - v_n)/h + f_int(q_n + h v, v) - f_ext - f_ff + h C_q^T (lambda + rho c)
  * with f_ff = (row sums of M) x gravity and c = (q_n + h v - X) on clamped DOFs.
  *   f_int   ndof float64 holding f_int(q_n + h v, v) already (e.g. from the
- *           fused tl_assemble_hessian pass), or NULL to evaluate it here
+ *           fused tl_assemble_hessian pass), or NULL to evaluate it here in
+ *           float64 class for both element forms (TL_FP32_ELEM handles: in
+ *           double-float arithmetic when force_split is set, else float64)
  *   f_ext   ndof float64 or NULL (zero)
  *   lambda  3*nfixed float64 (multiplier of DOF d of the j-th fixed node at
  *           3j+d, fixed nodes in ascending id order), or NULL (zero)
@@ -205,8 +207,8 @@ tl_status tl_eval_residual(tl_mesh* m, const tl_params* p, const double* q_n, co
  * device memory is owned by its own pool allocator or fixed budget, or a
  * latency-critical loop in which a cudaMalloc (which may synchronize the
  * device) is not acceptable.
- *   It computes the same g and ||g||_2 as tl_eval_residual, with the same
- * kernels, but keeps its norm partials in a fixed scratch array compiled into
+ *   It computes the same g and ||g||_2 as tl_eval_residual (with the mass
+ * product always in float64, whatever residual_split says), but keeps its norm partials in a fixed scratch array compiled into
  * the library (128 KiB of device memory held by every GPU that loads the
  * library, until the process exits) instead of a buffer owned by the handle.
  * It calls no cudaMalloc, cudaFree or allocating library routine.
@@ -296,6 +298,8 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
  *     float32 iteration 8, 16 or 32 lanes per node along the contiguous rows;
  *   the fastest exchanged FP32 variant with per-tile aggregation of shared node pairs;
  *   residual: 1 or 4 lanes per node, or the double-float mass product;
+ *   TL_FP32_ELEM: the Newton residual's internal force in float64 and double-float (timed
+ *     and reported only; force_split is left as the caller set it);
  * reps timed launches per variant after one warm-up.  Needs the pattern;
  * allocates and frees one CSR values array and one force array.  Synchronous.
  * The result does not change any computed value beyond the rounding order of
@@ -332,6 +336,12 @@ typedef struct tl_tune_result {
                                  (float32 pairs with 48-bit significands, error-free products and sums;
                                  the rest of the residual float64); 0: float64 (default 1) */
   float ms_residual_split;    /* measured time of the double-float residual (0: not measured) */
+  int32_t force_split;        /* TL_FP32_ELEM: 1 = the float64-class internal force of the Newton residual
+                                 in double-float arithmetic (48-bit significands), 0 = float64 (default 0).
+                                 A precision trade, never chosen by tl_autotune: under large rotations the
+                                 cancellation in the strain amplifies its rounding (observed: the force error
+                                 reached 1.65x a 1e-8 Newton target on a 452k-DOF cantilever) */
+  float ms_force[2];          /* measured residual force, float64 and double-float (0: not measured) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

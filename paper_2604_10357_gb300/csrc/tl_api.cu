@@ -60,7 +60,7 @@ void free_mesh(tl_mesh* m) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
-  void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_geo32, m->d_X, m->d_node_ptr, m->d_node_col,
+  void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_geo32, m->d_geo_df, m->d_X, m->d_node_ptr, m->d_node_col,
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
                   m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_values};
   solver_destroy(m->solver);
@@ -279,6 +279,17 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
   TRYC(cudaMemcpy(m->d_user_of, h_user.data(), sizeof(int32_t) * ne_pad, cudaMemcpyHostToDevice));
   TRYC(cudaMemcpy(m->d_geo64, h_geo64.data(), sizeof(double) * 16 * ne_pad, cudaMemcpyHostToDevice));
   TRYC(cudaMemcpy(m->d_geo32, h_geo32.data(), sizeof(float) * 16 * ne_pad, cudaMemcpyHostToDevice));
+  if (precision == TL_FP32_ELEM) {
+    // double-float copy (hi, lo float pairs) for the float64-class residual force
+    std::vector<float> h_geodf(32 * ne_pad);
+    for (int64_t i = 0; i < 16 * ne_pad; ++i) {
+      const float hi = (float)h_geo64[i];
+      h_geodf[2 * i] = hi;
+      h_geodf[2 * i + 1] = (float)(h_geo64[i] - (double)hi);
+    }
+    TRYC(cudaMalloc(&m->d_geo_df, sizeof(float) * 32 * ne_pad));
+    TRYC(cudaMemcpy(m->d_geo_df, h_geodf.data(), sizeof(float) * 32 * ne_pad, cudaMemcpyHostToDevice));
+  }
   TRYC(cudaMemcpy(m->d_X, X, sizeof(double) * 3 * nn, cudaMemcpyHostToDevice));
   TRYC(cudaMemset(m->d_flags, 0, sizeof(uint32_t) * 4));
 #undef TRYC
@@ -343,7 +354,7 @@ tl_status tl_eval_residual(tl_mesh* m, const tl_params* p, const double* q_n, co
   if (!m || !p || !q_n || !v_n || !v || !g || !g_norm || !(p->h > 0.0)) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
   if (!f_int) {
-    tl_status s = launch_force(m, q_n, v, p->h, g);    // g <- f_int(q_n + h v, v)
+    tl_status s = launch_force_prec(m, q_n, v, p->h, g, true);   // g <- f_int(q_n + h v, v), float64 class
     if (s != TL_OK) return s;
     f_int = g;
   }

@@ -6,6 +6,7 @@ namespace tl {
 
 tl_status elem_force_f32(tl_mesh*, const double*, const double*, double, double*);
 tl_status elem_force_f64(tl_mesh*, const double*, const double*, double, double*);
+tl_status elem_force_df(tl_mesh*, const double*, const double*, double, double*);
 tl_status elem_tangent_f32(tl_mesh*, const double*, const double*, double, double, double, double, bool, double*,
                            void*, void*);
 tl_status elem_tangent_f64(tl_mesh*, const double*, const double*, double, double, double, double, bool, double*,
@@ -20,6 +21,8 @@ tl_status launch_force(tl_mesh* m, const double* q_n, const double* v, double h,
 tl_status launch_force_prec(tl_mesh* m, const double* q_n, const double* v, double h, double* f, bool fp64) {
   TL_CUDA(m, cudaMemsetAsync(f, 0, sizeof(double) * 3 * m->nn, m->stream));
   if (m->precision == TL_FP32_ELEM && !fp64) return elem_force_f32(m, q_n, v, h, f);
+  // float32 handles: the float64-class force in double-float arithmetic
+  if (m->precision == TL_FP32_ELEM && m->tune.force_split && m->d_geo_df) return elem_force_df(m, q_n, v, h, f);
   return elem_force_f64(m, q_n, v, h, f);
 }
 

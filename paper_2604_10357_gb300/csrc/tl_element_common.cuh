@@ -7,6 +7,7 @@
 // Kelvin-Voigt as stated in include/tl.h.
 #pragma once
 
+#include "tl_dfloat.cuh"
 #include "tl_internal.cuh"
 
 namespace tl {
@@ -42,6 +43,10 @@ template <>
 __device__ __forceinline__ float rcbrt_t<float>(float x) { return rcbrtf(x); }
 template <>
 __device__ __forceinline__ double rcbrt_t<double>(double x) { return rcbrt(x); }
+template <>
+__device__ __forceinline__ dfl rcbrt_t<dfl>(dfl x) {      // float64 reciprocal cube root, once per qp
+  return dfl(rcbrt((double)x));
+}
 
 // ---------------------------------------------------------------------------
 // Constitutive update at one quadrature point.

@@ -641,7 +641,7 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
   __syncthreads();
   if (P && e0_next >= 0) prefetch_stage2(A, *P);
   if (DO_FORCE) force_phase(A, sm, e0);
-  if (DO_TANGENT) {
+  if constexpr (DO_TANGENT) {
     const int w = threadIdx.x >> 5;
     const int p = w / 3, i = w % 3;
     if constexpr (std::is_same<T, float>::value) {
@@ -1047,7 +1047,8 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   Args<T> A;
   A.conn = m->d_conn;
   A.geo = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m->d_geo32)
-                                        : reinterpret_cast<const T*>(m->d_geo64);
+          : std::is_same<T, dfl>::value   ? reinterpret_cast<const T*>(m->d_geo_df)
+                                          : reinterpret_cast<const T*>(m->d_geo64);
   A.blk = m->d_blk;
   A.node_ptr = m->d_node_ptr;
   A.user_of = m->d_user_of;

@@ -57,6 +57,7 @@ struct Tune {
   int elem_ws = 0;        // float32 CSR assembly: 1 = warp-specialised scatter (needs prefetch, persistent grid)
   int residual_lanes = 1; // lanes per node in the residual (1 or 4)
   int residual_split = 1; // residual: 1 = mass product in double-float (float32 pairs, 48-bit significands)
+  int force_split = 0;    // float32 handles: 1 = the float64-class residual force in double-float arithmetic
   int elem_occ2 = 1;      // float32 CSR assembly: 1 = two CTAs per SM (64 registers, overlaid exchange buffer)
   int elem_spread = 0;    // element kernels: 1 = tiles in flight spread over the mesh (permuted launch order)
   int pcg_f32 = 1;        // float32 Hessian: 1 = PCG vectors in float32 (dot products float64)
@@ -82,6 +83,7 @@ struct tl_mesh {
   int32_t* d_user_of = nullptr;   // ne_pad: user element id, -1 for padding
   double* d_geo64 = nullptr;      // ne_pad * 16: grad L (4x3), V, 0,0,0
   float* d_geo32 = nullptr;       // same in float32 (TL_FP32_ELEM)
+  float* d_geo_df = nullptr;      // same as double-float pairs (TL_FP32_ELEM: float64-class residual force)
   double* d_X = nullptr;          // 3 nn
 
   // pattern (tl_build_pattern)

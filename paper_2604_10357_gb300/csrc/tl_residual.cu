@@ -122,18 +122,20 @@ __global__ void velocity_change(const double* v, const double* v_n, int64_t n, d
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 split_f64(double x) {
   const float hi = __double2float_rn(x);
-  return make_float2(hi, __double2float_rn(x - (double)hi));
+  return make_float2(hi, __double2float_rn(__dsub_rn(x, (double)hi)));
 }
 
+// The _rn intrinsics are never contracted into FMAs, which the error-free
+// transformations rely on.
 __device__ __forceinline__ void df_mac(float& s_hi, float& s_lo, float2 a, float2 b) {
-  const float p = a.x * b.x;
+  const float p = __fmul_rn(a.x, b.x);
   float e = __fmaf_rn(a.x, b.x, -p);                      // exact error of the high product
   e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));        // cross terms
-  const float s = s_hi + p;                               // two-sum of s_hi and p
-  const float bb = s - s_hi;
-  const float err = (s_hi - (s - bb)) + (p - bb);
+  const float s = __fadd_rn(s_hi, p);                     // two-sum of s_hi and p
+  const float bb = __fsub_rn(s, s_hi);
+  const float err = __fadd_rn(__fsub_rn(s_hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   s_hi = s;
-  s_lo += err + e;
+  s_lo = __fadd_rn(s_lo, __fadd_rn(err, e));
 }
 
 __global__ void split_array(const double* x, int64_t n, float2* out) {

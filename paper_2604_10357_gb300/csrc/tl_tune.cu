@@ -16,7 +16,10 @@
 //   * PCG product H p: 4, 8 or 16 lanes per node, one neighbour per lane;
 //     for the float32 iteration also 8, 16 or 32 lanes per node along the
 //     contiguous rows;
-//   * residual: 1 or 4 lanes per node, or the double-float mass product.
+//   * residual: 1 or 4 lanes per node, or the double-float mass product;
+//   * float32 handles: the float64-class residual force in float64 and in
+//     double-float arithmetic (timed and reported only: that choice trades
+//     precision, so it stays with the caller).
 // Each variant is warmed up once and timed over `reps` launches with CUDA
 // events on the handle's stream; the fastest is kept in the handle and used by
 // every later call (a captured Newton graph is rebuilt on its next use).
@@ -139,6 +142,19 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     }
   }
   m->tune = saved;
+  // float64-class residual force of a float32 handle, float64 and
+  // double-float: timed and reported, not chosen (the double-float force is
+  // a precision trade: 48-bit significands can miss a 1e-8 Newton target
+  // under large rotations), so the caller's setting stays
+  if (st == TL_OK && fp32 && m->d_geo_df) {
+    for (int k = 0; k < 2 && st == TL_OK; ++k) {
+      m->tune.force_split = k;
+      float ms = 0.f;
+      st = time_reps(m, reps, [&]() { return launch_force_prec(m, q_n, v, h, f, true); }, &ms);
+      if (st == TL_OK) r.ms_force[k] = ms;
+    }
+    m->tune.force_split = saved.force_split;
+  }
   // PCG product: lanes per node
   if (st == TL_OK) st = pcg_ensure(m);
   m->tune.spmv_row = 0;
@@ -235,6 +251,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.spmv_row = chosen.spmv_row;
   r.elem_agg = chosen.elem_agg;
   r.residual_split = chosen.residual_split;
+  r.force_split = chosen.force_split;
   if (out) *out = r;
   return TL_OK;
 }
@@ -254,6 +271,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.spmv_row = m->tune.spmv_row;
   r.elem_agg = m->tune.elem_agg;
   r.residual_split = m->tune.residual_split;
+  r.force_split = m->tune.force_split;
   *out = r;
   return TL_OK;
 }
@@ -267,7 +285,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
       (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1) ||
       (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1) ||
       (in->spmv_row != 0 && in->spmv_row != 1) || (in->elem_agg != 0 && in->elem_agg != 1) ||
-      (in->residual_split != 0 && in->residual_split != 1))
+      (in->residual_split != 0 && in->residual_split != 1) || (in->force_split != 0 && in->force_split != 1))
     return TL_ERR_INVALID_ARG;
   if (in->elem_agg && m->precision == TL_FP32_ELEM) TL_TRY(tile_maps_ensure(m));
   m->tune.spmv_group = in->spmv_group;
@@ -282,6 +300,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   m->tune.spmv_row = in->spmv_row;
   m->tune.elem_agg = in->elem_agg;
   m->tune.residual_split = in->residual_split;
+  m->tune.force_split = in->force_split;
   m->tune.generation += 1;
   return TL_OK;
 }

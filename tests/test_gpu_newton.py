@@ -180,6 +180,29 @@ def test_pcg_vector_precisions_reach_same_state(use_graph):
     assert np.linalg.norm(v1 - v0) <= 1e-7 * np.linalg.norm(v0)
 
 
+def test_double_float_residual_force_reaches_same_state():
+    """Float32 handle: the Newton residual's internal force in float64 and in
+    double-float arithmetic give the same converged step (the residual's
+    tolerance), with the same Newton counts."""
+    tl = _tl()
+    w = inputs.workload_small_svk()
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
+    g.build_pattern(m.fixed_nodes)
+    p = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, use_graph=1)
+    out = {}
+    for split in (0, 1):
+        g.tune_set(force_split=split, residual_split=split)
+        lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+        v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+        assert st["converged"] == 1 and st["g_norm"] <= 1e-8 * st["g_ref"]
+        out[split] = (v.cpu().numpy(), st)
+    (v0, s0), (v1, s1) = out[0], out[1]
+    assert s1["inner_iters"] == s0["inner_iters"] and s1["outer_iters"] == s0["outer_iters"]
+    assert s1["g_ref"] == pytest.approx(s0["g_ref"], rel=1e-11)
+    assert np.linalg.norm(v1 - v0) <= 1e-8 * np.linalg.norm(v0)
+
+
 def test_newton_graph_caps_and_rebuild():
     """Iteration caps end the captured loops with NOT_CONVERGED and the same
     statistics as the host loop; a parameter change rebuilds the graph and a

@@ -152,15 +152,18 @@ def test_hessian_values_and_fused_force_parity(case, prec):
     assert force_error(f.cpu().numpy(), om.internal_force(w["q_n"], w["v"], h), fe) < tol
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("split", [0, 1])
-def test_residual_parity(case, split):
-    """float64 residual, and the residual whose mass product runs in
-    double-float arithmetic (48-bit significands): both within the float64
-    bar of the oracle."""
+def test_residual_parity(case, prec, split):
+    """The residual with its internal force evaluated here: float64
+    throughout, or with the mass product and (float32 handles) the internal
+    force in double-float arithmetic (48-bit significands); every combination
+    within the float64 bar of the oracle (a float32 handle's residual force is
+    float64-class too)."""
     tl = _tl()
     name, w, om = case
-    g = _gpu_mesh(tl, w, tl.TL_FP64)
-    g.tune_set(residual_split=split)
+    g = _gpu_mesh(tl, w, tl.TL_FP64 if prec == "fp64" else tl.TL_FP32_ELEM)
+    g.tune_set(residual_split=split, force_split=split)
     m = w["mesh"]
     rng = np.random.default_rng(5)
     v_n = w["v"] + 0.01 * rng.normal(size=w["v"].shape)

@@ -58,10 +58,12 @@ def test_autotune_reports_and_keeps_a_choice():
         assert rep["ms_spmv"][(4, 8, 16).index(rep["spmv_group"])] == spmv_best
     assert rep["ms_residual"][(1, 4).index(rep["residual_lanes"])] == min(rep["ms_residual"])
     assert rep["ms_residual_split"] > 0
+    assert all(t > 0 for t in rep["ms_force"])                # float32 handle: both residual forces timed
+    assert rep["force_split"] == 0                            # a precision trade: never chosen by the tuner
     assert bool(rep["residual_split"]) == (rep["ms_residual_split"] < min(rep["ms_residual"]))
     cur = g.tune_get()
     keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes", "elem_occ2",
-            "elem_spread", "spmv_row", "pcg_f32", "elem_agg", "residual_split")
+            "elem_spread", "spmv_row", "pcg_f32", "elem_agg", "residual_split", "force_split")
     assert all(cur[k] == rep[k] for k in keys)
     with pytest.raises(tl.TLError):
         g.tune_set(spmv_group=5)
