@@ -1129,7 +1129,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       TL_CUDA(m, cudaGetLastError());
       ++m->launches;
       continue;
-    }
+    } else {   // the 15-warp kernels (not instantiated for force-only passes)
     void (*kern)(Args<T>, SegTable<T>, int*) = nullptr;
     int threads = NT;
     if constexpr (std::is_same<T, float>::value && DO_TANGENT) {
@@ -1194,6 +1194,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     kern<<<(unsigned)grid, (unsigned)threads, smem_l, m->stream>>>(Al, S, counter);
     TL_CUDA(m, cudaGetLastError());
     ++m->launches;
+    }
   }
   timer_close(m, t0, kTimeElement);
   return TL_OK;
