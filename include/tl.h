@@ -335,7 +335,7 @@ typedef struct tl_tune_result {
   int32_t residual_split;     /* 1: the residual's mass product M (v - v_n) in double-float arithmetic
                                  (float32 pairs with 48-bit significands, error-free products and sums;
                                  the rest of the residual float64); 0: float64 (default 1) */
-  float ms_residual_split;    /* measured time of the double-float residual (0: not measured) */
+  float ms_residual_split[2]; /* measured double-float residual with 1 and 4 lanes per node (0: not measured) */
   int32_t force_split;        /* TL_FP32_ELEM: 1 = the float64-class internal force of the Newton residual
                                  in double-float arithmetic (48-bit significands), 0 = float64 (default 0).
                                  A precision trade, never chosen by tl_autotune: under large rotations the

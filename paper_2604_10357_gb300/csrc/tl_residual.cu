@@ -148,25 +148,51 @@ __global__ void velocity_change_split(const double* v, const double* v_n, int64_
   if (i < n) dv[i] = split_f64(v[i] - v_n[i]);
 }
 
-__global__ void __launch_bounds__(kResBlock)
+// (s_hi, s_lo) += (o_hi, o_lo): two-sum of the high parts, low parts added.
+__device__ __forceinline__ void df_combine(float& s_hi, float& s_lo, float o_hi, float o_lo) {
+  const float s = __fadd_rn(s_hi, o_hi);
+  const float bb = __fsub_rn(s, s_hi);
+  const float err = __fadd_rn(__fsub_rn(s_hi, __fsub_rn(s, bb)), __fsub_rn(o_hi, bb));
+  s_hi = s;
+  s_lo = __fadd_rn(s_lo, __fadd_rn(err, o_lo));
+}
+
+// LANES lanes per node: lane l takes the mass-row entries l, l + LANES, ...;
+// the lanes' double-float sums are combined by shuffles (two-sums of the high
+// parts) and the first lane forms the node's residual.  A block holds
+// kResBlock nodes.
+template <int LANES>
+__global__ void __launch_bounds__(kResBlock * LANES)
     residual_split_kernel(const int32_t* node_ptr, const int32_t* node_col, const float2* mass2, const double* mrow,
                           const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double inv_h,
                           double rho, double gx, double gy, double gz, const double* q_n, const double* v,
                           const float2* dv2, const double* f_int, const double* f_ext, const double* lambda,
                           double* g, double* partials) {
-  __shared__ double red[kResBlock / 32];
-  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  __shared__ double red[kResBlock * LANES / 32];
+  const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LANES;
+  const int l = threadIdx.x & (LANES - 1);
   double sq = 0.0;
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
   if (I < nn) {
     const int p0 = node_ptr[I], p1 = node_ptr[I + 1];
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
-    for (int p = p0; p < p1; ++p) {
+    for (int p = p0 + l; p < p1; p += LANES) {
       const int64_t J = node_col[p];
       const float2 mij = mass2[p];
       df_mac(h0, l0, mij, dv2[3 * J]);
       df_mac(h1, l1, mij, dv2[3 * J + 1]);
       df_mac(h2, l2, mij, dv2[3 * J + 2]);
     }
+  }
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) {
+    const float a0 = __shfl_xor_sync(0xffffffffu, h0, o), b0 = __shfl_xor_sync(0xffffffffu, l0, o);
+    const float a1 = __shfl_xor_sync(0xffffffffu, h1, o), b1 = __shfl_xor_sync(0xffffffffu, l1, o);
+    const float a2 = __shfl_xor_sync(0xffffffffu, h2, o), b2 = __shfl_xor_sync(0xffffffffu, l2, o);
+    df_combine(h0, l0, a0, b0);
+    df_combine(h1, l1, a1, b1);
+    df_combine(h2, l2, a2, b2);
+  }
+  if (I < nn && l == 0) {
     const double acc[3] = {(double)h0 + (double)l0, (double)h1 + (double)l1, (double)h2 + (double)l2};
     const double grav[3] = {gx, gy, gz};
     const int j = fixed_of_node[I];
@@ -255,10 +281,16 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   const int64_t n3 = 3 * m->nn;
   if (m->tune.residual_split && m->d_mass2) {
     velocity_change_split<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv2);
-    residual_split_kernel<<<nb, kResBlock, 0, m->stream>>>(
-        m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
-        p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
-        m->d_partials);
+    if (m->tune.residual_lanes == 4)
+      residual_split_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
+          m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
+          p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
+          m->d_partials);
+    else
+      residual_split_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
+          m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
+          p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
+          m->d_partials);
   } else {
   velocity_change<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv);
   if (m->tune.residual_lanes == 4)

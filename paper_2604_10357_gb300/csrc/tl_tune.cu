@@ -215,18 +215,24 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
       chosen.residual_split = 0;
     }
   }
-  // residual with the double-float mass product
+  // residual with the double-float mass product, 1 and 4 lanes per node
   if (st == TL_OK && m->d_mass2) {
     m->tune.residual_split = 1;
-    float ms = 0.f;
-    st = time_reps(m, reps, [&]() {
-      return launch_residual(m, &prm, q_n, v, v, f, nullptr, nullptr, g, g + 3 * m->nn);
-    }, &ms);
-    m->tune.residual_split = saved.residual_split;
-    if (st == TL_OK) {
-      r.ms_residual_split = ms;
-      if (ms < best) chosen.residual_split = 1;
+    for (int k = 0; k < 2 && st == TL_OK; ++k) {
+      m->tune.residual_lanes = lanes[k];
+      float ms = 0.f;
+      st = time_reps(m, reps, [&]() {
+        return launch_residual(m, &prm, q_n, v, v, f, nullptr, nullptr, g, g + 3 * m->nn);
+      }, &ms);
+      if (st != TL_OK) break;
+      r.ms_residual_split[k] = ms;
+      if (ms < best) {
+        best = ms;
+        chosen.residual_split = 1;
+        chosen.residual_lanes = lanes[k];
+      }
     }
+    m->tune.residual_split = saved.residual_split;
   }
   cudaStreamSynchronize(m->stream);
   cudaFree(values);

@@ -71,7 +71,7 @@ class tl_tune_result(C.Structure):
                 ("ms_residual", C.c_float * 2), ("ms_occ2", C.c_float), ("ms_spread", C.c_float),
                 ("pcg_f32", C.c_int32), ("spmv_row", C.c_int32), ("ms_spmv_row", C.c_float * 3),
                 ("elem_agg", C.c_int32), ("ms_agg", C.c_float), ("residual_split", C.c_int32),
-                ("ms_residual_split", C.c_float), ("force_split", C.c_int32), ("ms_force", C.c_float * 2)]
+                ("ms_residual_split", C.c_float * 2), ("force_split", C.c_int32), ("ms_force", C.c_float * 2)]
 
 
 # every symbol declared in include/tl.h, with (restype, argtypes)
@@ -165,7 +165,7 @@ def _tune_dict(r):
                 ms_ws=r.ms_ws, ms_spmv=list(r.ms_spmv), ms_residual=list(r.ms_residual), ms_occ2=r.ms_occ2,
                 ms_spread=r.ms_spread, pcg_f32=r.pcg_f32,
                 spmv_row=r.spmv_row, ms_spmv_row=list(r.ms_spmv_row), elem_agg=r.elem_agg, ms_agg=r.ms_agg,
-                residual_split=r.residual_split, ms_residual_split=r.ms_residual_split,
+                residual_split=r.residual_split, ms_residual_split=list(r.ms_residual_split),
                 force_split=r.force_split, ms_force=list(r.ms_force))
 
 
