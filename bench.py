@@ -426,6 +426,13 @@ def run_newton(args):
            "speedup": p_sum["v_n"]["mean_ms"] / c_sum[c_mode]["mean_ms"],
            "launch_shapes": shapes,
            "model": os.path.relpath(model_path, ROOT) if model is not None else None}
+    # the chosen arm with the Armijo line search of eq. armijo (trial residual
+    # per Newton step; here every full step is accepted)
+    chosen_ls = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, line_search=1,
+                          use_graph=0 if args.newton_no_graph else 1)
+    warmstart.evaluate(g32, tr, test_idx[:1], chosen_ls, model, modes=[c_mode])
+    l_sum, _ = warmstart.evaluate(g32, tr, test_idx, chosen_ls, model, modes=[c_mode])
+    out["chosen_line_search"] = dict(l_sum[c_mode], desc="chosen arm with the Armijo line search")
     if args.newton_direct:
         direct = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_DIRECT)
         d_sum, _ = warmstart.evaluate(g64, tr, test_idx[:1], direct, modes=["v_n"])

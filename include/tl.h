@@ -103,6 +103,13 @@ typedef struct tl_params {
   int32_t lin_adaptive;       /* 1: inexact Newton (solve only as tightly as the target needs) */
   int32_t use_graph;          /* 1: run the step as one captured CUDA graph with device-side */
                               /* convergence control (PCG only; see tl_newton_step)           */
+  int32_t line_search;        /* 1: Armijo backtracking on phi = ||g||^2 / 2 (eq. armijo) after */
+                              /* each Newton solve: accept v + a dv once                        */
+                              /* phi(a) <= (1 - 2 c1 a) phi(0), a = 1, beta, beta^2, ...; after   */
+                              /* ls_max_trials rejected trials v is kept and the inner loop ends  */
+  int32_t ls_max_trials;      /* j_max (0: 10) */
+  double ls_c1;               /* c1 (0: 1e-4) */
+  double ls_beta;             /* beta (0: 0.5) */
 } tl_params;
 
 typedef struct tl_newton_stats {
@@ -117,7 +124,7 @@ typedef struct tl_newton_stats {
   double ms_assembly;         /* residual + Hessian assembly kernels */
   double ms_solver;           /* factorisation + solves (or PCG) */
   int32_t lin_iters;          /* PCG iterations summed over the step */
-  int32_t _pad2;
+  int32_t ls_trials;          /* line-search trial points evaluated over the step */
   double g_init;              /* ||g|| at the start velocity (v_init or v_n) */
 } tl_newton_stats;
 

@@ -120,7 +120,7 @@ struct tl_mesh {
   tl::NewtonGraph* ngraph = nullptr;
   tl::Tune tune;
   // Newton work buffers (tl_newton_step), allocated on first use
-  double *nw_g = nullptr, *nw_f = nullptr, *nw_dv = nullptr, *nw_scal = nullptr;
+  double *nw_g = nullptr, *nw_f = nullptr, *nw_dv = nullptr, *nw_scal = nullptr, *nw_vt = nullptr;
   void* nw_values = nullptr;
 
   // instrumentation (tl_timing_*)

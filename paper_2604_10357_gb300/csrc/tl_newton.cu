@@ -34,6 +34,12 @@ __global__ void axpy_kernel(double* y, const double* x, double a, int64_t n) {
   if (i < n) y[i] += a * x[i];
 }
 
+// y = v + a dx (line-search trial point)
+__global__ void axpby_kernel(const double* v, const double* dx, double a, int64_t n, double* y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = v[i] + a * dx[i];
+}
+
 __global__ void q_from_v(const double* q_n, const double* v, double h, int64_t n, double* q) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) q[i] = q_n[i] + h * v[i];
@@ -78,7 +84,9 @@ __global__ void clamp_constraint(const int32_t* fixed_of_node, const double* X,
 
 struct NewtonCtl {
   double g_ref, target, gn, g_init, cn, tol2, eta;
+  double ls_alpha, ls_phi0;                       // line search: current step, phi(0)
   int32_t l, inner_total, outer, inner_ok, converged, lin_total, pcg_it, abort;
+  int32_t ls_j, ls_ok, ls_trials, _pad;
 };
 
 __global__ void ctl_reset(NewtonCtl* c) {
@@ -151,6 +159,46 @@ __global__ void ctl_pcg(NewtonCtl* c, const double* pscal, int chunk, int lin_ma
 }
 
 __global__ void ctl_pcg_done(NewtonCtl* c) { c->lin_total += c->pcg_it; }
+
+// line search (eq. armijo): arm the backtracking loop at a = 1
+__global__ void ctl_ls_arm(NewtonCtl* c, cudaGraphConditionalHandle h_ls) {
+  c->ls_phi0 = 0.5 * c->gn * c->gn;
+  c->ls_alpha = 1.0;
+  c->ls_j = 0;
+  c->ls_ok = 0;
+  cudaGraphSetConditional(h_ls, 1u);
+}
+
+// trial point v + a dv with the current a
+__global__ void ls_trial(const double* v, const double* dv, const NewtonCtl* c, int64_t n, double* vt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) vt[i] = v[i] + c->ls_alpha * dv[i];
+}
+
+// sufficient decrease at the trial point, else a *= beta (at most j_max trials)
+__global__ void ctl_ls(NewtonCtl* c, const double* gnorm, double c1, double beta, int j_max,
+                       cudaGraphConditionalHandle h_ls) {
+  const double gt = *gnorm;
+  c->ls_trials += 1;
+  c->ls_j += 1;
+  if (0.5 * gt * gt <= (1.0 - 2.0 * c1 * c->ls_alpha) * c->ls_phi0) {   // false for a non-finite norm
+    c->ls_ok = 1;
+    cudaGraphSetConditional(h_ls, 0u);
+    return;
+  }
+  c->ls_alpha *= beta;
+  cudaGraphSetConditional(h_ls, c->ls_j < j_max ? 1u : 0u);
+}
+
+// accepted: v = trial point; rejected j_max times: keep v and end the inner loop
+__global__ void ls_commit(double* v, const double* vt, const NewtonCtl* c, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && c->ls_ok) v[i] = vt[i];
+}
+
+__global__ void ctl_ls_done(const NewtonCtl* c, cudaGraphConditionalHandle h_in) {
+  if (!c->ls_ok) cudaGraphSetConditional(h_in, 0u);
+}
 
 __global__ void ctl_outer(NewtonCtl* c, const double* cnorm, double eps_out, int max_outer,
                           cudaGraphConditionalHandle h_out) {
@@ -248,8 +296,12 @@ tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
   double *g = m->nw_g, *f = m->nw_f, *dv = m->nw_dv, *scal = m->nw_scal;
   void* values = m->nw_values;
   NewtonCtl* c = G->ctl;
-  cudaGraphConditionalHandle h_out = 0, h_in = 0, h_step = 0, h_pcg = 0;
-  cudaGraph_t b_outer = nullptr, b_inner = nullptr, b_step = nullptr, b_pcg = nullptr, tmp = nullptr;
+  cudaGraphConditionalHandle h_out = 0, h_in = 0, h_step = 0, h_pcg = 0, h_ls = 0;
+  cudaGraph_t b_outer = nullptr, b_inner = nullptr, b_step = nullptr, b_pcg = nullptr, b_ls = nullptr,
+              tmp = nullptr;
+  double* vt = m->nw_vt;
+  const int ls_max = p->ls_max_trials > 0 ? p->ls_max_trials : 10;
+  const double ls_c1 = p->ls_c1 > 0.0 ? p->ls_c1 : 1e-4, ls_beta = p->ls_beta > 0.0 ? p->ls_beta : 0.5;
   auto end_capture = [&](cudaGraph_t* out) { return cudaStreamEndCapture(s, out); };
   // top level: reference residual at v_n, the outer loop, q = q_n + h v
   TL_CUDA(m, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
@@ -314,6 +366,7 @@ tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
   {
     tl_status st = TL_OK;
     cudaError_t e = capture_handle(s, &h_pcg);
+    if (e == cudaSuccess && p->line_search) e = capture_handle(s, &h_ls);
     if (e == cudaSuccess) e = cudaMemsetAsync(values, 0, vb * m->nnz, s);
     if (e == cudaSuccess) {
       st = launch_tangent(m, G->q_n, G->v, p->h, p->h, 1.0, 1.0 / p->h, false, nullptr, values, nullptr);
@@ -325,13 +378,33 @@ tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
         if (e == cudaSuccess) {
           ctl_pcg_done<<<1, 1, 0, s>>>(c);
           st = pcg_result(m, dv);
-          if (st == TL_OK) axpy_kernel<<<nb, 256, 0, s>>>(G->v, dv, 1.0, ndof);
+          if (st == TL_OK && !p->line_search) axpy_kernel<<<nb, 256, 0, s>>>(G->v, dv, 1.0, ndof);
+          if (st == TL_OK && p->line_search) {
+            ctl_ls_arm<<<1, 1, 0, s>>>(c, h_ls);
+            e = capture_conditional(s, h_ls, cudaGraphCondTypeWhile, &b_ls);
+            if (e == cudaSuccess) {
+              ls_commit<<<nb, 256, 0, s>>>(G->v, vt, c, ndof);
+              ctl_ls_done<<<1, 1, 0, s>>>(c, h_in);
+            }
+          }
         }
       }
     }
     cudaError_t e2 = end_capture(&tmp);
     if (st != TL_OK) return st;
     TL_CUDA(m, e);
+    TL_CUDA(m, e2);
+  }
+  // line-search body: trial point, its residual and the sufficient-decrease test
+  if (p->line_search) {
+    TL_CUDA(m, cudaStreamBeginCaptureToGraph(s, b_ls, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    tl_status st = TL_OK;
+    ls_trial<<<nb, 256, 0, s>>>(G->v, dv, c, ndof, vt);
+    st = launch_force_prec(m, G->q_n, vt, p->h, f, true);
+    if (st == TL_OK) st = launch_residual(m, p, G->q_n, G->v_n, vt, f, G->f_ext, G->lam, g, scal);
+    if (st == TL_OK) ctl_ls<<<1, 1, 0, s>>>(c, scal, ls_c1, ls_beta, ls_max, h_ls);
+    cudaError_t e2 = end_capture(&tmp);
+    if (st != TL_OK) return st;
     TL_CUDA(m, e2);
   }
   // PCG body: kPcgChunk iterations and the device-side residual test
@@ -432,6 +505,7 @@ tl_status newton_step_graph(tl_mesh* m, const tl_params* p, const double* q_n, c
     stats->ms_assembly = 0.0;   // not split inside the graph
     stats->ms_solver = 0.0;
     stats->lin_iters = c.lin_total;
+    stats->ls_trials = c.ls_trials;
     stats->g_init = c.g_init;
   }
   if (c.abort) return fail(m, TL_ERR_NONFINITE, "non-finite residual in the captured Newton step");
@@ -463,6 +537,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
   const int64_t ndof = 3 * m->nn;
   const size_t vb = (m->precision == TL_FP32_ELEM ? sizeof(float) : sizeof(double));
   // work buffers: allocated on the first call, owned by the handle
+  if (!m->nw_vt) TL_CUDA(m, cudaMalloc(&m->nw_vt, sizeof(double) * ndof));   // line-search trial velocity
   if (!m->nw_g) {
     TL_CUDA(m, cudaMalloc(&m->nw_g, sizeof(double) * ndof));
     TL_CUDA(m, cudaMalloc(&m->nw_f, sizeof(double) * ndof));
@@ -519,14 +594,18 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
   double g_ref = 0.0;
   NTRY(residual(v_n, &g_ref));
   const double target = std::max(p->atol, p->rtol * g_ref);
-  int inner_total = 0, outer = 0;
+  const int ls_max = p->ls_max_trials > 0 ? p->ls_max_trials : 10;
+  const double ls_c1 = p->ls_c1 > 0.0 ? p->ls_c1 : 1e-4, ls_beta = p->ls_beta > 0.0 ? p->ls_beta : 0.5;
+  int inner_total = 0, outer = 0, ls_trials = 0;
   bool converged = false;
+  bool g_current = false;     // w.f, w.g and gn already hold the residual at v (an accepted trial)
   double gn = 0.0, cn = 0.0, g_init = -1.0;
   for (outer = 1; outer <= p->max_outer; ++outer) {
     bool inner_ok = false;
     for (int l = 0; l < p->max_inner; ++l) {
       cudaEventRecord(ev[0], s);
-      NTRY(residual(v, &gn));
+      if (!g_current) NTRY(residual(v, &gn));
+      g_current = false;
       if (g_init < 0.0) g_init = gn;
       if (gn <= target) {
         inner_ok = true;
@@ -552,9 +631,36 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
       } else {
         NTRY(solver_factor_solve(m, w.values, w.g, w.dv));
       }
-      axpy_kernel<<<nb, 256, 0, s>>>(v, w.dv, 1.0, ndof);
-      NCUDA(cudaGetLastError());
-      ++m->launches;
+      bool ls_failed = false;
+      if (p->line_search) {
+        // eq. armijo: backtrack from a = 1 on phi = ||g||^2 / 2; the trial
+        // residual of an accepted step is the next iteration's residual
+        const double phi0 = 0.5 * gn * gn;
+        double alpha = 1.0, gt = 0.0;
+        bool accepted = false;
+        for (int j = 0; j < ls_max && !accepted; ++j) {
+          axpby_kernel<<<nb, 256, 0, s>>>(v, w.dv, alpha, ndof, m->nw_vt);
+          NCUDA(cudaGetLastError());
+          ++m->launches;
+          ++ls_trials;
+          NTRY(residual(m->nw_vt, &gt));
+          if (0.5 * gt * gt <= (1.0 - 2.0 * ls_c1 * alpha) * phi0)
+            accepted = true;
+          else
+            alpha *= ls_beta;
+        }
+        if (accepted) {
+          NCUDA(cudaMemcpyAsync(v, m->nw_vt, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
+          gn = gt;
+          g_current = true;
+        } else {
+          ls_failed = true;   // Alg. 3: keep v and leave the inner loop
+        }
+      } else {
+        axpy_kernel<<<nb, 256, 0, s>>>(v, w.dv, 1.0, ndof);
+        NCUDA(cudaGetLastError());
+        ++m->launches;
+      }
       cudaEventRecord(ev[2], s);
       cudaEventSynchronize(ev[2]);
       float t1 = 0.f, t2 = 0.f;
@@ -563,7 +669,9 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
       ms_asm += t1;
       ms_sol += t2;
       ++inner_total;
+      if (ls_failed) break;
     }
+    g_current = false;        // the multiplier update below changes g
     clamp_constraint<<<1, 1024, 0, s>>>(m->d_fixed_of_node, m->d_X, q_n, v, p->h, m->nn, p->rho_alm,
                                          inner_ok ? 1 : 0, nullptr, lambda, w.scal + 1);
     NCUDA(cudaGetLastError());
@@ -595,6 +703,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
     stats->ms_assembly = ms_asm;
     stats->ms_solver = ms_sol;
     stats->lin_iters = lin_total;
+    stats->ls_trials = ls_trials;
     stats->g_init = g_init;
   }
   return converged ? TL_OK : fail(m, TL_ERR_NOT_CONVERGED, "Newton / ALM iteration caps reached");

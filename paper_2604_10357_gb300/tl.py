@@ -42,14 +42,16 @@ class tl_params(C.Structure):
     _fields_ = [("h", C.c_double), ("rho_alm", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
                 ("eps_out", C.c_double), ("gravity", C.c_double * 3), ("max_inner", C.c_int32),
                 ("max_outer", C.c_int32), ("linear_solver", C.c_int32), ("lin_max_iter", C.c_int32),
-                ("lin_rtol", C.c_double), ("lin_adaptive", C.c_int32), ("use_graph", C.c_int32)]
+                ("lin_rtol", C.c_double), ("lin_adaptive", C.c_int32), ("use_graph", C.c_int32),
+                ("line_search", C.c_int32), ("ls_max_trials", C.c_int32), ("ls_c1", C.c_double),
+                ("ls_beta", C.c_double)]
 
 
 class tl_newton_stats(C.Structure):
     _fields_ = [("inner_iters", C.c_int32), ("outer_iters", C.c_int32), ("converged", C.c_int32),
                 ("_pad", C.c_int32), ("g_ref", C.c_double), ("g_norm", C.c_double), ("c_norm", C.c_double),
                 ("ms_total", C.c_double), ("ms_assembly", C.c_double), ("ms_solver", C.c_double),
-                ("lin_iters", C.c_int32), ("_pad2", C.c_int32), ("g_init", C.c_double)]
+                ("lin_iters", C.c_int32), ("ls_trials", C.c_int32), ("g_init", C.c_double)]
 
 
 class tl_timing(C.Structure):
@@ -143,7 +145,7 @@ def material(kind="svk", E=0.0, nu=0.0, rho0=1000.0, C10=0.0, C01=0.0, kappa=0.0
 
 def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-4, gravity=(0.0, 0.0, -9.81),
            max_inner=20, max_outer=5, linear_solver=TL_SOLVER_DIRECT, lin_max_iter=0, lin_rtol=0.0,
-           lin_adaptive=0, use_graph=0):
+           lin_adaptive=0, use_graph=0, line_search=0, ls_max_trials=0, ls_c1=0.0, ls_beta=0.0):
     p = tl_params()
     p.h, p.rho_alm, p.rtol, p.atol, p.eps_out = h, rho_alm, rtol, atol, eps_out
     for i in range(3):
@@ -152,6 +154,7 @@ def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-4, gravity=(0.0
     p.linear_solver, p.lin_max_iter, p.lin_rtol = linear_solver, lin_max_iter, lin_rtol
     p.lin_adaptive = lin_adaptive
     p.use_graph = use_graph
+    p.line_search, p.ls_max_trials, p.ls_c1, p.ls_beta = line_search, ls_max_trials, ls_c1, ls_beta
     return p
 
 

@@ -198,7 +198,7 @@ def evaluate(g, tr, test_idx, prm, model=None, modes=None):
     import torch
     if modes is None:
         modes = ["v_n", "extrapolation"] + (["mlp"] if model is not None else [])
-    res = {m: dict(iters=[], ms=[], ms_start=[], dev=[], g0=[], lin=[]) for m in modes}
+    res = {m: dict(iters=[], ms=[], ms_start=[], dev=[], g0=[], lin=[], ls=[]) for m in modes}
     work = torch.empty(13 * g.nn, dtype=torch.float32, device="cuda")
     vinit = torch.empty(g.ndof, dtype=torch.float64, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -229,8 +229,10 @@ def evaluate(g, tr, test_idx, prm, model=None, modes=None):
             r["dev"].append((torch.linalg.norm(v_new - ref) / torch.linalg.norm(ref)).item())
             r["g0"].append(st["g_init"] / st["g_ref"])
             r["lin"].append(st["lin_iters"])
+            r["ls"].append(st["ls_trials"])
     summary = {m: dict(mean_iters=float(np.mean(r["iters"])), mean_ms=float(np.mean(r["ms"])),
                        mean_ms_start=float(np.mean(r["ms_start"])), max_rel_dev=float(np.max(r["dev"])),
-                       median_g0_ratio=float(np.median(r["g0"])), mean_lin_iters=float(np.mean(r["lin"])))
+                       median_g0_ratio=float(np.median(r["g0"])), mean_lin_iters=float(np.mean(r["lin"])),
+                       mean_ls_trials=float(np.mean(r["ls"])))
                for m, r in res.items()}
     return summary, res

@@ -64,6 +64,45 @@ def test_newton_step_matches_oracle(small_case, prec, solver):
     assert np.abs(lam_gpu - ref["lam"]).max() <= 1e-6 * np.abs(ref["lam"]).max()
 
 
+@pytest.fixture(scope="module")
+def line_search_case():
+    """The 240-element SVK box with h = 1e-2: the full Newton step overshoots
+    (the residual grows at the fourth iteration), so the Armijo backtracking
+    of eq. armijo shortens steps before the step converges."""
+    w = inputs.workload_small_svk()
+    m = w["mesh"]
+    om = asm.OracleMesh(m.X, m.conn, [w["material"]], fixed_nodes=m.fixed_nodes)
+    prm = nt.NewtonParams(h=1e-2, rtol=1e-8, solver="dense", line_search=True)
+    lam0 = np.zeros(3 * len(m.fixed_nodes))
+    ref = nt.newton_step(om, w["q_n"].ravel(), w["v"].ravel(), lam0, prm)
+    assert ref["converged"]
+    return w, om, prm, ref
+
+
+@pytest.mark.parametrize("solver", ["direct", "pcg", "pcg_graph"])
+def test_newton_line_search_matches_oracle(line_search_case, solver):
+    """Line search on: the same converged step as the oracle's Newton step with
+    the same backtracking rule (c1 = 1e-4, beta = 0.5, 10 trials), the same
+    Newton count, and more trial points than Newton steps (some steps were
+    shortened)."""
+    tl = _tl()
+    w, om, prm, ref = line_search_case
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+    g.build_pattern(m.fixed_nodes)
+    lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+    p = tl.params(h=prm.h, rho_alm=prm.rho_alm, rtol=prm.rtol, eps_out=prm.eps_out, line_search=1,
+                  linear_solver=tl.TL_SOLVER_DIRECT if solver == "direct" else tl.TL_SOLVER_PCG,
+                  use_graph=1 if solver == "pcg_graph" else 0)
+    v, q, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+    v = v.cpu().numpy()
+    assert st["converged"] == 1
+    assert st["inner_iters"] == ref["inner_iters"]
+    assert st["ls_trials"] > st["inner_iters"]
+    assert np.linalg.norm(v - ref["v"]) <= 1e-8 * np.linalg.norm(ref["v"])
+    assert abs(st["g_ref"] - ref["g_ref"]) <= 1e-10 * ref["g_ref"]
+
+
 def test_newton_free_fall_closed_form():
     """Unclamped, unstressed body at rest: one step gives v = h g exactly."""
     tl = _tl()

@@ -155,3 +155,31 @@ def test_newton_quadratic_convergence_and_solver_independence(small_workload):
     assert a["converged"] and b["converged"]
     assert a["g_norm"] <= a["target"] and b["g_norm"] <= b["target"]
     assert np.linalg.norm(a["v"] - b["v"]) < 1e-9 * np.linalg.norm(a["v"])
+
+
+def test_newton_line_search(small_workload):
+    """Eq. armijo in the oracle's Newton step.  With h = 1e-3 every full step
+    already decreases phi = |g|^2/2 enough, so the line search accepts a = 1
+    throughout and the iterates equal those without it.  With h = 1e-2 the
+    full step overshoots (|g| grows within the inner loop); with the line
+    search every accepted step decreases |g| (the Armijo condition
+    phi(a) <= (1 - 2 c1 a) phi(0) < phi(0)), and both runs reach the same
+    converged velocity (each to |g| <= 1e-8 |g_ref|, which fixes v to ~1e-7
+    here)."""
+    w = small_workload
+    m = w["mesh"]
+    om = asm.OracleMesh(m.X, m.conn, [w["material"]], fixed_nodes=m.fixed_nodes)
+    lam0 = np.zeros(3 * len(m.fixed_nodes))
+    q, v = w["q_n"].ravel(), w["v"].ravel()
+    run = lambda h, ls: nt.newton_step(om, q, v, lam0, nt.NewtonParams(h=h, rtol=1e-8, solver="dense",
+                                                                        line_search=ls))
+    a, b = run(1e-3, False), run(1e-3, True)
+    assert a["history"] == b["history"] and np.array_equal(a["v"], b["v"])
+    c, d = run(1e-2, False), run(1e-2, True)
+    assert c["converged"] and d["converged"]
+    hc, hd = np.array(c["history"]), np.array(d["history"])
+    assert np.any(np.diff(hc[:c["inner_iters"] + 1]) > 0)          # the full step overshoots
+    assert np.all(np.diff(hd[:d["inner_iters"] + 1]) < 0)          # monotone with the line search
+    assert d["inner_iters"] > c["inner_iters"]                     # shortened steps
+    assert c["g_norm"] <= c["target"] and d["g_norm"] <= d["target"]
+    assert np.linalg.norm(c["v"] - d["v"]) <= 1e-6 * np.linalg.norm(c["v"])
