@@ -289,6 +289,52 @@ tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double* q_n, cons
                          const double* v_init, const double* f_ext, double* lambda,
                          double* v_out, double* q_out, tl_newton_stats* stats);
 
+/* ---- first-order inner solver: AdamW (Algorithm 2) -----------------------
+ * Hyperparameters of Algorithm 2; the paper prints none of the AdamW values
+ * (it tunes them per problem), so all are the caller's.  Inner stop, tested
+ * every check_every iterations: ||g|| <= eps_in (1 + ||v||) or
+ * ||g|| <= eps_rel ||g_0|| (g_0: first gradient of the outer iteration). */
+typedef struct tl_adamw_params {
+  double lr;                  /* step size alpha (constant) */
+  double beta1, beta2;        /* moment decay rates, in [0, 1) */
+  double eps;                 /* > 0, added to sqrt(s_hat) */
+  double weight_decay;        /* lambda_wd (decoupled) */
+  double eps_in, eps_rel;     /* inner stopping tolerances */
+  int32_t max_inner;          /* L_max >= 1 */
+  int32_t check_every;        /* >= 1 */
+} tl_adamw_params;
+
+typedef struct tl_adamw_stats {
+  int32_t inner_iters;        /* AdamW iterations summed over outer loops */
+  int32_t outer_iters;
+  int32_t converged;          /* 1 when the inner test and ||c|| <= eps_out were met */
+  int32_t _pad;
+  double g_norm;              /* last gradient norm */
+  double c_norm;              /* last ||c||_2 */
+  double ms_total;            /* wall time of the step */
+} tl_adamw_stats;
+
+/* One backward-Euler step with the AdamW inner solver inside the ALM loop
+ * (Algorithm 2 with Algorithm 1's multiplier update).  Per inner iteration,
+ * on the device: m and s from the previous gradient (reset to zero at every
+ * outer iteration), bias correction, v = (1 - lr wd) v - lr m_hat /
+ * (sqrt(s_hat) + eps), the internal force at q_n + h v (float64 class) and
+ * g of eq. grad_L with ||g||.  After the inner loop v is committed as the
+ * velocity the inertia term is measured from (v_n <- v, as Algorithm 2
+ * prints it), lambda += rho c and ||c|| ends the outer loop when the inner
+ * test was met and ||c|| <= eps_out.
+ *   p: h, rho_alm, eps_out, max_outer and gravity are used (the Newton fields
+ *      are ignored); a: the AdamW parameters above
+ *   q_n, v_n, v_init (nullable: v_n), f_ext (nullable), lambda (in/out,
+ *   3*nfixed), v_out, q_out: device float64 arrays as in tl_newton_step.
+ * Returns TL_OK when converged, TL_ERR_NOT_CONVERGED when the caps are
+ * reached (v_out, q_out, lambda hold the last iterate),
+ * TL_ERR_NONFINITE on a non-finite gradient, TL_ERR_INVALID_ARG on bad
+ * parameters.  Synchronous. */
+tl_status tl_adamw_step(tl_mesh* m, const tl_params* p, const tl_adamw_params* a, const double* q_n,
+                        const double* v_n, const double* v_init, const double* f_ext, double* lambda,
+                        double* v_out, double* q_out, tl_adamw_stats* stats);
+
 /* ---- autotuner of the launch shapes (no counterpart in the paper) --------
  * Times, on this handle's mesh at the state (q_n, v, h), every compiled
  * variant of the two hot launches and keeps the fastest for later calls:

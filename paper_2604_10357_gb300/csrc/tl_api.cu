@@ -62,7 +62,8 @@ void free_mesh(tl_mesh* m) {
   cudaSetDevice(m->device);
   void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_geo32, m->d_geo_df, m->d_X, m->d_node_ptr, m->d_node_col,
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
-                  m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_vt, m->nw_values};
+                  m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_vt, m->nw_values,
+                  m->aw_m1, m->aw_m2, m->aw_vn};
   solver_destroy(m->solver);
   pcg_destroy(m->pcg);
   tile_maps_free(m);

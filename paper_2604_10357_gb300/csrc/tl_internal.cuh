@@ -121,6 +121,7 @@ struct tl_mesh {
   tl::Tune tune;
   // Newton work buffers (tl_newton_step), allocated on first use
   double *nw_g = nullptr, *nw_f = nullptr, *nw_dv = nullptr, *nw_scal = nullptr, *nw_vt = nullptr;
+  double *aw_m1 = nullptr, *aw_m2 = nullptr, *aw_vn = nullptr;   // AdamW moments, committed velocity
   void* nw_values = nullptr;
 
   // instrumentation (tl_timing_*)

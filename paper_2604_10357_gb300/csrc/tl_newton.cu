@@ -1,6 +1,7 @@
 // One backward-Euler time step by Newton's method inside the augmented
-// Lagrangian loop (Algorithm 3 without line search; Algorithm 1 for the
-// multiplier update, eq. lambda_update).
+// Lagrangian loop (Algorithm 3, with the optional Armijo line search of eq.
+// armijo; Algorithm 1 for the multiplier update, eq. lambda_update), and the
+// same step with the first-order AdamW inner solver (Algorithm 2).
 //
 // Per inner iteration: residual g and ||g|| (eq. residual) on the device, the
 // norm to the host for the convergence test, Hessian assembly (eq. hessian),
@@ -32,6 +33,36 @@ namespace {
 __global__ void axpy_kernel(double* y, const double* x, double a, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] += a * x[i];
+}
+
+// AdamW update of Algorithm 2 per DOF: moments from the previous gradient,
+// bias correction (bc1 = 1 - beta1^l, bc2 = 1 - beta2^l), velocity update with
+// decoupled weight decay.
+__global__ void adamw_update(double* v, double* m1, double* m2, const double* g, int64_t n, double beta1,
+                             double beta2, double bc1, double bc2, double lr, double wd, double eps) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double gi = g[i];
+  const double a = beta1 * m1[i] + (1.0 - beta1) * gi;
+  const double b = beta2 * m2[i] + (1.0 - beta2) * gi * gi;
+  m1[i] = a;
+  m2[i] = b;
+  v[i] = (1.0 - lr * wd) * v[i] - lr * (a / bc1) / (sqrt(b / bc2) + eps);
+}
+
+// ||x||_2 in one block (deterministic order); the AdamW absolute test needs |v|
+__global__ void norm_one_block(const double* x, int64_t n, double* out) {
+  __shared__ double red[32];
+  double sq = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) sq += x[i] * x[i];
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *out = sqrt(t);
+  }
 }
 
 // y = v + a dx (line-search trial point)
@@ -707,4 +738,108 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
     stats->g_init = g_init;
   }
   return converged ? TL_OK : fail(m, TL_ERR_NOT_CONVERGED, "Newton / ALM iteration caps reached");
+}
+
+// One time step with the AdamW inner solver (Algorithm 2): per inner
+// iteration the AdamW update, the internal force at q = q_n + h v (float64
+// class) and the gradient g of eq. grad_L with its norm, all on the device; the
+// norms go to the host at the check interval (and once for g_0).  After the
+// inner loop the velocity is committed (v_n <- v, as printed), lambda += rho c
+// and ||c|| is read for the outer test.
+extern "C" tl_status tl_adamw_step(tl_mesh* m, const tl_params* p, const tl_adamw_params* a, const double* q_n,
+                                   const double* v_n, const double* v_init, const double* f_ext, double* lambda,
+                                   double* v_out, double* q_out, tl_adamw_stats* stats) {
+  if (!m || !p || !a || !q_n || !v_n || !v_out || !q_out || !(p->h > 0.0) || p->max_outer < 1 ||
+      a->max_inner < 1 || a->check_every < 1 || !(a->lr > 0.0) || !(a->beta1 >= 0.0 && a->beta1 < 1.0) ||
+      !(a->beta2 >= 0.0 && a->beta2 < 1.0) || !(a->eps > 0.0))
+    return TL_ERR_INVALID_ARG;
+  if (m->nfixed > 0 && !lambda) return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  const auto t_start = std::chrono::steady_clock::now();
+  const int64_t ndof = 3 * m->nn;
+  cudaStream_t s = m->stream;
+  const unsigned nb = (unsigned)((ndof + 255) / 256);
+  if (!m->nw_g) {
+    TL_CUDA(m, cudaMalloc(&m->nw_g, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&m->nw_f, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&m->nw_dv, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&m->nw_scal, sizeof(double) * 4));
+  }
+  if (!m->aw_m1) {
+    TL_CUDA(m, cudaMalloc(&m->aw_m1, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&m->aw_m2, sizeof(double) * ndof));
+    TL_CUDA(m, cudaMalloc(&m->aw_vn, sizeof(double) * ndof));
+  }
+  TL_TRY(residual_ensure(m));
+  double *g = m->nw_g, *f = m->nw_f, *scal = m->nw_scal, *vn = m->aw_vn, *v = v_out;
+  TL_CUDA(m, cudaMemcpyAsync(v, v_init ? v_init : v_n, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
+  TL_CUDA(m, cudaMemcpyAsync(vn, v_n, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
+  auto read2 = [&](double* host) -> tl_status {     // scal[0] = ||g||, scal[2] = ||v||
+    TL_CUDA(m, cudaMemcpyAsync(host, scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    TL_CUDA(m, cudaStreamSynchronize(s));
+    return TL_OK;
+  };
+  int total = 0, outer = 0;
+  bool converged = false;
+  double gn = 0.0, cn = 0.0;
+  for (outer = 1; outer <= p->max_outer; ++outer) {
+    TL_CUDA(m, cudaMemsetAsync(g, 0, sizeof(double) * ndof, s));
+    TL_CUDA(m, cudaMemsetAsync(m->aw_m1, 0, sizeof(double) * ndof, s));
+    TL_CUDA(m, cudaMemsetAsync(m->aw_m2, 0, sizeof(double) * ndof, s));
+    double g0 = -1.0;
+    bool inner_ok = false;
+    for (int l = 1; l <= a->max_inner; ++l) {
+      const double bc1 = 1.0 - std::pow(a->beta1, (double)l), bc2 = 1.0 - std::pow(a->beta2, (double)l);
+      adamw_update<<<nb, 256, 0, s>>>(v, m->aw_m1, m->aw_m2, g, ndof, a->beta1, a->beta2, bc1, bc2, a->lr,
+                                      a->weight_decay, a->eps);
+      TL_CUDA(m, cudaGetLastError());
+      ++m->launches;
+      TL_TRY(launch_force_prec(m, q_n, v, p->h, f, true));
+      TL_TRY(launch_residual(m, p, q_n, vn, v, f, f_ext, lambda, g, scal));
+      ++total;
+      const bool check = (l % a->check_every) == 0;
+      if (l == 1 || check || l == a->max_inner) {
+        if (check) {
+          norm_one_block<<<1, 1024, 0, s>>>(v, ndof, scal + 2);
+          TL_CUDA(m, cudaGetLastError());
+          ++m->launches;
+        }
+        double hs[3] = {0.0, 0.0, 0.0};
+        TL_TRY(read2(hs));
+        gn = hs[0];
+        if (!std::isfinite(gn)) return fail(m, TL_ERR_NONFINITE, "non-finite AdamW gradient");
+        if (l == 1) g0 = gn;
+        if (check && (gn <= a->eps_in * (1.0 + hs[2]) || gn <= a->eps_rel * g0)) {
+          inner_ok = true;
+          break;
+        }
+      }
+    }
+    // commit v_n <- v; lambda += rho c(q_n + h v); ||c||
+    TL_CUDA(m, cudaMemcpyAsync(vn, v, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
+    clamp_constraint<<<1, 1024, 0, s>>>(m->d_fixed_of_node, m->d_X, q_n, v, p->h, m->nn, p->rho_alm, 1, nullptr,
+                                         lambda, scal + 1);
+    TL_CUDA(m, cudaGetLastError());
+    ++m->launches;
+    TL_CUDA(m, cudaMemcpyAsync(&cn, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TL_CUDA(m, cudaStreamSynchronize(s));
+    if (inner_ok && cn <= p->eps_out) {
+      converged = true;
+      break;
+    }
+  }
+  if (outer > p->max_outer) outer = p->max_outer;
+  q_from_v<<<nb, 256, 0, s>>>(q_n, v, p->h, ndof, q_out);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
+  TL_CUDA(m, cudaStreamSynchronize(s));
+  if (stats) {
+    stats->inner_iters = total;
+    stats->outer_iters = outer;
+    stats->converged = converged ? 1 : 0;
+    stats->g_norm = gn;
+    stats->c_norm = cn;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return converged ? TL_OK : fail(m, TL_ERR_NOT_CONVERGED, "AdamW / ALM iteration caps reached");
 }

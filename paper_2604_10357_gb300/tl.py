@@ -54,6 +54,17 @@ class tl_newton_stats(C.Structure):
                 ("lin_iters", C.c_int32), ("ls_trials", C.c_int32), ("g_init", C.c_double)]
 
 
+class tl_adamw_params(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("weight_decay", C.c_double), ("eps_in", C.c_double), ("eps_rel", C.c_double),
+                ("max_inner", C.c_int32), ("check_every", C.c_int32)]
+
+
+class tl_adamw_stats(C.Structure):
+    _fields_ = [("inner_iters", C.c_int32), ("outer_iters", C.c_int32), ("converged", C.c_int32),
+                ("_pad", C.c_int32), ("g_norm", C.c_double), ("c_norm", C.c_double), ("ms_total", C.c_double)]
+
+
 class tl_timing(C.Structure):
     _fields_ = [("ms_element", C.c_double), ("ms_residual", C.c_double), ("n_element", C.c_int64),
                 ("n_residual", C.c_int64), ("launches", C.c_int64)]
@@ -90,6 +101,7 @@ SIGNATURES = {
     "tl_timing_enable": (C.c_int, [_P, C.c_int32]),
     "tl_timing_read": (C.c_int, [_P, _P]),
     "tl_newton_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tl_adamw_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "tl_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "tl_mlp_backward": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P, _P]),
     "tl_mlp_mse_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
@@ -156,6 +168,14 @@ def params(h=1e-3, rho_alm=1e12, rtol=1e-8, atol=0.0, eps_out=1e-4, gravity=(0.0
     p.use_graph = use_graph
     p.line_search, p.ls_max_trials, p.ls_c1, p.ls_beta = line_search, ls_max_trials, ls_c1, ls_beta
     return p
+
+
+def adamw_params(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, eps_in=1e-4, eps_rel=1e-6,
+                 max_inner=1000, check_every=10):
+    a = tl_adamw_params()
+    a.lr, a.beta1, a.beta2, a.eps, a.weight_decay = lr, beta1, beta2, eps, weight_decay
+    a.eps_in, a.eps_rel, a.max_inner, a.check_every = eps_in, eps_rel, max_inner, check_every
+    return a
 
 
 MLP_NPARAM = 9219
@@ -359,6 +379,21 @@ class Mesh:
         rc = self.lib.tl_newton_step(self.h, C.byref(prm), _ptr(q_n), _ptr(v_n), _ptr(v_init), _ptr(f_ext),
                                      _ptr(lam), _ptr(v_out), _ptr(q_out), C.byref(st))
         stats = {f: getattr(st, f) for f, _ in tl_newton_stats._fields_ if not f.startswith("_pad")}
+        stats["status"] = rc
+        if rc != 0 and (raise_on_nonconvergence or rc != 6):
+            raise TLError(rc, self.lib.tl_last_error(self.h).decode())
+        return v_out, q_out, stats
+
+    def adamw_step(self, prm, aprm, q_n, v_n, lam, v_init=None, f_ext=None, v_out=None, q_out=None,
+                   raise_on_nonconvergence=True):
+        """tl_adamw_step; returns (v, q, stats dict).  lam is updated in place."""
+        torch = self._torch
+        v_out = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if v_out is None else v_out
+        q_out = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if q_out is None else q_out
+        st = tl_adamw_stats()
+        rc = self.lib.tl_adamw_step(self.h, C.byref(prm), C.byref(aprm), _ptr(q_n), _ptr(v_n), _ptr(v_init),
+                                    _ptr(f_ext), _ptr(lam), _ptr(v_out), _ptr(q_out), C.byref(st))
+        stats = {f: getattr(st, f) for f, _ in tl_adamw_stats._fields_ if not f.startswith("_pad")}
         stats["status"] = rc
         if rc != 0 and (raise_on_nonconvergence or rc != 6):
             raise TLError(rc, self.lib.tl_last_error(self.h).decode())
