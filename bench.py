@@ -433,6 +433,22 @@ def run_newton(args):
     warmstart.evaluate(g32, tr, test_idx[:1], chosen_ls, model, modes=[c_mode])
     l_sum, _ = warmstart.evaluate(g32, tr, test_idx, chosen_ls, model, modes=[c_mode])
     out["chosen_line_search"] = dict(l_sum[c_mode], desc="chosen arm with the Armijo line search")
+    # the first-order inner solver (Algorithm 2) from the first held-out state:
+    # cost per AdamW update and the gradient reduction a fixed budget reaches
+    t_a = test_idx[0]
+    lam_a = tr.lam[t_a].clone()
+    _, g0 = g32.eval_residual(tl.params(h=w["h"]), tr.q[t_a], tr.v[t_a], tr.v[t_a], f_ext=tr.f_ext[t_a], lam=lam_a)
+    g0 = g0.item()
+    a_prm = tl.adamw_params(lr=1e-4, max_inner=200, check_every=50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, st_a = g32.adamw_step(tl.params(h=w["h"], max_outer=1), a_prm, tr.q[t_a], tr.v[t_a], lam_a,
+                                f_ext=tr.f_ext[t_a], raise_on_nonconvergence=False)
+    ms_a = 1e3 * (time.perf_counter() - t0)
+    out["adamw"] = dict(inner_iters=st_a["inner_iters"], ms=ms_a, ms_per_update=ms_a / max(1, st_a["inner_iters"]),
+                        g_ratio=st_a["g_norm"] / g0, converged=st_a["converged"],
+                        desc="Algorithm 2, lr 1e-4, 200 updates from the first held-out state (not converged: "
+                             "a first-order rate)")
     if args.newton_direct:
         direct = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_DIRECT)
         d_sum, _ = warmstart.evaluate(g64, tr, test_idx[:1], direct, modes=["v_n"])
