@@ -12,9 +12,17 @@ Paper passages:
   * eq. hessian: H = M/h + h K_t + h^2 rho C_q^T C_q, plus the Kelvin-Voigt
     velocity tangent D (see element.py for that reading).
 
+  * Sec. 4.2 (general constraints): C_q in CSR with a user-given fixed
+    pattern; the Newton-matrix pattern also holds every DOF pair that a row
+    of C_q couples, so h^2 rho C_q^T C_q causes no fill-in.
+
 Readings: the DOF CSR stores the full symmetric matrix with ascending rows
 and columns; f_ff = int rho N_a g dV = (row sums of M) x gravity; the clamp
-constraint of DOF r is c_r(q) = q_r - X_r.
+constraint of DOF r is c_r(q) = q_r - X_r.  General constraints are linear,
+c(q) = C q - b, with C (ncon x 3nn) and b given; their rows follow the clamp
+rows in c, C_q and lambda.  The pattern lifts them at node level: two nodes
+whose DOFs share a row of C become adjacent (their whole 3x3 block enters the
+pattern).
 """
 from __future__ import annotations
 
@@ -29,13 +37,18 @@ from . import t10
 # Sparsity (Sec. 4.2)
 # ---------------------------------------------------------------------------
 
-def node_adjacency(conn, nn):
+def node_adjacency(conn, nn, extra_pairs=None):
     """Coefficient-level CSR: 64-bit keys I*nn + J for every element-local
-    pair, sorted and de-duplicated, then row counts and an exclusive scan."""
+    pair (and every node pair in `extra_pairs`, an (k, 2) array), sorted and
+    de-duplicated, then row counts and an exclusive scan."""
     a = np.repeat(np.arange(10), 10)
     b = np.tile(np.arange(10), 10)
     I = conn[:, a].astype(np.int64).ravel()
     J = conn[:, b].astype(np.int64).ravel()
+    if extra_pairs is not None and len(extra_pairs):
+        ep = np.asarray(extra_pairs, dtype=np.int64).reshape(-1, 2)
+        I = np.concatenate([I, ep[:, 0], ep[:, 1]])
+        J = np.concatenate([J, ep[:, 1], ep[:, 0]])
     keys = np.unique(I * nn + J)
     rows = keys // nn
     cols = keys % nn
@@ -102,7 +115,7 @@ class OracleMesh:
     materials: list of material dicts; mat_of_elem: (ne,) index (or None).
     """
 
-    def __init__(self, X, conn, materials, mat_of_elem=None, fixed_nodes=()):
+    def __init__(self, X, conn, materials, mat_of_elem=None, fixed_nodes=(), constraints=None):
         self.X = np.asarray(X, dtype=np.float64)
         self.conn = np.asarray(conn, dtype=np.int64)
         self.nn = self.X.shape[0]
@@ -116,12 +129,28 @@ class OracleMesh:
             raise ValueError("element with non-positive reference Jacobian")
         rho = np.array([m["rho0"] for m in self.materials])[self.mat_of_elem]
         self.Me = t10.element_mass(self.X, self.conn, rho)           # (ne, 10, 10)
+        # general linear constraints c = C q - b (rows after the clamp rows)
+        if constraints is None:
+            self.C_lin = sp.csr_matrix((0, 3 * self.nn))
+            self.b_lin = np.zeros(0)
+        else:
+            self.C_lin = sp.csr_matrix(constraints[0], shape=(len(constraints[1]), 3 * self.nn))
+            self.b_lin = np.asarray(constraints[1], dtype=np.float64).reshape(-1)
         self._pattern = None
 
     # --- pattern ---------------------------------------------------------
+    def constraint_node_pairs(self):
+        """Node pairs (I, J) whose DOFs share a row of the general C."""
+        pairs = []
+        C = self.C_lin.tocsr()
+        for r in range(C.shape[0]):
+            nodes = np.unique(C.indices[C.indptr[r]:C.indptr[r + 1]] // 3)
+            pairs += [(I, J) for I in nodes for J in nodes]
+        return np.array(pairs, dtype=np.int64).reshape(-1, 2)
+
     def pattern(self):
         if self._pattern is None:
-            node_ptr, node_col = node_adjacency(self.conn, self.nn)
+            node_ptr, node_col = node_adjacency(self.conn, self.nn, self.constraint_node_pairs())
             row_ptr, col = dof_pattern(node_ptr, node_col)
             self._pattern = (node_ptr, node_col, row_ptr, col)
         return self._pattern
@@ -190,6 +219,9 @@ class OracleMesh:
         np.add.at(values, slot_map(self.conn, row_ptr, col).ravel(), Kfull.reshape(-1))
         fd = self.fixed_dofs
         values[csr_positions(row_ptr, col, fd, fd)] += h * h * rho_alm
+        if self.C_lin.shape[0]:
+            CtC = (self.C_lin.T @ self.C_lin).tocoo()
+            np.add.at(values, csr_positions(row_ptr, col, CtC.row, CtC.col), h * h * rho_alm * CtC.data)
         return values
 
     def hessian_matrix(self, q_n, v, h, rho_alm):
@@ -224,9 +256,14 @@ class OracleMesh:
         return phi
 
     def constraint(self, q):
-        """c(q) for the clamp rows: q_r - X_r at every fixed DOF r."""
+        """c(q): the clamp rows q_r - X_r at every fixed DOF r, then the
+        general rows C q - b."""
         fd = self.fixed_dofs
-        return np.asarray(q).reshape(-1)[fd] - self.X.reshape(-1)[fd]
+        q = np.asarray(q).reshape(-1)
+        c = q[fd] - self.X.reshape(-1)[fd]
+        if self.C_lin.shape[0]:
+            c = np.concatenate([c, self.C_lin @ q - self.b_lin])
+        return c
 
     def residual(self, v, q_n, v_n, h, f_ext, gravity, lam, rho_alm, M=None):
         """g(v, lambda) of eq. residual, flat (3nn,)."""
@@ -242,5 +279,8 @@ class OracleMesh:
         g = g - self.gravity_force(gravity)
         q = q_n + h * v
         fd = self.fixed_dofs
-        g[fd] += h * (np.asarray(lam).reshape(-1) + rho_alm * self.constraint(q))
+        w = np.asarray(lam).reshape(-1) + rho_alm * self.constraint(q)     # lambda + rho c
+        g[fd] += h * w[:len(fd)]
+        if self.C_lin.shape[0]:
+            g = g + h * (self.C_lin.T @ w[len(fd):])                      # h C_q^T (lambda + rho c)
         return g

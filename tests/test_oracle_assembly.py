@@ -183,3 +183,64 @@ def test_newton_line_search(small_workload):
     assert d["inner_iters"] > c["inner_iters"]                     # shortened steps
     assert c["g_norm"] <= c["target"] and d["g_norm"] <= d["target"]
     assert np.linalg.norm(c["v"] - d["v"]) <= 1e-6 * np.linalg.norm(c["v"])
+
+
+def _tie_constraints(m):
+    """General linear constraints on the tiny box: the first and the last
+    corner node tied in x and z (2 rows, nodes not sharing an element), and
+    one row mixing three DOFs of three nodes; b = C X (satisfied at rest)."""
+    import scipy.sparse as sp
+    n0, n1 = 0, m.nn - 1
+    rows = [[(3 * n0, 1.0), (3 * n1, -1.0)],
+            [(3 * n0 + 2, 1.0), (3 * n1 + 2, -1.0)],
+            [(3 * 5 + 1, 0.5), (3 * 9 + 1, -2.0), (3 * 12 + 2, 1.5)]]
+    ri, ci, vi = [], [], []
+    for r, row in enumerate(rows):
+        for c, val in row:
+            ri.append(r), ci.append(c), vi.append(val)
+    C = sp.csr_matrix((vi, (ri, ci)), shape=(len(rows), 3 * m.nn))
+    return C, C @ m.X.ravel()
+
+
+def test_general_constraints_pattern_hessian_and_gradient(tiny):
+    """Sec. 4.2 with a general C_q: (i) the pattern is the element adjacency
+    plus every node pair coupled by a row of C (brute force); (ii) the
+    Hessian values equal a dense assembly of M/h + h K + D + h^2 rho C_q^T C_q
+    with C_q = [clamp rows; C]; (iii) the residual stays the gradient of the
+    augmented cost (complex step), so the h C_q^T (lambda + rho c) term and
+    its Hessian are consistent."""
+    m, q, v = tiny
+    C, b = _tie_constraints(m)
+    om = asm.OracleMesh(m.X, m.conn, [SVK], fixed_nodes=m.fixed_nodes, constraints=(C, b))
+    # (i) pattern
+    _, _, row_ptr, col = om.pattern()
+    adj = np.zeros((m.nn, m.nn), bool)
+    for c in m.conn:
+        adj[np.ix_(c, c)] = True
+    assert not adj[0, m.nn - 1]                          # the tie is a true fill-in
+    Cd = C.toarray()
+    for r in range(C.shape[0]):
+        nodes = np.unique(np.nonzero(Cd[r])[0] // 3)
+        adj[np.ix_(nodes, nodes)] = True
+    dense = np.zeros((3 * m.nn, 3 * m.nn), bool)
+    for r in range(3 * m.nn):
+        dense[r, col[row_ptr[r]:row_ptr[r + 1]]] = True
+    assert np.array_equal(dense, np.kron(adj, np.ones((3, 3), bool)))
+    # (ii) Hessian
+    h, rho = 1e-3, 1e6
+    Hs = om.hessian_matrix(q.ravel(), v.ravel(), h, rho).toarray()
+    om0 = asm.OracleMesh(m.X, m.conn, [SVK], fixed_nodes=m.fixed_nodes)
+    H0 = om0.hessian_matrix(q.ravel(), v.ravel(), h, rho).toarray()
+    assert np.abs(Hs - H0 - h * h * rho * (Cd.T @ Cd)).max() <= 1e-13 * np.abs(Hs).max()
+    # (iii) gradient of the augmented cost
+    rng = np.random.default_rng(33)
+    v_n = 0.05 * rng.normal(size=v.shape)
+    lam = rng.normal(size=3 * len(m.fixed_nodes) + C.shape[0])
+    g = om.residual(v.ravel(), q.ravel(), v_n.ravel(), h, None, GRAV, lam, rho)
+    assert np.abs(om.constraint(q.ravel() + h * v.ravel())[-C.shape[0]:]).max() > 0   # violated
+    gcs = np.zeros_like(g)
+    for r in range(3 * m.nn):
+        vc = v.ravel().astype(complex)
+        vc[r] += 1e-30j
+        gcs[r] = om.augmented_cost(vc, q.ravel(), v_n.ravel(), h, None, GRAV, lam, rho).imag / 1e-30
+    assert np.abs(g - gcs).max() < 1e-10 * np.abs(g).max()
