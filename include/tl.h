@@ -149,6 +149,23 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
                          const tl_material* mats, int32_t nmat, const int32_t* mat_of_elem,
                          int32_t precision, void* stream, tl_mesh** out);
 
+/* General linear bilateral constraints c(q) = C q - b (Sec. 4.2: C_q in CSR
+ * with a user-given fixed pattern), in addition to the clamp rows of
+ * tl_build_pattern.  Must come before tl_build_pattern, which adds every node
+ * pair that a row couples to the Newton-matrix pattern (so h^2 rho C^T C has
+ * no fill-in).  Their multipliers follow the 3*nfixed clamp multipliers in
+ * every lambda array (length 3*nfixed + ncon); the residual adds
+ * h C^T (lambda + rho c), the Newton matrix h^2 rho C^T C, the ALM update
+ * lambda += rho c and ||c|| covers both kinds of rows.
+ *   ncon     number of rows (0: no-op)
+ *   row_ptr  HOST, ncon + 1 int32 offsets (row_ptr[0] = 0, ascending)
+ *   col      HOST, row_ptr[ncon] int32 DOF indices (3 I + d), in [0, 3 nn)
+ *   val, b   HOST, row_ptr[ncon] and ncon float64
+ * Copied to the device; TL_ERR_STATE after tl_build_pattern or when set
+ * twice, TL_ERR_INVALID_ARG on a malformed CSR. */
+tl_status tl_set_constraints(tl_mesh* m, int64_t ncon, const int32_t* row_ptr, const int32_t* col,
+                             const double* val, const double* b);
+
 /* Build, once, everything that depends only on topology and the reference
  * configuration (Sec. 4.2): the coefficient-level adjacency, the DOF-level
  * CSR pattern of H (3x3 blocks per adjacent node pair, rows and columns

@@ -62,7 +62,9 @@ void free_mesh(tl_mesh* m) {
   cudaSetDevice(m->device);
   void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_geo32, m->d_geo_df, m->d_X, m->d_node_ptr, m->d_node_col,
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
-                  m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_vt, m->nw_values,
+                  m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2,
+                  m->d_con_ptr, m->d_con_col, m->d_con_val, m->d_con_b, m->d_ct_ptr, m->d_ct_con, m->d_ct_val,
+                  m->d_con_w, m->d_con_sq, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_vt, m->nw_values,
                   m->aw_m1, m->aw_m2, m->aw_vn};
   solver_destroy(m->solver);
   pcg_destroy(m->pcg);
@@ -295,6 +297,73 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
   TRYC(cudaMemset(m->d_flags, 0, sizeof(uint32_t) * 4));
 #undef TRYC
   *out = m;
+  return TL_OK;
+}
+
+tl_status tl_set_constraints(tl_mesh* m, int64_t ncon, const int32_t* row_ptr, const int32_t* col,
+                             const double* val, const double* b) {
+  if (!m || ncon < 0 || (ncon > 0 && (!row_ptr || !col || !val || !b))) return TL_ERR_INVALID_ARG;
+  if (m->have_pattern) return fail(m, TL_ERR_STATE, "tl_set_constraints must come before tl_build_pattern");
+  if (m->ncon > 0) return fail(m, TL_ERR_STATE, "constraints already set");
+  if (ncon == 0) return TL_OK;
+  const int64_t ndof = 3 * m->nn;
+  if (row_ptr[0] != 0) return fail(m, TL_ERR_INVALID_ARG, "constraint row_ptr[0] must be 0");
+  for (int64_t r = 0; r < ncon; ++r)
+    if (row_ptr[r + 1] < row_ptr[r]) return fail(m, TL_ERR_INVALID_ARG, "constraint row_ptr not ascending");
+  const int64_t nnzc = row_ptr[ncon];
+  for (int64_t k = 0; k < nnzc; ++k)
+    if (col[k] < 0 || col[k] >= ndof) return fail(m, TL_ERR_INVALID_ARG, "constraint column out of range");
+  // C^T by DOF (the residual term h C_q^T (lambda + rho c), one DOF per thread)
+  std::vector<int32_t> ct_ptr(ndof + 1, 0), ct_con(nnzc);
+  std::vector<double> ct_val(nnzc);
+  for (int64_t k = 0; k < nnzc; ++k) ++ct_ptr[col[k] + 1];
+  for (int64_t i = 0; i < ndof; ++i) ct_ptr[i + 1] += ct_ptr[i];
+  {
+    std::vector<int32_t> cur(ct_ptr.begin(), ct_ptr.end() - 1);
+    for (int64_t r = 0; r < ncon; ++r)
+      for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+        const int32_t at = cur[col[k]]++;
+        ct_con[at] = (int32_t)r;
+        ct_val[at] = val[k];
+      }
+  }
+  // node pairs coupled by a row (the Sec. 4.2 fill), per node
+  std::vector<std::vector<int32_t>> ex(m->nn);
+  for (int64_t r = 0; r < ncon; ++r) {
+    std::vector<int32_t> nodes;
+    for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) nodes.push_back(col[k] / 3);
+    std::sort(nodes.begin(), nodes.end());
+    nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+    for (int32_t I : nodes)
+      for (int32_t J : nodes) ex[I].push_back(J);
+  }
+  m->h_ex_ptr.assign(m->nn + 1, 0);
+  m->h_ex_col.clear();
+  for (int64_t I = 0; I < m->nn; ++I) {
+    std::sort(ex[I].begin(), ex[I].end());
+    ex[I].erase(std::unique(ex[I].begin(), ex[I].end()), ex[I].end());
+    m->h_ex_col.insert(m->h_ex_col.end(), ex[I].begin(), ex[I].end());
+    m->h_ex_ptr[I + 1] = (int32_t)m->h_ex_col.size();
+  }
+  const size_t nz = (size_t)std::max<int64_t>(nnzc, 1);
+  TL_CUDA(m, cudaMalloc(&m->d_con_ptr, sizeof(int32_t) * (ncon + 1)));
+  TL_CUDA(m, cudaMalloc(&m->d_con_col, sizeof(int32_t) * nz));
+  TL_CUDA(m, cudaMalloc(&m->d_con_val, sizeof(double) * nz));
+  TL_CUDA(m, cudaMalloc(&m->d_con_b, sizeof(double) * ncon));
+  TL_CUDA(m, cudaMalloc(&m->d_ct_ptr, sizeof(int32_t) * (ndof + 1)));
+  TL_CUDA(m, cudaMalloc(&m->d_ct_con, sizeof(int32_t) * nz));
+  TL_CUDA(m, cudaMalloc(&m->d_ct_val, sizeof(double) * nz));
+  TL_CUDA(m, cudaMalloc(&m->d_con_w, sizeof(double) * ncon));
+  TL_CUDA(m, cudaMalloc(&m->d_con_sq, sizeof(double)));
+  TL_CUDA(m, cudaMemcpy(m->d_con_ptr, row_ptr, sizeof(int32_t) * (ncon + 1), cudaMemcpyHostToDevice));
+  TL_CUDA(m, cudaMemcpy(m->d_con_col, col, sizeof(int32_t) * nnzc, cudaMemcpyHostToDevice));
+  TL_CUDA(m, cudaMemcpy(m->d_con_val, val, sizeof(double) * nnzc, cudaMemcpyHostToDevice));
+  TL_CUDA(m, cudaMemcpy(m->d_con_b, b, sizeof(double) * ncon, cudaMemcpyHostToDevice));
+  TL_CUDA(m, cudaMemcpy(m->d_ct_ptr, ct_ptr.data(), sizeof(int32_t) * (ndof + 1), cudaMemcpyHostToDevice));
+  TL_CUDA(m, cudaMemcpy(m->d_ct_con, ct_con.data(), sizeof(int32_t) * nnzc, cudaMemcpyHostToDevice));
+  TL_CUDA(m, cudaMemcpy(m->d_ct_val, ct_val.data(), sizeof(double) * nnzc, cudaMemcpyHostToDevice));
+  TL_CUDA(m, cudaMemset(m->d_con_sq, 0, sizeof(double)));
+  m->ncon = ncon;
   return TL_OK;
 }
 

@@ -106,6 +106,16 @@ struct tl_mesh {
   uint16_t* agg_code = nullptr;   // ntiles x kAggCap
   int32_t* agg_nu = nullptr;      // ntiles
 
+  // general linear constraints c = C q - b (tl_set_constraints), rows after the clamp rows
+  int64_t ncon = 0;
+  int32_t *d_con_ptr = nullptr, *d_con_col = nullptr;   // C: ncon + 1 row offsets, DOF columns
+  double *d_con_val = nullptr, *d_con_b = nullptr;
+  int32_t *d_ct_ptr = nullptr, *d_ct_con = nullptr;     // C^T by DOF: 3 nn + 1 offsets, constraint ids
+  double* d_ct_val = nullptr;
+  double* d_con_w = nullptr;                            // lambda_c + rho c_c(q) of the last residual
+  double* d_con_sq = nullptr;                           // ||c_general||^2 of the last multiplier update
+  std::vector<int32_t> h_ex_ptr, h_ex_col;              // node pairs coupled by C (pattern fill), host
+
   // scratch
   uint32_t* d_flags = nullptr;    // sticky device status
   int* d_tile_counters = nullptr; // kTileCounters dynamic tile queues
@@ -182,6 +192,10 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
                           const double* v, const double* f_int, const double* f_ext,
                           const double* lambda, double* g, double* g_norm);
 tl_status launch_add_penalty(tl_mesh* m, double value, void* values);
+// general constraints: lambda_c += rho c_c(q_n + h v) when the flag (or
+// update) says so, and ||c_general||^2 into m->d_con_sq (no-op without them)
+tl_status launch_con_update(tl_mesh* m, const double* q_n, const double* v, double h, double rho,
+                            int update, const int32_t* update_flag, double* lambda_general);
 tl_status residual_ensure(tl_mesh* m);
 tl_status mass_split_build(tl_mesh* m, cudaStream_t s);
 

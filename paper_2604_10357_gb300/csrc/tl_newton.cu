@@ -81,7 +81,8 @@ __global__ void q_from_v(const double* q_n, const double* v, double h, int64_t n
 // (update_flag, when given, is read on the device instead of update_lambda.)
 __global__ void clamp_constraint(const int32_t* fixed_of_node, const double* X,
                                  const double* q_n, const double* v, double h, int64_t nn, double rho,
-                                 int update_lambda, const int32_t* update_flag, double* lambda, double* out) {
+                                 int update_lambda, const int32_t* update_flag, double* lambda, double* out,
+                                 const double* extra_sq) {
   __shared__ double red[32];
   if (update_flag) update_lambda = *update_flag;
   double sq = 0.0;
@@ -101,7 +102,7 @@ __global__ void clamp_constraint(const int32_t* fixed_of_node, const double* X,
   if (threadIdx.x < 32) {
     double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) *out = sqrt(t);
+    if (threadIdx.x == 0) *out = sqrt(t + (extra_sq ? *extra_sq : 0.0));   // + the general rows
   }
 }
 
@@ -365,8 +366,11 @@ tl_status capture_step(tl_mesh* m, const tl_params* p, NewtonGraph* G) {
       e = capture_conditional(s, h_in, cudaGraphCondTypeWhile, &b_inner);
     }
     if (e == cudaSuccess) {
+      const tl_status sc = launch_con_update(m, G->q_n, G->v, p->h, p->rho_alm, 0, &c->inner_ok,
+                                             G->lam + 3 * m->nfixed);
+      if (sc != TL_OK) e = cudaErrorUnknown;
       clamp_constraint<<<1, 1024, 0, s>>>(m->d_fixed_of_node, m->d_X, G->q_n, G->v, p->h, m->nn, p->rho_alm, 0,
-                                           &c->inner_ok, G->lam, scal + 1);
+                                           &c->inner_ok, G->lam, scal + 1, m->ncon ? m->d_con_sq : nullptr);
       ctl_outer<<<1, 1, 0, s>>>(c, scal + 1, p->eps_out, p->max_outer, h_out);
     }
     cudaError_t e2 = end_capture(&tmp);
@@ -467,7 +471,7 @@ tl_status ensure_graph(tl_mesh* m, const tl_params* p) {
     TL_CUDA(m, cudaMalloc(&G->v, sizeof(double) * ndof));
     TL_CUDA(m, cudaMalloc(&G->f_ext, sizeof(double) * ndof));
     TL_CUDA(m, cudaMalloc(&G->q_out, sizeof(double) * ndof));
-    TL_CUDA(m, cudaMalloc(&G->lam, sizeof(double) * std::max<int64_t>(1, 3 * m->nfixed)));
+    TL_CUDA(m, cudaMalloc(&G->lam, sizeof(double) * std::max<int64_t>(1, 3 * m->nfixed + m->ncon)));
     TL_CUDA(m, cudaMalloc(&G->ctl, sizeof(NewtonCtl)));
     TL_CUDA(m, cudaMallocHost(&G->ctl_host, sizeof(NewtonCtl)));
   }
@@ -508,7 +512,7 @@ tl_status newton_step_graph(tl_mesh* m, const tl_params* p, const double* q_n, c
   NewtonGraph* G = m->ngraph;
   cudaStream_t s = m->stream;
   const size_t vbytes = sizeof(double) * 3 * m->nn;
-  const size_t lbytes = sizeof(double) * 3 * m->nfixed;
+  const size_t lbytes = sizeof(double) * (3 * m->nfixed + m->ncon);
   TL_CUDA(m, cudaMemcpyAsync(G->q_n, q_n, vbytes, cudaMemcpyDeviceToDevice, s));
   TL_CUDA(m, cudaMemcpyAsync(G->v_n, v_n, vbytes, cudaMemcpyDeviceToDevice, s));
   TL_CUDA(m, cudaMemcpyAsync(G->v, v_init ? v_init : v_n, vbytes, cudaMemcpyDeviceToDevice, s));
@@ -552,7 +556,7 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
                                     double* q_out, tl_newton_stats* stats) {
   if (!m || !p || !q_n || !v_n || !v_out || !q_out || !(p->h > 0.0) || p->max_inner < 1 || p->max_outer < 1)
     return TL_ERR_INVALID_ARG;
-  if (m->nfixed > 0 && !lambda) return TL_ERR_INVALID_ARG;
+  if ((m->nfixed > 0 || m->ncon > 0) && !lambda) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
   const auto t_start = std::chrono::steady_clock::now();
   const bool use_pcg = p->linear_solver == TL_SOLVER_PCG;
@@ -703,8 +707,10 @@ extern "C" tl_status tl_newton_step(tl_mesh* m, const tl_params* p, const double
       if (ls_failed) break;
     }
     g_current = false;        // the multiplier update below changes g
+    NTRY(launch_con_update(m, q_n, v, p->h, p->rho_alm, inner_ok ? 1 : 0, nullptr, lambda + 3 * m->nfixed));
     clamp_constraint<<<1, 1024, 0, s>>>(m->d_fixed_of_node, m->d_X, q_n, v, p->h, m->nn, p->rho_alm,
-                                         inner_ok ? 1 : 0, nullptr, lambda, w.scal + 1);
+                                         inner_ok ? 1 : 0, nullptr, lambda, w.scal + 1,
+                                         m->ncon ? m->d_con_sq : nullptr);
     NCUDA(cudaGetLastError());
     ++m->launches;
     NCUDA(cudaMemcpyAsync(&cn, w.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -753,7 +759,7 @@ extern "C" tl_status tl_adamw_step(tl_mesh* m, const tl_params* p, const tl_adam
       a->max_inner < 1 || a->check_every < 1 || !(a->lr > 0.0) || !(a->beta1 >= 0.0 && a->beta1 < 1.0) ||
       !(a->beta2 >= 0.0 && a->beta2 < 1.0) || !(a->eps > 0.0))
     return TL_ERR_INVALID_ARG;
-  if (m->nfixed > 0 && !lambda) return TL_ERR_INVALID_ARG;
+  if ((m->nfixed > 0 || m->ncon > 0) && !lambda) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
   const auto t_start = std::chrono::steady_clock::now();
   const int64_t ndof = 3 * m->nn;
@@ -817,8 +823,9 @@ extern "C" tl_status tl_adamw_step(tl_mesh* m, const tl_params* p, const tl_adam
     }
     // commit v_n <- v; lambda += rho c(q_n + h v); ||c||
     TL_CUDA(m, cudaMemcpyAsync(vn, v, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
+    TL_TRY(launch_con_update(m, q_n, v, p->h, p->rho_alm, 1, nullptr, lambda + 3 * m->nfixed));
     clamp_constraint<<<1, 1024, 0, s>>>(m->d_fixed_of_node, m->d_X, q_n, v, p->h, m->nn, p->rho_alm, 1, nullptr,
-                                         lambda, scal + 1);
+                                         lambda, scal + 1, m->ncon ? m->d_con_sq : nullptr);
     TL_CUDA(m, cudaGetLastError());
     ++m->launches;
     TL_CUDA(m, cudaMemcpyAsync(&cn, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));

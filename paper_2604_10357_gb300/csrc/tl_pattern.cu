@@ -63,19 +63,24 @@ __device__ void warp_bitonic_sort(int32_t* buf, int n) {
   }
 }
 
-// One warp per node: gather conn of incident elements, sort, de-duplicate.
+// One warp per node: gather conn of incident elements (and the nodes that a
+// general constraint row couples to it, ex_ptr / ex_col, nullable), sort,
+// de-duplicate.
 // WRITE = false: deg[node] = number of distinct neighbours.
 // WRITE = true : node_col[node_ptr[node] + k] = k-th neighbour (ascending).
 template <bool WRITE>
 __global__ void node_neighbours(const int32_t* conn, const int32_t* inc_ptr, const int32_t* inc_list, int64_t nn,
-                                int32_t* deg, const int32_t* node_ptr, int32_t* node_col, uint32_t* flags) {
+                                int32_t* deg, const int32_t* node_ptr, int32_t* node_col, uint32_t* flags,
+                                const int32_t* ex_ptr, const int32_t* ex_col) {
   __shared__ int32_t sbuf[kWarpsPerBlock][kCap];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t node = blockIdx.x * (int64_t)kWarpsPerBlock + warp;
   if (node >= nn) return;
   int32_t* buf = sbuf[warp];
   const int i0 = inc_ptr[node], i1 = inc_ptr[node + 1];
-  const int ncand = (i1 - i0) * 10;
+  const int ne_cand = (i1 - i0) * 10;
+  const int x0 = ex_ptr ? ex_ptr[node] : 0, x1 = ex_ptr ? ex_ptr[node + 1] : 0;
+  const int ncand = ne_cand + (x1 - x0);
   if (ncand > kCap) {
     if (lane == 0) atomicOr(flags, kFlagBadIndex);
     if (!WRITE && lane == 0) deg[node] = 0;
@@ -85,7 +90,8 @@ __global__ void node_neighbours(const int32_t* conn, const int32_t* inc_ptr, con
   while (n < ncand) n <<= 1;
   for (int t = lane; t < n; t += 32) {
     int32_t val = INT_MAX;
-    if (t < ncand) val = conn[(int64_t)inc_list[i0 + t / 10] * 10 + t % 10];
+    if (t < ne_cand) val = conn[(int64_t)inc_list[i0 + t / 10] * 10 + t % 10];
+    else if (t < ncand) val = ex_col[x0 + t - ne_cand];
     buf[t] = val;
   }
   __syncwarp();
@@ -214,7 +220,7 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   for (int64_t j = 0; j < nfixed; ++j) fixed_of[fixed[j]] = (int32_t)j;
 
   int32_t *d_cnt = nullptr, *d_inc_ptr = nullptr, *d_cursor = nullptr, *d_inc = nullptr, *d_deg = nullptr,
-          *d_fixed = nullptr;
+          *d_fixed = nullptr, *d_ex_ptr = nullptr, *d_ex_col = nullptr;
   void* d_tmp = nullptr;
   size_t tmp_bytes = 0;
   tl_status st = TL_OK;
@@ -226,6 +232,8 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
     cudaFree(d_deg);
     cudaFree(d_fixed);
     cudaFree(d_tmp);
+    cudaFree(d_ex_ptr);
+    cudaFree(d_ex_col);
   };
 #define TRY(call)                                   \
   do {                                              \
@@ -256,9 +264,17 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
                                                            d_inc);
   TRY(cudaGetLastError());
   // ---- neighbours: count, scan, write ------------------------------------
+  if (m->ncon > 0) {   // node pairs coupled by general constraint rows (the Sec. 4.2 fill)
+    TRY(cudaMalloc(&d_ex_ptr, sizeof(int32_t) * (nn + 1)));
+    TRY(cudaMalloc(&d_ex_col, sizeof(int32_t) * std::max<size_t>(m->h_ex_col.size(), 1)));
+    TRY(cudaMemcpyAsync(d_ex_ptr, m->h_ex_ptr.data(), sizeof(int32_t) * (nn + 1), cudaMemcpyHostToDevice, s));
+    if (!m->h_ex_col.empty())
+      TRY(cudaMemcpyAsync(d_ex_col, m->h_ex_col.data(), sizeof(int32_t) * m->h_ex_col.size(),
+                          cudaMemcpyHostToDevice, s));
+  }
   TRY(cudaMemsetAsync(d_deg, 0, sizeof(int32_t) * (nn + 1), s));
   node_neighbours<false><<<nblocks(nn, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
-      m->d_conn, d_inc_ptr, d_inc, nn, d_deg, nullptr, nullptr, m->d_flags);
+      m->d_conn, d_inc_ptr, d_inc, nn, d_deg, nullptr, nullptr, m->d_flags, d_ex_ptr, d_ex_col);
   TRY(cudaGetLastError());
   TRY(cudaMalloc(&m->d_node_ptr, sizeof(int32_t) * (nn + 1)));
   size_t tmp2 = 0;
@@ -277,7 +293,8 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   TRY(cudaStreamSynchronize(s));
   if (flags & kFlagBadIndex) {
     cleanup();
-    return fail(m, TL_ERR_UNSUPPORTED, "a node has more than 204 incident elements");
+    return fail(m, TL_ERR_UNSUPPORTED, "a node has more than 2,048 neighbour candidates (10 per incident element "
+                                       "plus its constraint couplings)");
   }
   const int64_t nnz = 9 * (int64_t)nnz_node;
   if (nnz >= (int64_t)INT_MAX) {
@@ -288,7 +305,7 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   m->nnz = nnz;
   TRY(cudaMalloc(&m->d_node_col, sizeof(int32_t) * std::max<int64_t>(nnz_node, 1)));
   node_neighbours<true><<<nblocks(nn, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
-      m->d_conn, d_inc_ptr, d_inc, nn, d_deg, m->d_node_ptr, m->d_node_col, m->d_flags);
+      m->d_conn, d_inc_ptr, d_inc, nn, d_deg, m->d_node_ptr, m->d_node_col, m->d_flags, d_ex_ptr, d_ex_col);
   TRY(cudaGetLastError());
   // ---- DOF pattern --------------------------------------------------------
   TRY(cudaMalloc(&m->d_row_ptr, sizeof(int32_t) * (3 * nn + 1)));

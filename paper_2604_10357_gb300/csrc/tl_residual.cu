@@ -20,6 +20,94 @@ namespace {
 
 constexpr int kResBlock = 256;
 
+// General constraints in the residual: g_r += h sum_c C_cr (lambda_c + rho c_c)
+// over the constraints c of DOF r (C^T by DOF; w = lambda + rho c, formed
+// first).  ptr == nullptr: no general constraints.
+struct ConTerm {
+  const int32_t* ptr;
+  const int32_t* con;
+  const double* val;
+  const double* w;
+};
+
+__device__ __forceinline__ double con_term(const ConTerm& ct, int64_t r) {
+  double t = 0.0;
+  for (int32_t k = ct.ptr[r]; k < ct.ptr[r + 1]; ++k) t += ct.val[k] * ct.w[ct.con[k]];
+  return t;
+}
+
+// w_c = lambda_c + rho c_c(q_n + h v), c_c = sum_k C_ck q_k - b_c (one thread per row)
+__global__ void con_eval(const int32_t* cptr, const int32_t* ccol, const double* cval, const double* b, int64_t ncon,
+                         const double* q_n, const double* v, double h, const double* lambda, double rho, double* w) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncon) return;
+  double s = -b[c];
+  for (int32_t k = cptr[c]; k < cptr[c + 1]; ++k) {
+    const int32_t i = ccol[k];
+    s += cval[k] * (q_n[i] + h * v[i]);
+  }
+  w[c] = (lambda ? lambda[c] : 0.0) + rho * s;
+}
+
+// lambda_c += rho c_c when the flag says so; ||c||^2 into *sq (one block)
+__global__ void con_update(const int32_t* cptr, const int32_t* ccol, const double* cval, const double* b,
+                           int64_t ncon, const double* q_n, const double* v, double h, double rho, int update,
+                           const int32_t* update_flag, double* lambda, double* sq) {
+  __shared__ double red[32];
+  if (update_flag) update = *update_flag;
+  double t = 0.0;
+  for (int64_t c = threadIdx.x; c < ncon; c += blockDim.x) {
+    double s = -b[c];
+    for (int32_t k = cptr[c]; k < cptr[c + 1]; ++k) {
+      const int32_t i = ccol[k];
+      s += cval[k] * (q_n[i] + h * v[i]);
+    }
+    t += s * s;
+    if (update) lambda[c] += rho * s;
+  }
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double u = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    if (threadIdx.x == 0) *sq = u;
+  }
+}
+
+// h^2 rho C^T C into the CSR values: one thread per constraint row, every pair
+// of its entries, the position of (i, j) by binary search in node I's sorted
+// neighbour list (the pattern holds every coupled pair, Sec. 4.2)
+template <typename T>
+__global__ void con_penalty(const int32_t* cptr, const int32_t* ccol, const double* cval, int64_t ncon,
+                            const int32_t* node_ptr, const int32_t* node_col, double value, T* values,
+                            uint32_t* flags) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncon) return;
+  for (int32_t a = cptr[c]; a < cptr[c + 1]; ++a) {
+    const int32_t i = ccol[a], I = i / 3, d = i % 3;
+    const int32_t p0 = node_ptr[I], deg = node_ptr[I + 1] - p0;
+    for (int32_t bb = cptr[c]; bb < cptr[c + 1]; ++bb) {
+      const int32_t j = ccol[bb], J = j / 3, e = j % 3;
+      int lo = 0, hi = deg - 1, pos = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int32_t x = node_col[p0 + mid];
+        if (x == J) {
+          pos = mid;
+          break;
+        }
+        if (x < J) lo = mid + 1; else hi = mid - 1;
+      }
+      if (pos < 0) {
+        atomicOr(flags, kFlagBadIndex);
+        continue;
+      }
+      atomicAdd(&values[9 * (int64_t)p0 + 3 * (int64_t)deg * d + 3 * pos + e], T(value * cval[a] * cval[bb]));
+    }
+  }
+}
+
 // Scratch of the allocation-free residual (tl_eval_residual_noalloc): one
 // partial sum of ||g||^2 per block of kResBlock nodes.  It lives in the
 // library image, so every GPU that loads the library holds these 128 KiB until
@@ -42,7 +130,7 @@ __global__ void __launch_bounds__(kResBlock * LANES)
                     double gx,
                     double gy, double gz, const double* q_n, const double* v_n, const double* v, const double* dv,
                     const double* f_int, const double* f_ext, const double* lambda, double* g,
-                    double* partials) {
+                    double* partials, ConTerm ct) {
   __shared__ double red[kResBlock * LANES / 32];
   const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LANES;
   const int l = threadIdx.x & (LANES - 1);
@@ -87,6 +175,7 @@ __global__ void __launch_bounds__(kResBlock * LANES)
         const double c = (q_n[r] + h * v[r]) - X[r];
         gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
       }
+      if (ct.ptr) gd += h * con_term(ct, r);
       g[r] = gd;
       sq += gd * gd;
     }
@@ -167,7 +256,7 @@ __global__ void __launch_bounds__(kResBlock * LANES)
                           const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double inv_h,
                           double rho, double gx, double gy, double gz, const double* q_n, const double* v,
                           const float2* dv2, const double* f_int, const double* f_ext, const double* lambda,
-                          double* g, double* partials) {
+                          double* g, double* partials, ConTerm ct) {
   __shared__ double red[kResBlock * LANES / 32];
   const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LANES;
   const int l = threadIdx.x & (LANES - 1);
@@ -206,6 +295,7 @@ __global__ void __launch_bounds__(kResBlock * LANES)
         const double c = (q_n[r] + h * v[r]) - X[r];
         gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
       }
+      if (ct.ptr) gd += h * con_term(ct, r);
       g[r] = gd;
       sq += gd * gd;
     }
@@ -245,6 +335,31 @@ __global__ void add_diag(const int32_t* diag, int64_t n, T value, T* values) {
 
 }  // namespace
 
+namespace {
+
+// w = lambda + rho c for the general constraint rows (their multipliers follow
+// the 3 nfixed clamp multipliers in lambda) and the C^T term of the residual.
+ConTerm con_prepare(tl_mesh* m, const tl_params* p, const double* q_n, const double* v, const double* lambda) {
+  if (m->ncon == 0) return ConTerm{nullptr, nullptr, nullptr, nullptr};
+  con_eval<<<(unsigned)((m->ncon + 255) / 256), 256, 0, m->stream>>>(
+      m->d_con_ptr, m->d_con_col, m->d_con_val, m->d_con_b, m->ncon, q_n, v, p->h,
+      lambda ? lambda + 3 * m->nfixed : nullptr, p->rho_alm, m->d_con_w);
+  ++m->launches;
+  return ConTerm{m->d_ct_ptr, m->d_ct_con, m->d_ct_val, m->d_con_w};
+}
+
+}  // namespace
+
+tl_status launch_con_update(tl_mesh* m, const double* q_n, const double* v, double h, double rho, int update,
+                            const int32_t* update_flag, double* lambda_general) {
+  if (m->ncon == 0) return TL_OK;
+  con_update<<<1, 1024, 0, m->stream>>>(m->d_con_ptr, m->d_con_col, m->d_con_val, m->d_con_b, m->ncon, q_n, v, h,
+                                        rho, update, update_flag, lambda_general, m->d_con_sq);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
+  return TL_OK;
+}
+
 // float32 pairs of the node-level mass (double-float mass product); once per
 // handle, after the mass is assembled.
 tl_status mass_split_build(tl_mesh* m, cudaStream_t s) {
@@ -279,28 +394,29 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   cudaEvent_t t0 = timer_open(m);
   // f_int may alias g: each thread reads its own entries before writing them
   const int64_t n3 = 3 * m->nn;
+  const ConTerm ct = con_prepare(m, p, q_n, v, lambda);
   if (m->tune.residual_split && m->d_mass2) {
     velocity_change_split<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv2);
     if (m->tune.residual_lanes == 4)
       residual_split_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
           m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
           p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
-          m->d_partials);
+          m->d_partials, ct);
     else
       residual_split_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
           m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
           p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
-          m->d_partials);
+          m->d_partials, ct);
   } else {
   velocity_change<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv);
   if (m->tune.residual_lanes == 4)
     residual_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
         m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
-        p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials);
+        p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials, ct);
   else
     residual_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
         m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
-        p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials);
+        p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials, ct);
   }
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(m->d_partials, nb, g_norm, m->d_flags);
@@ -336,14 +452,28 @@ tl_status noalloc_scratch(tl_mesh* m, int dev, double** out) {
 
 tl_status launch_add_penalty(tl_mesh* m, double value, void* values) {
   const int64_t n = 3 * m->nfixed;
-  if (n == 0) return TL_OK;
-  const unsigned nb = (unsigned)((n + 255) / 256);
-  if (m->precision == TL_FP32_ELEM)
-    add_diag<float><<<nb, 256, 0, m->stream>>>(m->d_fixed_diag, n, (float)value, (float*)values);
-  else
-    add_diag<double><<<nb, 256, 0, m->stream>>>(m->d_fixed_diag, n, value, (double*)values);
-  TL_CUDA(m, cudaGetLastError());
-  ++m->launches;
+  if (n > 0) {
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (m->precision == TL_FP32_ELEM)
+      add_diag<float><<<nb, 256, 0, m->stream>>>(m->d_fixed_diag, n, (float)value, (float*)values);
+    else
+      add_diag<double><<<nb, 256, 0, m->stream>>>(m->d_fixed_diag, n, value, (double*)values);
+    TL_CUDA(m, cudaGetLastError());
+    ++m->launches;
+  }
+  if (m->ncon > 0) {    // h^2 rho C^T C of the general rows
+    const unsigned nb = (unsigned)((m->ncon + 127) / 128);
+    if (m->precision == TL_FP32_ELEM)
+      con_penalty<float><<<nb, 128, 0, m->stream>>>(m->d_con_ptr, m->d_con_col, m->d_con_val, m->ncon,
+                                                    m->d_node_ptr, m->d_node_col, value, (float*)values,
+                                                    m->d_flags);
+    else
+      con_penalty<double><<<nb, 128, 0, m->stream>>>(m->d_con_ptr, m->d_con_col, m->d_con_val, m->ncon,
+                                                     m->d_node_ptr, m->d_node_col, value, (double*)values,
+                                                     m->d_flags);
+    TL_CUDA(m, cudaGetLastError());
+    ++m->launches;
+  }
   return TL_OK;
 }
 
@@ -368,7 +498,8 @@ extern "C" tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, co
   if (s != TL_OK) return s;
   residual_kernel<1><<<(unsigned)nb, kResBlock, 0, m->stream>>>(
       m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
-      p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, nullptr, f_int, f_ext, lambda, g, partials);
+      p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, nullptr, f_int, f_ext, lambda, g, partials,
+      con_prepare(m, p, q_n, v, lambda));
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(partials, (int)nb, g_norm, m->d_flags);
   TL_CUDA(m, cudaGetLastError());

@@ -102,6 +102,7 @@ SIGNATURES = {
     "tl_timing_read": (C.c_int, [_P, _P]),
     "tl_newton_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "tl_adamw_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tl_set_constraints": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "tl_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "tl_mlp_backward": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P, _P]),
     "tl_mlp_mse_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
@@ -281,6 +282,17 @@ class Mesh:
             pass
 
     # -- ABI calls -----------------------------------------------------------
+    def set_constraints(self, row_ptr, col, val, b):
+        """tl_set_constraints: general linear rows c = C q - b (C in CSR over
+        DOFs, host arrays); before build_pattern."""
+        rp = np.ascontiguousarray(np.asarray(row_ptr, dtype=np.int32).reshape(-1))
+        cc = np.ascontiguousarray(np.asarray(col, dtype=np.int32).reshape(-1))
+        vv = np.ascontiguousarray(np.asarray(val, dtype=np.float64).reshape(-1))
+        bb = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(-1))
+        self._check(self.lib.tl_set_constraints(self.h, len(bb), rp.ctypes.data_as(_P), cc.ctypes.data_as(_P),
+                                                vv.ctypes.data_as(_P), bb.ctypes.data_as(_P)))
+        self.ncon = len(bb)
+
     def build_pattern(self, fixed_nodes=()):
         fixed = np.ascontiguousarray(np.asarray(fixed_nodes, dtype=np.int32).reshape(-1))
         nnz = C.c_int64()
