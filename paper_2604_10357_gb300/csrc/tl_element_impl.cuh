@@ -710,8 +710,19 @@ __device__ __forceinline__ void force_tile(const Args<T>& A, SmemF<T>& sm, int64
     const int64_t g = 3 * (int64_t)sm.node[c / 3][e] + c % 3;
     const double vv = A.v[g];
     const double x = A.q_n[g] + h * vv;
-    sm.u[c * E + e] = T(x - A.X[g]);
-    sm.vel[c * E + e] = T(vv);
+    double u = x - A.X[g], vr = vv;
+    if constexpr (std::is_same<T, dfl>::value) {
+      // double-float: displacements and velocities relative to the element's
+      // first node, formed in float64 (H = sum_a u_a n_a and Fdot = sum_a v_a n_a
+      // are unchanged since sum_a n_a = 0), so the 48-bit significands carry the
+      // small within-element differences instead of a large rigid motion
+      const int64_t g0 = 3 * (int64_t)sm.node[0][e] + c % 3;
+      const double v0 = A.v[g0];
+      u -= (A.q_n[g0] + h * v0) - A.X[g0];
+      vr -= v0;
+    }
+    sm.u[c * E + e] = T(u);
+    sm.vel[c * E + e] = T(vr);
   }
   __syncthreads();
   const int q = tid >> 5, e = tid & 31;
