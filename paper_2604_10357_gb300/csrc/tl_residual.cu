@@ -123,7 +123,7 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 // precomputed when given (one subtraction per DOF instead of one per mass
 // entry: on GB300 the float64 subtractions and multiply-adds bound this
 // kernel), else formed inline.
-template <int LANES>
+template <int LANES, bool CON>
 __global__ void __launch_bounds__(kResBlock * LANES)
     residual_kernel(const int32_t* node_ptr, const int32_t* node_col, const double* mass, const double* mrow,
                     const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double inv_h, double rho,
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kResBlock * LANES)
         const double c = (q_n[r] + h * v[r]) - X[r];
         gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
       }
-      if (ct.ptr) gd += h * con_term(ct, r);
+      if (CON) gd += h * con_term(ct, r);
       g[r] = gd;
       sq += gd * gd;
     }
@@ -250,7 +250,7 @@ __device__ __forceinline__ void df_combine(float& s_hi, float& s_lo, float o_hi,
 // the lanes' double-float sums are combined by shuffles (two-sums of the high
 // parts) and the first lane forms the node's residual.  A block holds
 // kResBlock nodes.
-template <int LANES>
+template <int LANES, bool CON>
 __global__ void __launch_bounds__(kResBlock * LANES)
     residual_split_kernel(const int32_t* node_ptr, const int32_t* node_col, const float2* mass2, const double* mrow,
                           const int32_t* fixed_of_node, const double* X, int64_t nn, double h, double inv_h,
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kResBlock * LANES)
         const double c = (q_n[r] + h * v[r]) - X[r];
         gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
       }
-      if (ct.ptr) gd += h * con_term(ct, r);
+      if (CON) gd += h * con_term(ct, r);
       g[r] = gd;
       sq += gd * gd;
     }
@@ -398,23 +398,23 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   if (m->tune.residual_split && m->d_mass2) {
     velocity_change_split<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv2);
     if (m->tune.residual_lanes == 4)
-      residual_split_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
+      (ct.ptr ? residual_split_kernel<4, true> : residual_split_kernel<4, false>)<<<nb, kResBlock * 4, 0, m->stream>>>(
           m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
           p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
           m->d_partials, ct);
     else
-      residual_split_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
+      (ct.ptr ? residual_split_kernel<1, true> : residual_split_kernel<1, false>)<<<nb, kResBlock, 0, m->stream>>>(
           m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
           p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
           m->d_partials, ct);
   } else {
   velocity_change<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv);
   if (m->tune.residual_lanes == 4)
-    residual_kernel<4><<<nb, kResBlock * 4, 0, m->stream>>>(
+    (ct.ptr ? residual_kernel<4, true> : residual_kernel<4, false>)<<<nb, kResBlock * 4, 0, m->stream>>>(
         m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
         p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials, ct);
   else
-    residual_kernel<1><<<nb, kResBlock, 0, m->stream>>>(
+    (ct.ptr ? residual_kernel<1, true> : residual_kernel<1, false>)<<<nb, kResBlock, 0, m->stream>>>(
         m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
         p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, m->d_dv, f_int, f_ext, lambda, g, m->d_partials, ct);
   }
@@ -496,10 +496,10 @@ extern "C" tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, co
   double* partials = nullptr;
   tl_status s = noalloc_scratch(m, dev, &partials);
   if (s != TL_OK) return s;
-  residual_kernel<1><<<(unsigned)nb, kResBlock, 0, m->stream>>>(
+  const ConTerm ct = con_prepare(m, p, q_n, v, lambda);
+  (ct.ptr ? residual_kernel<1, true> : residual_kernel<1, false>)<<<(unsigned)nb, kResBlock, 0, m->stream>>>(
       m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
-      p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, nullptr, f_int, f_ext, lambda, g, partials,
-      con_prepare(m, p, q_n, v, lambda));
+      p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, nullptr, f_int, f_ext, lambda, g, partials, ct);
   TL_CUDA(m, cudaGetLastError());
   finish_norm<<<1, 1024, 0, m->stream>>>(partials, (int)nb, g_norm, m->d_flags);
   TL_CUDA(m, cudaGetLastError());
