@@ -123,3 +123,48 @@ def test_newton_step_with_constraints(case, solver):
     assert np.abs(lg - ref["lam"]).max() <= 1e-6 * np.abs(ref["lam"]).max()
     c = C @ (w["q_n"].ravel() + prm.h * v) - bvec           # the tie holds to the ALM tolerance
     assert np.linalg.norm(c) <= prm.eps_out
+
+
+def test_float32_graph_step_with_constraints(case):
+    """The float32 element form with the captured graph and inexact-Newton PCG:
+    the converged step satisfies the oracle's residual target and the ties."""
+    tl = _tl()
+    w, C, bvec, om = case
+    m = w["mesh"]
+    prm = nt.NewtonParams(h=w["h"], rtol=1e-8, solver="dense")
+    lam0 = np.zeros(3 * len(m.fixed_nodes) + C.shape[0])
+    ref = nt.newton_step(om, w["q_n"].ravel(), w["v"].ravel(), lam0, prm)
+    g = _mesh(tl, w, C, bvec, tl.TL_FP32_ELEM)
+    lam = _dev(lam0)
+    p = tl.params(h=prm.h, rho_alm=prm.rho_alm, rtol=prm.rtol, eps_out=prm.eps_out,
+                  linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, use_graph=1)
+    v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+    v = v.cpu().numpy()
+    assert st["converged"] == 1
+    lam_inner = lam.cpu().numpy() - prm.rho_alm * om.constraint(w["q_n"].ravel() + prm.h * v)
+    g_at = om.residual(v, w["q_n"].ravel(), w["v"].ravel(), prm.h, None, prm.gravity, lam_inner, prm.rho_alm)
+    assert np.linalg.norm(g_at) <= 1.05 * 1e-8 * ref["g_ref"]
+    assert np.linalg.norm(C @ (w["q_n"].ravel() + prm.h * v) - bvec) <= prm.eps_out
+
+
+def test_adamw_with_constraints_matches_oracle(case):
+    """Algorithm 2 with general rows: two outer iterations of fixed length
+    (velocity commit, multiplier update of both kinds of rows)."""
+    from oracle import adamw as aw
+    tl = _tl()
+    w, C, bvec, om = case
+    m = w["mesh"]
+    ap = dict(lr=1e-4, max_inner=30, check_every=1000, eps_in=0.0, eps_rel=0.0)
+    lam0 = np.zeros(3 * len(m.fixed_nodes) + C.shape[0])
+    ref = aw.adamw_step(om, w["q_n"].ravel(), w["v"].ravel(), lam0,
+                        aw.AdamWParams(h=w["h"], rho_alm=1e12, max_outer=2, **ap))
+    g = _mesh(tl, w, C, bvec, tl.TL_FP64)
+    lam = _dev(lam0)
+    v, _, st = g.adamw_step(tl.params(h=w["h"], rho_alm=1e12, max_outer=2), tl.adamw_params(**ap),
+                            _dev(w["q_n"]), _dev(w["v"]), lam, raise_on_nonconvergence=False)
+    assert st["inner_iters"] == 60 and st["outer_iters"] == 2
+    v = v.cpu().numpy()
+    assert np.linalg.norm(v - ref["v"]) <= 1e-9 * np.linalg.norm(ref["v"])
+    lg = lam.cpu().numpy()
+    assert np.abs(lg - ref["lam"]).max() <= 1e-9 * np.abs(ref["lam"]).max()
+    assert st["c_norm"] == pytest.approx(ref["c_norm"], rel=1e-9)
