@@ -491,6 +491,74 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_constraints(args):
+    """Cost of general linear constraint rows (Sec. 4.2) in the assembly and
+    the residual: the 103,680-element cantilever with its tip face tied into a
+    plate (each tip-face node tied to its next neighbour along y in all three
+    DOFs: rows c = q_I - q_J - (X_I - X_J)), against the same handle shape
+    without them; Hessian assembly (fused force) + residual per pass, CUDA
+    events over 20 passes after 3 warm-ups."""
+    import torch
+
+    from paper_2604_10357_gb300 import inputs, tl
+    w = inputs.workload_warm_start_svk()
+    m = w["mesh"]
+    X = m.X
+    tip = np.nonzero(np.isclose(X[:, 0], X[:, 0].max()))[0]
+    order = np.lexsort((X[tip, 1], X[tip, 2]))
+    tip = tip[order]
+    ny = len(np.unique(np.round(X[tip, 1], 9)))
+    rows_ptr, rows_col, rows_val = [0], [], []
+    for k in range(len(tip) - 1):
+        if (k + 1) % ny == 0:
+            continue                                      # the next node is on the next z line
+        a, b = tip[k], tip[k + 1]
+        for d in range(3):
+            rows_col += [3 * a + d, 3 * b + d]
+            rows_val += [1.0, -1.0]
+            rows_ptr.append(len(rows_col))
+    rows_ptr = np.array(rows_ptr, dtype=np.int32)
+    rows_col = np.array(rows_col, dtype=np.int32)
+    rows_val = np.array(rows_val)
+    bvec = np.array([rows_val[rows_ptr[r]:rows_ptr[r + 1]] @ X.ravel()[rows_col[rows_ptr[r]:rows_ptr[r + 1]]]
+                     for r in range(len(rows_ptr) - 1)])
+    rng = np.random.default_rng(77)
+    q = torch.as_tensor(inputs.uniform_perturbation(m, 0.01, rng).reshape(-1), device="cuda")
+    v = torch.as_tensor(inputs.gaussian_velocity(m, 0.05, rng).reshape(-1), device="cuda")
+    h, rho = w["h"], 1e12
+    out = {"workload": w["name"], "ncon": int(len(bvec)), "rows": "tip face tied along y (3 per node pair)"}
+    for tag, with_c in (("without", False), ("with", True)):
+        g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
+        if with_c:
+            g.set_constraints(rows_ptr, rows_col, rows_val, bvec)
+        g.build_pattern(m.fixed_nodes)
+        lam = torch.zeros(3 * len(m.fixed_nodes) + (len(bvec) if with_c else 0), dtype=torch.float64,
+                          device="cuda")
+        vals = torch.empty(g.nnz, dtype=torch.float32, device="cuda")
+        f = torch.empty(3 * m.nn, dtype=torch.float64, device="cuda")
+        res = torch.empty_like(f)
+        gn = torch.empty(1, dtype=torch.float64, device="cuda")
+        prm = tl.params(h=h, rho_alm=rho)
+
+        def one():
+            g.assemble_hessian(q, v, h, rho, values=vals, f_int=f)
+            g.eval_residual(prm, q, v, v, lam=lam, f_int=f, g=res, g_norm=gn)
+
+        for _ in range(3):
+            one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            one()
+        e1.record()
+        torch.cuda.synchronize()
+        out[tag] = {"ms": e0.elapsed_time(e1) / 20, "nnz": int(g.nnz)}
+        g.close()
+    out["overhead"] = out["with"]["ms"] / out["without"]["ms"] - 1.0
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,6 +578,7 @@ def main():
                     help="chosen arm from the host loop (same kernels; for launch lists, which do not see "
                          "kernels inside conditional graph nodes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-constraints", action="store_true", help="skip the general-constraint cost measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -538,6 +607,8 @@ def main():
                                               f"{reps} passes in {el:.1f} s (numpy, one thread)"}
         if not args.no_newton and world == 1:
             line["newton"] = run_newton(args)
+        if not args.no_constraints and world == 1:
+            line["constraints"] = run_constraints(args)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch
