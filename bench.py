@@ -2,9 +2,10 @@
 
 One step = one pass of the hot path over the 960,000-element box
 (20 x 4 x 2 m, 200 x 40 x 20 hexes x 6 T10, SVK + Kelvin-Voigt, FP32 element
-form, FP64 residual): the fused element kernel (internal force + 30x30
-tangent + scatter into the fixed-pattern CSR Hessian, values zeroed first),
-the clamp-penalty diagonal and the residual g with its norm.
+form, float64-class residual): the fused element kernel (internal force +
+30x30 tangent + scatter into the fixed-pattern CSR Hessian, values zeroed
+first), the clamp-penalty diagonal and the residual g with its norm (float64,
+its mass product in double-float arithmetic when the autotuner picks it).
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent
 replica of the workload (the assembly needs no exchange; weak scaling).
@@ -356,7 +357,9 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == tl.TL_FP32_ELEM else "f64", "data": "synthetic",
         "config": {"workload": w["name"], "ne": m.ne, "nn": m.nn, "ndof": 3 * m.nn, "nnz": nnz,
-                   "precision": "FP32 element form, FP64 residual" if prec == tl.TL_FP32_ELEM else "FP64",
+                   "precision": ("FP32 element form, float64 residual (mass product double-float: "
+                                 f"{'yes' if tune.get('residual_split') else 'no'})")
+                                if prec == tl.TL_FP32_ELEM else "FP64",
                    "material": "SVK E=1e7 nu=0.3 + Kelvin-Voigt 1e3", "h": h,
                    "l2": "no flush: the H values written every step (%.2f GB) exceed L2" % (nnz * vbytes / 1e9),
                    "parallelism": f"replicas x{world}", "pattern_build_s": t_pat,
