@@ -131,6 +131,7 @@ typedef struct tl_newton_stats {
 typedef struct tl_mesh_info {
   int64_t nn, ne, ndof, nnz, nnz_node, nfixed;
   int32_t precision, nmat;
+  int64_t ncon;               /* general constraint rows (lambda arrays hold 3*nfixed + ncon) */
 } tl_mesh_info;
 
 typedef struct tl_mesh tl_mesh;   /* opaque, library-owned */

@@ -480,6 +480,7 @@ tl_status tl_mesh_info_get(const tl_mesh* m, tl_mesh_info* out) {
   out->nfixed = m->nfixed;
   out->precision = m->precision;
   out->nmat = (int32_t)m->mats.size();
+  out->ncon = m->ncon;
   return TL_OK;
 }
 

@@ -73,7 +73,7 @@ class tl_timing(C.Structure):
 class tl_mesh_info(C.Structure):
     _fields_ = [("nn", C.c_int64), ("ne", C.c_int64), ("ndof", C.c_int64), ("nnz", C.c_int64),
                 ("nnz_node", C.c_int64), ("nfixed", C.c_int64), ("precision", C.c_int32),
-                ("nmat", C.c_int32)]
+                ("nmat", C.c_int32), ("ncon", C.c_int64)]
 
 
 class tl_tune_result(C.Structure):

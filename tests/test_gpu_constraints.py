@@ -64,6 +64,7 @@ def test_pattern_with_constraint_fill(case):
     g = _mesh(tl, w, C, bvec, tl.TL_FP64)
     row_ptr, col = (a.cpu().numpy() for a in g.get_pattern()[:2])
     _, _, r_ref, c_ref = om.pattern()
+    assert g.info()["ncon"] == C.shape[0]
     assert np.array_equal(row_ptr, r_ref) and np.array_equal(col, c_ref)
     plain = asm.OracleMesh(w["mesh"].X, w["mesh"].conn, [w["material"]]).pattern()[3]
     assert len(col) > len(plain)                          # the tie is a fill-in
