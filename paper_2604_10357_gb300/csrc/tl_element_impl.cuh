@@ -473,6 +473,66 @@ __device__ __forceinline__ void accumulate_blockrow(const Args<T>& A, const Smem
       if (k == i) acc[j][k] += ms * T(c_mass420[A0][A0 + j]);
 }
 
+// Both block rows of warp group P (a0 = P: b = P..9; a1 = 9 - P: b = 9-P..9)
+// in one pass over the quadrature points: the tangent row is read once per
+// point for both, and each n_b once (b >= 9 - P serves both rows).  Needs
+// ~90 registers: used by the one-CTA-per-SM kernels only.
+template <int P>
+__device__ __forceinline__ void accumulate_blockrows_merged(const Args<float>& A, const Smem<float>& sm, int i,
+                                                           float (&acc0)[10 - P][3], float (&acc1)[P + 1][3]) {
+  constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
+  const int e = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < n0; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc0[j][k] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < n1; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc1[j][k] = 0.0f;
+#pragma unroll 1
+  for (int q = 0; q < 5; ++q) {
+    const float* nq = &sm.n[e * kNStride + q * 30];
+    const float* Aq = &sm.A[e * kAStride + q * kAQp + i * kARow];
+    const float na0[3] = {nq[a0 * 3], nq[a0 * 3 + 1], nq[a0 * 3 + 2]};
+    const float na1[3] = {nq[a1 * 3], nq[a1 * 3 + 1], nq[a1 * 3 + 2]};
+    float av[27];
+#pragma unroll
+    for (int c = 0; c < 27; ++c) av[c] = Aq[c];
+    float An0[3][3], An1[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int L = 0; L < 3; ++L) {
+        An0[k][L] = na0[0] * av[k * 3 + L] + na0[1] * av[9 + k * 3 + L] + na0[2] * av[18 + k * 3 + L];
+        An1[k][L] = na1[0] * av[k * 3 + L] + na1[1] * av[9 + k * 3 + L] + na1[2] * av[18 + k * 3 + L];
+      }
+#pragma unroll
+    for (int j = 0; j < n0; ++j) {
+      const int b = a0 + j;
+      const float n0b = nq[b * 3], n1b = nq[b * 3 + 1], n2b = nq[b * 3 + 2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc0[j][k] += An0[k][0] * n0b + An0[k][1] * n1b + An0[k][2] * n2b;
+      if (b >= a1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          acc1[b - a1][k] += An1[k][0] * n0b + An1[k][1] * n1b + An1[k][2] * n2b;
+      }
+    }
+  }
+  const float ms = A.mass_scale * A.mat.rho * sm.geo[12][e] * (1.0f / 420.0f);
+#pragma unroll
+  for (int j = 0; j < n0; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k == i) acc0[j][k] += ms * c_mass420[a0][a0 + j];
+#pragma unroll
+  for (int j = 0; j < n1; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k == i) acc1[j][k] += ms * c_mass420[a1][a1 + j];
+}
+
 __device__ __forceinline__ void red_v4(float* p, float x, float y, float z, float w) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
 }
@@ -516,14 +576,18 @@ __device__ __forceinline__ void red_run(const Args<float>& A, int s, float x0, f
 // CSR entries (row 3I+i, columns 3J..3J+2).  The scatter loop is not unrolled
 // (it is bound by the L2 reductions, and unrolled copies of it for every
 // block-row pair made the kernel miss in the instruction cache).
-template <int P>
+template <int P, bool MERGE = false>
 __device__ __forceinline__ void tangent_xchg_accumulate(const Args<float>& A, const Smem<float>& sm, float* X,
                                                         int i, bool wait_empty = false, bool block_sync = false) {
   constexpr int a0 = P, n0 = 10 - P, a1 = 9 - P, n1 = P + 1;
   const int e = threadIdx.x & 31;
   float acc0[n0][3], acc1[n1][3];
-  accumulate_blockrow<float, a0, n0>(A, sm, i, acc0);
-  accumulate_blockrow<float, a1, n1>(A, sm, i, acc1);
+  if constexpr (MERGE) {
+    accumulate_blockrows_merged<P>(A, sm, i, acc0, acc1);
+  } else {
+    accumulate_blockrow<float, a0, n0>(A, sm, i, acc0);
+    accumulate_blockrow<float, a1, n1>(A, sm, i, acc1);
+  }
   // warp-specialised kernel: the scatter warps must have finished issuing the
   // previous tile from X (every compute warp takes this branch alike)
   if (wait_empty) bar_sync_all(kBarEmpty);
@@ -629,7 +693,7 @@ __device__ __forceinline__ void tangent_rows(const Args<T>& A, const Smem<T>& sm
 // One tile of 32 elements starting at internal element e0, already staged in
 // shared memory.  With a prefetch buffer P the next tile (first element
 // e0_next >= 0) is fetched while this one computes.
-template <typename T, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
+template <typename T, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT, bool MERGE = false>
 __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_raw, int64_t e0,
                                           Prefetch<T>* P, int64_t e0_next) {
   Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
@@ -650,11 +714,11 @@ __device__ __forceinline__ void elem_tile(const Args<T>& A, unsigned char* smem_
         float* X = reinterpret_cast<float*>(alias ? smem_raw + offsetof(Smem<float>, fq)
                                                   : smem_raw + sizeof(Smem<float>));
         switch (p) {                   // warp-uniform
-          case 0: tangent_xchg_accumulate<0>(A, sm, X, i, false, alias); break;
-          case 1: tangent_xchg_accumulate<1>(A, sm, X, i, false, alias); break;
-          case 2: tangent_xchg_accumulate<2>(A, sm, X, i, false, alias); break;
-          case 3: tangent_xchg_accumulate<3>(A, sm, X, i, false, alias); break;
-          default: tangent_xchg_accumulate<4>(A, sm, X, i, false, alias); break;
+          case 0: tangent_xchg_accumulate<0, MERGE>(A, sm, X, i, false, alias); break;
+          case 1: tangent_xchg_accumulate<1, MERGE>(A, sm, X, i, false, alias); break;
+          case 2: tangent_xchg_accumulate<2, MERGE>(A, sm, X, i, false, alias); break;
+          case 3: tangent_xchg_accumulate<3, MERGE>(A, sm, X, i, false, alias); break;
+          default: tangent_xchg_accumulate<4, MERGE>(A, sm, X, i, false, alias); break;
         }
         __syncthreads();               // reached by every thread of the block
         if (A.agg)
@@ -810,17 +874,17 @@ __device__ __forceinline__ int tile_at(const SegTable<T>& S, int k) {
 }
 
 // One tile through the kernel of its (material, Kelvin-Voigt) pair.
-template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT>
+template <typename T, int COMBO, bool DO_FORCE, bool DO_TANGENT, bool MERGE = false>
 __device__ __forceinline__ void dispatch_tile(const Args<T>& a, unsigned char* smem_raw, int64_t e0, int combo,
                                               Prefetch<T>* P, int64_t e0_next) {
   if constexpr (COMBO < 4) {
-    elem_tile<T, COMBO / 2, (COMBO % 2) != 0, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next);
+    elem_tile<T, COMBO / 2, (COMBO % 2) != 0, DO_FORCE, DO_TANGENT, MERGE>(a, smem_raw, e0, P, e0_next);
   } else {
     switch (combo) {                                 // block-uniform
-      case 0: elem_tile<T, TL_SVK, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
-      case 1: elem_tile<T, TL_SVK, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
-      case 2: elem_tile<T, TL_MOONEY_RIVLIN, false, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
-      default: elem_tile<T, TL_MOONEY_RIVLIN, true, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, P, e0_next); break;
+      case 0: elem_tile<T, TL_SVK, false, DO_FORCE, DO_TANGENT, MERGE>(a, smem_raw, e0, P, e0_next); break;
+      case 1: elem_tile<T, TL_SVK, true, DO_FORCE, DO_TANGENT, MERGE>(a, smem_raw, e0, P, e0_next); break;
+      case 2: elem_tile<T, TL_MOONEY_RIVLIN, false, DO_FORCE, DO_TANGENT, MERGE>(a, smem_raw, e0, P, e0_next); break;
+      default: elem_tile<T, TL_MOONEY_RIVLIN, true, DO_FORCE, DO_TANGENT, MERGE>(a, smem_raw, e0, P, e0_next); break;
     }
   }
 }
@@ -898,7 +962,7 @@ __global__ void __launch_bounds__(NT, MINB) elem_kernel(Args<T> A, SegTable<T> S
     a.real_end = S.s[cur.sg].real_end;
     nxt = in_order ? cur : SegWalk();
     const int64_t e0_next = (P && k_next < S.ntiles) ? nxt.e0(S, tile_at(S, k_next)) : -1;
-    dispatch_tile<T, COMBO, DO_FORCE, DO_TANGENT>(a, smem_raw, e0, S.s[cur.sg].combo, P, e0_next);
+    dispatch_tile<T, COMBO, DO_FORCE, DO_TANGENT, (MINB == 1)>(a, smem_raw, e0, S.s[cur.sg].combo, P, e0_next);
     if (P) cp_async_wait_all();
     __syncthreads();                                 // this tile's shared data is consumed
     if (k_next >= S.ntiles) break;
