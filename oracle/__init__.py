@@ -1,4 +1,5 @@
-"""CPU oracle for the T10 Total-Lagrangian force / tangent / Hessian path.
+"""CPU oracle for the Total-Lagrangian force / tangent / Hessian path (T10
+elements, and the ANCF3243 beam and ANCF3443 shell elements in ancf.py).
 
 TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, FP64 restatement of
 what the paper's hot path computes (Sec. 2 residual and augmented cost,

@@ -41,8 +41,9 @@ def node_adjacency(conn, nn, extra_pairs=None):
     """Coefficient-level CSR: 64-bit keys I*nn + J for every element-local
     pair (and every node pair in `extra_pairs`, an (k, 2) array), sorted and
     de-duplicated, then row counts and an exclusive scan."""
-    a = np.repeat(np.arange(10), 10)
-    b = np.tile(np.arange(10), 10)
+    nen = conn.shape[1]
+    a = np.repeat(np.arange(nen), nen)
+    b = np.tile(np.arange(nen), nen)
     I = conn[:, a].astype(np.int64).ravel()
     J = conn[:, b].astype(np.int64).ravel()
     if extra_pairs is not None and len(extra_pairs):
@@ -92,17 +93,17 @@ def csr_positions(row_ptr, col, rows, cols):
 
 
 def element_dofs(conn):
-    """(ne, 30) global DOF of local row 3a+i."""
-    return (3 * conn[:, :, None].astype(np.int64) + np.arange(3)).reshape(conn.shape[0], 30)
+    """(ne, 3 nen) global DOF of local row 3a+i."""
+    return (3 * conn[:, :, None].astype(np.int64) + np.arange(3)).reshape(conn.shape[0], 3 * conn.shape[1])
 
 
 def slot_map(conn, row_ptr, col):
-    """(ne, 900) CSR position of K_elem entry (r, s), r = 3a+i, s = 3b+k."""
+    """(ne, (3 nen)^2) CSR position of K_elem entry (r, s), r = 3a+i, s = 3b+k."""
     dofs = element_dofs(conn)
-    ne = conn.shape[0]
-    R = np.repeat(dofs, 30, axis=1)
-    S = np.tile(dofs, (1, 30))
-    return csr_positions(row_ptr, col, R.ravel(), S.ravel()).reshape(ne, 900)
+    ne, nd = dofs.shape
+    R = np.repeat(dofs, nd, axis=1)
+    S = np.tile(dofs, (1, nd))
+    return csr_positions(row_ptr, col, R.ravel(), S.ravel()).reshape(ne, nd * nd)
 
 
 # ---------------------------------------------------------------------------
@@ -124,11 +125,11 @@ class OracleMesh:
         self.mat_of_elem = (np.zeros(self.ne, dtype=np.int64) if mat_of_elem is None
                             else np.asarray(mat_of_elem, dtype=np.int64))
         self.fixed_nodes = np.sort(np.asarray(fixed_nodes, dtype=np.int64))
-        self.gradN, self.J0, self.wJ0 = t10.reference_geometry(self.X, self.conn)
+        self.nen = self.conn.shape[1]
+        rho = np.array([m["rho0"] for m in self.materials])[self.mat_of_elem]
+        self._reference(rho)
         if np.any(self.J0 <= 0.0):
             raise ValueError("element with non-positive reference Jacobian")
-        rho = np.array([m["rho0"] for m in self.materials])[self.mat_of_elem]
-        self.Me = t10.element_mass(self.X, self.conn, rho)           # (ne, 10, 10)
         # general linear constraints c = C q - b (rows after the clamp rows)
         if constraints is None:
             self.C_lin = sp.csr_matrix((0, 3 * self.nn))
@@ -137,6 +138,12 @@ class OracleMesh:
             self.C_lin = sp.csr_matrix(constraints[0], shape=(len(constraints[1]), 3 * self.nn))
             self.b_lin = np.asarray(constraints[1], dtype=np.float64).reshape(-1)
         self._pattern = None
+
+    def _reference(self, rho):
+        """Sec. 4.1 constants of the T10 elements: grad_X N per quadrature
+        point, J0, w_q J0 and the element mass (ne, 10, 10)."""
+        self.gradN, self.J0, self.wJ0 = t10.reference_geometry(self.X, self.conn)
+        self.Me = t10.element_mass(self.X, self.conn, rho)
 
     # --- pattern ---------------------------------------------------------
     def constraint_node_pairs(self):
@@ -162,8 +169,8 @@ class OracleMesh:
     # --- mass ------------------------------------------------------------
     def mass_matrix(self):
         """Global scalar (node-level) consistent mass, scipy CSR (nn x nn)."""
-        a = np.repeat(np.arange(10), 10)
-        b = np.tile(np.arange(10), 10)
+        a = np.repeat(np.arange(self.nen), self.nen)
+        b = np.tile(np.arange(self.nen), self.nen)
         I = self.conn[:, a].ravel()
         J = self.conn[:, b].ravel()
         return sp.coo_matrix((self.Me.reshape(-1), (I, J)), shape=(self.nn, self.nn)).tocsr()
@@ -181,15 +188,16 @@ class OracleMesh:
                 yield idx, mat
 
     def element_forces(self, x, v):
-        """(ne, 10, 3) element forces at nodal positions x and velocities v (nn,3)."""
-        fe = np.zeros((self.ne, 10, 3), dtype=np.result_type(x, v))
+        """(ne, nen, 3) element forces at nodal positions x and velocities v (nn,3)."""
+        fe = np.zeros((self.ne, self.nen, 3), dtype=np.result_type(x, v))
         for idx, mat in self._by_material():
             c = self.conn[idx]
             fe[idx] = elem.element_force(x[c], v[c], self.gradN[idx], self.wJ0[idx], mat)
         return fe
 
     def element_tangents(self, x, v, alpha=1.0, beta=0.0):
-        Ke = np.zeros((self.ne, 30, 30), dtype=np.result_type(x, v))
+        nd = 3 * self.nen
+        Ke = np.zeros((self.ne, nd, nd), dtype=np.result_type(x, v))
         for idx, mat in self._by_material():
             c = self.conn[idx]
             Ke[idx] = elem.element_tangent(x[c], v[c], self.gradN[idx], self.wJ0[idx],
@@ -214,7 +222,8 @@ class OracleMesh:
         Ke = self.element_tangents(q_n + h * v, v, alpha=h, beta=1.0)
         # mass: M_e/h on the (3I+d, 3J+d) entries
         Me = self.Me / h
-        Kfull = Ke + np.einsum("eab,ik->eaibk", Me, np.eye(3)).reshape(self.ne, 30, 30)
+        nd = 3 * self.nen
+        Kfull = Ke + np.einsum("eab,ik->eaibk", Me, np.eye(3)).reshape(self.ne, nd, nd)
         values = np.zeros(len(col))
         np.add.at(values, slot_map(self.conn, row_ptr, col).ravel(), Kfull.reshape(-1))
         fd = self.fixed_dofs

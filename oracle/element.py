@@ -74,15 +74,16 @@ def _tangent_blocks(A, gradN, wJ0):
 
 
 def element_tangent(x_e, v_e, gradN, wJ0, mat, alpha=1.0, beta=0.0):
-    """alpha * K_t,e + beta * D_e as (ne, 30, 30), row 3a+i, column 3b+k."""
+    """alpha * K_t,e + beta * D_e as (ne, 3 nen, 3 nen), row 3a+i, column 3b+k
+    (nen = 10 for T10; the same contraction serves the ANCF elements)."""
     F = kinematics(x_e, gradN)
     Fdot = kinematics(v_e, gradN)
     st = stresses(F, Fdot, mat, want_tangent=True)
-    ne = x_e.shape[0]
+    ne, nen = x_e.shape[0], x_e.shape[1]
     K = alpha * _tangent_blocks(st["A_t"], gradN, wJ0)
     if beta != 0.0 and st["A_vis"] is not None:
         K = K + beta * _tangent_blocks(st["A_vis"], gradN, wJ0)
-    return K.reshape(ne, 30, 30)
+    return K.reshape(ne, 3 * nen, 3 * nen)
 
 
 def element_force_and_tangent(x_e, v_e, gradN, wJ0, mat, alpha=1.0, beta=0.0):

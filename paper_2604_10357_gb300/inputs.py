@@ -350,3 +350,131 @@ def workload_batched(nbodies=48, seed=1000 + 3, lo=1000, hi=60000):
     return dict(name=f"{nbodies} bodies, {mesh.ne:,} T10 total", mesh=mesh,
                 q_n=np.concatenate(qs), v=np.concatenate(vs), materials=mats,
                 mat_of_elem=mesh.body_of_elem.copy(), h=1e-3, meshes=meshes)
+
+
+# ---------------------------------------------------------------------------
+# ANCF meshes (the beam and shell scaling benchmarks, Sec. 5.2 and 5.3)
+#
+# Coefficient convention (shared interface, not arithmetic): physical node p
+# owns the four coefficient vectors 4p + (0: position r, 1: r_x, 2: r_y,
+# 3: r_z).  A beam element lists its two nodes' coefficients (8); a shell
+# element its four corners' (16), corners in the order (-1,-1), (1,-1),
+# (1,1), (-1,1) of its natural coordinates.  E0 holds the reference
+# coefficients: node positions and the unit axis vectors as gradients.
+# ---------------------------------------------------------------------------
+
+ANCF_BEAM = "ancf3243"
+ANCF_SHELL = "ancf3443"
+
+# Material of the paper's element-type scaling benchmarks (SVK, E = 7e8 Pa,
+# nu = 0.33, rho0 = 2700 kg/m^3).
+SVK_7E8 = dict(kind="svk", E=7e8, nu=0.33, rho0=2700.0, eta_d=0.0, lambda_d=0.0)
+
+
+@dataclass
+class AncfMesh:
+    kind: str                # ANCF_BEAM or ANCF_SHELL
+    E0: np.ndarray           # (ncoef, 3) float64 reference coefficient vectors
+    conn: np.ndarray         # (ne, nen) int32 coefficient indices
+    dims: np.ndarray         # (ne, 3) element length, width, height
+    fixed_nodes: np.ndarray  # (nfixed,) int32 clamped coefficients, sorted
+    nphys: int               # physical nodes
+    phys_x: np.ndarray       # (nphys, 3) physical node positions
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nn(self):
+        return self.E0.shape[0]
+
+    @property
+    def ne(self):
+        return self.conn.shape[0]
+
+    @property
+    def X(self):
+        return self.E0
+
+
+def _ancf_coefficients(P):
+    """Reference coefficients of physical nodes at P (np, 3): r = P, r_x, r_y,
+    r_z = the global unit vectors."""
+    E0 = np.zeros((4 * len(P), 3))
+    E0[0::4] = P
+    E0[1::4] = (1.0, 0.0, 0.0)
+    E0[2::4] = (0.0, 1.0, 0.0)
+    E0[3::4] = (0.0, 0.0, 1.0)
+    return E0
+
+
+def beam_ancf3243(ne, L=0.2, W=0.1, H=0.1):
+    """A chain of ne beam elements along x (element e spans nodes e, e+1);
+    node 0 clamped (its four coefficients)."""
+    P = np.zeros((ne + 1, 3))
+    P[:, 0] = L * np.arange(ne + 1)
+    e = np.arange(ne)[:, None]
+    conn = np.concatenate([4 * e + np.arange(4), 4 * (e + 1) + np.arange(4)], axis=1).astype(np.int32)
+    dims = np.tile([L, W, H], (ne, 1)).astype(np.float64)
+    return AncfMesh(ANCF_BEAM, _ancf_coefficients(P), conn, dims, np.arange(4, dtype=np.int32), ne + 1, P)
+
+
+def shell_ancf3443(nx, ny, Lx=4.0, Ly=2.0, H=0.1):
+    """An nx x ny grid of shell elements on [0, Lx] x [0, Ly] (node (i, j) has
+    id i (ny + 1) + j); every node on the edge x = 0 clamped."""
+    i, j = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="ij")
+    P = np.stack([i.ravel() * (Lx / nx), j.ravel() * (Ly / ny), np.zeros(i.size)], axis=1)
+    nid = lambda a, b: a * (ny + 1) + b
+    ei, ej = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    ei, ej = ei.ravel(), ej.ravel()
+    corners = np.stack([nid(ei, ej), nid(ei + 1, ej), nid(ei + 1, ej + 1), nid(ei, ej + 1)], axis=1)
+    conn = (4 * corners[:, :, None] + np.arange(4)).reshape(-1, 16).astype(np.int32)
+    dims = np.tile([Lx / nx, Ly / ny, H], (nx * ny, 1)).astype(np.float64)
+    fixed = (4 * nid(0, np.arange(ny + 1))[:, None] + np.arange(4)).ravel().astype(np.int32)
+    return AncfMesh(ANCF_SHELL, _ancf_coefficients(P), conn, dims, np.sort(fixed), P.shape[0], P)
+
+
+def ancf_bend(mesh, kappa):
+    """Coefficients of the reference body bent about the y axis with curvature
+    kappa (x along the arc): r = (sin(kx)/k, y, (1 - cos(kx))/k), r_x and r_z
+    rotated by the angle kx, r_y unchanged."""
+    E = mesh.E0.copy()
+    x = mesh.phys_x[:, 0]
+    t = kappa * x
+    E[0::4, 0] = np.sin(t) / kappa
+    E[0::4, 2] = (1.0 - np.cos(t)) / kappa
+    E[1::4] = np.stack([np.cos(t), np.zeros_like(t), np.sin(t)], axis=1)
+    E[3::4] = np.stack([-np.sin(t), np.zeros_like(t), np.cos(t)], axis=1)
+    return E
+
+
+def ancf_perturbation(mesh, q, frac, rng):
+    """q + U(-frac, frac) scaled per coefficient: positions by the element
+    dimensions, gradients by 1 (dimensionless); clamped coefficients keep E0."""
+    scale = np.ones_like(q)
+    scale[0::4] = mesh.dims[0][None, :]
+    d = rng.uniform(-1.0, 1.0, size=q.shape) * frac * scale
+    out = q + d
+    out[mesh.fixed_nodes] = mesh.E0[mesh.fixed_nodes]
+    return out
+
+
+def workload_ancf_beam(ne=10, seed=1000 + 6):
+    """ANCF3243 beam (L = 0.2, W = H = 0.1 per element; SVK 7e8 / 0.33 / 2700),
+    bent to a curvature of 0.5 / m and perturbed by 1%; v ~ N(0, 0.01)."""
+    rng = np.random.default_rng(seed)
+    m = beam_ancf3243(ne)
+    q = ancf_perturbation(m, ancf_bend(m, 0.5), 0.01, rng)
+    v = rng.normal(0.0, 0.01, size=q.shape)
+    v[m.fixed_nodes] = 0.0
+    return dict(name=f"ANCF3243 beam, {ne:,} elements", mesh=m, q_n=q, v=v, material=dict(SVK_7E8), h=1e-3)
+
+
+def workload_ancf_shell(nx=4, ny=3, seed=1000 + 7):
+    """ANCF3443 shell 4 x 2 x 0.1 m (SVK 7e8 / 0.33 / 2700) on an nx x ny grid,
+    bent to a curvature of 0.25 / m about y and perturbed by 1%; v ~ N(0, 0.01)."""
+    rng = np.random.default_rng(seed)
+    m = shell_ancf3443(nx, ny)
+    q = ancf_perturbation(m, ancf_bend(m, 0.25), 0.01, rng)
+    v = rng.normal(0.0, 0.01, size=q.shape)
+    v[m.fixed_nodes] = 0.0
+    return dict(name=f"ANCF3443 shell, {nx}x{ny} = {nx * ny:,} elements", mesh=m, q_n=q, v=v,
+                material=dict(SVK_7E8), h=5e-4)
