@@ -132,7 +132,19 @@ typedef struct tl_mesh_info {
   int64_t nn, ne, ndof, nnz, nnz_node, nfixed;
   int32_t precision, nmat;
   int64_t ncon;               /* general constraint rows (lambda arrays hold 3*nfixed + ncon) */
+  int32_t element_kind;       /* tl_element_kind */
+  int32_t nen;                /* nodes (T10) or coefficients (ANCF) per element */
 } tl_mesh_info;
+
+/* Element kinds (Sec. 4.3): 10-node tetrahedra, the two-node ANCF3243 beam
+ * and the four-node ANCF3443 shell.  An ANCF physical node carries four
+ * coefficient vectors (position r and gradients r_x, r_y, r_z, Sec. 2), and
+ * every "node" of the calls below is then a coefficient: ndof = 3 ncoef. */
+typedef enum tl_element_kind {
+  TL_ELEM_T10 = 0,
+  TL_ELEM_ANCF3243 = 1,
+  TL_ELEM_ANCF3443 = 2
+} tl_element_kind;
 
 typedef struct tl_mesh tl_mesh;   /* opaque, library-owned */
 
@@ -149,6 +161,34 @@ typedef struct tl_mesh tl_mesh;   /* opaque, library-owned */
 tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64_t ne,
                          const tl_material* mats, int32_t nmat, const int32_t* mat_of_elem,
                          int32_t precision, void* stream, tl_mesh** out);
+
+/* Create an ANCF mesh handle (Sec. 2, Sec. 4.3: 8 shape functions and a
+ * 3 x 2 x 2 Gauss-Legendre rule per beam element, 16 and 4 x 4 x 3 per shell
+ * element; Sec. 4.1: exact consistent mass).
+ *   kind         TL_ELEM_ANCF3243 or TL_ELEM_ANCF3443
+ *   E0           HOST, ncoef*3 float64 reference coefficient vectors
+ *   ncoef        number of coefficients (four per physical node)
+ *   conn         HOST, ne*8 (beam) or ne*16 (shell) int32 coefficient ids.
+ *                Beam: node A's r, r_x, r_y, r_z, then node B's, A at
+ *                xi = -1.  Shell: the corners at (xi, eta) = (-1,-1), (1,-1),
+ *                (1,1), (-1,1), each r, r_x, r_y, r_z.
+ *   dims         HOST, ne*3 float64 element length L, width W and height /
+ *                thickness H.  Beam: x = L (1+xi)/2, y = W eta/2,
+ *                z = H zeta/2; shell: x = L (1+xi)/2, y = W (1+eta)/2,
+ *                z = H zeta/2 (the shape functions are scaled by them).
+ *   mats, nmat, mat_of_elem, stream   as tl_mesh_create
+ *   precision    TL_FP64 (TL_FP32_ELEM gives TL_ERR_UNSUPPORTED)
+ * Validates coefficient ids, positive dims and det J0 > 0 at every element
+ * quadrature point (TL_ERR_INVALID_ARG otherwise).  The handle takes every
+ * call below: fixed nodes are coefficients (clamp c = e - e0 on all three
+ * components), q, v, f_ext and lambda are per coefficient, the gravity load
+ * is g int rho S_a dV, and tl_get_pattern's slot map and tl_eval_tangent's
+ * K_elem hold (3 nen)^2 entries per element.  The float32 element form, the
+ * launch-shape choices of the autotuner and the learned warm start are T10
+ * features.  Synchronous. */
+tl_status tl_mesh_create_ancf(int32_t kind, const double* E0, int64_t ncoef, const int32_t* conn, int64_t ne,
+                              const double* dims, const tl_material* mats, int32_t nmat,
+                              const int32_t* mat_of_elem, int32_t precision, void* stream, tl_mesh** out);
 
 /* General linear bilateral constraints c(q) = C q - b (Sec. 4.2: C_q in CSR
  * with a user-given fixed pattern), in addition to the clamp rows of
@@ -184,9 +224,9 @@ tl_status tl_build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixe
 
 /* Copy the pattern out (device pointers, caller-allocated):
  *   row_ptr   (ndof+1) int32, col (nnz) int32: the CSR of H
- *   slot_map  (ne*900) int32 or NULL: position in values[] of K_elem entry
- *             (r, s), r = 3a+i (row), s = 3b+k (column), element order as
- *             given to tl_mesh_create. */
+ *   slot_map  (ne*nd*nd, nd = 3 nen: 900 for T10) int32 or NULL: position in
+ *             values[] of K_elem entry (r, s), r = 3a+i (row), s = 3b+k
+ *             (column), element order as given at creation. */
 tl_status tl_get_pattern(const tl_mesh* m, int32_t* row_ptr, int32_t* col, int32_t* slot_map);
 
 /* Internal force f_int(q_n + h v, v) (eq. residual's force term, eq. fint_local
@@ -195,7 +235,7 @@ tl_status tl_get_pattern(const tl_mesh* m, int32_t* row_ptr, int32_t* col, int32
 tl_status tl_eval_force(tl_mesh* m, const double* q_n, const double* v, double h, double* f_int);
 
 /* Element tangents (eq. tangent_block) at q = q_n + h v:
- *   K_elem[e*900 + 30 r + s] = alpha * K_t,e + beta * D_e
+ *   K_elem[e*nd*nd + nd r + s] = alpha * K_t,e + beta * D_e   (nd = 3 nen)
  * with K_t the stiffness (geometric term with the total second Piola-Kirchhoff
  * stress, elastic plus viscous) and D the Kelvin-Voigt velocity tangent
  * df/dv at fixed q.  float64 for TL_FP64 meshes, float32 for TL_FP32_ELEM. */

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "tl_ancf.cuh"
 #include "tl_internal.cuh"
 
 namespace tl {
@@ -60,7 +61,7 @@ void free_mesh(tl_mesh* m) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
-  void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_geo32, m->d_geo_df, m->d_X, m->d_node_ptr, m->d_node_col,
+  void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_ancf_me, m->d_geo32, m->d_geo_df, m->d_X, m->d_node_ptr, m->d_node_col,
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
                   m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2,
                   m->d_con_ptr, m->d_con_col, m->d_con_val, m->d_con_b, m->d_ct_ptr, m->d_ct_con, m->d_ct_val,
@@ -124,6 +125,141 @@ const int kEdge[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
 // Reason of the last failed tl_mesh_create on this thread (no handle exists).
 thread_local std::string g_create_error;
 
+// A fresh handle on the current device.
+tl_mesh* new_mesh(void* stream, int32_t precision, int64_t nn, int64_t ne) {
+  tl_mesh* m = new (std::nothrow) tl_mesh();
+  if (!m) return nullptr;
+  cudaGetDevice(&m->device);
+  if (cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess ||
+      m->num_sms < 1)
+    m->num_sms = 1;
+  m->stream = (cudaStream_t)stream;
+  m->precision = precision;
+  if (precision == TL_FP32_ELEM) {     // float32 PCG iteration: the row-contiguous product, 8 lanes per node
+    m->tune.spmv_group = 8;
+    m->tune.spmv_row = 1;
+  }
+  m->nn = nn;
+  m->ne = ne;
+  return m;
+}
+
+// Material table: Lame constants of SVK, the Mooney-Rivlin and Kelvin-Voigt
+// constants as given; false on an unknown kind.
+bool add_materials(tl_mesh* m, const tl_material* mats, int nmat) {
+  for (int k = 0; k < nmat; ++k) {
+    const tl_material& t = mats[k];
+    MaterialDev md{};
+    md.kind = t.kind;
+    if (t.kind != TL_SVK && t.kind != TL_MOONEY_RIVLIN) return false;
+    md.lam = t.E * t.nu / ((1.0 + t.nu) * (1.0 - 2.0 * t.nu));
+    md.mu = t.E / (2.0 * (1.0 + t.nu));
+    md.C10 = t.C10;
+    md.C01 = t.C01;
+    md.kappa = t.kappa;
+    md.eta = t.eta_d;
+    md.lam_d = t.lambda_d;
+    md.kv = (t.eta_d != 0.0 || t.lambda_d != 0.0) ? 1 : 0;
+    md.rho = t.rho0;
+    m->mats.push_back(md);
+  }
+  return true;
+}
+
+// det J0 > 0 at every element quadrature point of an ANCF element, J0 the
+// natural-coordinate Jacobian of its reference coefficients.
+template <int ET>
+bool ancf_jacobians_positive(const double* E0, const int32_t* c, const double dims[3]) {
+  for (int q = 0; q < ancf::Traits<ET>::NQP; ++q) {
+    double p[3], w;
+    ancf::element_point<ET>(q, p, w);
+    double J0[3][3] = {}, Ji[3][3];
+    for (int a = 0; a < ancf::Traits<ET>::NEN; ++a) {
+      double d[3];
+      ancf::shape<ET>(a, p, dims, nullptr, d);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J0[i][j] += E0[3 * c[a] + i] * d[j];
+    }
+    if (!(ancf::inv3(J0, Ji) > 0.0)) return false;
+  }
+  return true;
+}
+
+// Internal element order (material segments, each padded to a multiple of
+// kTile), then the uploads.  On failure the handle is freed.
+tl_status upload_mesh(tl_mesh* m, int nmat, const std::vector<std::vector<int64_t>>& by_mat, const int32_t* conn,
+                      int nen, const std::vector<double>& geo_user, const double* X) {
+  std::vector<int32_t> h_conn, h_user;
+  std::vector<double> h_geo64;
+  int64_t pos = 0;
+  for (int k = 0; k < nmat; ++k) {
+    if (by_mat[k].empty()) continue;
+    Segment sg;
+    sg.begin = pos;
+    sg.end = pos + (int64_t)by_mat[k].size();
+    const int64_t padded = ((int64_t)by_mat[k].size() + kTile - 1) / kTile * kTile;
+    sg.padded_end = pos + padded;
+    sg.mat = k;
+    for (int64_t i = 0; i < padded; ++i) {
+      if (i < (int64_t)by_mat[k].size()) {
+        const int64_t e = by_mat[k][i];
+        h_conn.insert(h_conn.end(), conn + nen * e, conn + nen * e + nen);
+        h_user.push_back((int32_t)e);
+        h_geo64.insert(h_geo64.end(), &geo_user[16 * e], &geo_user[16 * e] + 16);
+      } else {
+        h_conn.insert(h_conn.end(), nen, 0);
+        h_user.push_back(-1);
+        h_geo64.insert(h_geo64.end(), 16, 0.0);
+      }
+    }
+    pos += padded;
+    m->segs.push_back(sg);
+  }
+  m->ne_pad = pos;
+  const int64_t ne_pad = std::max<int64_t>(pos, 1);
+  std::vector<float> h_geo32(h_geo64.begin(), h_geo64.end());
+  h_conn.resize((size_t)nen * ne_pad, 0);
+  h_user.resize(ne_pad, -1);
+  h_geo64.resize(16 * ne_pad, 0.0);
+  h_geo32.resize(16 * ne_pad, 0.0f);
+  tl_status st = TL_OK;
+#define TRYC(call)                        \
+  do {                                    \
+    cudaError_t _e = (call);              \
+    if (_e != cudaSuccess) {              \
+      st = cuda_fail(m, _e, #call);       \
+      free_mesh(m);                       \
+      return st;                          \
+    }                                     \
+  } while (0)
+  TRYC(cudaMalloc(&m->d_conn, sizeof(int32_t) * nen * ne_pad));
+  TRYC(cudaMalloc(&m->d_user_of, sizeof(int32_t) * ne_pad));
+  TRYC(cudaMalloc(&m->d_geo64, sizeof(double) * 16 * ne_pad));
+  TRYC(cudaMalloc(&m->d_geo32, sizeof(float) * 16 * ne_pad));
+  TRYC(cudaMalloc(&m->d_X, sizeof(double) * 3 * m->nn));
+  TRYC(cudaMalloc(&m->d_flags, sizeof(uint32_t) * 4));
+  TRYC(cudaMalloc(&m->d_tile_counters, sizeof(int) * kTileCounters));
+  TRYC(cudaMemcpy(m->d_conn, h_conn.data(), sizeof(int32_t) * nen * ne_pad, cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(m->d_user_of, h_user.data(), sizeof(int32_t) * ne_pad, cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(m->d_geo64, h_geo64.data(), sizeof(double) * 16 * ne_pad, cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(m->d_geo32, h_geo32.data(), sizeof(float) * 16 * ne_pad, cudaMemcpyHostToDevice));
+  if (m->precision == TL_FP32_ELEM) {
+    // double-float copy (hi, lo float pairs) for the float64-class residual force
+    std::vector<float> h_geodf(32 * ne_pad);
+    for (int64_t i = 0; i < 16 * ne_pad; ++i) {
+      const float hi = (float)h_geo64[i];
+      h_geodf[2 * i] = hi;
+      h_geodf[2 * i + 1] = (float)(h_geo64[i] - (double)hi);
+    }
+    TRYC(cudaMalloc(&m->d_geo_df, sizeof(float) * 32 * ne_pad));
+    TRYC(cudaMemcpy(m->d_geo_df, h_geodf.data(), sizeof(float) * 32 * ne_pad, cudaMemcpyHostToDevice));
+  }
+  TRYC(cudaMemcpy(m->d_X, X, sizeof(double) * 3 * m->nn, cudaMemcpyHostToDevice));
+  TRYC(cudaMemset(m->d_flags, 0, sizeof(uint32_t) * 4));
+#undef TRYC
+  return TL_OK;
+}
+
 }  // namespace
 }  // namespace tl
 
@@ -159,39 +295,11 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
   if (precision != TL_FP64 && precision != TL_FP32_ELEM) return TL_ERR_INVALID_ARG;
   if (nn >= (int64_t)1 << 29) return TL_ERR_OVERFLOW;      // 9 * 3 nn row bases fit in int32
   g_create_error.clear();
-  tl_mesh* m = new (std::nothrow) tl_mesh();
+  tl_mesh* m = new_mesh(stream, precision, nn, ne);
   if (!m) return TL_ERR_OOM;
-  cudaGetDevice(&m->device);
-  if (cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess ||
-      m->num_sms < 1)
-    m->num_sms = 1;
-  m->stream = (cudaStream_t)stream;
-  m->precision = precision;
-  if (precision == TL_FP32_ELEM) {     // float32 PCG iteration: the row-contiguous product, 8 lanes per node
-    m->tune.spmv_group = 8;
-    m->tune.spmv_row = 1;
-  }
-  m->nn = nn;
-  m->ne = ne;
-  // ---- materials ----------------------------------------------------------
-  for (int k = 0; k < nmat; ++k) {
-    const tl_material& t = mats[k];
-    MaterialDev md{};
-    md.kind = t.kind;
-    if (t.kind != TL_SVK && t.kind != TL_MOONEY_RIVLIN) {
-      free_mesh(m);
-      return TL_ERR_INVALID_ARG;
-    }
-    md.lam = t.E * t.nu / ((1.0 + t.nu) * (1.0 - 2.0 * t.nu));
-    md.mu = t.E / (2.0 * (1.0 + t.nu));
-    md.C10 = t.C10;
-    md.C01 = t.C01;
-    md.kappa = t.kappa;
-    md.eta = t.eta_d;
-    md.lam_d = t.lambda_d;
-    md.kv = (t.eta_d != 0.0 || t.lambda_d != 0.0) ? 1 : 0;
-    md.rho = t.rho0;
-    m->mats.push_back(md);
+  if (!add_materials(m, mats, nmat)) {
+    free_mesh(m);
+    return TL_ERR_INVALID_ARG;
   }
   // ---- validate connectivity and geometry; element order by material ------
   std::vector<std::vector<int64_t>> by_mat(nmat);
@@ -227,75 +335,71 @@ tl_status tl_mesh_create(const double* X, int64_t nn, const int32_t* conn, int64
     }
     by_mat[mk].push_back(e);
   }
-  // internal order: material segments, each padded to a multiple of kTile
-  std::vector<int32_t> h_conn, h_user;
-  std::vector<double> h_geo64;
-  int64_t pos = 0;
-  for (int k = 0; k < nmat; ++k) {
-    if (by_mat[k].empty()) continue;
-    Segment sg;
-    sg.begin = pos;
-    sg.end = pos + (int64_t)by_mat[k].size();
-    const int64_t padded = ((int64_t)by_mat[k].size() + kTile - 1) / kTile * kTile;
-    sg.padded_end = pos + padded;
-    sg.mat = k;
-    for (int64_t i = 0; i < padded; ++i) {
-      if (i < (int64_t)by_mat[k].size()) {
-        const int64_t e = by_mat[k][i];
-        h_conn.insert(h_conn.end(), conn + 10 * e, conn + 10 * e + 10);
-        h_user.push_back((int32_t)e);
-        h_geo64.insert(h_geo64.end(), &geo_user[16 * e], &geo_user[16 * e] + 16);
-      } else {
-        h_conn.insert(h_conn.end(), 10, 0);
-        h_user.push_back(-1);
-        h_geo64.insert(h_geo64.end(), 16, 0.0);
+  m->nen = 10;
+  tl_status us = upload_mesh(m, nmat, by_mat, conn, 10, geo_user, X);
+  if (us != TL_OK) return us;
+  *out = m;
+  return TL_OK;
+}
+
+tl_status tl_mesh_create_ancf(int32_t kind, const double* E0, int64_t ncoef, const int32_t* conn, int64_t ne,
+                              const double* dims, const tl_material* mats, int32_t nmat,
+                              const int32_t* mat_of_elem, int32_t precision, void* stream, tl_mesh** out) {
+  if (!out) return TL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!E0 || !conn || !dims || !mats || ncoef <= 0 || ne < 0 || nmat < 1) return TL_ERR_INVALID_ARG;
+  if (kind != TL_ELEM_ANCF3243 && kind != TL_ELEM_ANCF3443) return TL_ERR_INVALID_ARG;
+  if (precision != TL_FP64 && precision != TL_FP32_ELEM) return TL_ERR_INVALID_ARG;
+  if (ncoef >= (int64_t)1 << 29) return TL_ERR_OVERFLOW;
+  g_create_error.clear();
+  if (precision != TL_FP64) {
+    g_create_error = "ANCF elements run in float64 only";
+    return TL_ERR_UNSUPPORTED;
+  }
+  const int nen = kind == TL_ELEM_ANCF3243 ? 8 : 16;
+  tl_mesh* m = new_mesh(stream, precision, ncoef, ne);
+  if (!m) return TL_ERR_OOM;
+  m->etype = kind;
+  m->nen = nen;
+  if (!add_materials(m, mats, nmat)) {
+    free_mesh(m);
+    return TL_ERR_INVALID_ARG;
+  }
+  std::vector<std::vector<int64_t>> by_mat(nmat);
+  std::vector<double> geo_user(16 * (size_t)ne, 0.0);
+  for (int64_t e = 0; e < ne; ++e) {
+    const int32_t* c = conn + (int64_t)nen * e;
+    for (int a = 0; a < nen; ++a)
+      if (c[a] < 0 || c[a] >= ncoef) {
+        g_create_error = "element " + std::to_string(e) + " references a coefficient out of range";
+        free_mesh(m);
+        return TL_ERR_INVALID_ARG;
       }
+    const double* dm = dims + 3 * e;
+    if (!(dm[0] > 0.0 && dm[1] > 0.0 && dm[2] > 0.0 && std::isfinite(dm[0] + dm[1] + dm[2]))) {
+      g_create_error = "element " + std::to_string(e) + " has non-positive dimensions";
+      free_mesh(m);
+      return TL_ERR_INVALID_ARG;
     }
-    pos += padded;
-    m->segs.push_back(sg);
-  }
-  m->ne_pad = pos;
-  const int64_t ne_pad = std::max<int64_t>(pos, 1);
-  std::vector<float> h_geo32(h_geo64.begin(), h_geo64.end());
-  h_conn.resize(10 * ne_pad, 0);
-  h_user.resize(ne_pad, -1);
-  h_geo64.resize(16 * ne_pad, 0.0);
-  h_geo32.resize(16 * ne_pad, 0.0f);
-  tl_status st = TL_OK;
-#define TRYC(call)                        \
-  do {                                    \
-    cudaError_t _e = (call);              \
-    if (_e != cudaSuccess) {              \
-      st = cuda_fail(m, _e, #call);       \
-      free_mesh(m);                       \
-      return st;                          \
-    }                                     \
-  } while (0)
-  TRYC(cudaMalloc(&m->d_conn, sizeof(int32_t) * 10 * ne_pad));
-  TRYC(cudaMalloc(&m->d_user_of, sizeof(int32_t) * ne_pad));
-  TRYC(cudaMalloc(&m->d_geo64, sizeof(double) * 16 * ne_pad));
-  TRYC(cudaMalloc(&m->d_geo32, sizeof(float) * 16 * ne_pad));
-  TRYC(cudaMalloc(&m->d_X, sizeof(double) * 3 * nn));
-  TRYC(cudaMalloc(&m->d_flags, sizeof(uint32_t) * 4));
-  TRYC(cudaMalloc(&m->d_tile_counters, sizeof(int) * kTileCounters));
-  TRYC(cudaMemcpy(m->d_conn, h_conn.data(), sizeof(int32_t) * 10 * ne_pad, cudaMemcpyHostToDevice));
-  TRYC(cudaMemcpy(m->d_user_of, h_user.data(), sizeof(int32_t) * ne_pad, cudaMemcpyHostToDevice));
-  TRYC(cudaMemcpy(m->d_geo64, h_geo64.data(), sizeof(double) * 16 * ne_pad, cudaMemcpyHostToDevice));
-  TRYC(cudaMemcpy(m->d_geo32, h_geo32.data(), sizeof(float) * 16 * ne_pad, cudaMemcpyHostToDevice));
-  if (precision == TL_FP32_ELEM) {
-    // double-float copy (hi, lo float pairs) for the float64-class residual force
-    std::vector<float> h_geodf(32 * ne_pad);
-    for (int64_t i = 0; i < 16 * ne_pad; ++i) {
-      const float hi = (float)h_geo64[i];
-      h_geodf[2 * i] = hi;
-      h_geodf[2 * i + 1] = (float)(h_geo64[i] - (double)hi);
+    const bool ok = kind == TL_ELEM_ANCF3243 ? ancf_jacobians_positive<ancf::kBeam>(E0, c, dm)
+                                             : ancf_jacobians_positive<ancf::kShell>(E0, c, dm);
+    if (!ok) {
+      g_create_error = "element " + std::to_string(e) + " has a non-positive reference Jacobian";
+      free_mesh(m);
+      return TL_ERR_INVALID_ARG;
     }
-    TRYC(cudaMalloc(&m->d_geo_df, sizeof(float) * 32 * ne_pad));
-    TRYC(cudaMemcpy(m->d_geo_df, h_geodf.data(), sizeof(float) * 32 * ne_pad, cudaMemcpyHostToDevice));
+    geo_user[16 * e + 0] = dm[0];
+    geo_user[16 * e + 1] = dm[1];
+    geo_user[16 * e + 2] = dm[2];
+    const int mk = mat_of_elem ? mat_of_elem[e] : 0;
+    if (mk < 0 || mk >= nmat) {
+      free_mesh(m);
+      return TL_ERR_INVALID_ARG;
+    }
+    by_mat[mk].push_back(e);
   }
-  TRYC(cudaMemcpy(m->d_X, X, sizeof(double) * 3 * nn, cudaMemcpyHostToDevice));
-  TRYC(cudaMemset(m->d_flags, 0, sizeof(uint32_t) * 4));
-#undef TRYC
+  tl_status us = upload_mesh(m, nmat, by_mat, conn, nen, geo_user, E0);
+  if (us != TL_OK) return us;
   *out = m;
   return TL_OK;
 }
@@ -481,6 +585,8 @@ tl_status tl_mesh_info_get(const tl_mesh* m, tl_mesh_info* out) {
   out->precision = m->precision;
   out->nmat = (int32_t)m->mats.size();
   out->ncon = m->ncon;
+  out->element_kind = m->etype;
+  out->nen = m->nen;
   return TL_OK;
 }
 

@@ -73,15 +73,18 @@ struct tl_mesh {
   int num_sms = 1;                // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   int precision = TL_FP64;
+  int etype = TL_ELEM_T10;        // tl_element_kind
+  int nen = 10;                   // nodes (T10) or coefficients (ANCF) per element
   int64_t nn = 0, ne = 0, ne_pad = 0;
   std::vector<tl::MaterialDev> mats;
   std::vector<tl::Segment> segs;
   std::string last_error;
 
   // internal element order (segments by material, padded)
-  int32_t* d_conn = nullptr;      // ne_pad * 10
+  int32_t* d_conn = nullptr;      // ne_pad * nen
   int32_t* d_user_of = nullptr;   // ne_pad: user element id, -1 for padding
-  double* d_geo64 = nullptr;      // ne_pad * 16: grad L (4x3), V, 0,0,0
+  double* d_geo64 = nullptr;      // ne_pad * 16: T10 grad L (4x3), V, 0,0,0; ANCF L, W, H, 0...
+  double* d_ancf_me = nullptr;    // ANCF: ne_pad * nen(nen+1)/2 exact element mass (upper triangle)
   float* d_geo32 = nullptr;       // same in float32 (TL_FP32_ELEM)
   float* d_geo_df = nullptr;      // same as double-float pairs (TL_FP32_ELEM: float64-class residual force)
   double* d_X = nullptr;          // 3 nn
@@ -93,7 +96,7 @@ struct tl_mesh {
   int32_t* d_node_col = nullptr;  // nnz_node
   int32_t* d_row_ptr = nullptr;   // 3 nn + 1
   int32_t* d_col = nullptr;       // nnz
-  uint8_t* d_blk = nullptr;       // ne_pad * 100: k of conn[b] in adj(conn[a])
+  uint8_t* d_blk = nullptr;       // ne_pad * nen^2: k of conn[b] in adj(conn[a])
   double* d_mass = nullptr;       // nnz_node consistent mass M_IJ
   double* d_mrow = nullptr;       // nn row sums of M
   int64_t nfixed = 0;
@@ -182,6 +185,11 @@ tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv,
 tl_status launch_tangent(tl_mesh* m, const double* q_n, const double* v, double h,
                          double alpha, double beta, double mass_scale, bool do_force,
                          double* f, void* values, void* K_elem);
+
+// ANCF elements (tl_ancf.cu): exact mass, and the element passes
+tl_status ancf_build_mass(tl_mesh* m);
+tl_status ancf_launch(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
+                      double mass_scale, bool do_force, bool do_tangent, double* f, void* values, void* K_elem);
 
 // pattern kernels (tl_pattern.cu)
 tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed);

@@ -24,18 +24,18 @@ namespace {
 constexpr int kCap = 2048;          // max candidate neighbours of one node
 constexpr int kWarpsPerBlock = 4;
 
-__global__ void count_incidence(const int32_t* conn, const int32_t* user_of, int64_t ne_pad, int32_t* cnt) {
+__global__ void count_incidence(const int32_t* conn, const int32_t* user_of, int64_t ne_pad, int nen, int32_t* cnt) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ne_pad * 10) return;
-  if (user_of[t / 10] < 0) return;
+  if (t >= ne_pad * nen) return;
+  if (user_of[t / nen] < 0) return;
   atomicAdd(&cnt[conn[t]], 1);
 }
 
-__global__ void fill_incidence(const int32_t* conn, const int32_t* user_of, int64_t ne_pad, const int32_t* ptr,
-                               int32_t* cursor, int32_t* list) {
+__global__ void fill_incidence(const int32_t* conn, const int32_t* user_of, int64_t ne_pad, int nen,
+                               const int32_t* ptr, int32_t* cursor, int32_t* list) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ne_pad * 10) return;
-  const int64_t e = t / 10;
+  if (t >= ne_pad * nen) return;
+  const int64_t e = t / nen;
   if (user_of[e] < 0) return;
   const int node = conn[t];
   const int slot = atomicAdd(&cursor[node], 1);
@@ -69,16 +69,16 @@ __device__ void warp_bitonic_sort(int32_t* buf, int n) {
 // WRITE = false: deg[node] = number of distinct neighbours.
 // WRITE = true : node_col[node_ptr[node] + k] = k-th neighbour (ascending).
 template <bool WRITE>
-__global__ void node_neighbours(const int32_t* conn, const int32_t* inc_ptr, const int32_t* inc_list, int64_t nn,
-                                int32_t* deg, const int32_t* node_ptr, int32_t* node_col, uint32_t* flags,
-                                const int32_t* ex_ptr, const int32_t* ex_col) {
+__global__ void node_neighbours(const int32_t* conn, int nen, const int32_t* inc_ptr, const int32_t* inc_list,
+                                int64_t nn, int32_t* deg, const int32_t* node_ptr, int32_t* node_col,
+                                uint32_t* flags, const int32_t* ex_ptr, const int32_t* ex_col) {
   __shared__ int32_t sbuf[kWarpsPerBlock][kCap];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t node = blockIdx.x * (int64_t)kWarpsPerBlock + warp;
   if (node >= nn) return;
   int32_t* buf = sbuf[warp];
   const int i0 = inc_ptr[node], i1 = inc_ptr[node + 1];
-  const int ne_cand = (i1 - i0) * 10;
+  const int ne_cand = (i1 - i0) * nen;
   const int x0 = ex_ptr ? ex_ptr[node] : 0, x1 = ex_ptr ? ex_ptr[node + 1] : 0;
   const int ncand = ne_cand + (x1 - x0);
   if (ncand > kCap) {
@@ -90,7 +90,7 @@ __global__ void node_neighbours(const int32_t* conn, const int32_t* inc_ptr, con
   while (n < ncand) n <<= 1;
   for (int t = lane; t < n; t += 32) {
     int32_t val = INT_MAX;
-    if (t < ne_cand) val = conn[(int64_t)inc_list[i0 + t / 10] * 10 + t % 10];
+    if (t < ne_cand) val = conn[(int64_t)inc_list[i0 + t / nen] * nen + t % nen];
     else if (t < ncand) val = ex_col[x0 + t - ne_cand];
     buf[t] = val;
   }
@@ -139,14 +139,15 @@ __device__ __forceinline__ int find_in_row(const int32_t* node_col, int p0, int 
   return -1;
 }
 
-// blk[e][a*10+b] = position of conn[e][b] in the adjacency of conn[e][a].
-__global__ void slot_blocks(const int32_t* conn, int64_t ne_pad, const int32_t* node_ptr, const int32_t* node_col,
-                            uint8_t* blk, uint32_t* flags) {
+// blk[e][a*nen+b] = position of conn[e][b] in the adjacency of conn[e][a].
+__global__ void slot_blocks(const int32_t* conn, int64_t ne_pad, int nen, const int32_t* node_ptr,
+                            const int32_t* node_col, uint8_t* blk, uint32_t* flags) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ne_pad * 100) return;
-  const int64_t e = t / 100;
-  const int ab = (int)(t % 100), a = ab / 10, b = ab % 10;
-  const int I = conn[e * 10 + a], J = conn[e * 10 + b];
+  const int nen2 = nen * nen;
+  if (t >= ne_pad * nen2) return;
+  const int64_t e = t / nen2;
+  const int ab = (int)(t % nen2), a = ab / nen, b = ab % nen;
+  const int I = conn[e * nen + a], J = conn[e * nen + b];
   const int k = find_in_row(node_col, node_ptr[I], node_ptr[I + 1], J);
   if (k < 0 || k > 255) {
     atomicOr(flags, kFlagBadIndex);
@@ -163,8 +164,8 @@ __constant__ double c_mass420_d[10][10] = {
     {-4, -6, -4, -6, 16, 16, 32, 16, 8, 16},  {-4, -6, -6, -4, 16, 8, 16, 32, 16, 16},
     {-6, -4, -6, -4, 16, 16, 8, 16, 32, 16},  {-6, -6, -4, -4, 8, 16, 16, 16, 16, 32}};
 
-// Consistent mass M_IJ (node level, same pattern as the adjacency) and its
-// row sums, for the real elements of one material segment.
+// Consistent mass M_IJ of T10 elements (node level, same pattern as the
+// adjacency) and its row sums, for the real elements of one material segment.
 __global__ void assemble_mass(const int32_t* conn, const double* geo64, const uint8_t* blk, const int32_t* node_ptr,
                               int64_t e_begin, int64_t e_end, double rho, double* mass, double* mrow) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -188,18 +189,19 @@ __global__ void fixed_diag(const int32_t* fixed, int64_t nfixed, const int32_t* 
   for (int d = 0; d < 3; ++d) diag[3 * j + d] = 9 * p0 + 3 * deg * d + 3 * k + d;
 }
 
-__global__ void expand_slots(const int32_t* conn, const uint8_t* blk, const int32_t* node_ptr,
+__global__ void expand_slots(const int32_t* conn, int nen, const uint8_t* blk, const int32_t* node_ptr,
                              const int32_t* user_of, int64_t ne_pad, int32_t* slot_map) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ne_pad * 900) return;
-  const int64_t e = t / 900;
+  const int nd = 3 * nen, nd2 = nd * nd;
+  if (t >= ne_pad * nd2) return;
+  const int64_t e = t / nd2;
   const int ue = user_of[e];
   if (ue < 0) return;
-  const int rs = (int)(t % 900), r = rs / 30, s = rs % 30;
+  const int rs = (int)(t % nd2), r = rs / nd, s = rs % nd;
   const int a = r / 3, i = r % 3, b = s / 3, k = s % 3;
-  const int I = conn[e * 10 + a];
+  const int I = conn[e * nen + a];
   const int p0 = node_ptr[I], deg = node_ptr[I + 1] - p0;
-  slot_map[(int64_t)ue * 900 + rs] = 9 * p0 + 3 * deg * i + 3 * blk[e * 100 + a * 10 + b] + k;
+  slot_map[(int64_t)ue * nd2 + rs] = 9 * p0 + 3 * deg * i + 3 * blk[e * nen * nen + a * nen + b] + k;
 }
 
 inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -245,7 +247,8 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
     }                                               \
   } while (0)
 
-  const int64_t ninc = m->ne * 10;
+  const int nen = m->nen;
+  const int64_t ninc = m->ne * nen;
   TRY(cudaMalloc(&d_cnt, sizeof(int32_t) * (nn + 1)));
   TRY(cudaMalloc(&d_inc_ptr, sizeof(int32_t) * (nn + 1)));
   TRY(cudaMalloc(&d_cursor, sizeof(int32_t) * (nn + 1)));
@@ -254,14 +257,14 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * (nn + 1), s));
   TRY(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * (nn + 1), s));
   TRY(cudaMemsetAsync(m->d_flags, 0, sizeof(uint32_t), s));
-  count_incidence<<<nblocks(ne_pad * 10, 256), 256, 0, s>>>(m->d_conn, m->d_user_of, ne_pad, d_cnt);
+  count_incidence<<<nblocks(ne_pad * nen, 256), 256, 0, s>>>(m->d_conn, m->d_user_of, ne_pad, nen, d_cnt);
   TRY(cudaGetLastError());
   // exclusive scan of (nn + 1) counts (the last count is 0) -> pointers
   TRY(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_cnt, d_inc_ptr, (int)(nn + 1), s));
   TRY(cudaMalloc(&d_tmp, tmp_bytes));
   TRY(cub::DeviceScan::ExclusiveSum(d_tmp, tmp_bytes, d_cnt, d_inc_ptr, (int)(nn + 1), s));
-  fill_incidence<<<nblocks(ne_pad * 10, 256), 256, 0, s>>>(m->d_conn, m->d_user_of, ne_pad, d_inc_ptr, d_cursor,
-                                                           d_inc);
+  fill_incidence<<<nblocks(ne_pad * nen, 256), 256, 0, s>>>(m->d_conn, m->d_user_of, ne_pad, nen, d_inc_ptr,
+                                                            d_cursor, d_inc);
   TRY(cudaGetLastError());
   // ---- neighbours: count, scan, write ------------------------------------
   if (m->ncon > 0) {   // node pairs coupled by general constraint rows (the Sec. 4.2 fill)
@@ -274,7 +277,7 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   }
   TRY(cudaMemsetAsync(d_deg, 0, sizeof(int32_t) * (nn + 1), s));
   node_neighbours<false><<<nblocks(nn, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
-      m->d_conn, d_inc_ptr, d_inc, nn, d_deg, nullptr, nullptr, m->d_flags, d_ex_ptr, d_ex_col);
+      m->d_conn, nen, d_inc_ptr, d_inc, nn, d_deg, nullptr, nullptr, m->d_flags, d_ex_ptr, d_ex_col);
   TRY(cudaGetLastError());
   TRY(cudaMalloc(&m->d_node_ptr, sizeof(int32_t) * (nn + 1)));
   size_t tmp2 = 0;
@@ -293,8 +296,8 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   TRY(cudaStreamSynchronize(s));
   if (flags & kFlagBadIndex) {
     cleanup();
-    return fail(m, TL_ERR_UNSUPPORTED, "a node has more than 2,048 neighbour candidates (10 per incident element "
-                                       "plus its constraint couplings)");
+    return fail(m, TL_ERR_UNSUPPORTED, "a node has more than 2,048 neighbour candidates (nen per incident "
+                                       "element plus its constraint couplings)");
   }
   const int64_t nnz = 9 * (int64_t)nnz_node;
   if (nnz >= (int64_t)INT_MAX) {
@@ -305,7 +308,7 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   m->nnz = nnz;
   TRY(cudaMalloc(&m->d_node_col, sizeof(int32_t) * std::max<int64_t>(nnz_node, 1)));
   node_neighbours<true><<<nblocks(nn, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
-      m->d_conn, d_inc_ptr, d_inc, nn, d_deg, m->d_node_ptr, m->d_node_col, m->d_flags, d_ex_ptr, d_ex_col);
+      m->d_conn, nen, d_inc_ptr, d_inc, nn, d_deg, m->d_node_ptr, m->d_node_col, m->d_flags, d_ex_ptr, d_ex_col);
   TRY(cudaGetLastError());
   // ---- DOF pattern --------------------------------------------------------
   TRY(cudaMalloc(&m->d_row_ptr, sizeof(int32_t) * (3 * nn + 1)));
@@ -313,21 +316,29 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
   dof_pattern<<<nblocks(nn, 8), 256, 0, s>>>(m->d_node_ptr, m->d_node_col, nn, m->d_row_ptr, m->d_col);
   TRY(cudaGetLastError());
   // ---- slot blocks -------------------------------------------------------
-  TRY(cudaMalloc(&m->d_blk, 100 * ne_pad));
-  slot_blocks<<<nblocks(ne_pad * 100, 256), 256, 0, s>>>(m->d_conn, ne_pad, m->d_node_ptr, m->d_node_col, m->d_blk,
-                                                        m->d_flags);
+  TRY(cudaMalloc(&m->d_blk, (size_t)nen * nen * std::max<int64_t>(ne_pad, 1)));
+  slot_blocks<<<nblocks(ne_pad * nen * nen, 256), 256, 0, s>>>(m->d_conn, ne_pad, nen, m->d_node_ptr,
+                                                              m->d_node_col, m->d_blk, m->d_flags);
   TRY(cudaGetLastError());
   // ---- mass --------------------------------------------------------------
   TRY(cudaMalloc(&m->d_mass, sizeof(double) * std::max<int64_t>(nnz_node, 1)));
   TRY(cudaMalloc(&m->d_mrow, sizeof(double) * nn));
   TRY(cudaMemsetAsync(m->d_mass, 0, sizeof(double) * std::max<int64_t>(nnz_node, 1), s));
   TRY(cudaMemsetAsync(m->d_mrow, 0, sizeof(double) * nn, s));
-  for (const Segment& sg : m->segs) {
-    const int64_t cnt = (sg.end - sg.begin) * 100;
-    if (cnt == 0) continue;
-    assemble_mass<<<nblocks(cnt, 256), 256, 0, s>>>(m->d_conn, m->d_geo64, m->d_blk, m->d_node_ptr, sg.begin,
-                                                   sg.end, m->mats[sg.mat].rho, m->d_mass, m->d_mrow);
-    TRY(cudaGetLastError());
+  if (m->etype == TL_ELEM_T10) {
+    for (const Segment& sg : m->segs) {
+      const int64_t cnt = (sg.end - sg.begin) * 100;
+      if (cnt == 0) continue;
+      assemble_mass<<<nblocks(cnt, 256), 256, 0, s>>>(m->d_conn, m->d_geo64, m->d_blk, m->d_node_ptr, sg.begin,
+                                                     sg.end, m->mats[sg.mat].rho, m->d_mass, m->d_mrow);
+      TRY(cudaGetLastError());
+    }
+  } else {
+    const tl_status ms = ancf_build_mass(m);    // exact mass, gravity weights, element mass table
+    if (ms != TL_OK) {
+      cleanup();
+      return ms;
+    }
   }
   {
     const tl_status ms = mass_split_build(m, s);     // float32 pairs of the mass (double-float residual)
@@ -358,8 +369,9 @@ tl_status build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixed) 
 }
 
 tl_status expand_slot_map(const tl_mesh* m, int32_t* slot_map, cudaStream_t s) {
-  expand_slots<<<nblocks(m->ne_pad * 900, 256), 256, 0, s>>>(m->d_conn, m->d_blk, m->d_node_ptr, m->d_user_of,
-                                                            m->ne_pad, slot_map);
+  const int nd = 3 * m->nen;
+  expand_slots<<<nblocks(m->ne_pad * nd * nd, 256), 256, 0, s>>>(m->d_conn, m->nen, m->d_blk, m->d_node_ptr,
+                                                                m->d_user_of, m->ne_pad, slot_map);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TL_OK : TL_ERR_CUDA;
 }

@@ -459,10 +459,10 @@ def ancf_perturbation(mesh, q, frac, rng):
 
 def workload_ancf_beam(ne=10, seed=1000 + 6):
     """ANCF3243 beam (L = 0.2, W = H = 0.1 per element; SVK 7e8 / 0.33 / 2700),
-    bent to a curvature of 0.5 / m and perturbed by 1%; v ~ N(0, 0.01)."""
+    bent to a curvature of 0.5 / m and perturbed by 0.1%; v ~ N(0, 0.01)."""
     rng = np.random.default_rng(seed)
     m = beam_ancf3243(ne)
-    q = ancf_perturbation(m, ancf_bend(m, 0.5), 0.01, rng)
+    q = ancf_perturbation(m, ancf_bend(m, 0.5), 0.001, rng)
     v = rng.normal(0.0, 0.01, size=q.shape)
     v[m.fixed_nodes] = 0.0
     return dict(name=f"ANCF3243 beam, {ne:,} elements", mesh=m, q_n=q, v=v, material=dict(SVK_7E8), h=1e-3)
@@ -470,10 +470,10 @@ def workload_ancf_beam(ne=10, seed=1000 + 6):
 
 def workload_ancf_shell(nx=4, ny=3, seed=1000 + 7):
     """ANCF3443 shell 4 x 2 x 0.1 m (SVK 7e8 / 0.33 / 2700) on an nx x ny grid,
-    bent to a curvature of 0.25 / m about y and perturbed by 1%; v ~ N(0, 0.01)."""
+    bent to a curvature of 0.25 / m about y and perturbed by 0.1%; v ~ N(0, 0.01)."""
     rng = np.random.default_rng(seed)
     m = shell_ancf3443(nx, ny)
-    q = ancf_perturbation(m, ancf_bend(m, 0.25), 0.01, rng)
+    q = ancf_perturbation(m, ancf_bend(m, 0.25), 0.001, rng)
     v = rng.normal(0.0, 0.01, size=q.shape)
     v[m.fixed_nodes] = 0.0
     return dict(name=f"ANCF3443 shell, {nx}x{ny} = {nx * ny:,} elements", mesh=m, q_n=q, v=v,

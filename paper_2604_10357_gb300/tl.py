@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtl_gb300.so")
 
 TL_FP64, TL_FP32_ELEM = 0, 1
+TL_ELEM_T10, TL_ELEM_ANCF3243, TL_ELEM_ANCF3443 = 0, 1, 2
 TL_SVK, TL_MOONEY_RIVLIN = 0, 1
 
 STATUS = {0: "TL_OK", 1: "TL_ERR_INVALID_ARG", 2: "TL_ERR_OOM", 3: "TL_ERR_CUDA", 4: "TL_ERR_INVERTED",
@@ -73,7 +74,7 @@ class tl_timing(C.Structure):
 class tl_mesh_info(C.Structure):
     _fields_ = [("nn", C.c_int64), ("ne", C.c_int64), ("ndof", C.c_int64), ("nnz", C.c_int64),
                 ("nnz_node", C.c_int64), ("nfixed", C.c_int64), ("precision", C.c_int32),
-                ("nmat", C.c_int32), ("ncon", C.c_int64)]
+                ("nmat", C.c_int32), ("ncon", C.c_int64), ("element_kind", C.c_int32), ("nen", C.c_int32)]
 
 
 class tl_tune_result(C.Structure):
@@ -91,6 +92,8 @@ class tl_tune_result(C.Structure):
 _P = C.c_void_p
 SIGNATURES = {
     "tl_mesh_create": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P, C.c_int32, _P, _P]),
+    "tl_mesh_create_ancf": (C.c_int, [C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, _P, C.c_int32, _P, C.c_int32,
+                                      _P, _P]),
     "tl_build_pattern": (C.c_int, [_P, _P, C.c_int64, _P]),
     "tl_get_pattern": (C.c_int, [_P, _P, _P, _P]),
     "tl_eval_force": (C.c_int, [_P, _P, _P, C.c_double, _P]),
@@ -257,8 +260,44 @@ class Mesh:
                                 C.c_void_p(self.stream.cuda_stream), C.byref(h))
         if st != 0:
             raise TLError(st, lib.tl_last_error(None).decode())
+        self._finish(h, X.shape[0], conn.shape[0], 10, precision)
+
+    @classmethod
+    def ancf(cls, kind, E0, conn, dims, materials, mat_of_elem=None, precision=TL_FP64, stream=None):
+        """tl_mesh_create_ancf: kind TL_ELEM_ANCF3243 / TL_ELEM_ANCF3443 (or
+        "ancf3243" / "ancf3443"); E0 (ncoef, 3) reference coefficients, conn
+        (ne, 8 | 16) coefficient ids, dims (ne, 3) element L, W, H.  Every
+        "node" of the other calls is then a coefficient."""
+        import torch
+        if isinstance(kind, str):
+            kind = {"ancf3243": TL_ELEM_ANCF3243, "ancf3443": TL_ELEM_ANCF3443}[kind]
+        nen = 8 if kind == TL_ELEM_ANCF3243 else 16
+        self = cls.__new__(cls)
+        self._torch = torch
+        lib = load_library()
+        self.lib = lib
+        E0 = np.ascontiguousarray(E0, dtype=np.float64).reshape(-1, 3)
+        conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, nen)
+        dims = np.ascontiguousarray(dims, dtype=np.float64).reshape(-1, 3)
+        if isinstance(materials, dict):
+            materials = [materials]
+        mats = (tl_material * len(materials))(*[material(**m) for m in materials])
+        moe = None if mat_of_elem is None else np.ascontiguousarray(mat_of_elem, dtype=np.int32)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = lib.tl_mesh_create_ancf(int(kind), E0.ctypes.data_as(_P), E0.shape[0], conn.ctypes.data_as(_P),
+                                     conn.shape[0], dims.ctypes.data_as(_P), C.cast(mats, _P), len(materials),
+                                     None if moe is None else moe.ctypes.data_as(_P), int(precision),
+                                     C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise TLError(st, lib.tl_last_error(None).decode())
+        self._finish(h, E0.shape[0], conn.shape[0], nen, precision)
+        return self
+
+    def _finish(self, h, nn, ne, nen, precision):
+        torch = self._torch
         self.h = h
-        self.nn, self.ne = X.shape[0], conn.shape[0]
+        self.nn, self.ne, self.nen = nn, ne, nen
         self.ndof = 3 * self.nn
         self.precision = precision
         self.vdtype = torch.float32 if precision == TL_FP32_ELEM else torch.float64
@@ -306,7 +345,7 @@ class Mesh:
         torch = self._torch
         row_ptr = torch.empty(self.ndof + 1, dtype=torch.int32, device="cuda")
         col = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
-        slot = torch.empty(self.ne * 900, dtype=torch.int32, device="cuda") if with_slot_map else None
+        slot = torch.empty(self.ne * (3 * self.nen) ** 2, dtype=torch.int32, device="cuda") if with_slot_map else None
         self._check(self.lib.tl_get_pattern(self.h, _ptr(row_ptr), _ptr(col), _ptr(slot)))
         return row_ptr, col, slot
 
@@ -318,7 +357,7 @@ class Mesh:
 
     def eval_tangent(self, q_n, v, h, alpha=1.0, beta=0.0, out=None):
         torch = self._torch
-        out = torch.empty(self.ne * 900, dtype=self.vdtype, device="cuda") if out is None else out
+        out = torch.empty(self.ne * (3 * self.nen) ** 2, dtype=self.vdtype, device="cuda") if out is None else out
         self._check(self.lib.tl_eval_tangent(self.h, _ptr(q_n), _ptr(v), float(h), float(alpha),
                                              float(beta), _ptr(out)))
         return out
