@@ -562,6 +562,139 @@ def run_constraints(args):
     return out
 
 
+# Algorithmic float64 flops per element of the ANCF passes (SVK), counted from
+# the formulas the kernels evaluate (FMA = 2), n shape functions, per point:
+# shape derivatives 10n, J0 18n, its inverse 41, grad S 18n, u 6n, H 18n,
+# F / E / J - 1 / S / B 141, S n_a and F n_a 30n, w J0 1 = 100n + 183
+# (force pass: 85n + 147 without F n_a and B); force sum 21 per (a, point);
+# tangent 77 per block pair (a <= b) and point: n_a.n_b 5, n_a.S n_b 5,
+# weights 4, nine entries of c1 g_a g_b^T + c2 (g_b g_a^T + (n_a.n_b) B) 60,
+# diagonal 3; mass on the diagonal 3 per pair.
+ANCF_SHAPE = {"ancf3243": (8, 12), "ancf3443": (16, 48)}     # shape functions, points
+
+
+def ancf_flops_per_elem(kind, tangent=True):
+    n, nq = ANCF_SHAPE[kind]
+    npair = n * (n + 1) // 2
+    force = 21 * n * nq
+    if not tangent:
+        return nq * (85 * n + 147) + force
+    return nq * (100 * n + 183) + force + npair * nq * 77 + 3 * npair
+
+
+FP64_FMA_PER_SM_CLK = 2
+
+
+def fp64_alu_peak_tflops():
+    """152 SMs x 2 float64 FMA per clock x 2 flop x 2.07 GHz (GB300's float64
+    rate: its nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz)."""
+    return SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def run_ancf(args):
+    """ANCF3243 beam and ANCF3443 shell at the largest resolutions of the
+    paper's element-type scaling tables (500,000 beam elements of 0.2 x 0.1 x
+    0.1 m; a 200 x 200 shell of 4 x 2 x 0.1 m), SVK 7e8 / 0.33 / 2700, bent and
+    perturbed by 0.1%: the Hessian assembly pass (values zeroed, fused
+    internal force + tangent + exact mass + clamp penalty) and the force pass,
+    CUDA events over 10 passes after 3 warm-ups, the element kernel alone from
+    the library's event timers, against the float64 ALU roofline.  Then one
+    Newton steps from rest under the paper's tip loads (beam: F_z = 5,000 N at
+    the free end; shell: -500 N spread over the free edge) at the RES0
+    resolution, vendor direct solver and the captured PCG graph, inner stop
+    max(1e-4, 1e-8 relative), the paper's eps_in at RES0."""
+    import torch
+
+    from paper_2604_10357_gb300 import inputs, tl
+    out = {"roofline_peak_tflops": fp64_alu_peak_tflops(), "peak_kind": "float64 ALU, derived"}
+    mat = dict(inputs.SVK_7E8)
+    for kind in ("ancf3243", "ancf3443"):
+        rng = np.random.default_rng(1000 + 8)
+        if kind == "ancf3243":
+            m, h, curv = inputs.beam_ancf3243(max(8, int(round(500_000 * args.ancf_scale)))), 1e-3, 1e-5
+        else:
+            ns = max(2, int(round(200 * args.ancf_scale ** 0.5)))
+            m, h, curv = inputs.shell_ancf3443(ns, ns), 5e-4, 0.25
+        q = inputs.ancf_perturbation(m, inputs.ancf_bend(m, curv), 0.001, rng)
+        v = rng.normal(0.0, 0.01, size=q.shape)
+        v[m.fixed_nodes] = 0.0
+        g = tl.Mesh.ancf(kind, m.E0, m.conn, m.dims, [mat])
+        g.build_pattern(m.fixed_nodes)
+        qd = torch.as_tensor(q.reshape(-1), device="cuda")
+        vd = torch.as_tensor(v.reshape(-1), device="cuda")
+        vals = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+        f = torch.empty(3 * m.nn, dtype=torch.float64, device="cuda")
+        res = {}
+        for tag, fn in (("assembly", lambda: g.assemble_hessian(qd, vd, h, 1e12, values=vals, f_int=f)),
+                        ("force", lambda: g.eval_force(qd, vd, h, out=f))):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            g.timing_read()
+            g.timing_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            tim = g.timing_read()
+            g.timing_enable(False)
+            ms = e0.elapsed_time(e1) / 10
+            kms = tim["ms_element"] / max(1, tim["n_element"])
+            fl = ancf_flops_per_elem(kind, tag == "assembly")
+            res[tag] = {"ms": ms, "elems_per_s": m.ne / ms * 1e3, "kernel_ms": kms,
+                        "flops_per_elem": fl, "achieved_tflops": fl * m.ne / (kms * 1e-3) / 1e12,
+                        "frac": fl * m.ne / (kms * 1e-3) / 1e12 / fp64_alu_peak_tflops()}
+        g.sync()
+        res.update(elements=int(m.ne), coefficients=int(m.nn), dofs=int(3 * m.nn), nnz=int(g.nnz))
+        g.close()
+        if args.ancf_no_newton:
+            out[kind] = res
+            continue
+        # Newton steps from rest under the tip load at the RES0 resolution of
+        # the paper's tables, the vendor direct solver and the captured PCG graph
+        if kind == "ancf3243":
+            mn = inputs.beam_ancf3243(1_000)
+            fe = np.zeros_like(mn.E0)
+            fe[4 * (mn.nphys - 1), 2] = 5000.0
+            res_name, paper_rtf = "RES0 (1,000 elements)", 4.85
+        else:
+            mn = inputs.shell_ancf3443(10, 10)
+            fe = np.zeros_like(mn.E0)
+            edge = np.nonzero(np.isclose(mn.phys_x[:, 0], mn.phys_x[:, 0].max()))[0]
+            fe[4 * edge, 2] = -500.0 / len(edge)
+            res_name, paper_rtf = "RES0 (10 x 10)", 8.11
+        newton = {"resolution": res_name, "h_s": h, "paper_rtf_other_gpu": paper_rtf,
+                  "tol": "max(1e-4, 1e-8 g_ref), eps_out 1e-4 (the paper's eps_in / eps_out at RES0)",
+                  "note": "RTF = wall time / simulated time; the paper's stopping rule and GPU differ"}
+        for arm, solver, graph in (("direct", tl.TL_SOLVER_DIRECT, 0), ("pcg_graph", tl.TL_SOLVER_PCG, 1)):
+            gn = tl.Mesh.ancf(kind, mn.E0, mn.conn, mn.dims, [mat])
+            gn.build_pattern(mn.fixed_nodes)
+            p = tl.params(h=h, rtol=1e-8, atol=1e-4, eps_out=1e-4, linear_solver=solver, use_graph=graph)
+            qn = torch.as_tensor(mn.E0.reshape(-1), device="cuda")
+            vn = torch.zeros_like(qn)
+            fx = torch.as_tensor(fe.reshape(-1), device="cuda")
+            lam = torch.zeros(3 * len(mn.fixed_nodes), dtype=torch.float64, device="cuda")
+            steps, t_ms, iters, status = 10, [], [], []
+            for k in range(steps + 2):           # the first two steps include the solver / graph set-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                vv, qq, st = gn.newton_step(p, qn, vn, lam, f_ext=fx, raise_on_nonconvergence=False)
+                torch.cuda.synchronize()
+                if k >= 2:
+                    t_ms.append((time.perf_counter() - t0) * 1e3)
+                    iters.append(int(st["inner_iters"]))
+                    status.append(int(st["status"]))
+                qn, vn = qq.clone(), vv.clone()
+            gn.close()
+            newton[arm] = {"steps": steps, "ms_per_step": statistics.median(t_ms), "inner_iters": iters,
+                           "status": status, "rtf": statistics.median(t_ms) / (h * 1e3)}
+        res["newton"] = newton
+        out[kind] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -583,6 +716,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-constraints", action="store_true", help="skip the general-constraint cost measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-ancf", action="store_true", help="skip the ANCF beam / shell measurement")
+    ap.add_argument("--ancf-only", action="store_true", help="run only the ANCF measurement and print it")
+    ap.add_argument("--ancf-scale", type=float, default=1.0,
+                    help="element-count scale of the ANCF meshes (1.0 = 500,000 beam and 200 x 200 shell elements)")
+    ap.add_argument("--ancf-no-newton", action="store_true", help="skip the ANCF Newton steps")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -596,6 +734,10 @@ def main():
     if args.newton_only:
         if rank == 0:
             print(json.dumps(run_newton(args)), flush=True)
+        return
+    if args.ancf_only:
+        if rank == 0:
+            print(json.dumps(run_ancf(args)), flush=True)
         return
     if world > 1:
         import torch
@@ -612,6 +754,8 @@ def main():
             line["newton"] = run_newton(args)
         if not args.no_constraints and world == 1:
             line["constraints"] = run_constraints(args)
+        if not args.no_ancf and world == 1:
+            line["ancf"] = run_ancf(args)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

@@ -46,6 +46,7 @@ struct Cfg {
   static constexpr int NEN = Traits<ET>::NEN, NQP = Traits<ET>::NQP, NP = NEN * (NEN + 1) / 2;
   static constexpr int EPB = ET == kBeam ? 8 : 1;           // elements per CTA
   static constexpr int NT = ET == kBeam ? 288 : 160;        // >= EPB * NP pair threads
+  static constexpr int MINB = ET == kBeam ? 1 : 2;          // resident CTAs per SM the registers allow
 };
 
 // Per-point record in shared memory (doubles).
@@ -68,7 +69,7 @@ constexpr size_t smem_bytes() {
 }
 
 template <int ET, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
-__global__ void __launch_bounds__(Cfg<ET>::NT) elem_kernel(Args A) {
+__global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A) {
   constexpr int NEN = Cfg<ET>::NEN, NQP = Cfg<ET>::NQP, NP = Cfg<ET>::NP, EPB = Cfg<ET>::EPB, NT = Cfg<ET>::NT;
   constexpr bool MR = MAT == TL_MOONEY_RIVLIN;
   using RC = Rec<ET, DO_TANGENT, MR>;
