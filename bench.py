@@ -596,7 +596,8 @@ def run_ancf(args):
     paper's element-type scaling tables (500,000 beam elements of 0.2 x 0.1 x
     0.1 m; a 200 x 200 shell of 4 x 2 x 0.1 m), SVK 7e8 / 0.33 / 2700, bent and
     perturbed by 0.1%: the Hessian assembly pass (values zeroed, fused
-    internal force + tangent + exact mass + clamp penalty) and the force pass,
+    internal force + tangent + exact mass + clamp penalty) in float64 and in
+    the float32 element form, and the float64 force pass,
     CUDA events over 10 passes after 3 warm-ups, the element kernel alone from
     the library's event timers, against the float64 ALU roofline.  Then one
     Newton steps from rest under the paper's tip loads (beam: F_z = 5,000 N at
@@ -649,6 +650,32 @@ def run_ancf(args):
         g.sync()
         res.update(elements=int(m.ne), coefficients=int(m.nn), dofs=int(3 * m.nn), nnz=int(g.nnz))
         g.close()
+        # the float32 element form: the same assembly pass with float32 tangent and values
+        g32 = tl.Mesh.ancf(kind, m.E0, m.conn, m.dims, [mat], precision=tl.TL_FP32_ELEM)
+        g32.build_pattern(m.fixed_nodes)
+        vals32 = torch.empty(g32.nnz, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            g32.assemble_hessian(qd, vd, h, 1e12, values=vals32, f_int=f)
+        torch.cuda.synchronize()
+        g32.timing_read()
+        g32.timing_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            g32.assemble_hessian(qd, vd, h, 1e12, values=vals32, f_int=f)
+        e1.record()
+        torch.cuda.synchronize()
+        tim = g32.timing_read()
+        g32.timing_enable(False)
+        g32.sync()
+        ms = e0.elapsed_time(e1) / 10
+        kms = tim["ms_element"] / max(1, tim["n_element"])
+        fl = ancf_flops_per_elem(kind, True)
+        res["assembly_fp32"] = {"ms": ms, "elems_per_s": m.ne / ms * 1e3, "kernel_ms": kms, "flops_per_elem": fl,
+                                "achieved_tflops": fl * m.ne / (kms * 1e-3) / 1e12,
+                                "frac_fp32_alu": fl * m.ne / (kms * 1e-3) / 1e12 / fp32_alu_peak_tflops(),
+                                "speedup_vs_fp64": res["assembly"]["ms"] / ms}
+        g32.close()
         if args.ancf_no_newton:
             out[kind] = res
             continue

@@ -1,6 +1,8 @@
 // ANCF elements: the exact consistent mass (node-level CSR, gravity weights
 // and the per-element mass folded into the Hessian) and the dispatch of the
-// element passes to the beam / shell kernels.
+// element passes to the beam / shell kernels (float64; the tangent passes of
+// float32 handles in the float32 element form, their residual forces in
+// float64).
 //
 // Paper: arxiv 2604.10357 Sec. 4.1 (m_ij = int rho S_i S_j dV, constant,
 // M_e = [m_ij I3]) and Sec. 4.3 (element passes).  The mass is integrated by
@@ -17,6 +19,10 @@ tl_status ancf_launch_beam(tl_mesh*, const double*, const double*, double, doubl
                            double*, double*, double*);
 tl_status ancf_launch_shell(tl_mesh*, const double*, const double*, double, double, double, double, bool, bool,
                             double*, double*, double*);
+tl_status ancf_launch_beam_f32(tl_mesh*, const double*, const double*, double, double, double, double, bool,
+                               double*, float*, float*);
+tl_status ancf_launch_shell_f32(tl_mesh*, const double*, const double*, double, double, double, double, bool,
+                                double*, float*, float*);
 
 namespace {
 
@@ -43,14 +49,14 @@ __global__ void ancf_mass(const int32_t* conn, const double* geo, const double* 
 #pragma unroll
     for (int b = 0; b < NEN; ++b) {
       double d[3];
-      ancf::shape<ET>(b, p, dims, &S[b], d);
+      ancf::shape<ET, double>(b, p, dims, &S[b], d);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) J0[i][j] += X[3 * c[b] + i] * d[j];
     }
     double Ji[3][3];
-    const double dv = rho * w * ancf::inv3(J0, Ji);
+    const double dv = rho * w * ancf::inv3<double>(J0, Ji);
     const double sa = dv * S[a];
     wa += sa;
 #pragma unroll
@@ -98,11 +104,17 @@ tl_status ancf_build_mass(tl_mesh* m) {
 
 tl_status ancf_launch(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
                       double mass_scale, bool do_force, bool do_tangent, double* f, void* values, void* K_elem) {
-  if (m->precision != TL_FP64) return fail(m, TL_ERR_UNSUPPORTED, "ANCF elements run in float64 only");
   if (do_tangent && !m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
   cudaEvent_t t0 = timer_open(m);
   tl_status s;
-  if (m->etype == TL_ELEM_ANCF3243)
+  if (m->precision == TL_FP32_ELEM && do_tangent) {     // the float32 element form: float values / K_elem
+    if (m->etype == TL_ELEM_ANCF3243)
+      s = ancf_launch_beam_f32(m, q_n, v, h, alpha, beta, mass_scale, do_force, f,
+                               reinterpret_cast<float*>(values), reinterpret_cast<float*>(K_elem));
+    else
+      s = ancf_launch_shell_f32(m, q_n, v, h, alpha, beta, mass_scale, do_force, f,
+                                reinterpret_cast<float*>(values), reinterpret_cast<float*>(K_elem));
+  } else if (m->etype == TL_ELEM_ANCF3243)
     s = ancf_launch_beam(m, q_n, v, h, alpha, beta, mass_scale, do_force, do_tangent, f,
                          reinterpret_cast<double*>(values), reinterpret_cast<double*>(K_elem));
   else

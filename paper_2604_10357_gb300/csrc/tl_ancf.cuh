@@ -83,85 +83,87 @@ __host__ __device__ inline void mass_point(int q, double p[3], double& w) {
   w = w0 * w1 * w2;
 }
 
-// Shape function a: value S (optional) and d/d(xi, eta, zeta) at p; dims = L, W, H.
-template <int ET>
-__host__ __device__ inline void shape(int a, const double p[3], const double dims[3], double* S, double d[3]) {
-  const double xi = p[0], eta = p[1], zeta = p[2];
-  const double L = dims[0], W = dims[1], H = dims[2];
+// Shape function a: value S (optional) and d/d(xi, eta, zeta) at p; dims = L, W, H
+// (T = double, or float for the float32 element form).
+template <int ET, typename T>
+__host__ __device__ inline void shape(int a, const T p[3], const T dims[3], T* S, T d[3]) {
+  const T xi = p[0], eta = p[1], zeta = p[2];
+  const T L = dims[0], W = dims[1], H = dims[2];
   if (ET == kBeam) {
     const int node = a >> 2, k = a & 3;
-    const double sg = node ? 1.0 : -1.0;          // end at xi = -1 (node 0) or +1 (node 1)
-    const double lin = 0.5 * (1.0 + sg * xi);     // linear end function
+    const T sg = node ? T(1.0) : -T(1.0);          // end at xi = -1 (node 0) or +1 (node 1)
+    const T lin = T(0.5) * (T(1.0) + sg * xi);     // linear end function
     switch (k) {
       case 0:   // (2 -+ 3 xi +- xi^3) / 4
-        if (S) *S = 0.25 * (2.0 + sg * (3.0 * xi - xi * xi * xi));
-        d[0] = 0.75 * sg * (1.0 - xi * xi);
-        d[1] = d[2] = 0.0;
+        if (S) *S = T(0.25) * (T(2.0) + sg * (T(3.0) * xi - xi * xi * xi));
+        d[0] = T(0.75) * sg * (T(1.0) - xi * xi);
+        d[1] = d[2] = T(0.0);
         break;
       case 1:   // L (1 + sg xi)^2 (sg xi - 1) sg / 8
       {
-        const double a1 = 1.0 + sg * xi;
-        if (S) *S = 0.125 * L * sg * a1 * a1 * (sg * xi - 1.0);
-        d[0] = 0.125 * L * a1 * (3.0 * sg * xi - 1.0);
-        d[1] = d[2] = 0.0;
+        const T a1 = T(1.0) + sg * xi;
+        if (S) *S = T(0.125) * L * sg * a1 * a1 * (sg * xi - T(1.0));
+        d[0] = T(0.125) * L * a1 * (T(3.0) * sg * xi - T(1.0));
+        d[1] = d[2] = T(0.0);
         break;
       }
       case 2:   // y lin
-        if (S) *S = 0.5 * W * eta * lin;
-        d[0] = 0.25 * W * eta * sg;
-        d[1] = 0.5 * W * lin;
-        d[2] = 0.0;
+        if (S) *S = T(0.5) * W * eta * lin;
+        d[0] = T(0.25) * W * eta * sg;
+        d[1] = T(0.5) * W * lin;
+        d[2] = T(0.0);
         break;
       default:  // z lin
-        if (S) *S = 0.5 * H * zeta * lin;
-        d[0] = 0.25 * H * zeta * sg;
-        d[1] = 0.0;
-        d[2] = 0.5 * H * lin;
+        if (S) *S = T(0.5) * H * zeta * lin;
+        d[0] = T(0.25) * H * zeta * sg;
+        d[1] = T(0.0);
+        d[2] = T(0.5) * H * lin;
         break;
     }
   } else {
     const int c = a >> 2, k = a & 3;
-    const double xc = (c == 1 || c == 2) ? 1.0 : -1.0;
-    const double yc = (c >= 2) ? 1.0 : -1.0;
-    const double A = 1.0 + xc * xi, B = 1.0 + yc * eta;
+    const T xc = (c == 1 || c == 2) ? T(1.0) : -T(1.0);
+    const T yc = (c >= 2) ? T(1.0) : -T(1.0);
+    const T A = T(1.0) + xc * xi, B = T(1.0) + yc * eta;
     switch (k) {
       case 0: {  // A B (2 + xc xi + yc eta - xi^2 - eta^2) / 8
-        const double g = 2.0 + xc * xi + yc * eta - xi * xi - eta * eta;
-        if (S) *S = 0.125 * A * B * g;
-        d[0] = 0.125 * B * (xc * g + A * (xc - 2.0 * xi));
-        d[1] = 0.125 * A * (yc * g + B * (yc - 2.0 * eta));
-        d[2] = 0.0;
+        const T g = T(2.0) + xc * xi + yc * eta - xi * xi - eta * eta;
+        if (S) *S = T(0.125) * A * B * g;
+        d[0] = T(0.125) * B * (xc * g + A * (xc - T(2.0) * xi));
+        d[1] = T(0.125) * A * (yc * g + B * (yc - T(2.0) * eta));
+        d[2] = T(0.0);
         break;
       }
       case 1:    // (L/16) xc A^2 (xc xi - 1) B
-        if (S) *S = L / 16.0 * xc * A * A * (xc * xi - 1.0) * B;
-        d[0] = L / 16.0 * A * B * (3.0 * xc * xi - 1.0);
-        d[1] = L / 16.0 * xc * A * A * (xc * xi - 1.0) * yc;
-        d[2] = 0.0;
+        if (S) *S = L / T(16.0) * xc * A * A * (xc * xi - T(1.0)) * B;
+        d[0] = L / T(16.0) * A * B * (T(3.0) * xc * xi - T(1.0));
+        d[1] = L / T(16.0) * xc * A * A * (xc * xi - T(1.0)) * yc;
+        d[2] = T(0.0);
         break;
       case 2:    // (W/16) yc B^2 (yc eta - 1) A
-        if (S) *S = W / 16.0 * yc * B * B * (yc * eta - 1.0) * A;
-        d[0] = W / 16.0 * yc * B * B * (yc * eta - 1.0) * xc;
-        d[1] = W / 16.0 * A * B * (3.0 * yc * eta - 1.0);
-        d[2] = 0.0;
+        if (S) *S = W / T(16.0) * yc * B * B * (yc * eta - T(1.0)) * A;
+        d[0] = W / T(16.0) * yc * B * B * (yc * eta - T(1.0)) * xc;
+        d[1] = W / T(16.0) * A * B * (T(3.0) * yc * eta - T(1.0));
+        d[2] = T(0.0);
         break;
       default:   // (H/8) zeta A B
-        if (S) *S = 0.125 * H * zeta * A * B;
-        d[0] = 0.125 * H * zeta * xc * B;
-        d[1] = 0.125 * H * zeta * yc * A;
-        d[2] = 0.125 * H * A * B;
+        if (S) *S = T(0.125) * H * zeta * A * B;
+        d[0] = T(0.125) * H * zeta * xc * B;
+        d[1] = T(0.125) * H * zeta * yc * A;
+        d[2] = T(0.125) * H * A * B;
         break;
     }
   }
 }
 
 // det of a 3 x 3 matrix and its inverse (returns det).
-__host__ __device__ inline double inv3(const double J[3][3], double Ji[3][3]) {
-  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-  const double r = 1.0 / det;
+template <typename T>
+__host__ __device__ inline T inv3(const T J[3][3], T Ji[3][3]) {
+  const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  const T r = T(1.0) / det;
   Ji[0][0] = c00 * r;
   Ji[1][0] = c01 * r;
   Ji[2][0] = c02 * r;

@@ -1,13 +1,17 @@
-// Element kernel of the ANCF3243 beam and ANCF3443 shell elements (float64):
-// internal force, tangent and its CSR assembly, instantiated per element
-// kind in tl_ancf_beam.cu and tl_ancf_shell.cu.
+// Element kernel of the ANCF3243 beam and ANCF3443 shell elements: internal
+// force, tangent and its CSR assembly, in float64 or in the float32 element
+// form, instantiated per element kind and arithmetic type in tl_ancf_*.cu.
 //
 // Paper: arxiv 2604.10357 Sec. 4.3 (Stage 1: P at every (element, quadrature
 // point), 12 points per beam and 48 per shell element; Stage 2: f_a = sum_q
 // P grad S_a w J0, eq. fint_local) and Sec. 4.4 (eq. tangent_block, 24 x 24
 // and 48 x 48 element tangents, scattered into the fixed CSR pattern).
 //
-// One CTA holds EPB elements.  Phase 1: a thread per (element, point)
+// One CTA holds EPB elements.  Staging: per coefficient, the displacement
+// u = q_n + h v - e0 and the velocity (formed in float64) and the reference
+// coefficient e0, positions taken relative to the element's first position
+// (the Jacobian depends only on differences of positions; this keeps float32
+// exact to its precision on a 100 km beam).  Phase 1: a thread per (element, point)
 // computes J0 from the reference coefficients, grad_X S_a = J0^{-T} dS_a,
 // F, the stresses, and keeps per point n_a = grad_X S_a, g_a = F n_a,
 // s_a = S n_a, F, B = F F^T, w J0 (and the tangent rows for Mooney-Rivlin)
@@ -18,12 +22,15 @@
 // and its transpose through the slot map (the Hessian is symmetric).
 #pragma once
 
+#include <type_traits>
+
 #include "tl_ancf.cuh"
 #include "tl_element_common.cuh"
 
 namespace tl {
 namespace ancf {
 
+template <typename T>
 struct Args {
   const int32_t* conn;      // ne_pad x NEN coefficient ids
   const double* geo;        // ne_pad x 16: L, W, H
@@ -32,13 +39,14 @@ struct Args {
   const int32_t* user_of;
   const double* me;         // ne_pad x NP exact element mass (upper triangle)
   const double *q_n, *v, *X;
-  double h, alpha, beta, mass_scale;
+  double h, mass_scale;
+  T alpha, beta;
   double* f;
-  double* values;
-  double* K_elem;
+  T* values;
+  T* K_elem;
   uint32_t* flags;
   int64_t begin, end;       // this segment's element range
-  MatT<double> mat;
+  MatT<T> mat;
 };
 
 template <int ET>
@@ -46,10 +54,16 @@ struct Cfg {
   static constexpr int NEN = Traits<ET>::NEN, NQP = Traits<ET>::NQP, NP = NEN * (NEN + 1) / 2;
   static constexpr int EPB = ET == kBeam ? 8 : 1;           // elements per CTA
   static constexpr int NT = ET == kBeam ? 288 : 160;        // >= EPB * NP pair threads
-  static constexpr int MINB = ET == kBeam ? 1 : 2;          // resident CTAs per SM the registers allow
 };
 
-// Per-point record in shared memory (doubles).
+// Resident CTAs per SM the register budget is capped for (float64: 1 beam /
+// 2 shell CTAs; the float32 form needs fewer registers: 2 / 3).
+template <typename T, int ET>
+constexpr int min_blocks() {
+  return std::is_same<T, float>::value ? (ET == kBeam ? 2 : 3) : (ET == kBeam ? 1 : 2);
+}
+
+// Per-point record in shared memory (elements of type T).
 template <int ET, bool TAN, bool MR>
 struct Rec {
   static constexpr int NEN = Traits<ET>::NEN;
@@ -63,22 +77,38 @@ struct Rec {
   static constexpr int R = oA + (TAN && MR ? 81 : 0);
 };
 
-template <int ET, bool TAN, bool MR>
+// Dynamic shared memory: the per-point records, then the staged coefficients
+// (u, v, e0 per coefficient: 9 values).
+template <typename T, int ET, bool TAN, bool MR>
 constexpr size_t smem_bytes() {
-  return sizeof(double) * (size_t)Rec<ET, TAN, MR>::R * Cfg<ET>::NQP * Cfg<ET>::EPB;
+  return sizeof(T) * ((size_t)Rec<ET, TAN, MR>::R * Cfg<ET>::NQP + 9 * Cfg<ET>::NEN) * Cfg<ET>::EPB;
 }
 
-template <int ET, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
-__global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A) {
+template <typename T, int ET, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
+__global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(Args<T> A) {
   constexpr int NEN = Cfg<ET>::NEN, NQP = Cfg<ET>::NQP, NP = Cfg<ET>::NP, EPB = Cfg<ET>::EPB, NT = Cfg<ET>::NT;
   constexpr bool MR = MAT == TL_MOONEY_RIVLIN;
   using RC = Rec<ET, DO_TANGENT, MR>;
-  extern __shared__ double sm[];
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* stg = sm + (size_t)RC::R * NQP * EPB;                  // [el][a][u 3, v 3, e0 3]
   __shared__ int32_t s_conn[EPB][NEN];
   const int64_t ebase = A.begin + (int64_t)blockIdx.x * EPB;
   for (int t = threadIdx.x; t < EPB * NEN; t += NT) {
     const int64_t e = ebase + t / NEN;
     s_conn[t / NEN][t % NEN] = e < A.end ? A.conn[e * NEN + t % NEN] : 0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < EPB * NEN * 3; t += NT) {
+    const int el = t / (NEN * 3), a = (t / 3) % NEN, i = t % 3;
+    if (ebase + el >= A.end) continue;
+    const int c = s_conn[el][a];
+    const double vi = A.v[3 * c + i], x0 = A.X[3 * c + i];
+    T* st = stg + (el * NEN + a) * 9;
+    st[i] = T((A.q_n[3 * c + i] + A.h * vi) - x0);
+    st[3 + i] = T(vi);
+    // positions relative to the element's first position coefficient
+    st[6 + i] = T((a & 3) == 0 ? x0 - A.X[3 * s_conn[el][0] + i] : x0);
   }
   __syncthreads();
 
@@ -88,49 +118,48 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A
     const int el = t / NQP, q = t % NQP;
     const int64_t e = ebase + el;
     if (e >= A.end) continue;
-    double* rec = sm + (size_t)(el * NQP + q) * RC::R;
-    const double dims[3] = {A.geo[e * 16 + 0], A.geo[e * 16 + 1], A.geo[e * 16 + 2]};
-    double p[3], w;
-    element_point<ET>(q, p, w);
-    double J0[3][3] = {};
+    T* rec = sm + (size_t)(el * NQP + q) * RC::R;
+    const T* st = stg + el * NEN * 9;
+    const T dims[3] = {T(A.geo[e * 16 + 0]), T(A.geo[e * 16 + 1]), T(A.geo[e * 16 + 2])};
+    double pd[3], wd;
+    element_point<ET>(q, pd, wd);
+    const T p[3] = {T(pd[0]), T(pd[1]), T(pd[2])};
+    T J0[3][3] = {};
     for (int a = 0; a < NEN; ++a) {
-      double d[3];
-      shape<ET>(a, p, dims, nullptr, d);
-      const int c = s_conn[el][a];
+      T d[3];
+      shape<ET, T>(a, p, dims, nullptr, d);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const double x0 = A.X[3 * c + i];
+        const T x0 = st[a * 9 + 6 + i];
 #pragma unroll
         for (int j = 0; j < 3; ++j) J0[i][j] += x0 * d[j];
       }
     }
-    double Ji[3][3];
-    const double det = inv3(J0, Ji);
-    if (!(det > 0.0)) inverted = true;
-    double Hm[3][3] = {}, Fd[3][3] = {};
+    T Ji[3][3];
+    const T det = inv3<T>(J0, Ji);
+    if (!(det > T(0))) inverted = true;
+    T Hm[3][3] = {}, Fd[3][3] = {};
     for (int a = 0; a < NEN; ++a) {
-      double d[3], n[3];
-      shape<ET>(a, p, dims, nullptr, d);
+      T d[3], n[3];
+      shape<ET, T>(a, p, dims, nullptr, d);
 #pragma unroll
       for (int J = 0; J < 3; ++J) n[J] = d[0] * Ji[0][J] + d[1] * Ji[1][J] + d[2] * Ji[2][J];
-      const int c = s_conn[el][a];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const double vi = A.v[3 * c + i];
-        const double ui = (A.q_n[3 * c + i] + A.h * vi) - A.X[3 * c + i];
+        const T ui = st[a * 9 + i], vi = st[a * 9 + 3 + i];
 #pragma unroll
         for (int J = 0; J < 3; ++J) {
           Hm[i][J] += ui * n[J];
-          Fd[i][J] += vi * n[J];
+          if (KV) Fd[i][J] += vi * n[J];
         }
       }
 #pragma unroll
       for (int J = 0; J < 3; ++J) rec[RC::oN + 3 * a + J] = n[J];
     }
-    QP<double> s;
-    constitutive<double, MAT, KV>(Hm, Fd, A.mat, s, inverted);
+    QP<T> s;
+    constitutive<T, MAT, KV>(Hm, Fd, A.mat, s, inverted);
     for (int a = 0; a < NEN; ++a) {
-      const double n0 = rec[RC::oN + 3 * a], n1 = rec[RC::oN + 3 * a + 1], n2 = rec[RC::oN + 3 * a + 2];
+      const T n0 = rec[RC::oN + 3 * a], n1 = rec[RC::oN + 3 * a + 1], n2 = rec[RC::oN + 3 * a + 2];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         rec[RC::oS + 3 * a + i] = s.S[i][0] * n0 + s.S[i][1] * n1 + s.S[i][2] * n2;
@@ -144,12 +173,12 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A
         rec[RC::oF + 3 * i + j] = s.F[i][j];
         if (DO_TANGENT) rec[RC::oB + 3 * i + j] = s.B[i][j];
       }
-    const double wJ = w * det;
+    const T wJ = T(wd) * det;
     rec[RC::oW] = wJ;
     if constexpr (DO_TANGENT && MR) {
-      tangent_row<double, MAT, KV, 0>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA);
-      tangent_row<double, MAT, KV, 1>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA + 27);
-      tangent_row<double, MAT, KV, 2>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA + 54);
+      tangent_row<T, MAT, KV, 0>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA);
+      tangent_row<T, MAT, KV, 1>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA + 27);
+      tangent_row<T, MAT, KV, 2>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA + 54);
     }
   }
   if (inverted) atomicOr(A.flags, kFlagInverted);
@@ -160,48 +189,48 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A
     for (int t = threadIdx.x; t < EPB * NEN; t += NT) {
       const int el = t / NEN, a = t % NEN;
       if (ebase + el >= A.end) continue;
-      double fa[3] = {0.0, 0.0, 0.0};
+      T fa[3] = {T(0), T(0), T(0)};
       for (int q = 0; q < NQP; ++q) {
-        const double* rec = sm + (size_t)(el * NQP + q) * RC::R;
-        const double wJ = rec[RC::oW];
-        const double s0 = rec[RC::oS + 3 * a], s1 = rec[RC::oS + 3 * a + 1], s2 = rec[RC::oS + 3 * a + 2];
+        const T* rec = sm + (size_t)(el * NQP + q) * RC::R;
+        const T wJ = rec[RC::oW];
+        const T s0 = rec[RC::oS + 3 * a], s1 = rec[RC::oS + 3 * a + 1], s2 = rec[RC::oS + 3 * a + 2];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           fa[i] += wJ * (rec[RC::oF + 3 * i] * s0 + rec[RC::oF + 3 * i + 1] * s1 + rec[RC::oF + 3 * i + 2] * s2);
       }
       const int c = s_conn[el][a];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) atomicAdd(&A.f[3 * c + i], fa[i]);
+      for (int i = 0; i < 3; ++i) atomicAdd(&A.f[3 * c + i], (double)fa[i]);
     }
   }
 
   // ---- tangent blocks (a <= b) ---------------------------------------------
   if (DO_TANGENT) {
-    const double c1 = A.alpha * A.mat.lam + (KV ? A.beta * A.mat.lam_d : 0.0);
-    const double c2 = A.alpha * A.mat.mu + (KV ? A.beta * A.mat.eta : 0.0);
+    const T c1 = A.alpha * A.mat.lam + (KV ? A.beta * A.mat.lam_d : T(0));
+    const T c2 = A.alpha * A.mat.mu + (KV ? A.beta * A.mat.eta : T(0));
     for (int t = threadIdx.x; t < EPB * NP; t += NT) {
       const int el = t / NP, pr = t % NP;
       const int64_t e = ebase + el;
       if (e >= A.end) continue;
       int a, b;
       pair_of(pr, NEN, a, b);
-      double K[3][3] = {};
+      T K[3][3] = {};
       for (int q = 0; q < NQP; ++q) {
-        const double* rec = sm + (size_t)(el * NQP + q) * RC::R;
-        const double* na = rec + RC::oN + 3 * a;
-        const double* nb = rec + RC::oN + 3 * b;
+        const T* rec = sm + (size_t)(el * NQP + q) * RC::R;
+        const T* na = rec + RC::oN + 3 * a;
+        const T* nb = rec + RC::oN + 3 * b;
         if constexpr (!MR) {
           // [K_ab]_ik = wJ [c1 g_a,i g_b,k + c2 (g_b,i g_a,k + (n_a.n_b) B_ik) + alpha d_ik n_a.S n_b]
-          const double wJ = rec[RC::oW];
-          const double* ga = rec + RC::oG + 3 * a;
-          const double* gb = rec + RC::oG + 3 * b;
-          const double* sb = rec + RC::oS + 3 * b;
-          const double nn = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
-          const double sn = na[0] * sb[0] + na[1] * sb[1] + na[2] * sb[2];
-          const double w1 = wJ * c1, w2 = wJ * c2, w2n = w2 * nn, w3 = wJ * A.alpha * sn;
+          const T wJ = rec[RC::oW];
+          const T* ga = rec + RC::oG + 3 * a;
+          const T* gb = rec + RC::oG + 3 * b;
+          const T* sb = rec + RC::oS + 3 * b;
+          const T nn = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
+          const T sn = na[0] * sb[0] + na[1] * sb[1] + na[2] * sb[2];
+          const T w1 = wJ * c1, w2 = wJ * c2, w2n = w2 * nn, w3 = wJ * A.alpha * sn;
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            const double gai = ga[i], gbi = gb[i];
+            const T gai = ga[i], gbi = gb[i];
 #pragma unroll
             for (int k = 0; k < 3; ++k)
               K[i][k] += w1 * gai * gb[k] + w2 * gbi * ga[k] + w2n * rec[RC::oB + 3 * i + k];
@@ -209,12 +238,12 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A
           }
         } else {
           // [K_ab]_ik = sum_J n_a,J sum_L A^_iJkL n_b,L (rows already scaled by wJ, alpha, beta)
-          const double* Ar = rec + RC::oA;
+          const T* Ar = rec + RC::oA;
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int J = 0; J < 3; ++J) {
-              const double* r = Ar + i * 27 + J * 9;
+              const T* r = Ar + i * 27 + J * 9;
 #pragma unroll
               for (int k = 0; k < 3; ++k)
                 K[i][k] += na[J] * (r[k * 3] * nb[0] + r[k * 3 + 1] * nb[1] + r[k * 3 + 2] * nb[2]);
@@ -222,7 +251,7 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A
         }
       }
       if (A.mass_scale != 0.0) {
-        const double ms = A.mass_scale * A.me[e * NP + pr];
+        const T ms = T(A.mass_scale * A.me[e * NP + pr]);
         K[0][0] += ms;
         K[1][1] += ms;
         K[2][2] += ms;
@@ -247,7 +276,7 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A
       }
       if (A.K_elem) {
         constexpr int ND = 3 * NEN;
-        double* Ke = A.K_elem + (int64_t)A.user_of[e] * ND * ND;
+        T* Ke = A.K_elem + (int64_t)A.user_of[e] * ND * ND;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -261,12 +290,12 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, Cfg<ET>::MINB) elem_kernel(Args A
 }
 
 // One launch per material segment; dispatch on (material kind, Kelvin-Voigt,
-// pass).
-template <int ET>
+// pass).  T = float instantiates the tangent passes only (the float32 element
+// form; its forces for the residual come from the float64 kernels).
+template <typename T, int ET>
 tl_status launch_kind(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
-                      double mass_scale, bool do_force, bool do_tangent, double* f, double* values,
-                      double* K_elem) {
-  Args A;
+                      double mass_scale, bool do_force, bool do_tangent, double* f, T* values, T* K_elem) {
+  Args<T> A;
   A.conn = m->d_conn;
   A.geo = m->d_geo64;
   A.blk = m->d_blk;
@@ -277,43 +306,50 @@ tl_status launch_kind(tl_mesh* m, const double* q_n, const double* v, double h, 
   A.v = v;
   A.X = m->d_X;
   A.h = h;
-  A.alpha = alpha;
-  A.beta = beta;
+  A.alpha = T(alpha);
+  A.beta = T(beta);
   A.mass_scale = mass_scale;
   A.f = f;
   A.values = values;
   A.K_elem = K_elem;
   A.flags = m->d_flags;
+  constexpr bool kF64 = std::is_same<T, double>::value;
   for (const Segment& sg : m->segs) {
     const int64_t cnt = sg.end - sg.begin;
     if (cnt == 0) continue;
     const MaterialDev& md = m->mats[sg.mat];
     A.begin = sg.begin;
     A.end = sg.end;
-    A.mat = to_matT<double>(md);
+    A.mat = to_matT<T>(md);
     const int combo = 2 * (md.kind == TL_SVK ? 0 : 1) + (md.kv ? 1 : 0);
     const int pass = (do_force ? 1 : 0) + (do_tangent ? 2 : 0);
-    void (*kern)(Args) = nullptr;
+    void (*kern)(Args<T>) = nullptr;
     size_t smem = 0;
 #define TL_ANCF_CASE(MATK, KVK, FO, TA)                                             \
-  kern = elem_kernel<ET, MATK, KVK, FO, TA>;                                         \
-  smem = smem_bytes<ET, TA, MATK == TL_MOONEY_RIVLIN>();
+  kern = elem_kernel<T, ET, MATK, KVK, FO, TA>;                                      \
+  smem = smem_bytes<T, ET, TA, MATK == TL_MOONEY_RIVLIN>();
+    if constexpr (kF64) {
+      switch (combo * 4 + pass) {
+        case 0 * 4 + 1: TL_ANCF_CASE(TL_SVK, false, true, false) break;
+        case 1 * 4 + 1: TL_ANCF_CASE(TL_SVK, true, true, false) break;
+        case 2 * 4 + 1: TL_ANCF_CASE(TL_MOONEY_RIVLIN, false, true, false) break;
+        case 3 * 4 + 1: TL_ANCF_CASE(TL_MOONEY_RIVLIN, true, true, false) break;
+        default: break;
+      }
+    }
     switch (combo * 4 + pass) {
-      case 0 * 4 + 1: TL_ANCF_CASE(TL_SVK, false, true, false) break;
       case 0 * 4 + 2: TL_ANCF_CASE(TL_SVK, false, false, true) break;
       case 0 * 4 + 3: TL_ANCF_CASE(TL_SVK, false, true, true) break;
-      case 1 * 4 + 1: TL_ANCF_CASE(TL_SVK, true, true, false) break;
       case 1 * 4 + 2: TL_ANCF_CASE(TL_SVK, true, false, true) break;
       case 1 * 4 + 3: TL_ANCF_CASE(TL_SVK, true, true, true) break;
-      case 2 * 4 + 1: TL_ANCF_CASE(TL_MOONEY_RIVLIN, false, true, false) break;
       case 2 * 4 + 2: TL_ANCF_CASE(TL_MOONEY_RIVLIN, false, false, true) break;
       case 2 * 4 + 3: TL_ANCF_CASE(TL_MOONEY_RIVLIN, false, true, true) break;
-      case 3 * 4 + 1: TL_ANCF_CASE(TL_MOONEY_RIVLIN, true, true, false) break;
       case 3 * 4 + 2: TL_ANCF_CASE(TL_MOONEY_RIVLIN, true, false, true) break;
       case 3 * 4 + 3: TL_ANCF_CASE(TL_MOONEY_RIVLIN, true, true, true) break;
-      default: return TL_OK;   // nothing requested
+      default: break;
     }
 #undef TL_ANCF_CASE
+    if (!kern) return pass == 0 ? TL_OK : fail(m, TL_ERR_UNSUPPORTED, "ANCF element pass selection");
     TL_CUDA(m, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t nblk = (cnt + Cfg<ET>::EPB - 1) / Cfg<ET>::EPB;
     kern<<<(unsigned)nblk, Cfg<ET>::NT, smem, m->stream>>>(A);

@@ -1,4 +1,4 @@
-// ANCF3443 shell element passes (kernels in tl_ancf_impl.cuh).
+// ANCF3443 shell element passes in float64 (kernels in tl_ancf_impl.cuh).
 #include "tl_ancf_impl.cuh"
 
 namespace tl {
@@ -6,7 +6,8 @@ namespace tl {
 tl_status ancf_launch_shell(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
                         double mass_scale, bool do_force, bool do_tangent, double* f, double* values,
                         double* K_elem) {
-  return ancf::launch_kind<ancf::kShell>(m, q_n, v, h, alpha, beta, mass_scale, do_force, do_tangent, f, values, K_elem);
+  return ancf::launch_kind<double, ancf::kShell>(m, q_n, v, h, alpha, beta, mass_scale, do_force, do_tangent, f,
+                                              values, K_elem);
 }
 
 }  // namespace tl

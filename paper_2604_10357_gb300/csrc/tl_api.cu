@@ -176,11 +176,11 @@ bool ancf_jacobians_positive(const double* E0, const int32_t* c, const double di
     double J0[3][3] = {}, Ji[3][3];
     for (int a = 0; a < ancf::Traits<ET>::NEN; ++a) {
       double d[3];
-      ancf::shape<ET>(a, p, dims, nullptr, d);
+      ancf::shape<ET, double>(a, p, dims, nullptr, d);
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) J0[i][j] += E0[3 * c[a] + i] * d[j];
     }
-    if (!(ancf::inv3(J0, Ji) > 0.0)) return false;
+    if (!(ancf::inv3<double>(J0, Ji) > 0.0)) return false;
   }
   return true;
 }
@@ -352,10 +352,6 @@ tl_status tl_mesh_create_ancf(int32_t kind, const double* E0, int64_t ncoef, con
   if (precision != TL_FP64 && precision != TL_FP32_ELEM) return TL_ERR_INVALID_ARG;
   if (ncoef >= (int64_t)1 << 29) return TL_ERR_OVERFLOW;
   g_create_error.clear();
-  if (precision != TL_FP64) {
-    g_create_error = "ANCF elements run in float64 only";
-    return TL_ERR_UNSUPPORTED;
-  }
   const int nen = kind == TL_ELEM_ANCF3243 ? 8 : 16;
   tl_mesh* m = new_mesh(stream, precision, ncoef, ne);
   if (!m) return TL_ERR_OOM;
@@ -478,7 +474,7 @@ tl_status tl_build_pattern(tl_mesh* m, const int32_t* fixed_nodes, int64_t nfixe
   if (s != TL_OK) return s;
   // float32 handles: the per-tile aggregation maps of the assembly, built
   // with the pattern so that the default launch shape can use them
-  if (m->precision == TL_FP32_ELEM && m->nn < (int64_t(1) << 24)) {
+  if (m->precision == TL_FP32_ELEM && m->etype == TL_ELEM_T10 && m->nn < (int64_t(1) << 24)) {
     s = tile_maps_ensure(m);
     if (s != TL_OK) return s;
   }

@@ -148,6 +148,7 @@ void tile_maps_free(tl_mesh* m);
 // whose node ids do not fit the 24-bit key keep the per-element scatter.
 tl_status tile_maps_ensure(tl_mesh* m) {
   if (m->agg_nu) return TL_OK;
+  if (m->etype != TL_ELEM_T10) return TL_OK;     // the T10 float32 assembly's maps; ANCF kernels use none
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tile maps need the pattern");
   if (m->nn >= (int64_t(1) << 24)) return fail(m, TL_ERR_INVALID_ARG, "tile maps: more than 2^24 nodes");
   const int64_t ntiles = std::max<int64_t>(m->ne_pad / kTile, 1);

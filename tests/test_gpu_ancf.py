@@ -12,7 +12,7 @@ from oracle import assembly as asm
 from oracle import newton as nt
 from paper_2604_10357_gb300 import inputs
 
-from helpers import TOL_FP64, force_error, values_error
+from helpers import TOL_FP32, TOL_FP64, force_error, values_error
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def _workload(kind):
     return inputs.workload_ancf_beam(21) if kind == ancf.BEAM else inputs.workload_ancf_shell(5, 3)
 
 
-def _case(kind, mats_key, clamp=True):
+def _case(kind, mats_key, clamp=True, fp32=False):
     w = _workload(kind)
     m = w["mesh"]
     mats = MATS[mats_key]
@@ -52,7 +52,8 @@ def _case(kind, mats_key, clamp=True):
     fixed = m.fixed_nodes if clamp else np.zeros(0, dtype=np.int32)
     om = ancf.OracleAncfMesh(kind, m.E0, m.conn, m.dims, mats, mat_of_elem=moe, fixed_nodes=fixed)
     tl = _tl()
-    g = tl.Mesh.ancf(kind, m.E0, m.conn, m.dims, mats, mat_of_elem=moe)
+    g = tl.Mesh.ancf(kind, m.E0, m.conn, m.dims, mats, mat_of_elem=moe,
+                     precision=tl.TL_FP32_ELEM if fp32 else tl.TL_FP64)
     g.build_pattern(fixed)
     return w, om, g, tl
 
@@ -170,13 +171,67 @@ def test_free_fall_closed_form(kind):
     np.testing.assert_allclose(v.cpu().numpy().reshape(-1, 3), ref, atol=1e-12)
 
 
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("mats_key", ["svk", "svk_kv", "mr", "mr_kv"])
+def test_element_tangents_fp32(kind, mats_key):
+    """The float32 element form: K_elem in float32 within 1e-5 of the oracle."""
+    w, om, g, tl = _case(kind, mats_key, fp32=True)
+    h = w["h"]
+    K = g.eval_tangent(_dev(w["q_n"]), _dev(w["v"]), h, h, 1.0)
+    g.sync()
+    assert K.dtype == torch.float32
+    x = w["q_n"] + h * w["v"]
+    assert _tangent_error(K.cpu().numpy(), om.element_tangents(x, w["v"], h, 1.0)) < TOL_FP32
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("mats_key", ["svk", "mixed"])
+def test_hessian_values_fp32(kind, mats_key):
+    """Float32 CSR values within 1e-5; the residual force of the handle stays
+    float64-class (1e-11)."""
+    w, om, g, tl = _case(kind, mats_key, fp32=True)
+    h, rho = w["h"], 1e8
+    vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho).cpu().numpy().astype(np.float64)
+    g.sync()
+    emax, e2 = values_error(vals, om.hessian_values(w["q_n"], w["v"], h, rho))
+    assert emax < TOL_FP32 and e2 < TOL_FP32
+    prm = tl.params(h=h, rho_alm=1e6)
+    lam = np.zeros(3 * len(w["mesh"].fixed_nodes))
+    gg, _ = g.eval_residual(prm, _dev(w["q_n"]), _dev(w["v"]), _dev(w["v"]), None, _dev(lam))
+    g.sync()
+    g_ora = om.residual(w["v"], w["q_n"], w["v"], h, None, prm.gravity[:], lam, 1e6)
+    fe = om.element_forces(w["q_n"] + h * w["v"], w["v"])
+    assert force_error(gg.cpu().numpy(), g_ora, fe) < TOL_FP64
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_newton_step_fp32_graph(kind):
+    """Float32 element form, captured graph, inexact-Newton PCG: the step meets
+    the oracle's residual target at the converged velocity."""
+    w, om, g, tl = _case(kind, "svk", fp32=True)
+    m = w["mesh"]
+    prm = nt.NewtonParams(h=w["h"], rtol=1e-8, solver="dense")
+    lam0 = np.zeros(3 * len(m.fixed_nodes))
+    ref = nt.newton_step(om, w["q_n"].ravel(), w["v"].ravel(), lam0, prm)
+    lam = _dev(lam0)
+    p = tl.params(h=prm.h, rho_alm=prm.rho_alm, rtol=prm.rtol, eps_out=prm.eps_out,
+                  linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, use_graph=1)
+    v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+    v = v.cpu().numpy()
+    assert st["converged"] == 1
+    lam_inner = lam.cpu().numpy() - prm.rho_alm * om.constraint(w["q_n"].ravel() + prm.h * v)
+    g_at = om.residual(v, w["q_n"].ravel(), w["v"].ravel(), prm.h, None, prm.gravity, lam_inner, prm.rho_alm)
+    assert np.linalg.norm(g_at) <= 1.05 * 1e-8 * ref["g_ref"]
+    assert np.linalg.norm(v - ref["v"]) <= 1e-6 * np.linalg.norm(ref["v"])
+
+
 def test_argument_errors():
     tl = _tl()
     m = inputs.beam_ancf3243(4)
     mat = [dict(inputs.SVK_7E8)]
     with pytest.raises(tl.TLError) as ei:
-        tl.Mesh.ancf("ancf3243", m.E0, m.conn, m.dims, mat, precision=tl.TL_FP32_ELEM)
-    assert ei.value.status == 10                                   # TL_ERR_UNSUPPORTED
+        tl.Mesh.ancf(7, m.E0, m.conn, m.dims, mat)                   # not an ANCF kind
+    assert ei.value.status == 1                                    # TL_ERR_INVALID_ARG
     bad = m.conn.copy()
     bad[2, 5] = m.nn
     with pytest.raises(tl.TLError) as ei:
