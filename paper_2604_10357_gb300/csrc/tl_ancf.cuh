@@ -35,34 +35,36 @@ struct Traits<kShell> {
   static constexpr int NEN = 16, NQP = 48, NMQ = 32;
 };
 
-// n-point Gauss-Legendre abscissa / weight on [-1, 1], i = 0..n-1 (n = 2, 3, 4).
-__host__ __device__ inline void gauss(int n, int i, double& x, double& w) {
+// n-point Gauss-Legendre abscissa / weight on [-1, 1], i = 0..n-1 (n = 2, 3, 4),
+// evaluated in T (float: single-precision square roots, no float64 work).
+template <typename T>
+__host__ __device__ inline void gauss(int n, int i, T& x, T& w) {
   if (n == 2) {
-    x = (i == 0 ? -1.0 : 1.0) / sqrt(3.0);
-    w = 1.0;
+    x = (i == 0 ? T(-1) : T(1)) / sqrt(T(3));
+    w = T(1);
   } else if (n == 3) {
-    x = i == 1 ? 0.0 : (i == 0 ? -1.0 : 1.0) * sqrt(0.6);
-    w = i == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
+    x = i == 1 ? T(0) : (i == 0 ? T(-1) : T(1)) * sqrt(T(0.6));
+    w = i == 1 ? T(8) / T(9) : T(5) / T(9);
   } else {   // 4 points: +-sqrt(3/7 -+ 2/7 sqrt(6/5)), weights (18 +- sqrt 30)/36
-    const double r = 2.0 / 7.0 * sqrt(1.2);
+    const T r = T(2) / T(7) * sqrt(T(1.2));
     const bool inner = (i == 1 || i == 2);
-    x = (i < 2 ? -1.0 : 1.0) * sqrt(3.0 / 7.0 + (inner ? -r : r));
-    w = (18.0 + (inner ? 1.0 : -1.0) * sqrt(30.0)) / 36.0;
+    x = (i < 2 ? T(-1) : T(1)) * sqrt(T(3) / T(7) + (inner ? -r : r));
+    w = (T(18) + (inner ? T(1) : T(-1)) * sqrt(T(30))) / T(36);
   }
 }
 
 // Point q of the element rule (xi slowest, zeta fastest) and its weight.
-template <int ET>
-__host__ __device__ inline void element_point(int q, double p[3], double& w) {
-  double w0, w1, w2;
+template <int ET, typename T>
+__host__ __device__ inline void element_point(int q, T p[3], T& w) {
+  T w0, w1, w2;
   if (ET == kBeam) {            // 3 x 2 x 2
-    gauss(3, q / 4, p[0], w0);
-    gauss(2, (q / 2) % 2, p[1], w1);
-    gauss(2, q % 2, p[2], w2);
+    gauss<T>(3, q / 4, p[0], w0);
+    gauss<T>(2, (q / 2) % 2, p[1], w1);
+    gauss<T>(2, q % 2, p[2], w2);
   } else {                      // 4 x 4 x 3
-    gauss(4, q / 12, p[0], w0);
-    gauss(4, (q / 3) % 4, p[1], w1);
-    gauss(3, q % 3, p[2], w2);
+    gauss<T>(4, q / 12, p[0], w0);
+    gauss<T>(4, (q / 3) % 4, p[1], w1);
+    gauss<T>(3, q % 3, p[2], w2);
   }
   w = w0 * w1 * w2;
 }
@@ -72,13 +74,13 @@ template <int ET>
 __host__ __device__ inline void mass_point(int q, double p[3], double& w) {
   double w0, w1, w2;
   if (ET == kBeam) {            // 4 x 2 x 2
-    gauss(4, q / 4, p[0], w0);
-    gauss(2, (q / 2) % 2, p[1], w1);
-    gauss(2, q % 2, p[2], w2);
+    gauss<double>(4, q / 4, p[0], w0);
+    gauss<double>(2, (q / 2) % 2, p[1], w1);
+    gauss<double>(2, q % 2, p[2], w2);
   } else {                      // 4 x 4 x 2
-    gauss(4, q / 8, p[0], w0);
-    gauss(4, (q / 2) % 4, p[1], w1);
-    gauss(2, q % 2, p[2], w2);
+    gauss<double>(4, q / 8, p[0], w0);
+    gauss<double>(4, (q / 2) % 4, p[1], w1);
+    gauss<double>(2, q % 2, p[2], w2);
   }
   w = w0 * w1 * w2;
 }

@@ -78,10 +78,10 @@ struct Rec {
 };
 
 // Dynamic shared memory: the per-point records, then the staged coefficients
-// (u, v, e0 per coefficient: 9 values).
+// (u, v, e0 per coefficient: 9 values) and the element dimensions (4).
 template <typename T, int ET, bool TAN, bool MR>
 constexpr size_t smem_bytes() {
-  return sizeof(T) * ((size_t)Rec<ET, TAN, MR>::R * Cfg<ET>::NQP + 9 * Cfg<ET>::NEN) * Cfg<ET>::EPB;
+  return sizeof(T) * ((size_t)Rec<ET, TAN, MR>::R * Cfg<ET>::NQP + 9 * Cfg<ET>::NEN + 4) * Cfg<ET>::EPB;
 }
 
 template <typename T, int ET, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
   extern __shared__ unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   T* stg = sm + (size_t)RC::R * NQP * EPB;                  // [el][a][u 3, v 3, e0 3]
+  T* sdim = stg + 9 * NEN * EPB;                            // [el][L, W, H, -]
   __shared__ int32_t s_conn[EPB][NEN];
   const int64_t ebase = A.begin + (int64_t)blockIdx.x * EPB;
   for (int t = threadIdx.x; t < EPB * NEN; t += NT) {
@@ -110,6 +111,10 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
     // positions relative to the element's first position coefficient
     st[6 + i] = T((a & 3) == 0 ? x0 - A.X[3 * s_conn[el][0] + i] : x0);
   }
+  for (int t = threadIdx.x; t < EPB * 3; t += NT) {
+    const int64_t e = ebase + t / 3;
+    if (e < A.end) sdim[4 * (t / 3) + t % 3] = T(A.geo[e * 16 + t % 3]);
+  }
   __syncthreads();
 
   // ---- phase 1: kinematics and stresses at every (element, point) --------
@@ -120,10 +125,9 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
     if (e >= A.end) continue;
     T* rec = sm + (size_t)(el * NQP + q) * RC::R;
     const T* st = stg + el * NEN * 9;
-    const T dims[3] = {T(A.geo[e * 16 + 0]), T(A.geo[e * 16 + 1]), T(A.geo[e * 16 + 2])};
-    double pd[3], wd;
-    element_point<ET>(q, pd, wd);
-    const T p[3] = {T(pd[0]), T(pd[1]), T(pd[2])};
+    const T dims[3] = {sdim[4 * el], sdim[4 * el + 1], sdim[4 * el + 2]};
+    T p[3], wq;
+    element_point<ET, T>(q, p, wq);
     T J0[3][3] = {};
     for (int a = 0; a < NEN; ++a) {
       T d[3];
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
         rec[RC::oF + 3 * i + j] = s.F[i][j];
         if (DO_TANGENT) rec[RC::oB + 3 * i + j] = s.B[i][j];
       }
-    const T wJ = T(wd) * det;
+    const T wJ = wq * det;
     rec[RC::oW] = wJ;
     if constexpr (DO_TANGENT && MR) {
       tangent_row<T, MAT, KV, 0>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA);
