@@ -322,3 +322,73 @@ def test_fullsize_sampled(kind):
         gv = vals[torch.as_tensor([got[k] for k in row], device="cuda")].cpu().numpy()
         ref = np.array(list(row.values()))
         assert np.abs(gv - ref).max() < tol * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# the other rows of the framework on ANCF handles
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_adamw_step(kind):
+    """Algorithm 2 on an ANCF handle: two outer iterations of 30 fixed updates
+    (velocity commit and multiplier update between them) against the oracle's."""
+    from oracle import adamw as aw
+    w, om, g, tl = _case(kind, "svk")
+    m = w["mesh"]
+    ap = dict(lr=1e-4, max_inner=30, check_every=1000, eps_in=0.0, eps_rel=0.0)
+    lam0 = np.zeros(3 * len(m.fixed_nodes))
+    ref = aw.adamw_step(om, w["q_n"].ravel(), w["v"].ravel(), lam0,
+                        aw.AdamWParams(h=w["h"], rho_alm=1e12, max_outer=2, **ap))
+    lam = _dev(lam0)
+    v, _, st = g.adamw_step(tl.params(h=w["h"], rho_alm=1e12, max_outer=2), tl.adamw_params(**ap),
+                            _dev(w["q_n"]), _dev(w["v"]), lam, raise_on_nonconvergence=False)
+    assert st["inner_iters"] == 60 and st["outer_iters"] == 2
+    v = v.cpu().numpy()
+    assert np.linalg.norm(v - ref["v"]) <= 1e-9 * np.linalg.norm(ref["v"])
+    assert np.abs(lam.cpu().numpy() - ref["lam"]).max() <= 1e-9 * np.abs(ref["lam"]).max()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_general_constraints(kind):
+    """General linear rows on ANCF coefficients (Sec. 4.2): the tip position
+    tied in z to a mid-span position, and a row over gradient components of
+    coefficients that share no element, both holding at the start state;
+    pattern with the fill (bit-exact), Hessian values and the Newton step
+    against the oracle (the rows still hold after the step)."""
+    import scipy.sparse as sp
+    w = _workload(kind)
+    m = w["mesh"]
+    tl = _tl()
+    last, mid = 4 * (m.nphys - 1), 4 * (m.nphys // 2)
+    far = 4 * 1 + 2                                     # r_y of node 1
+    rows = [[(3 * last + 2, 1.0), (3 * mid + 2, -1.0)],
+            [(3 * far + 1, 0.5), (3 * (last + 1) + 0, -2.0), (3 * (mid + 3) + 2, 1.5)]]
+    ri, ci, vi = zip(*[(r, c, val) for r, row in enumerate(rows) for c, val in row])
+    C = sp.csr_matrix((vi, (ri, ci)), shape=(len(rows), 3 * m.nn))
+    C.sort_indices()
+    bvec = C @ w["q_n"].ravel()                         # the rows hold at the start state
+    mat = [dict(inputs.SVK_7E8)]
+    om = ancf.OracleAncfMesh(kind, m.E0, m.conn, m.dims, mat, fixed_nodes=m.fixed_nodes, constraints=(C, bvec))
+    g = tl.Mesh.ancf(kind, m.E0, m.conn, m.dims, mat)
+    g.set_constraints(C.indptr, C.indices, C.data, bvec)
+    g.build_pattern(m.fixed_nodes)
+    row_ptr, col = (a.cpu().numpy() for a in g.get_pattern()[:2])
+    _, _, r_ref, c_ref = om.pattern()
+    assert np.array_equal(row_ptr, r_ref) and np.array_equal(col, c_ref)
+    h, rho = w["h"], 1e8
+    vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho).cpu().numpy()
+    g.sync()
+    emax, e2 = values_error(vals, om.hessian_values(w["q_n"], w["v"], h, rho))
+    assert emax < TOL_FP64 and e2 < TOL_FP64
+    prm = nt.NewtonParams(h=h, rtol=1e-8, solver="dense")
+    lam0 = np.zeros(3 * len(m.fixed_nodes) + C.shape[0])
+    ref = nt.newton_step(om, w["q_n"].ravel(), w["v"].ravel(), lam0, prm)
+    assert ref["converged"]
+    lam = _dev(lam0)
+    p = tl.params(h=prm.h, rho_alm=prm.rho_alm, rtol=prm.rtol, eps_out=prm.eps_out,
+                  linear_solver=tl.TL_SOLVER_DIRECT)
+    v, _, st = g.newton_step(p, _dev(w["q_n"]), _dev(w["v"]), lam)
+    v = v.cpu().numpy()
+    assert st["converged"] == 1 and st["outer_iters"] == ref["outer_iters"]
+    assert np.linalg.norm(v - ref["v"]) <= 1e-8 * np.linalg.norm(ref["v"])
+    assert np.linalg.norm(C @ (w["q_n"].ravel() + h * v) - bvec) <= prm.eps_out
