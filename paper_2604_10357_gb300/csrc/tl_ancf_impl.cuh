@@ -63,8 +63,13 @@ constexpr int min_blocks() {
   return std::is_same<T, float>::value ? (ET == kBeam ? 2 : 3) : (ET == kBeam ? 1 : 2);
 }
 
-// Per-point record in shared memory (elements of type T).
-template <int ET, bool TAN, bool MR>
+// Per-point record in shared memory (elements of type T).  WG (float64 SVK
+// tangents): the weighted vectors wJ0 c1 g_a and wJ0 c2 g_a and the scalars
+// wJ0 c2, wJ0 alpha are kept too, so that the pair loop runs no multiplies
+// outside its multiply-adds (float64 operations are GB300's scarce resource;
+// the float32 form keeps the smaller record: its pair loop is bound by
+// shared-memory loads, not arithmetic).
+template <int ET, bool TAN, bool MR, bool WG>
 struct Rec {
   static constexpr int NEN = Traits<ET>::NEN;
   static constexpr int oN = 0;
@@ -73,22 +78,34 @@ struct Rec {
   static constexpr int oF = oS + 3 * NEN;
   static constexpr int oB = oF + 9;                         // tangent only
   static constexpr int oW = TAN ? oB + 9 : oF + 9;
-  static constexpr int oA = oW + 1;                         // Mooney-Rivlin tangent rows
+  static constexpr int oX = oW + 1;                         // WG: wJ0 c2, wJ0 alpha
+  static constexpr int oH1 = oX + (WG ? 2 : 0);             // WG: wJ0 c1 g_a
+  static constexpr int oH2 = oH1 + (WG ? 3 * NEN : 0);      // WG: wJ0 c2 g_a
+  static constexpr int oA = oH2 + (WG ? 3 * NEN : 0);       // Mooney-Rivlin tangent rows
   static constexpr int R = oA + (TAN && MR ? 81 : 0);
 };
+
+template <typename T, bool TAN, bool MR>
+__host__ __device__ constexpr bool weighted_g() {
+  return std::is_same<T, double>::value && TAN && !MR;
+}
 
 // Dynamic shared memory: the per-point records, then the staged coefficients
 // (u, v, e0 per coefficient: 9 values) and the element dimensions (4).
 template <typename T, int ET, bool TAN, bool MR>
 constexpr size_t smem_bytes() {
-  return sizeof(T) * ((size_t)Rec<ET, TAN, MR>::R * Cfg<ET>::NQP + 9 * Cfg<ET>::NEN + 4) * Cfg<ET>::EPB;
+  return sizeof(T) * ((size_t)Rec<ET, TAN, MR, weighted_g<T, TAN, MR>()>::R * Cfg<ET>::NQP +
+                      9 * Cfg<ET>::NEN + 4) * Cfg<ET>::EPB;
 }
 
 template <typename T, int ET, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
 __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(Args<T> A) {
   constexpr int NEN = Cfg<ET>::NEN, NQP = Cfg<ET>::NQP, NP = Cfg<ET>::NP, EPB = Cfg<ET>::EPB, NT = Cfg<ET>::NT;
   constexpr bool MR = MAT == TL_MOONEY_RIVLIN;
-  using RC = Rec<ET, DO_TANGENT, MR>;
+  constexpr bool WG = weighted_g<T, DO_TANGENT, MR>();
+  using RC = Rec<ET, DO_TANGENT, MR, WG>;
+  const T c1 = A.alpha * A.mat.lam + (KV ? A.beta * A.mat.lam_d : T(0));
+  const T c2 = A.alpha * A.mat.mu + (KV ? A.beta * A.mat.eta : T(0));
   extern __shared__ unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   T* stg = sm + (size_t)RC::R * NQP * EPB;                  // [el][a][u 3, v 3, e0 3]
@@ -162,12 +179,20 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
     }
     QP<T> s;
     constitutive<T, MAT, KV>(Hm, Fd, A.mat, s, inverted);
+    const T wJ = wq * det;
     for (int a = 0; a < NEN; ++a) {
       const T n0 = rec[RC::oN + 3 * a], n1 = rec[RC::oN + 3 * a + 1], n2 = rec[RC::oN + 3 * a + 2];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         rec[RC::oS + 3 * a + i] = s.S[i][0] * n0 + s.S[i][1] * n1 + s.S[i][2] * n2;
-        if (DO_TANGENT) rec[RC::oG + 3 * a + i] = s.F[i][0] * n0 + s.F[i][1] * n1 + s.F[i][2] * n2;
+        if (DO_TANGENT) {
+          const T gi = s.F[i][0] * n0 + s.F[i][1] * n1 + s.F[i][2] * n2;
+          rec[RC::oG + 3 * a + i] = gi;
+          if (WG) {
+            rec[RC::oH1 + 3 * a + i] = (wJ * c1) * gi;
+            rec[RC::oH2 + 3 * a + i] = (wJ * c2) * gi;
+          }
+        }
       }
     }
 #pragma unroll
@@ -177,8 +202,11 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
         rec[RC::oF + 3 * i + j] = s.F[i][j];
         if (DO_TANGENT) rec[RC::oB + 3 * i + j] = s.B[i][j];
       }
-    const T wJ = wq * det;
     rec[RC::oW] = wJ;
+    if (WG) {
+      rec[RC::oX] = wJ * c2;
+      rec[RC::oX + 1] = wJ * A.alpha;
+    }
     if constexpr (DO_TANGENT && MR) {
       tangent_row<T, MAT, KV, 0>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA);
       tangent_row<T, MAT, KV, 1>(s, A.mat, A.alpha, A.beta, wJ, rec + RC::oA + 27);
@@ -210,8 +238,6 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
 
   // ---- tangent blocks (a <= b) ---------------------------------------------
   if (DO_TANGENT) {
-    const T c1 = A.alpha * A.mat.lam + (KV ? A.beta * A.mat.lam_d : T(0));
-    const T c2 = A.alpha * A.mat.mu + (KV ? A.beta * A.mat.eta : T(0));
     for (int t = threadIdx.x; t < EPB * NP; t += NT) {
       const int el = t / NP, pr = t % NP;
       const int64_t e = ebase + el;
@@ -223,7 +249,25 @@ __global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(
         const T* rec = sm + (size_t)(el * NQP + q) * RC::R;
         const T* na = rec + RC::oN + 3 * a;
         const T* nb = rec + RC::oN + 3 * b;
-        if constexpr (!MR) {
+        if constexpr (WG) {
+          // the same block from the weighted vectors: (wJ c1 g_a)_i g_b,k + (wJ c2 g_b)_i g_a,k + ...
+          const T* ga = rec + RC::oG + 3 * a;
+          const T* gb = rec + RC::oG + 3 * b;
+          const T* h1a = rec + RC::oH1 + 3 * a;
+          const T* h2b = rec + RC::oH2 + 3 * b;
+          const T* sb = rec + RC::oS + 3 * b;
+          const T nn = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
+          const T sn = na[0] * sb[0] + na[1] * sb[1] + na[2] * sb[2];
+          const T w2n = rec[RC::oX] * nn, w3 = rec[RC::oX + 1] * sn;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const T hai = h1a[i], hbi = h2b[i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+              K[i][k] += hai * gb[k] + hbi * ga[k] + w2n * rec[RC::oB + 3 * i + k];
+            K[i][i] += w3;
+          }
+        } else if constexpr (!MR) {
           // [K_ab]_ik = wJ [c1 g_a,i g_b,k + c2 (g_b,i g_a,k + (n_a.n_b) B_ik) + alpha d_ik n_a.S n_b]
           const T wJ = rec[RC::oW];
           const T* ga = rec + RC::oG + 3 * a;
