@@ -1,4 +1,5 @@
-"""Seeded synthetic inputs: T10 box / cylinder meshes, nodal fields, load schedules.
+"""Seeded synthetic inputs: T10 box / cylinder meshes, ANCF beam / shell meshes,
+nodal fields, load schedules.
 
 This module is shared by the CUDA path's tests and benchmark and by the CPU
 oracle's tests. It holds none of the method's arithmetic: it only builds
