@@ -184,6 +184,35 @@ def oracle_step_rate(budget_s=12.0, min_reps=1, nx=10, ny=4, nz=4):
     return reps * m.ne / el, reps, m.ne, el
 
 
+def oracle_ancf_rate(kind, budget_s=6.0, min_reps=1):
+    """Elements/s of the oracle's ANCF Hessian assembly (element force +
+    tangent + CSR values, the assembly pass the GPU arm times) on a bounded
+    sample of the same element kind, material and state recipe: a 64-element
+    beam or a 4 x 4 shell.  Reference geometry and mass are built untimed
+    (precomputation, as on the device)."""
+    from oracle import ancf as oancf
+    from paper_2604_10357_gb300 import inputs
+    if kind == "ancf3243":
+        m, h, curv = inputs.beam_ancf3243(64), 1e-3, 1e-5
+    else:
+        m, h, curv = inputs.shell_ancf3443(4, 4), 5e-4, 0.25
+    rng = np.random.default_rng(1000 + 8)
+    q = inputs.ancf_perturbation(m, inputs.ancf_bend(m, curv), 0.001, rng)
+    v = rng.normal(0.0, 0.01, size=q.shape)
+    v[m.fixed_nodes] = 0.0
+    om = oancf.OracleAncfMesh(kind, m.E0, m.conn, m.dims, [dict(inputs.SVK_7E8)], fixed_nodes=m.fixed_nodes)
+    om.pattern()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        om.hessian_values(q, v, h, 1e12)
+        om.internal_force(q, v, h)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= budget_s:
+            break
+    return reps * m.ne / el, reps, m.ne, el
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -603,7 +632,9 @@ def run_ancf(args):
     Newton steps from rest under the paper's tip loads (beam: F_z = 5,000 N at
     the free end; shell: -500 N spread over the free edge) at the RES0
     resolution, vendor direct solver and the captured PCG graph, inner stop
-    max(1e-4, 1e-8 relative), the paper's eps_in at RES0."""
+    max(1e-4, 1e-8 relative), the paper's eps_in at RES0.  The oracle's
+    assembly rate on a bounded sample of each kind is reported beside the GPU
+    numbers (`cpu_baseline`, skipped with --no-cpu-baseline)."""
     import torch
 
     from paper_2604_10357_gb300 import inputs, tl
@@ -676,6 +707,11 @@ def run_ancf(args):
                                 "frac_fp32_alu": fl * m.ne / (kms * 1e-3) / 1e12 / fp32_alu_peak_tflops(),
                                 "speedup_vs_fp64": res["assembly"]["ms"] / ms}
         g32.close()
+        if not args.no_cpu_baseline:
+            rate, reps, n, el = oracle_ancf_rate(kind)
+            res["cpu_baseline"] = {"kind": "oracle", "value": rate, "unit": "elems/s", "cores": 1,
+                                   "sample": f"{n}-element {kind} of the same recipe, Hessian assembly + force, "
+                                             f"{reps} passes in {el:.1f} s (numpy, one thread)"}
         if args.ancf_no_newton:
             out[kind] = res
             continue
