@@ -3,8 +3,9 @@ Gauss-Legendre rules, the shape functions (textbook closed forms,
 interpolation conditions, derivatives, affine completeness), the reference
 geometry, the zero / rigid / homogeneous-deformation force checks, the
 energy and complex-step derivatives, the exact mass and gravity weights, the
-pattern counts, the paper's printed mesh statistics, and the closed-form
-free fall of one Newton step."""
+pattern counts, the paper's printed mesh statistics, the closed-form free
+fall of one Newton step, and the Euler-Bernoulli deflection of a slender
+cantilever."""
 import os
 
 import numpy as np
@@ -12,7 +13,6 @@ import pytest
 
 from oracle import ancf
 from oracle import element as el
-from oracle import materials as mats
 from oracle import newton as nt
 from paper_2604_10357_gb300 import inputs
 
