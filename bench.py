@@ -8,7 +8,10 @@ first), the clamp-penalty diagonal and the residual g with its norm (float64,
 its mass product in double-float arithmetic when the autotuner picks it).
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent
-replica of the workload (the assembly needs no exchange; weak scaling).
+replica of the workload (the assembly needs no exchange; weak scaling).  At N = 1
+the line also carries the Newton comparison (`newton`), the cost of general
+constraint rows (`constraints`) and the ANCF3243 beam / ANCF3443 shell passes at the
+paper's largest resolutions with their Newton steps (`ancf`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
