@@ -244,3 +244,30 @@ def test_general_constraints_pattern_hessian_and_gradient(tiny):
         vc[r] += 1e-30j
         gcs[r] = om.augmented_cost(vc, q.ravel(), v_n.ravel(), h, None, GRAV, lam, rho).imag / 1e-30
     assert np.abs(g - gcs).max() < 1e-10 * np.abs(g).max()
+
+
+def test_t10_cantilever_bending_matches_beam_theory():
+    """A 2 m cantilever of 0.1 x 0.1 m section (20 x 2 x 2 hexes x 6 = 480 T10,
+    E = 7e8, nu = 0) under a 1 N tip load shared by the tip-face nodes: the
+    linear static tip deflection equals P L^3 / (3 E I) times the Timoshenko
+    shear factor 1 + 6 I / (kappa A L^2) (kappa = 5/6, G = E / 2) within 0.1 %."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    E, Lx, a = 7e8, 2.0, 0.1
+    mat = dict(kind="svk", E=E, nu=0.0, rho0=1000.0, eta_d=0.0, lambda_d=0.0)
+    m = inputs.box_t10(20, 2, 2, Lx, a, a)
+    om = asm.OracleMesh(m.X, m.conn, [mat], fixed_nodes=m.fixed_nodes)
+    Ke = om.element_tangents(m.X, 0 * m.X, 1.0, 0.0)
+    dofs = asm.element_dofs(om.conn)
+    K = sp.coo_matrix((Ke.ravel(), (np.repeat(dofs, 30, axis=1).ravel(), np.tile(dofs, (1, 30)).ravel())),
+                      shape=(3 * m.nn, 3 * m.nn)).tocsr()
+    fixed = om.fixed_dofs
+    free = np.setdiff1d(np.arange(3 * m.nn), fixed)
+    tip = np.nonzero(np.isclose(m.X[:, 0], Lx))[0]
+    f = np.zeros(3 * m.nn)
+    f[3 * tip + 2] = 1.0 / len(tip)
+    u = np.zeros(3 * m.nn)
+    u[free] = spla.spsolve(K[free][:, free].tocsc(), f[free])
+    I, A = a ** 4 / 12, a * a
+    theory = Lx ** 3 / (3 * E * I) * (1.0 + 6.0 * I / (5.0 / 6.0 * A * Lx ** 2))
+    assert abs(u[3 * tip + 2].mean() / theory - 1.0) < 1e-3
