@@ -39,3 +39,20 @@ def values_error(v_gpu, v_ora):
 
 def material_list(w):
     return w["materials"] if "materials" in w else [w["material"]]
+
+
+def first_frequencies(om, nn, nen, k=2):
+    """Smallest natural frequencies of K phi = w^2 M phi (clamps eliminated),
+    K the element tangents at the reference state, M the consistent mass."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    Ke = om.element_tangents(om.X, 0 * om.X, 1.0, 0.0)
+    nd = 3 * nen
+    dofs = (3 * om.conn[:, :, None] + np.arange(3)).reshape(om.conn.shape[0], nd)
+    K = sp.coo_matrix((Ke.ravel(), (np.repeat(dofs, nd, axis=1).ravel(), np.tile(dofs, (1, nd)).ravel())),
+                      shape=(3 * nn, 3 * nn)).tocsr()
+    M = sp.kron(om.mass_matrix(), sp.eye(3)).tocsr()
+    free = np.setdiff1d(np.arange(3 * nn), om.fixed_dofs)
+    w2 = spla.eigsh(K[free][:, free].tocsc(), k=k, M=M[free][:, free].tocsc(), sigma=0.0, which="LM",
+                    return_eigenvectors=False)
+    return np.sqrt(np.sort(w2))

@@ -16,6 +16,8 @@ from oracle import element as el
 from oracle import newton as nt
 from paper_2604_10357_gb300 import inputs
 
+from helpers import first_frequencies
+
 SVK = dict(inputs.SVK_7E8)
 MR = dict(kind="mr", C10=5e5, C01=1e5, kappa=1e8, rho0=1000.0, eta_d=0.0, lambda_d=0.0)
 SVK_KV = dict(SVK, eta_d=1e3, lambda_d=1e3)
@@ -416,3 +418,23 @@ def test_cantilever_bending_matches_euler_bernoulli(kind):
     eb = 4.0 ** 3 / (3 * E * I)
     for d in tip:
         assert abs(d / eb - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_cantilever_first_frequency(kind):
+    """Exact mass with the stiffness: the first bending frequency of a 2 m
+    cantilever (E = 7e8, rho = 2700, nu = 0; beam 0.1 x 0.1 section in 10
+    elements, shell strip 0.2 m wide and 0.1 m thick in 20) is the
+    Euler-Bernoulli 1.8751^2 sqrt(E I / (rho A L^4)) within 0.3 %."""
+    E, rho = 7e8, 2700.0
+    mat = dict(kind="svk", E=E, nu=0.0, rho0=rho, eta_d=0.0, lambda_d=0.0)
+    if kind == ancf.BEAM:
+        m = inputs.beam_ancf3243(10, L=0.2, W=0.1, H=0.1)
+        I, A = 0.1 ** 4 / 12, 0.01
+    else:
+        m = inputs.shell_ancf3443(20, 1, Lx=2.0, Ly=0.2, H=0.1)
+        I, A = 0.2 * 0.1 ** 3 / 12, 0.02
+    om = ancf.OracleAncfMesh(kind, m.E0, m.conn, m.dims, [mat], fixed_nodes=m.fixed_nodes)
+    w_eb = 1.8751040687 ** 2 * np.sqrt(E * I / (rho * A * 2.0 ** 4))
+    w = first_frequencies(om, m.nn, ancf.nen_of(kind), k=1)
+    assert abs(w[0] / w_eb - 1.0) < 3e-3

@@ -8,6 +8,8 @@ from oracle import assembly as asm
 from oracle import newton as nt
 from paper_2604_10357_gb300 import inputs
 
+from helpers import first_frequencies
+
 SVK = dict(kind="svk", E=1e7, nu=0.3, rho0=1000.0)
 MR = dict(kind="mr", C10=5e5, C01=1e5, kappa=1e8, rho0=1000.0)
 GRAV = (0.0, 0.0, -9.81)
@@ -271,3 +273,16 @@ def test_t10_cantilever_bending_matches_beam_theory():
     I, A = a ** 4 / 12, a * a
     theory = Lx ** 3 / (3 * E * I) * (1.0 + 6.0 * I / (5.0 / 6.0 * A * Lx ** 2))
     assert abs(u[3 * tip + 2].mean() / theory - 1.0) < 1e-3
+
+
+def test_t10_cantilever_first_frequency():
+    """The consistent mass with the stiffness: the cantilever's first bending
+    frequency is the Euler-Bernoulli 1.8751^2 sqrt(E I / (rho A L^4)) within
+    0.3 % (shear and rotary inertia lower it by ~0.15 % here)."""
+    E, rho, Lx, a = 7e8, 2700.0, 2.0, 0.1
+    mat = dict(kind="svk", E=E, nu=0.0, rho0=rho, eta_d=0.0, lambda_d=0.0)
+    m = inputs.box_t10(20, 2, 2, Lx, a, a)
+    om = asm.OracleMesh(m.X, m.conn, [mat], fixed_nodes=m.fixed_nodes)
+    w_eb = 1.8751040687 ** 2 * np.sqrt(E * a ** 4 / 12 / (rho * a * a * Lx ** 4))
+    w = first_frequencies(om, m.nn, 10)
+    assert np.all(np.abs(w / w_eb - 1.0) < 3e-3)       # the two transverse directions
