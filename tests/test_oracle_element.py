@@ -232,3 +232,41 @@ def test_linear_stiffness_at_reference_equals_exact_integral():
     # rigid-body null space: 6 zero eigenvalues
     ev = np.linalg.eigvalsh(Kex)
     assert np.sum(np.abs(ev) < 1e-9 * ev.max()) == 6
+
+
+@pytest.mark.parametrize("mat", [SVK_KV, MR_KV], ids=["svk_kv", "mr_kv"])
+def test_kelvin_voigt_geometric_term_at_nonzero_velocity(mat):
+    """The Kelvin-Voigt part of K_t at v != 0: with the viscous stress S_v held
+    at its value, the derivative in x of f_a = sum_q wJ0 (P_el(F) + F S_v) n_a
+    is the hyperelastic tangent plus the geometric term delta_ik n_a.S_v n_b.
+    The oracle's K_t (alpha = 1, beta = 0) must equal that derivative, taken
+    here by complex step through the elastic stress and the frozen S_v, so a
+    wrong sign or factor of the viscous geometric term fails.  The velocity is
+    large enough that the term is ~1e-3 of K (far above the 1e-12 bar)."""
+    rng = np.random.default_rng(26)
+    X, conn, x, v, gradN, wJ0 = _one_element(rng)
+    v = 200.0 * v
+    xe, ve = x[conn], v[conn]
+    K = el.element_tangent(xe, ve, gradN, wJ0, mat, 1.0, 0.0)[0]
+    K0 = el.element_tangent(xe, np.zeros_like(ve), gradN, wJ0, mat, 1.0, 0.0)[0]
+    assert np.abs(K - K0).max() > 1e-4 * np.abs(K).max()          # the term is really exercised
+    F0 = el.kinematics(xe, gradN)
+    _, Sv0 = mats.kv_stress(F0, el.kinematics(ve, gradN), mat["eta_d"], mat["lambda_d"])
+
+    def f_frozen(xc):
+        F = el.kinematics(xc, gradN)
+        P_el, _, _ = mats.elastic_stress_and_tangent(F, mat, want_tangent=False)
+        P = P_el + F @ Sv0
+        return np.einsum("eqiJ,eqaJ,eq->eai", P, gradN, wJ0)
+
+    Kcs = np.zeros((30, 30))
+    for s in range(30):
+        b, k = divmod(s, 3)
+        dx = np.zeros((1, 10, 3), complex)
+        dx[0, b, k] = 1e-30j
+        Kcs[:, s] = f_frozen(xe + dx).imag.reshape(30) / 1e-30
+    assert np.abs(K - Kcs).max() < 1e-12 * np.abs(K).max()
+    # the same term by brute force: K - K_el(v = 0) = sum_q wJ0 delta_ik n_a.S_v n_b
+    geo = np.einsum("eqaJ,eqJL,eqbL,eq->eab", gradN, Sv0, gradN, wJ0)[0]
+    dK = (K - K0).reshape(10, 3, 10, 3)
+    assert np.abs(dK - np.einsum("ab,ik->aibk", geo, np.eye(3))).max() < 1e-9 * np.abs(geo).max()
