@@ -266,8 +266,12 @@ def run_ours(args, rank, world):
         g.assemble_hessian(qd, vd, h, rho, values=values, f_int=f)
         g.eval_residual(prm, qd, vd, vd, f_int=f, g=res, g_norm=gnorm)
 
-    # launch shapes picked by the library's autotuner on this mesh (untimed)
+    # launch shapes picked by the library's autotuner on this mesh (untimed),
+    # then any shape the command line fixes (--shape key=value)
     tune = g.autotune(q, v, h, reps=3) if not args.no_autotune else g.tune_get()
+    if args.shape:
+        g.tune_set(**{k: int(val) for k, val in (kv.split("=") for kv in args.shape)})
+        tune.update(g.tune_get())
 
     for _ in range(args.warmup):
         step(q, v)
@@ -395,10 +399,10 @@ def run_ours(args, rank, world):
                    "material": "SVK E=1e7 nu=0.3 + Kelvin-Voigt 1e3", "h": h,
                    "l2": "no flush: the H values written every step (%.2f GB) exceed L2" % (nnz * vbytes / 1e9),
                    "parallelism": f"replicas x{world}", "pattern_build_s": t_pat,
-                   "launch_shapes": {k: tune[k] for k in ("elem_ws", "elem_occ2", "elem_spread", "elem_prefetch",
-                                                          "elem_xchg", "elem_full_grid", "elem_agg", "spmv_group", "spmv_row",
-                                                          "residual_lanes", "residual_split")},
-                   "launch_shape_ms": {k: tune[k] for k in ("ms_ws", "ms_occ2", "ms_spread", "ms_element",
+                   "launch_shapes": {k: tune[k] for k in ("elem_pair", "elem_ws", "elem_occ2", "elem_spread",
+                                                          "elem_prefetch", "elem_xchg", "elem_full_grid", "elem_agg",
+                                                          "spmv_group", "spmv_row", "residual_lanes", "residual_split")},
+                   "launch_shape_ms": {k: tune[k] for k in ("ms_pair", "ms_ws", "ms_occ2", "ms_spread", "ms_element",
                                                             "ms_agg", "ms_spmv", "ms_spmv_row", "ms_residual",
                                                             "ms_residual_split")}},
         "roofline": roofline,
@@ -782,6 +786,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-constraints", action="store_true", help="skip the general-constraint cost measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--shape", action="append", default=[],
+                    help="fix a launch shape of the element workload after the autotuner (key=value, repeatable)")
     ap.add_argument("--no-ancf", action="store_true", help="skip the ANCF beam / shell measurement")
     ap.add_argument("--ancf-only", action="store_true", help="run only the ANCF measurement and print it")
     ap.add_argument("--ancf-scale", type=float, default=1.0,

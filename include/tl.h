@@ -454,6 +454,13 @@ typedef struct tl_tune_result {
                                  then measured 0.05x a 1e-8 Newton target on a 452k-DOF cantilever under large
                                  rotation (1.65x with absolute displacements) */
   float ms_force[2];          /* measured residual force, float64 and double-float (0: not measured) */
+  int32_t elem_pair;          /* TL_FP32_ELEM tangent passes: 1 = St. Venant-Kirchhoff (+ Kelvin-Voigt)
+                                 segments in the closed-form pair kernel (per node pair and point
+                                 [K_ab]_ik = wJ0 [c1 g_a,i g_b,k + c2 (g_b,i g_a,k + (n_a.n_b) B_ik)
+                                 + alpha delta_ik n_a.S n_b], g = F n, B = F F^T; CSR values through the
+                                 per-tile maps, needs elem_agg; or K_elem); Mooney-Rivlin segments keep
+                                 the generic kernel; default 1 */
+  float ms_pair;              /* fastest measured pair-kernel variant (0: not measured) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["tl_element_f32_ft.cu", "tl_element_f64_ft.cu", "tl_element_f32.cu", "tl_element_f64.cu",
            "tl_api.cu", "tl_pattern.cu", "tl_element.cu", "tl_residual.cu", "tl_solver.cu", "tl_pcg.cu",
            "tl_newton.cu", "tl_mlp.cu", "tl_tune.cu", "tl_tilemap.cu", "tl_element_df.cu",
-           "tl_ancf_beam.cu", "tl_ancf_shell.cu", "tl_ancf_beam_f32.cu", "tl_ancf_shell_f32.cu", "tl_ancf.cu"]
+           "tl_ancf_beam.cu", "tl_ancf_shell.cu", "tl_ancf_beam_f32.cu", "tl_ancf_shell_f32.cu", "tl_ancf.cu",
+           "tl_element_pair.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -84,7 +84,8 @@ struct Args {
   int32_t meta_off;    // byte offset of the second scatter-metadata buffer (warp-specialised kernel)
   int32_t x_alias;     // 1: the exchange buffer overlays the force and tangent arrays (two CTAs per SM)
   int32_t agg;         // 1: per-tile aggregation of shared node pairs (maps below)
-  const int2* agg_slot;        // per tile: CSR position of row 3I and row stride of each distinct pair
+  const int4* agg_slot;        // per tile and unordered pair {P, Q}: CSR positions and row strides of
+                               // the (P, Q) and (Q, P) blocks (the second -1 when P = Q)
   const uint16_t* agg_cptr;    // per tile: first contribution of each pair
   const uint16_t* agg_code;    // per tile: exchange-buffer block (+ transposed flag) of each contribution
   const int32_t* agg_nu;       // per tile: number of distinct pairs
@@ -624,60 +625,49 @@ __device__ __forceinline__ void tangent_xchg_scatter(const Args<float>& A, const
   }
 }
 
-// Aggregated scatter of one tile from the exchange buffer: thread -> distinct
-// node pair u of the tile (consecutive threads, consecutive CSR blocks), the
-// 3x3 block summed over the elements that contribute to it (an upper-triangle
-// block of X, or its transpose for a lower one), then one run of three
-// reductions per row.  Replaces one reduction per element entry by one per
-// entry of the tile.
+// Sum of the contributions of one unordered pair of the tile map: the 3x3
+// block of rows P, columns Q, from upper-triangle blocks of the exchange
+// buffer X (as stored, or transposed when the element's block runs from Q to
+// P), then one run of three reductions per row of (P, Q) and, for P != Q, per
+// row of (Q, P) = (P, Q)^T.
+template <typename CodeAt>
+__device__ __forceinline__ void agg_pair(const Args<float>& A, const float* X, int4 s, int c0, int c1,
+                                         CodeAt code_at) {
+  float v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = 0.0f;
+#pragma unroll 1
+  for (int c = c0; c < c1; ++c) {
+    const int cd = code_at(c);
+    const float* xb = X + (cd & 0x7fff);
+    const int sd = (cd & 0x8000) ? 1 : 3, sk = (cd & 0x8000) ? 3 : 1;   // row / column strides
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[3 * d + k] += xb[d * sd + k * sk];
+  }
+  red_run(A, s.x, v[0], v[1], v[2]);
+  red_run(A, s.x + s.y, v[3], v[4], v[5]);
+  red_run(A, s.x + 2 * s.y, v[6], v[7], v[8]);
+  if (s.z >= 0) {
+    red_run(A, s.z, v[0], v[3], v[6]);
+    red_run(A, s.z + s.w, v[1], v[4], v[7]);
+    red_run(A, s.z + 2 * s.w, v[2], v[5], v[8]);
+  }
+}
+
+// Aggregated scatter of one tile from the exchange buffer, map in global
+// memory: thread -> unordered pair u (consecutive threads, consecutive CSR
+// blocks of the rows P).  One sum per CSR block pair and tile instead of one
+// reduction per element entry.
 __device__ __forceinline__ void tangent_agg_scatter(const Args<float>& A, const float* X, int64_t tile) {
   const int nu = A.agg_nu[tile];
-  const int2* slot = A.agg_slot + tile * kAggCap;
-  const uint16_t* cptr = A.agg_cptr + tile * (kAggCap + 1);
+  const int4* slot = A.agg_slot + tile * kAggCap;
+  const uint16_t* cptr = A.agg_cptr + tile * kAggCptrStride;
   const uint16_t* code = A.agg_code + tile * kAggCap;
-  // the map entries of a thread's next pair are loaded before its current
-  // pair is summed (their global-load latency overlaps the shared-memory sums)
-  int u = threadIdx.x;
-  int2 s = make_int2(0, 0);
-  int c0 = 0, c1 = 0;
-  if (u < nu) {
-    s = slot[u];
-    c0 = cptr[u];
-    c1 = cptr[u + 1];
-  }
 #pragma unroll 1
-  while (u < nu) {
-    const int un = u + (int)blockDim.x;
-    int2 sn = make_int2(0, 0);
-    int c0n = 0, c1n = 0;
-    if (un < nu) {
-      sn = slot[un];
-      c0n = cptr[un];
-      c1n = cptr[un + 1];
-    }
-    float v[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) v[k] = 0.0f;
-    int cd = code[c0];                           // c0 < c1: every pair has a contribution
-#pragma unroll 1
-    for (int c = c0; c < c1; ++c) {
-      const int cdn = c + 1 < c1 ? (int)code[c + 1] : 0;
-      const float* xb = X + (cd & 0x7fff);
-      const int sd = (cd & 0x8000) ? 1 : 3, sk = (cd & 0x8000) ? 3 : 1;   // row / column strides
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) v[3 * d + k] += xb[d * sd + k * sk];
-      cd = cdn;
-    }
-    red_run(A, s.x, v[0], v[1], v[2]);
-    red_run(A, s.x + s.y, v[3], v[4], v[5]);
-    red_run(A, s.x + 2 * s.y, v[6], v[7], v[8]);
-    u = un;
-    s = sn;
-    c0 = c0n;
-    c1 = c1n;
-  }
+  for (int u = threadIdx.x; u < nu; u += (int)blockDim.x)
+    agg_pair(A, X, slot[u], cptr[u], cptr[u + 1], [&](int c) { return (int)code[c]; });
 }
 
 constexpr int kXFloats = 32 * 55 * 9;   // exchange buffer of the FP32 assembly
@@ -1096,6 +1086,11 @@ __global__ void __launch_bounds__(NTW, 1) elem_kernel_ws(Args<float> A, SegTable
   bar_arrive_all(kBarFull);
 }
 
+// The closed-form pair kernel of SVK (+ KV) segments, float32 element form
+// (tl_element_pair.cu): one persistent launch over the segments of S.
+tl_status pair_launch(tl_mesh* m, const Args<float>& A, const SegTable<float>& S, bool kv, bool do_force,
+                      int* counter);
+
 template <typename T, bool DO_FORCE, bool DO_TANGENT>
 tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
                      double mass_scale, double* f, void* values, void* K_elem) {
@@ -1153,6 +1148,10 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   A.agg_cptr = m->agg_cptr;
   A.agg_code = m->agg_code;
   A.agg_nu = m->agg_nu;
+  // float32 tangent passes: SVK segments go to the closed-form pair kernel
+  // (CSR values through the tile maps, or K_elem), in launches of their own
+  const bool pair_mode = std::is_same<T, float>::value && DO_TANGENT && m->tune.elem_pair &&
+                         ((K_elem && !values) || (values && !K_elem && m->tune.elem_agg && m->agg_nu));
   cudaEvent_t t0 = timer_open(m);
   // Segments in groups of at most kMaxSeg, one persistent launch per group.
   // The float32 kernels include an all-materials variant; the float64 ones
@@ -1175,6 +1174,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       const MaterialDev& md = m->mats[sg.mat];
       const int combo = 2 * (md.kind == TL_SVK ? 0 : 1) + (md.kv ? 1 : 0);
       if (!kMixed && combo0 >= 0 && combo != combo0) break;   // next launch starts here
+      if (pair_mode && combo0 >= 0 && (combo < 2) != (combo0 < 2)) break;   // SVK and MR apart
       SegEntry<T>& se = S.s[S.nseg++];
       se.begin = sg.begin;
       se.real_end = sg.end;
@@ -1205,6 +1205,16 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       ++m->launches;
       continue;
     } else {   // the 15-warp kernels (not instantiated for force-only passes)
+    if constexpr (std::is_same<T, float>::value) {
+      if (pair_mode && combo0 < 2) {
+        bool kv = false;
+        for (int j = 0; j < S.nseg; ++j) kv = kv || S.s[j].combo == 1;
+        int* counter = nlaunch < kTileCounters ? m->d_tile_counters + nlaunch : nullptr;
+        ++nlaunch;
+        TL_TRY(pair_launch(m, A, S, kv, DO_FORCE, counter));
+        continue;
+      }
+    }
     void (*kern)(Args<T>, SegTable<T>, int*) = nullptr;
     int threads = NT;
     if constexpr (std::is_same<T, float>::value && DO_TANGENT) {

@@ -17,12 +17,26 @@ namespace tl {
 // segment of the internal element order is padded to a multiple of this.
 constexpr int kTile = 32;
 
-// Capacity of a tile's aggregation map (distinct node-pair blocks and
-// contributions): 32 elements x 100 ordered pairs.
-constexpr int kAggCap = kTile * 100;
+// Capacity of a tile's aggregation map (distinct unordered node pairs and
+// contributions): 32 elements x 55 upper-triangle blocks.
+constexpr int kAggCap = kTile * 55;
+// Row stride of a tile's contribution pointers (kAggCap + 1 used): a multiple
+// of 8 entries, so every tile's row starts on a 16-byte boundary.
+constexpr int kAggCptrStride = kAggCap + 8;
 
 // Tile counters of the persistent element launches (one per launch of a pass).
 constexpr int kTileCounters = 256;
+
+// Offset of the upper-triangle block (a, b), a <= b, of element e in the
+// exchange buffer of the float32 assembly (9 floats per block, row-major
+// [i][k] of K_ab): block rows P and 9 - P of group P hold 11 blocks,
+// (P, P..9) then (9-P, 9-P..9); 55 blocks per element.  The tile maps
+// (tl_tilemap.cu) and every kernel that fills the buffer share this layout.
+__host__ __device__ __forceinline__ int xchg_offset(int e, int a, int b) {
+  const int P = a <= 4 ? a : 9 - a;
+  const int j = a <= 4 ? b - a : b + 1;
+  return e * 495 + P * 99 + j * 9;
+}
 
 // Device-side sticky status bits (tl_sync turns them into tl_status).
 enum : uint32_t { kFlagInverted = 1u, kFlagNonFinite = 2u, kFlagBadIndex = 4u };
@@ -62,6 +76,7 @@ struct Tune {
   int elem_spread = 0;    // element kernels: 1 = tiles in flight spread over the mesh (permuted launch order)
   int pcg_f32 = 1;        // float32 Hessian: 1 = PCG vectors in float32 (dot products float64)
   int elem_agg = 1;       // float32 exchanged assembly: 1 = per-tile aggregation of shared node pairs
+  int elem_pair = 1;      // float32 tangent passes: 1 = closed-form pair kernel for SVK (+ KV) segments
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };
@@ -104,8 +119,8 @@ struct tl_mesh {
   int32_t* d_fixed_diag = nullptr;     // 3 nfixed: CSR position of (r, r)
 
   // per-tile aggregation maps of the float32 assembly (tl_tilemap.cu), built on demand
-  int2* agg_slot = nullptr;       // ntiles x kAggCap
-  uint16_t* agg_cptr = nullptr;   // ntiles x (kAggCap + 1)
+  int4* agg_slot = nullptr;       // ntiles x kAggCap
+  uint16_t* agg_cptr = nullptr;   // ntiles x kAggCptrStride
   uint16_t* agg_code = nullptr;   // ntiles x kAggCap
   int32_t* agg_nu = nullptr;      // ntiles
 

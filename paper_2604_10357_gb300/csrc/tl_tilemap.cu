@@ -3,25 +3,32 @@
 // before the first assembly).
 //
 // The 32 elements of a tile share nodes: in the structured T10 meshes about
-// 44 % of the 3,200 ordered node-pair blocks of a tile repeat a pair that
-// another element of the same tile also adds to.  For each tile the map lists
-// its distinct (row node I, column slot block) pairs, sorted by CSR position,
-// and for each pair the exchange-buffer blocks that contribute to it.  The
-// assembly then sums the contributions of a pair in registers and issues one
-// reduction per CSR entry and tile instead of one per element entry; the
-// lanes of a warp take consecutive pairs, so their reductions fall on
-// neighbouring CSR entries.
+// 44 % of a tile's node-pair blocks repeat a pair that another element of
+// the same tile also adds to.  The Hessian is stored in full, so the block of
+// rows P, columns Q and the block of rows Q, columns P (its transpose) both
+// receive every contribution of the node pair {P, Q}.  For each tile the map
+// lists its distinct unordered node pairs {P <= Q}, sorted by the CSR
+// position of the (P, Q) block, and for each pair the element blocks that
+// contribute to it (upper-triangle blocks of the elements, 55 per element).
+// The assembly sums a pair's contributions once, in registers, and issues
+// one reduction per entry of the (P, Q) block and one per entry of the
+// (Q, P) block per tile, instead of one per element entry; the lanes of a
+// warp take consecutive pairs, so their reductions fall on neighbouring CSR
+// entries.
 //
-// Map of tile t (fixed capacity kAggCap per tile):
-//   agg_nu[t]                 number of distinct pairs U
-//   agg_slot[t][u]            {CSR position of row 3I of pair u, row stride 3 deg(I)}
-//   agg_cptr[t][u], u <= U    first contribution of pair u (agg_cptr[t][U] = count)
+// Map of tile t (fixed capacity kAggCap = 32 x 55 per tile):
+//   agg_nu[t]                 number of distinct unordered pairs U
+//   agg_slot[t][u]            {CSR position of row 3P of block (P, Q), row stride 3 deg(P),
+//                              CSR position of row 3Q of block (Q, P) (-1 when P = Q), 3 deg(Q)}
+//   agg_cptr[t][u], u <= U    first contribution of pair u (agg_cptr[t][U] = count);
+//                             rows of kAggCptrStride entries (16-byte aligned)
 //   agg_code[t][c]            contribution: bits 0-14 the offset of the element's
-//                             upper-triangle block in the exchange buffer, bit 15
-//                             set when the pair is the transposed block
-// Built on the device, one CTA per tile: keys (I << 8 | slot block) with the
-// contribution code as payload, bitonic sort in shared memory, then a block
-// scan over the heads of equal keys.
+//                             upper-triangle block (a <= b) in the exchange buffer,
+//                             bit 15 set when conn[a] = Q (the block is (Q, P)^T)
+// Built on the device, one CTA per tile: keys (P << 8 | slot block of Q in
+// P's row) with the contribution code as payload, bitonic sort in shared
+// memory, then a block scan over the heads of equal keys; the (Q, P)
+// position by a binary search of P in Q's sorted neighbour list.
 #include <algorithm>
 
 #include "tl_internal.cuh"
@@ -31,22 +38,24 @@ namespace tl {
 namespace {
 
 constexpr int kMapThreads = 512;
-constexpr int kKeys = 4096;                  // >= 32 elements x 100 ordered pairs, power of two
+constexpr int kKeys = 2048;                  // >= 32 elements x 55 upper blocks, power of two
 constexpr uint32_t kNoKey = 0xffffffffu;
 static_assert(kAggCap <= kKeys, "tile map capacity");
 
-// Offset of the upper-triangle block (a, b), a <= b, of element e in the
-// exchange buffer: block rows P and 9 - P of warp group P hold 11 blocks of 9
-// floats, (P, P..9) then (9-P, 9-P..9).
-__device__ __forceinline__ int xchg_offset(int e, int a, int b) {
-  const int P = a <= 4 ? a : 9 - a;
-  const int j = a <= 4 ? b - a : b + 1;
-  return e * 495 + P * 99 + j * 9;
+// Upper-triangle block j (0..54) of a 10-node element: (a, b), a <= b, row by row.
+__device__ __forceinline__ void upper_block(int j, int& a, int& b) {
+  a = 0;
+  while (j >= 10 - a) {
+    j -= 10 - a;
+    ++a;
+  }
+  b = a + j;
 }
 
 __global__ void __launch_bounds__(kMapThreads)
     build_tile_maps(const int32_t* conn, const int32_t* user_of, const uint8_t* blk, const int32_t* node_ptr,
-                    int64_t ntiles, int2* agg_slot, uint16_t* agg_cptr, uint16_t* agg_code, int32_t* agg_nu) {
+                    const int32_t* node_col, int64_t ntiles, int4* agg_slot, uint16_t* agg_cptr,
+                    uint16_t* agg_code, int32_t* agg_nu) {
   __shared__ uint32_t key[kKeys];
   __shared__ uint16_t pay[kKeys];
   __shared__ int wsum[kMapThreads / 32];
@@ -61,13 +70,20 @@ __global__ void __launch_bounds__(kMapThreads)
   for (int i = tid; i < kKeys; i += kMapThreads) {
     uint32_t k = kNoKey;
     uint16_t p = 0;
-    if (i < kTile * 100) {
-      const int e = i / 100, ab = i % 100, a = ab / 10, b = ab % 10;
+    if (i < kTile * 55) {
+      const int e = i / 55;
+      int a, b;
+      upper_block(i % 55, a, b);
       const int64_t ge = t * kTile + e;
       if (user_of[ge] >= 0) {
-        const uint32_t I = (uint32_t)conn[ge * 10 + a];
-        k = (I << 8) | blk[ge * 100 + ab];
-        p = (uint16_t)(a <= b ? xchg_offset(e, a, b) : (xchg_offset(e, b, a) | 0x8000));
+        const uint32_t I = (uint32_t)conn[ge * 10 + a], J = (uint32_t)conn[ge * 10 + b];
+        if (I <= J) {
+          k = (I << 8) | blk[ge * 100 + a * 10 + b];
+          p = (uint16_t)xchg_offset(e, a, b);
+        } else {
+          k = (J << 8) | blk[ge * 100 + b * 10 + a];
+          p = (uint16_t)(xchg_offset(e, a, b) | 0x8000);
+        }
       }
     }
     key[i] = k;
@@ -95,7 +111,7 @@ __global__ void __launch_bounds__(kMapThreads)
     }
   }
   // heads of runs of equal keys -> pair index u (block-wide exclusive scan;
-  // thread tid owns entries 8 tid .. 8 tid + 7)
+  // thread tid owns entries kPer tid .. kPer tid + kPer - 1)
   constexpr int kPer = kKeys / kMapThreads;
   int cnt = 0;
   for (int r = 0; r < kPer; ++r) {
@@ -113,8 +129,8 @@ __global__ void __launch_bounds__(kMapThreads)
   int before = 0;
   for (int k = 0; k < w; ++k) before += wsum[k];
   int u = before + incl - cnt;
-  int2* slot = agg_slot + t * kAggCap;
-  uint16_t* cptr = agg_cptr + t * (kAggCap + 1);
+  int4* slot = agg_slot + t * kAggCap;
+  uint16_t* cptr = agg_cptr + t * kAggCptrStride;
   uint16_t* code = agg_code + t * kAggCap;
   for (int r = 0; r < kPer; ++r) {
     const int i = tid * kPer + r;
@@ -122,9 +138,22 @@ __global__ void __launch_bounds__(kMapThreads)
     if (k == kNoKey) break;                    // sorted: the rest are empty too
     code[i] = pay[i];
     if (i == 0 || k != key[i - 1]) {
-      const int I = (int)(k >> 8), b = (int)(k & 0xffu);
-      const int p0 = node_ptr[I], p1 = node_ptr[I + 1];
-      slot[u] = make_int2(9 * p0 + 3 * b, 3 * (p1 - p0));
+      const int P = (int)(k >> 8), b = (int)(k & 0xffu);
+      const int p0 = node_ptr[P], p1 = node_ptr[P + 1];
+      const int Q = node_col[p0 + b];
+      int4 sl = make_int4(9 * p0 + 3 * b, 3 * (p1 - p0), -1, 0);
+      if (Q != P) {
+        int lo = node_ptr[Q], hi = node_ptr[Q + 1] - 1;   // P is in Q's sorted list
+        const int q0 = lo, q1 = hi + 1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (node_col[mid] < P) lo = mid + 1;
+          else hi = mid;
+        }
+        sl.z = 9 * q0 + 3 * (lo - q0);
+        sl.w = 3 * (q1 - q0);
+      }
+      slot[u] = sl;
       cptr[u] = (uint16_t)i;
       ++u;
     }
@@ -152,8 +181,8 @@ tl_status tile_maps_ensure(tl_mesh* m) {
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tile maps need the pattern");
   if (m->nn >= (int64_t(1) << 24)) return fail(m, TL_ERR_INVALID_ARG, "tile maps: more than 2^24 nodes");
   const int64_t ntiles = std::max<int64_t>(m->ne_pad / kTile, 1);
-  if (cudaMalloc(&m->agg_slot, sizeof(int2) * kAggCap * ntiles) != cudaSuccess ||
-      cudaMalloc(&m->agg_cptr, sizeof(uint16_t) * (kAggCap + 1) * ntiles) != cudaSuccess ||
+  if (cudaMalloc(&m->agg_slot, sizeof(int4) * kAggCap * ntiles) != cudaSuccess ||
+      cudaMalloc(&m->agg_cptr, sizeof(uint16_t) * kAggCptrStride * ntiles) != cudaSuccess ||
       cudaMalloc(&m->agg_code, sizeof(uint16_t) * kAggCap * ntiles) != cudaSuccess ||
       cudaMalloc(&m->agg_nu, sizeof(int32_t) * ntiles) != cudaSuccess) {
     tile_maps_free(m);
@@ -162,7 +191,8 @@ tl_status tile_maps_ensure(tl_mesh* m) {
   TL_CUDA(m, cudaMemsetAsync(m->agg_nu, 0, sizeof(int32_t) * ntiles, m->stream));
   if (m->ne_pad >= kTile)
     build_tile_maps<<<(unsigned)ntiles, kMapThreads, 0, m->stream>>>(m->d_conn, m->d_user_of, m->d_blk,
-                                                                     m->d_node_ptr, ntiles, m->agg_slot,
+                                                                     m->d_node_ptr, m->d_node_col, ntiles,
+                                                                     m->agg_slot,
                                                                      m->agg_cptr, m->agg_code, m->agg_nu);
   TL_CUDA(m, cudaGetLastError());
   ++m->launches;

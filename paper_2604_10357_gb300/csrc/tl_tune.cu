@@ -80,18 +80,24 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   // timed with and without the per-tile aggregation (the float64 kernels
   // have neither the exchange nor the prefetch)
   const bool agg_ok = fp32 && m->nn < (int64_t(1) << 24) && tile_maps_ensure(m) == TL_OK;
-  struct V { int pf, xchg, full, ws, occ2, agg; };
+  struct V { int pf, xchg, full, ws, occ2, agg, pair; };
   std::vector<V> variants;
   if (fp32) {
-    variants.push_back({1, 1, 0, 1, 0, 0});          // warp-specialised
-    variants.push_back({0, 1, 0, 0, 1, 0});          // two CTAs per SM
-    if (agg_ok) variants.push_back({0, 1, 0, 0, 1, 1});
+    variants.push_back({1, 1, 0, 1, 0, 0, 0});       // warp-specialised
+    variants.push_back({0, 1, 0, 0, 1, 0, 0});       // two CTAs per SM
+    if (agg_ok) variants.push_back({0, 1, 0, 0, 1, 1, 0});
+    // closed-form pair kernel for SVK segments (with and without the prefetch;
+    // Mooney-Rivlin segments take the two-CTA aggregated kernel)
+    if (agg_ok) {
+      variants.push_back({1, 1, 0, 0, 1, 1, 1});
+      variants.push_back({0, 1, 0, 0, 1, 1, 1});
+    }
   }
   for (int pf = fp32 ? 1 : 0; pf >= 0; --pf)
     for (int xchg = fp32 ? 1 : 0; xchg >= 0; --xchg)
       for (int full = 0; full <= 1; ++full) {
-        variants.push_back({pf, xchg, full, 0, 0, 0});
-        if (xchg && agg_ok) variants.push_back({pf, xchg, full, 0, 0, 1});
+        variants.push_back({pf, xchg, full, 0, 0, 0, 0});
+        if (xchg && agg_ok) variants.push_back({pf, xchg, full, 0, 0, 1, 0});
       }
   float best = 1e30f;
   Tune chosen = saved;
@@ -105,12 +111,15 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
     m->tune.elem_ws = vk.ws;
     m->tune.elem_occ2 = vk.occ2;
     m->tune.elem_agg = vk.agg;
+    m->tune.elem_pair = vk.pair;
     float ms = 0.f;
     st = time_reps(m, reps, [&]() {
       return launch_tangent(m, q_n, v, h, h, 1.0, 1.0 / h, true, f, values, nullptr);
     }, &ms);
     if (st != TL_OK) break;
-    if (vk.agg)
+    if (vk.pair)
+      r.ms_pair = r.ms_pair > 0.f ? std::min(r.ms_pair, ms) : ms;
+    else if (vk.agg)
       r.ms_agg = r.ms_agg > 0.f ? std::min(r.ms_agg, ms) : ms;
     else if (vk.ws)
       r.ms_ws = ms;
@@ -126,6 +135,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
       chosen.elem_ws = vk.ws;
       chosen.elem_occ2 = vk.occ2;
       chosen.elem_agg = vk.agg;
+      chosen.elem_pair = vk.pair;
     }
   }
   // tile order of the fastest element variant: in order or spread
@@ -258,6 +268,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.elem_agg = chosen.elem_agg;
   r.residual_split = chosen.residual_split;
   r.force_split = chosen.force_split;
+  r.elem_pair = chosen.elem_pair;
   if (out) *out = r;
   return TL_OK;
 }
@@ -278,6 +289,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.elem_agg = m->tune.elem_agg;
   r.residual_split = m->tune.residual_split;
   r.force_split = m->tune.force_split;
+  r.elem_pair = m->tune.elem_pair;
   *out = r;
   return TL_OK;
 }
@@ -291,9 +303,10 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
       (in->residual_lanes != 1 && in->residual_lanes != 4) || (in->elem_occ2 != 0 && in->elem_occ2 != 1) ||
       (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1) ||
       (in->spmv_row != 0 && in->spmv_row != 1) || (in->elem_agg != 0 && in->elem_agg != 1) ||
-      (in->residual_split != 0 && in->residual_split != 1) || (in->force_split != 0 && in->force_split != 1))
+      (in->residual_split != 0 && in->residual_split != 1) || (in->force_split != 0 && in->force_split != 1) ||
+      (in->elem_pair != 0 && in->elem_pair != 1))
     return TL_ERR_INVALID_ARG;
-  if (in->elem_agg && m->precision == TL_FP32_ELEM) TL_TRY(tile_maps_ensure(m));
+  if ((in->elem_agg || in->elem_pair) && m->precision == TL_FP32_ELEM) TL_TRY(tile_maps_ensure(m));
   m->tune.spmv_group = in->spmv_group;
   m->tune.elem_prefetch = in->elem_prefetch;
   m->tune.elem_ws = in->elem_ws;
@@ -307,6 +320,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   m->tune.elem_agg = in->elem_agg;
   m->tune.residual_split = in->residual_split;
   m->tune.force_split = in->force_split;
+  m->tune.elem_pair = in->elem_pair;
   m->tune.generation += 1;
   return TL_OK;
 }

@@ -37,8 +37,11 @@ def test_autotune_reports_and_keeps_a_choice():
     assert all(t > 0 for t in rep["ms_element"]) and all(t > 0 for t in rep["ms_spmv"]) and rep["ms_ws"] > 0
     assert rep["ms_occ2"] > 0
     assert rep["ms_agg"] > 0                                 # aggregation timed on the exchanged variants
-    best = min(min(rep["ms_element"]), rep["ms_ws"], rep["ms_occ2"], rep["ms_agg"])
-    if rep["elem_agg"]:
+    assert rep["ms_pair"] > 0                                # the closed-form pair kernel timed too
+    best = min(min(rep["ms_element"]), rep["ms_ws"], rep["ms_occ2"], rep["ms_agg"], rep["ms_pair"])
+    if rep["elem_pair"]:
+        assert rep["ms_pair"] == best
+    elif rep["elem_agg"]:
         assert rep["ms_agg"] == best
     elif rep["elem_ws"]:
         assert rep["ms_ws"] == best
@@ -64,7 +67,7 @@ def test_autotune_reports_and_keeps_a_choice():
     assert rep["force_split"] == 0                            # a precision trade: never chosen by the tuner
     cur = g.tune_get()
     keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes", "elem_occ2",
-            "elem_spread", "spmv_row", "pcg_f32", "elem_agg", "residual_split", "force_split")
+            "elem_spread", "spmv_row", "pcg_f32", "elem_agg", "residual_split", "force_split", "elem_pair")
     assert all(cur[k] == rep[k] for k in keys)
     with pytest.raises(tl.TLError):
         g.tune_set(spmv_group=5)
@@ -84,7 +87,7 @@ def test_every_element_variant_matches_oracle(xchg, full_grid, prefetch, ws, occ
     g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP32_ELEM)
     g.build_pattern(m.fixed_nodes)
     g.tune_set(spmv_group=8, elem_xchg=xchg, elem_full_grid=full_grid, elem_prefetch=prefetch, elem_ws=ws,
-               elem_occ2=occ2, elem_spread=spread, elem_agg=agg)
+               elem_occ2=occ2, elem_spread=spread, elem_agg=agg, elem_pair=0)   # the generic kernel's variants
     h, rho = w["h"], 1e12
     vals = g.assemble_hessian(_dev(w["q_n"]), _dev(w["v"]), h, rho).cpu().numpy().astype(np.float64)
     ref = om.hessian_values(w["q_n"], w["v"], h, rho)
