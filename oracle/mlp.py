@@ -2,8 +2,13 @@
 
 The paper starts every Newton solve from the previous velocity (Algorithm 3,
 v <- v_n).  The learned warm start replaces that start by
-v0 = 2 v_n - v_{n-1} + s_out * MLP(features) on free nodes (0 on clamped
-nodes), a learned correction of linear extrapolation, with a per-node MLP 10 -> 64 -> 64 -> 64 -> 3, tanh hidden layers, linear output.
+v0 = b + s_out * MLP(features) on free nodes (0 on clamped nodes), where b is
+the polynomial extrapolation of the velocity history that is available
+(cubic from v_n .. v_{n-3}; quadratic, linear or v_n itself when fewer
+previous velocities exist): the network learns a correction of it.  Inputs
+per node: the first, second and third backward differences of the velocity
+history (each divided by its own scale) and the fixed flag.
+Per-node MLP 10 -> 64 -> 64 -> 64 -> 3, tanh hidden layers, linear output.
 Weights and activations are bfloat16, products are accumulated in float32.
 
 This module restates the forward pass, the mean-squared-error loss and the
@@ -102,9 +107,49 @@ def adam_step(theta, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return theta
 
 
-def features(q_n, v_n, v_prev, X, fixed_mask, s_v, s_d, s_u):
-    """Per-node inputs: v_n / s_v, (v_n - v_{n-1}) / s_d, (q_n - X) / s_u, fixed
-    flag (the two previous velocities enter as v_n and their difference)."""
-    q_n, v_n, v_prev, X = (np.asarray(a).reshape(-1, 3) for a in (q_n, v_n, v_prev, X))
-    return np.concatenate([v_n / s_v, (v_n - v_prev) / s_d, (q_n - X) / s_u,
-                           np.asarray(fixed_mask, np.float64)[:, None]], axis=1)
+def backward_differences(v_n, v_prev=None, v_prev2=None, v_prev3=None):
+    """First, second and third backward differences of the velocity history at
+    step n (nabla v_n = v_n - v_{n-1}, nabla^2 v_n = v_n - 2 v_{n-1} + v_{n-2},
+    nabla^3 v_n = v_n - 3 v_{n-1} + 3 v_{n-2} - v_{n-3}); a difference that
+    needs a missing velocity is zero.  Each (nn, 3)."""
+    v = [np.asarray(a, dtype=np.float64).reshape(-1, 3) if a is not None else None
+         for a in (v_n, v_prev, v_prev2, v_prev3)]
+    z = np.zeros_like(v[0])
+    d1 = v[0] - v[1] if v[1] is not None else z
+    d2 = v[0] - 2.0 * v[1] + v[2] if v[1] is not None and v[2] is not None else z
+    d3 = (v[0] - 3.0 * v[1] + 3.0 * v[2] - v[3]
+          if v[1] is not None and v[2] is not None and v[3] is not None else z)
+    return d1, d2, d3
+
+
+def extrapolation(v_n, v_prev=None, v_prev2=None, v_prev3=None):
+    """Polynomial extrapolation of the velocity history to step n + 1 (Newton's
+    backward-difference form): v_n + nabla v_n + nabla^2 v_n + nabla^3 v_n, the
+    terms that need a missing velocity dropped (cubic, quadratic, linear or
+    v_n itself)."""
+    d1, d2, d3 = backward_differences(v_n, v_prev, v_prev2, v_prev3)
+    return np.asarray(v_n, dtype=np.float64).reshape(-1, 3) + d1 + d2 + d3
+
+
+def features(v_n, v_prev, v_prev2, v_prev3, fixed_mask, s1, s2, s3):
+    """Per-node inputs: nabla v / s1, nabla^2 v / s2, nabla^3 v / s3 (three
+    columns each) and the fixed flag."""
+    d1, d2, d3 = backward_differences(v_n, v_prev, v_prev2, v_prev3)
+    return np.concatenate([d1 / s1, d2 / s2, d3 / s3, np.asarray(fixed_mask, np.float64)[:, None]], axis=1)
+
+
+def target(v_next, v_n, v_prev, v_prev2, v_prev3, fixed_mask, s_out):
+    """Training target: (v_{n+1} - extrapolation) / s_out, zero on fixed nodes."""
+    t = (np.asarray(v_next, dtype=np.float64).reshape(-1, 3) - extrapolation(v_n, v_prev, v_prev2, v_prev3)) / s_out
+    t[np.asarray(fixed_mask, bool)] = 0.0
+    return t
+
+
+def start_velocity(out, v_n, v_prev, v_prev2, v_prev3, fixed_mask, s_out):
+    """v0 = extrapolation + s_out * out on free nodes, 0 on fixed nodes (out may
+    be None: the extrapolation alone)."""
+    v0 = extrapolation(v_n, v_prev, v_prev2, v_prev3)
+    if out is not None:
+        v0 = v0 + s_out * np.asarray(out, dtype=np.float64).reshape(-1, 3)
+    v0[np.asarray(fixed_mask, bool)] = 0.0
+    return v0

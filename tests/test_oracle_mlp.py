@@ -1,6 +1,10 @@
 """Pins of the warm-start MLP oracle: float64 gradients against central
-finite differences, and the bfloat16 rounding routine against its definition."""
+finite differences, the bfloat16 rounding routine against its definition, and
+the start's inputs and base: backward differences against their closed forms
+on cubic histories, the extrapolation's exactness on polynomial histories, the
+feature layout on a history built by hand, and the start / target round trip."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 
@@ -55,3 +59,69 @@ def test_adam_first_step_is_signed_lr():
     m, v = np.zeros(5, np.float32), np.zeros(5, np.float32)
     mlp.adam_step(theta, g, m, v, 1, lr=0.01)
     assert np.allclose(theta, -0.01 * np.sign(g), rtol=1e-5)
+
+
+def _poly_history(rng, deg, n=5):
+    """Velocities v_k = P(k) at k = 0, -1, -2, -3 for a random polynomial of
+    degree deg per node and component; returns the history, P(1) and the
+    coefficients (a, b, c, d) of a + b t + c t^2 + d t^3."""
+    coef = [rng.normal(size=(n, 3)) if k <= deg else np.zeros((n, 3)) for k in range(4)]
+    P = lambda t: coef[0] + coef[1] * t + coef[2] * t ** 2 + coef[3] * t ** 3   # noqa: E731
+    return [P(0.0), P(-1.0), P(-2.0), P(-3.0)], P(1.0), coef
+
+
+def test_backward_differences_of_a_cubic():
+    """For P(t) = a + b t + c t^2 + d t^3 sampled at t = 0, -1, -2, -3:
+    nabla P = b - c + d, nabla^2 P = 2c - 6d, nabla^3 P = 6d."""
+    rng = np.random.default_rng(41)
+    hist, _, (a, b, c, d) = _poly_history(rng, 3)
+    d1, d2, d3 = mlp.backward_differences(*hist)
+    assert np.allclose(d1, b - c + d, rtol=0, atol=1e-12)
+    assert np.allclose(d2, 2 * c - 6 * d, rtol=0, atol=1e-12)
+    assert np.allclose(d3, 6 * d, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_extrapolation_is_exact_for_polynomial_histories(deg):
+    """With the deg + 1 most recent velocities of a polynomial history of
+    degree deg, the extrapolation reproduces P(1) (Newton's backward-difference
+    formula); with all four it is exact for every degree <= 3."""
+    rng = np.random.default_rng(42 + deg)
+    hist, nxt, _ = _poly_history(rng, deg)
+    partial = hist[:deg + 1] + [None] * (3 - deg)
+    assert np.allclose(mlp.extrapolation(*partial), nxt, rtol=0, atol=1e-11)
+    assert np.allclose(mlp.extrapolation(*hist), nxt, rtol=0, atol=1e-11)
+    if deg >= 1:   # one velocity fewer than the degree needs: not exact
+        short = hist[:deg] + [None] * (4 - deg)
+        assert np.abs(mlp.extrapolation(*short) - nxt).max() > 1e-3
+
+
+def test_features_layout_on_a_hand_built_history():
+    """Two nodes, velocities chosen by hand: node 0's velocity has the constant
+    second difference (2, 0, -1) from v_{n-3} = (1, 1, 1) on; node 1 is fixed
+    and at rest.  Columns: nabla v / s1, nabla^2 v / s2, nabla^3 v / s3, flag."""
+    v3 = np.array([[1.0, 1.0, 1.0], [0.0, 0.0, 0.0]])
+    v2 = np.array([[3.0, 1.0, 0.0], [0.0, 0.0, 0.0]])
+    v1 = np.array([[7.0, 1.0, -2.0], [0.0, 0.0, 0.0]])
+    v0 = np.array([[13.0, 1.0, -5.0], [0.0, 0.0, 0.0]])
+    f = mlp.features(v0, v1, v2, v3, np.array([False, True]), 2.0, 0.5, 4.0)
+    expect = np.array([[3.0, 0.0, -1.5, 4.0, 0.0, -2.0, 0.0, 0.0, 0.0, 0.0],
+                       [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
+    assert np.array_equal(f, expect)
+    # missing history: the differences that need it are zero
+    f2 = mlp.features(v0, v1, None, None, np.array([False, True]), 2.0, 0.5, 4.0)
+    assert np.array_equal(f2[:, 3:9], np.zeros((2, 6))) and np.array_equal(f2[:, :3], expect[:, :3])
+
+
+def test_start_velocity_round_trip_and_fixed_nodes():
+    """The start built from the exact target reproduces v_{n+1} on free nodes;
+    fixed nodes start at rest whatever the network says."""
+    rng = np.random.default_rng(43)
+    hist = [rng.normal(size=(6, 3)) for _ in range(4)]
+    v_next = rng.normal(size=(6, 3))
+    fixed = np.array([True, False, False, True, False, False])
+    t = mlp.target(v_next, *hist, fixed, 0.25)
+    v0 = mlp.start_velocity(t, *hist, fixed, 0.25)
+    assert np.allclose(v0[~fixed], v_next[~fixed], rtol=0, atol=1e-12)
+    assert np.array_equal(v0[fixed], np.zeros((2, 3))) and np.array_equal(t[fixed], np.zeros((2, 3)))
+    assert np.array_equal(mlp.start_velocity(rng.normal(size=(6, 3)), *hist, fixed, 3.0)[fixed], np.zeros((2, 3)))
