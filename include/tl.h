@@ -492,17 +492,35 @@ tl_status tl_mlp_mse_grad(const float* out, const float* target, const float* we
 tl_status tl_mlp_adam(float* master, uint16_t* params, const float* grads, float* m1, float* m2,
                       int64_t n, float lr, float beta1, float beta2, float eps, int32_t step,
                       void* stream);
-/* feats[nn][10] = (v_n/s_v, (v_n - v_prev)/s_d, (q_n - X)/s_u, fixed flag): the two
- * previous velocities enter as v_n and their difference; v_prev NULL -> difference 0. */
-tl_status tl_mlp_features(tl_mesh* m, const double* q_n, const double* v_n, const double* v_prev,
-                          double s_v, double s_d, double s_u, float* feats);
-/* v_init = 2 v_n - v_prev + s_out * MLP(features) on free nodes, 0 on clamped
- * nodes: the network corrects the linear extrapolation of the two previous
- * velocities.  params NULL: extrapolation only (work unused); v_prev NULL:
- * v_n instead of the extrapolation.  work: 13*nn float32 scratch (device). */
-tl_status tl_warm_start(tl_mesh* m, const uint16_t* params, const double* q_n, const double* v_n,
-                        const double* v_prev, double s_v, double s_d, double s_u, double s_out,
-                        float* work, double* v_init);
+/* The start's inputs per node: feats[nn][10] = ((nabla v_n / s1, nabla^2 v_n / s2,
+ * nabla^3 v_n / s3) / r_I, fixed flag), the backward differences of the velocity
+ * history v_n, v_prev = v_{n-1}, v_prev2 = v_{n-2}, v_prev3 = v_{n-3} (device, 3*nn
+ * float64 each) formed in float64, scaled, divided by r_I, the norm of node I's nine
+ * scaled differences (0 where r_I = 0), and rounded to float32.  A NULL history
+ * velocity (and every older one) is not available: the differences that need it are
+ * 0.  s1, s2, s3 > 0 (else TL_ERR_INVALID_ARG).  Asynchronous on the handle's stream. */
+tl_status tl_mlp_features(tl_mesh* m, const double* v_n, const double* v_prev, const double* v_prev2,
+                          const double* v_prev3, double s1, double s2, double s3, float* feats);
+/* v_init = b + s_out r_I MLP(features) on free nodes, 0 on clamped nodes, where
+ * b = v_n + nabla v_n + nabla^2 v_n + nabla^3 v_n is the polynomial extrapolation
+ * of the available history (cubic with four velocities; quadratic, linear or v_n
+ * itself with fewer) and r_I the node scale of tl_mlp_features: the network learns
+ * a correction of b.  params NULL: b only (work and scales unused).  work: 13*nn
+ * float32 device scratch (features and outputs). */
+tl_status tl_warm_start(tl_mesh* m, const uint16_t* params, const double* v_n, const double* v_prev,
+                        const double* v_prev2, const double* v_prev3, double s1, double s2, double s3,
+                        double s_out, float* work, double* v_init);
+/* The training target target[nn][3] = (v_next - b) / (s_out r_I) (float64, then
+ * float32), 0 on clamped nodes and where r_I = 0; b and r_I as in tl_warm_start.
+ * s1, s2, s3, s_out > 0. */
+tl_status tl_mlp_target(tl_mesh* m, const double* v_next, const double* v_n, const double* v_prev,
+                        const double* v_prev2, const double* v_prev3, double s1, double s2, double s3,
+                        double s_out, float* target);
+/* out[c] += sum_i x[i][c]^2 (float64 accumulation) for the ncol (1..16) columns of
+ * the row-major float32 array x[n][ncol] (device): the statistics that set the
+ * input and output scales.  out is a device array of ncol doubles (zero it
+ * first).  Asynchronous on stream. */
+tl_status tl_mlp_col_sumsq(const float* x, int64_t n, int32_t ncol, double* out, void* stream);
 
 /* Wait for the handle's stream and return the first sticky device-side error
  * (TL_ERR_INVERTED, TL_ERR_NONFINITE) raised since the last tl_sync, then

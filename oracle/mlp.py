@@ -2,12 +2,14 @@
 
 The paper starts every Newton solve from the previous velocity (Algorithm 3,
 v <- v_n).  The learned warm start replaces that start by
-v0 = b + s_out * MLP(features) on free nodes (0 on clamped nodes), where b is
-the polynomial extrapolation of the velocity history that is available
+v0 = b + s_out r_I MLP(features) on free nodes (0 on clamped nodes), where b
+is the polynomial extrapolation of the velocity history that is available
 (cubic from v_n .. v_{n-3}; quadratic, linear or v_n itself when fewer
 previous velocities exist): the network learns a correction of it.  Inputs
 per node: the first, second and third backward differences of the velocity
-history (each divided by its own scale) and the fixed flag.
+history, each divided by its own scale, the nine divided by their norm r_I
+(so the map does not depend on the amplitude of the motion), and the fixed
+flag.
 Per-node MLP 10 -> 64 -> 64 -> 64 -> 3, tanh hidden layers, linear output.
 Weights and activations are bfloat16, products are accumulated in float32.
 
@@ -131,25 +133,42 @@ def extrapolation(v_n, v_prev=None, v_prev2=None, v_prev3=None):
     return np.asarray(v_n, dtype=np.float64).reshape(-1, 3) + d1 + d2 + d3
 
 
-def features(v_n, v_prev, v_prev2, v_prev3, fixed_mask, s1, s2, s3):
-    """Per-node inputs: nabla v / s1, nabla^2 v / s2, nabla^3 v / s3 (three
-    columns each) and the fixed flag."""
+def node_scale(v_n, v_prev, v_prev2, v_prev3, s1, s2, s3):
+    """r_I = || (nabla v / s1, nabla^2 v / s2, nabla^3 v / s3) || per node (the
+    9 scaled differences of node I): the network sees the history divided by
+    it and its correction is multiplied by it, so the learned map does not
+    depend on the amplitude of the motion (the extrapolation error is a
+    degree-one homogeneous function of the history)."""
     d1, d2, d3 = backward_differences(v_n, v_prev, v_prev2, v_prev3)
-    return np.concatenate([d1 / s1, d2 / s2, d3 / s3, np.asarray(fixed_mask, np.float64)[:, None]], axis=1)
+    return np.sqrt(np.sum((d1 / s1) ** 2 + (d2 / s2) ** 2 + (d3 / s3) ** 2, axis=1))
 
 
-def target(v_next, v_n, v_prev, v_prev2, v_prev3, fixed_mask, s_out):
-    """Training target: (v_{n+1} - extrapolation) / s_out, zero on fixed nodes."""
-    t = (np.asarray(v_next, dtype=np.float64).reshape(-1, 3) - extrapolation(v_n, v_prev, v_prev2, v_prev3)) / s_out
+def features(v_n, v_prev, v_prev2, v_prev3, fixed_mask, s1, s2, s3):
+    """Per-node inputs: (nabla v / s1, nabla^2 v / s2, nabla^3 v / s3) / r_I
+    (three columns each; zero where r_I = 0) and the fixed flag."""
+    d1, d2, d3 = backward_differences(v_n, v_prev, v_prev2, v_prev3)
+    r = node_scale(v_n, v_prev, v_prev2, v_prev3, s1, s2, s3)
+    inv = np.where(r > 0.0, 1.0 / np.where(r > 0.0, r, 1.0), 0.0)[:, None]
+    return np.concatenate([d1 / s1 * inv, d2 / s2 * inv, d3 / s3 * inv,
+                           np.asarray(fixed_mask, np.float64)[:, None]], axis=1)
+
+
+def target(v_next, v_n, v_prev, v_prev2, v_prev3, fixed_mask, s1, s2, s3, s_out):
+    """Training target: (v_{n+1} - extrapolation) / (s_out r_I), zero on fixed
+    nodes and where r_I = 0."""
+    r = node_scale(v_n, v_prev, v_prev2, v_prev3, s1, s2, s3)
+    e = np.asarray(v_next, dtype=np.float64).reshape(-1, 3) - extrapolation(v_n, v_prev, v_prev2, v_prev3)
+    t = np.where(r[:, None] > 0.0, e / (s_out * np.where(r > 0.0, r, 1.0))[:, None], 0.0)
     t[np.asarray(fixed_mask, bool)] = 0.0
     return t
 
 
-def start_velocity(out, v_n, v_prev, v_prev2, v_prev3, fixed_mask, s_out):
-    """v0 = extrapolation + s_out * out on free nodes, 0 on fixed nodes (out may
-    be None: the extrapolation alone)."""
+def start_velocity(out, v_n, v_prev, v_prev2, v_prev3, fixed_mask, s1, s2, s3, s_out):
+    """v0 = extrapolation + s_out r_I out on free nodes, 0 on fixed nodes (out
+    may be None: the extrapolation alone)."""
     v0 = extrapolation(v_n, v_prev, v_prev2, v_prev3)
     if out is not None:
-        v0 = v0 + s_out * np.asarray(out, dtype=np.float64).reshape(-1, 3)
+        r = node_scale(v_n, v_prev, v_prev2, v_prev3, s1, s2, s3)
+        v0 = v0 + s_out * r[:, None] * np.asarray(out, dtype=np.float64).reshape(-1, 3)
     v0[np.asarray(fixed_mask, bool)] = 0.0
     return v0

@@ -3,8 +3,13 @@
 // accumulation, its forward and backward passes, the MSE loss gradient and
 // the Adam update, all as device kernels.  The paper has no counterpart (it
 // starts Newton from v_n, Algorithm 3); the network predicts the start
-// v0 = 2 v_n - v_{n-1} + s_out * MLP(features) on free nodes: a learned
-// correction of the linear extrapolation of the two previous velocities.
+// v0 = b + s_out r_I MLP(features) on free nodes, where b is the polynomial
+// extrapolation of the velocity history (Newton's backward-difference form
+// v_n + nabla v_n + nabla^2 v_n + nabla^3 v_n: cubic from v_n .. v_{n-3}, lower
+// order when fewer previous velocities are given): a learned correction of
+// it.  Inputs: the three backward differences, each over its own scale, the
+// nine divided by their norm r_I (the map then does not depend on the
+// amplitude of the motion), and the fixed flag.
 //
 // Layout of the bf16 parameter vector (9219 entries): W1 (64x10), b1 (64),
 // W2 (64x64), b2 (64), W3 (64x64), b3 (64), W4 (3x64), b4 (3).
@@ -14,6 +19,8 @@
 // are reduced over the block's samples in shared memory and added to the
 // global gradient once per block.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "tl_internal.cuh"
 
@@ -186,34 +193,128 @@ __global__ void adam_kernel(float* master, uint16_t* P, const float* g, float* m
   P[i] = bf_bits(th);
 }
 
-// inputs: v_n / s_v, (v_n - v_prev) / s_d, (q_n - X) / s_u, fixed flag.  The
-// two previous velocities enter as v_n and their difference: in bfloat16 the
-// difference of two nearby velocities would be lost.
-__global__ void features_kernel(const double* q_n, const double* v_n, const double* v_prev, const double* X,
-                                const int32_t* fixed_of_node, int64_t nn, double inv_sv, double inv_sd,
-                                double inv_su, float* feats) {
+// Backward differences of the velocity history of DOF r (float64): a
+// difference that needs a missing velocity (NULL) is zero.
+struct Diffs {
+  double d1, d2, d3;
+};
+__device__ __forceinline__ Diffs history_diffs(const double* v_n, const double* v1, const double* v2,
+                                               const double* v3, int64_t r) {
+  Diffs d{0.0, 0.0, 0.0};
+  if (!v1) return d;
+  const double a = v_n[r], b = v1[r];
+  d.d1 = a - b;
+  if (!v2) return d;
+  const double c = v2[r];
+  d.d2 = a - 2.0 * b + c;
+  if (!v3) return d;
+  d.d3 = a - 3.0 * b + 3.0 * c - v3[r];
+  return d;
+}
+
+// r_I = || (nabla v / s1, nabla^2 v / s2, nabla^3 v / s3) || over the 9
+// scaled differences of node I (float64); the inputs are divided by it and
+// the correction multiplied by it, so the learned map does not depend on the
+// amplitude of the motion.
+__device__ __forceinline__ double node_scale(const Diffs (&x)[3], double inv1, double inv2, double inv3) {
+  double r2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double a = x[d].d1 * inv1, b = x[d].d2 * inv2, c = x[d].d3 * inv3;
+    r2 += a * a + b * b + c * c;
+  }
+  return sqrt(r2);
+}
+
+// inputs: (nabla v / s1, nabla^2 v / s2, nabla^3 v / s3) / r_I (float64,
+// then float32; zero where r_I = 0), fixed flag
+__global__ void features_kernel(const double* v_n, const double* v1, const double* v2, const double* v3,
+                                const int32_t* fixed_of_node, int64_t nn, double inv1, double inv2, double inv3,
+                                float* feats) {
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nn) return;
+  Diffs x[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = history_diffs(v_n, v1, v2, v3, 3 * I + d);
+  const double r = node_scale(x, inv1, inv2, inv3);
+  const double ir = r > 0.0 ? 1.0 / r : 0.0;
   float* f = feats + 10 * I;
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int64_t r = 3 * I + d;
-    f[d] = float(v_n[r] * inv_sv);
-    f[3 + d] = float((v_prev ? v_n[r] - v_prev[r] : 0.0) * inv_sd);
-    f[6 + d] = float((q_n[r] - X[r]) * inv_su);
+    f[d] = float(x[d].d1 * inv1 * ir);
+    f[3 + d] = float(x[d].d2 * inv2 * ir);
+    f[6 + d] = float(x[d].d3 * inv3 * ir);
   }
   f[9] = fixed_of_node[I] >= 0 ? 1.0f : 0.0f;
 }
 
-// v_init = 2 v_n - v_prev (+ s_out * out), 0 on clamped nodes; out may be null.
-__global__ void apply_kernel(const float* out, const double* v_n, const double* v_prev,
-                             const int32_t* fixed_of_node, int64_t nn, double s_out, double* v_init) {
+// v_init = b + s_out r_I out on free nodes (out may be null), 0 on clamped nodes
+__global__ void apply_kernel(const float* out, const double* v_n, const double* v1, const double* v2,
+                             const double* v3, const int32_t* fixed_of_node, int64_t nn, double inv1, double inv2,
+                             double inv3, double s_out, double* v_init) {
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nn) return;
   const bool fixed = fixed_of_node[I] >= 0;
+  Diffs x[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = history_diffs(v_n, v1, v2, v3, 3 * I + d);
+  const double sr = out ? s_out * node_scale(x, inv1, inv2, inv3) : 0.0;
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int64_t r = 3 * I + d;
-    const double base = v_prev ? 2.0 * v_n[r] - v_prev[r] : v_n[r];
-    v_init[r] = fixed ? 0.0 : base + (out ? s_out * double(out[r]) : 0.0);
+    const double base = v_n[r] + x[d].d1 + x[d].d2 + x[d].d3;
+    v_init[r] = fixed ? 0.0 : base + (out ? sr * double(out[r]) : 0.0);
+  }
+}
+
+// target = (v_next - b) / (s_out r_I) on free nodes (float32), 0 on clamped
+// nodes and where r_I = 0
+__global__ void target_kernel(const double* v_next, const double* v_n, const double* v1, const double* v2,
+                              const double* v3, const int32_t* fixed_of_node, int64_t nn, double inv1, double inv2,
+                              double inv3, double s_out, float* target) {
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  Diffs x[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = history_diffs(v_n, v1, v2, v3, 3 * I + d);
+  const double r = node_scale(x, inv1, inv2, inv3);
+  const bool zero = fixed_of_node[I] >= 0 || !(r > 0.0);
+  const double inv = zero ? 0.0 : 1.0 / (s_out * r);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t k = 3 * I + d;
+    target[k] = zero ? 0.0f : float((v_next[k] - (v_n[k] + x[d].d1 + x[d].d2 + x[d].d3)) * inv);
+  }
+}
+
+// out[c] += sum_i x[i][c]^2 for c < ncol <= 16: per-thread partial sums over
+// a grid-stride range, a block reduction per column, one float64 atomic per
+// column and block
+constexpr int kSumsqMaxCol = 16;
+__global__ void col_sumsq_kernel(const float* x, int64_t n, int ncol, double* out) {
+  __shared__ double red[kSumsqMaxCol][8];
+  double acc[kSumsqMaxCol];
+#pragma unroll
+  for (int c = 0; c < kSumsqMaxCol; ++c) acc[c] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int c = 0; c < kSumsqMaxCol; ++c)
+      if (c < ncol) {
+        const double v = x[i * ncol + c];
+        acc[c] += v * v;
+      }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < kSumsqMaxCol; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[c][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < ncol) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[threadIdx.x][k];
+    atomicAdd(&out[threadIdx.x], v);
   }
 }
 
@@ -269,38 +370,66 @@ tl_status tl_mlp_adam(float* master, uint16_t* params, const float* grads, float
   return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ERR_CUDA;
 }
 
-tl_status tl_mlp_features(tl_mesh* m, const double* q_n, const double* v_n, const double* v_prev, double s_v,
-                          double s_d, double s_u, float* feats) {
-  if (!m || !q_n || !v_n || !feats || !(s_v > 0.0) || !(s_d > 0.0) || !(s_u > 0.0)) return TL_ERR_INVALID_ARG;
+tl_status tl_mlp_features(tl_mesh* m, const double* v_n, const double* v_prev, const double* v_prev2,
+                          const double* v_prev3, double s1, double s2, double s3, float* feats) {
+  if (!m || !v_n || !feats || !(s1 > 0.0) || !(s2 > 0.0) || !(s3 > 0.0)) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
-  features_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(q_n, v_n, v_prev, m->d_X,
-                                                                         m->d_fixed_of_node, m->nn, 1.0 / s_v,
-                                                                         1.0 / s_d, 1.0 / s_u, feats);
+  features_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(
+      v_n, v_prev, v_prev ? v_prev2 : nullptr, v_prev && v_prev2 ? v_prev3 : nullptr, m->d_fixed_of_node, m->nn,
+      1.0 / s1, 1.0 / s2, 1.0 / s3, feats);
   TL_CUDA(m, cudaGetLastError());
   ++m->launches;
   return TL_OK;
 }
 
-tl_status tl_warm_start(tl_mesh* m, const uint16_t* params, const double* q_n, const double* v_n,
-                        const double* v_prev, double s_v, double s_d, double s_u, double s_out, float* work,
-                        double* v_init) {
-  if (!m || !q_n || !v_n || !v_init || (params && !work)) return TL_ERR_INVALID_ARG;
+tl_status tl_warm_start(tl_mesh* m, const uint16_t* params, const double* v_n, const double* v_prev,
+                        const double* v_prev2, const double* v_prev3, double s1, double s2, double s3,
+                        double s_out, float* work, double* v_init) {
+  if (!m || !v_n || !v_init || (params && !work)) return TL_ERR_INVALID_ARG;
   if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  const double* v2 = v_prev ? v_prev2 : nullptr;
+  const double* v3 = v2 ? v_prev3 : nullptr;
   float* out = nullptr;
   if (params) {
     float* feats = work;
     out = work + 10 * m->nn;
-    tl_status s = tl_mlp_features(m, q_n, v_n, v_prev, s_v, s_d, s_u, feats);
+    tl_status s = tl_mlp_features(m, v_n, v_prev, v2, v3, s1, s2, s3, feats);
     if (s != TL_OK) return s;
     s = tl_mlp_forward(params, feats, m->nn, out, nullptr, m->stream);
     if (s != TL_OK) return fail(m, s, "MLP forward launch failed");
     ++m->launches;
   }
-  apply_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(out, v_n, v_prev, m->d_fixed_of_node, m->nn,
-                                                                      s_out, v_init);
+  if (params && !(s1 > 0.0 && s2 > 0.0 && s3 > 0.0)) return TL_ERR_INVALID_ARG;
+  apply_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(
+      out, v_n, v_prev, v2, v3, m->d_fixed_of_node, m->nn, params ? 1.0 / s1 : 0.0, params ? 1.0 / s2 : 0.0,
+      params ? 1.0 / s3 : 0.0, s_out, v_init);
   TL_CUDA(m, cudaGetLastError());
   ++m->launches;
   return TL_OK;
+}
+
+tl_status tl_mlp_target(tl_mesh* m, const double* v_next, const double* v_n, const double* v_prev,
+                        const double* v_prev2, const double* v_prev3, double s1, double s2, double s3,
+                        double s_out, float* target) {
+  if (!m || !v_next || !v_n || !target || !(s_out > 0.0) || !(s1 > 0.0) || !(s2 > 0.0) || !(s3 > 0.0))
+    return TL_ERR_INVALID_ARG;
+  if (!m->have_pattern) return fail(m, TL_ERR_STATE, "tl_build_pattern must come first");
+  const double* v2 = v_prev ? v_prev2 : nullptr;
+  const double* v3 = v2 ? v_prev3 : nullptr;
+  target_kernel<<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(v_next, v_n, v_prev, v2, v3,
+                                                                       m->d_fixed_of_node, m->nn, 1.0 / s1,
+                                                                       1.0 / s2, 1.0 / s3, s_out, target);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
+  return TL_OK;
+}
+
+tl_status tl_mlp_col_sumsq(const float* x, int64_t n, int32_t ncol, double* out, void* stream) {
+  if (!x || !out || n < 0 || ncol < 1 || ncol > kSumsqMaxCol) return TL_ERR_INVALID_ARG;
+  if (n == 0) return TL_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 1024);
+  col_sumsq_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, n, ncol, out);
+  return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -112,8 +112,10 @@ SIGNATURES = {
     "tl_mlp_mse_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "tl_mlp_adam": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
                               C.c_int32, _P]),
-    "tl_mlp_features": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P]),
-    "tl_warm_start": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
+    "tl_mlp_features": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P]),
+    "tl_warm_start": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
+    "tl_mlp_target": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_double, _P]),
+    "tl_mlp_col_sumsq": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P]),
     "tl_autotune": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, _P]),
     "tl_tune_get": (C.c_int, [_P, _P]),
     "tl_tune_set": (C.c_int, [_P, _P]),
@@ -229,6 +231,13 @@ def mlp_mse_grad(out, target, weight, dout, loss):
     lib = load_library()
     _chk(lib.tl_mlp_mse_grad(_ptr(out), _ptr(target), _ptr(weight), out.shape[0], _ptr(dout), _ptr(loss),
                              _stream_ptr()), "tl_mlp_mse_grad")
+
+
+def mlp_col_sumsq(x, out):
+    """out[c] += sum_i x[i, c]^2 (float64) for a float32 CUDA tensor x of shape (n, ncol)."""
+    lib = load_library()
+    _chk(lib.tl_mlp_col_sumsq(_ptr(x), x.shape[0], x.shape[1], _ptr(out), _stream_ptr()), "tl_mlp_col_sumsq")
+    return out
 
 
 def mlp_adam(master, params_bf16, grads, m1, m2, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -451,21 +460,37 @@ class Mesh:
             raise TLError(rc, self.lib.tl_last_error(self.h).decode())
         return v_out, q_out, stats
 
-    def mlp_features(self, q_n, v_n, v_prev, s_v, s_d, s_u, feats=None):
+    def mlp_features(self, hist, scales, feats=None):
+        """tl_mlp_features: hist = (v_n, v_{n-1}, v_{n-2}, v_{n-3}) (None for a missing
+        velocity), scales = (s1, s2, s3)."""
         torch = self._torch
         feats = torch.empty(self.nn, 10, dtype=torch.float32, device="cuda") if feats is None else feats
-        self._check(self.lib.tl_mlp_features(self.h, _ptr(q_n), _ptr(v_n), _ptr(v_prev), float(s_v), float(s_d),
-                                             float(s_u), _ptr(feats)))
+        h = list(hist) + [None] * (4 - len(hist))
+        self._check(self.lib.tl_mlp_features(self.h, _ptr(h[0]), _ptr(h[1]), _ptr(h[2]), _ptr(h[3]),
+                                             float(scales[0]), float(scales[1]), float(scales[2]), _ptr(feats)))
         return feats
 
-    def warm_start(self, params_bf16, q_n, v_n, v_prev, s_v, s_d, s_u, s_out, work=None, v_init=None):
+    def mlp_target(self, v_next, hist, scales, s_out, target=None):
+        """tl_mlp_target: (v_next - extrapolation of hist) / (s_out r_I), float32 (nn, 3)."""
+        torch = self._torch
+        target = torch.empty(self.nn, 3, dtype=torch.float32, device="cuda") if target is None else target
+        h = list(hist) + [None] * (4 - len(hist))
+        self._check(self.lib.tl_mlp_target(self.h, _ptr(v_next), _ptr(h[0]), _ptr(h[1]), _ptr(h[2]), _ptr(h[3]),
+                                           float(scales[0]), float(scales[1]), float(scales[2]), float(s_out),
+                                           _ptr(target)))
+        return target
+
+    def warm_start(self, params_bf16, hist, scales=(1.0, 1.0, 1.0), s_out=0.0, work=None, v_init=None):
+        """tl_warm_start: hist = (v_n, v_{n-1}, v_{n-2}, v_{n-3}) (None for a missing
+        velocity); params None -> the extrapolation alone."""
         torch = self._torch
         if work is None and params_bf16 is not None:
             work = torch.empty(13 * self.nn, dtype=torch.float32, device="cuda")
         v_init = torch.empty(self.ndof, dtype=torch.float64, device="cuda") if v_init is None else v_init
-        self._check(self.lib.tl_warm_start(self.h, _ptr(params_bf16), _ptr(q_n), _ptr(v_n), _ptr(v_prev),
-                                           float(s_v), float(s_d), float(s_u), float(s_out), _ptr(work),
-                                           _ptr(v_init)))
+        h = list(hist) + [None] * (4 - len(hist))
+        self._check(self.lib.tl_warm_start(self.h, _ptr(params_bf16), _ptr(h[0]), _ptr(h[1]), _ptr(h[2]),
+                                           _ptr(h[3]), float(scales[0]), float(scales[1]), float(scales[2]),
+                                           float(s_out), _ptr(work), _ptr(v_init)))
         return v_init
 
     def sync(self):

@@ -1,14 +1,18 @@
 """Learned Newton warm start: generate backward-Euler trajectories with the
 plain Newton step (start v_n), train the per-node MLP with the library's own
 kernels, and compare Newton iterations / time to the same 1e-8 residual from
-three starts: v_n (the paper's), linear extrapolation 2 v_n - v_{n-1}, and the
-MLP, which learns a correction of that extrapolation.  The inner tolerance is relative to the residual at v_n in every case,
-so all three converge to the same state within the Newton tolerance.
+the starts v_n (the paper's), the polynomial extrapolations of the velocity
+history (linear from v_n, v_{n-1}; cubic from v_n .. v_{n-3}) and the MLP,
+which learns a correction of the cubic extrapolation from the backward
+differences of the history.  The inner tolerance is relative to the residual
+at v_n in every case, so all starts converge to the same state within the
+Newton tolerance.
 
 Orchestration only: every array operation of the method (Newton steps,
-features, forward / backward passes, loss gradient, Adam) runs in the CUDA
-kernels behind include/tl.h; torch provides device memory, random minibatch
-indices and timing events.
+features, training targets, normalisation statistics, forward / backward
+passes, loss gradient, Adam) runs in the CUDA kernels behind include/tl.h;
+torch provides device memory, random minibatch choice and timing events, and
+the host turns a handful of float64 sums into scales.
 """
 from __future__ import annotations
 
@@ -62,36 +66,60 @@ def generate(g, X, f_ext_fn, nsteps, prm, q0=None, v0=None, record_from=0, log_e
 @dataclass
 class WarmStartModel:
     params: object          # int16 CUDA tensor of bf16 bits (9219)
-    s_v: float
-    s_d: float
-    s_u: float
+    s1: float               # scales of the first, second and third backward differences
+    s2: float
+    s3: float
     s_out: float            # output scale (shrinkage included)
     alpha: float = 1.0      # shrinkage factor chosen on the validation steps
     val_loss: float = float("nan")
 
+    @property
+    def scales(self):
+        return (self.s1, self.s2, self.s3)
+
     def to_npz(self, path):
-        np.savez(path, params=self.params.cpu().numpy(), s_v=self.s_v, s_d=self.s_d, s_u=self.s_u, s_out=self.s_out,
+        np.savez(path, params=self.params.cpu().numpy(), s1=self.s1, s2=self.s2, s3=self.s3, s_out=self.s_out,
                  alpha=self.alpha, val_loss=self.val_loss)
 
     @classmethod
     def from_npz(cls, path):
         import torch
         d = np.load(path)
-        return cls(torch.as_tensor(d["params"], device="cuda"), float(d["s_v"]), float(d["s_d"]), float(d["s_u"]),
-                   float(d["s_out"]), float(d["alpha"]) if "alpha" in d else 1.0,
-                   float(d["val_loss"]) if "val_loss" in d else float("nan"))
+        return cls(torch.as_tensor(d["params"], device="cuda"), float(d["s1"]), float(d["s2"]), float(d["s3"]),
+                   float(d["s_out"]), float(d["alpha"]), float(d["val_loss"]))
 
 
-def _scales(g, tr, idx, X):
-    """Standard deviations of velocity, velocity difference, displacement and
-    velocity change over the training steps (torch reductions)."""
+def history(tr, t, order=4):
+    """(v_t, v_{t-1}, ..., ) of length `order` from a trajectory (None before its start)."""
+    return tuple(tr.v[t - k] if t - k >= 0 else None for k in range(order))
+
+
+def _scales(g, tr, idx, rounds=4):
+    """Scales of the inputs and the output from the library's feature / target
+    kernels and column sums over the steps idx.  s1, s2, s3 balance the three
+    backward differences: each round divides s_k by the square root of group
+    k's share of the nodes' (unit) input vectors times three, so that the three
+    groups end with equal shares; s_out is the RMS of the resulting target."""
     import torch
-    Xd = torch.as_tensor(np.asarray(X).reshape(-1), device="cuda")
-    sv = torch.cat([tr.v[i] for i in idx]).std().item()
-    sd = torch.cat([tr.v[i] - tr.v[i - 1] for i in idx if i > 0]).std().item()
-    su = torch.cat([tr.q[i] - Xd for i in idx]).std().item()
-    so = torch.cat([tr.v[i + 1] - 2.0 * tr.v[i] + tr.v[i - 1] for i in idx if i > 0]).std().item()
-    return tuple(max(x, 1e-12) for x in (sv, sd, su, so))
+    nn = g.nn
+    feats = torch.empty(nn, 10, dtype=torch.float32, device="cuda")
+    target = torch.empty(nn, 3, dtype=torch.float32, device="cuda")
+    sc = np.ones(3)
+    pick = idx[np.linspace(0, len(idx) - 1, min(20, len(idx))).astype(int)]
+    for _ in range(rounds):
+        sf = torch.zeros(10, dtype=torch.float64, device="cuda")
+        for t in pick:
+            g.mlp_features(history(tr, t), tuple(sc), feats)
+            tl.mlp_col_sumsq(feats, sf)
+        e = sf.cpu().numpy()[:9].reshape(3, 3).sum(axis=1)
+        share = e / max(e.sum(), 1e-300)
+        sc = sc * np.sqrt(np.maximum(3.0 * share, 1e-12))
+    st = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for t in idx:
+        g.mlp_target(tr.v[t + 1], history(tr, t), tuple(sc), 1.0, target)
+        tl.mlp_col_sumsq(target, st)
+    s_out = np.sqrt(st.cpu().numpy().sum() / (3.0 * nn * len(idx)))
+    return tuple(float(max(x, 1e-30)) for x in (*sc, s_out))
 
 
 def _glorot_init(rng):
@@ -106,25 +134,28 @@ def _glorot_init(rng):
     return np.concatenate(out)
 
 
-def train(g, tr, X, fixed_nodes, train_idx, iters=2000, lr=2e-3, seed=0, log_every=0, val_frac=0.1,
+def train(g, tr, fixed_nodes, train_idx, iters=2000, lr=2e-3, seed=0, log_every=0, val_frac=0.1,
           eval_every=100):
-    """Fit the MLP to predict (v_{t+1} - 2 v_t + v_{t-1}) / s_out (the error of
-    linear extrapolation) from the features at step t (mean squared error over
-    free nodes).  Each iteration uses every node of one randomly drawn
-    training step; Adam on a float32 master copy.
+    """Fit the MLP to predict (v_{t+1} - b_t) / (s_out r_I), b_t the cubic
+    extrapolation of v_t .. v_{t-3} (the error of that extrapolation), from the
+    node-normalised backward differences at step t (mean squared error over
+    free nodes).  Each
+    iteration uses every node of one randomly drawn training step; Adam on a
+    float32 master copy.
 
     Model selection on the last `val_frac` of the training steps (never
     trained on): the parameters with the lowest validation loss are kept, and
     the output scale is shrunk by the least-squares factor alpha in [0, 1] of
     the network output against the validation targets, so a network that does
-    not generalise falls back towards plain extrapolation (alpha = 0)."""
+    not generalise falls back towards the extrapolation itself (alpha = 0)."""
     import torch
     rng = np.random.default_rng(seed)
     train_idx = np.asarray(train_idx)
-    train_idx = train_idx[train_idx > 0]
+    train_idx = train_idx[train_idx >= 3]
     n_val = max(1, int(round(val_frac * len(train_idx))))
     fit_idx, val_idx = train_idx[:-n_val], train_idx[-n_val:]
-    s_v, s_d, s_u, s_out = _scales(g, tr, fit_idx, X)
+    s1, s2, s3, s_out = _scales(g, tr, fit_idx)
+    scales = (s1, s2, s3)
     nn = g.nn
     master = torch.as_tensor(_glorot_init(rng), device="cuda")
     P = torch.empty(NPARAM, dtype=torch.int16, device="cuda")
@@ -138,72 +169,83 @@ def train(g, tr, X, fixed_nodes, train_idx, iters=2000, lr=2e-3, seed=0, log_eve
     feats = torch.empty(nn, 10, dtype=torch.float32, device="cuda")
     acts = torch.empty(nn, 192, dtype=torch.int16, device="cuda")
     out = torch.empty(nn, 3, dtype=torch.float32, device="cuda")
+    target = torch.empty(nn, 3, dtype=torch.float32, device="cuda")
+    zeros3 = torch.zeros(nn, 3, dtype=torch.float32, device="cuda")
     dout = torch.empty_like(out)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
 
-    def target_of(t):
-        return ((tr.v[t + 1] - 2.0 * tr.v[t] + tr.v[t - 1]) / s_out).to(torch.float32).view(nn, 3)
+    def prepare(t):
+        g.mlp_features(history(tr, t), scales, feats)
+        g.mlp_target(tr.v[t + 1], history(tr, t), scales, s_out, target)
 
     val_pick = val_idx[np.linspace(0, len(val_idx) - 1, min(10, len(val_idx))).astype(int)]
+
+    def weighted_sq(a, b):
+        loss.zero_()
+        tl.mlp_mse_grad(a, b, weight, dout, loss)
+        return loss.item()
 
     def val_loss():
         tot = 0.0
         for t in val_pick:
-            g.mlp_features(tr.q[t], tr.v[t], tr.v[t - 1], s_v, s_d, s_u, feats)
+            prepare(t)
             tl.mlp_forward(P, feats, out=out)
-            loss.zero_()
-            tl.mlp_mse_grad(out, target_of(t), weight, dout, loss)
-            tot += loss.item()
+            tot += weighted_sq(out, target)
         return tot / len(val_pick)
 
-    history = []
+    history_ = []
     best = (val_loss(), P.clone())
-    history.append((0, float("nan"), best[0]))
+    history_.append((0, float("nan"), best[0]))
     for it in range(iters):
         t = int(rng.choice(fit_idx))
-        g.mlp_features(tr.q[t], tr.v[t], tr.v[t - 1], s_v, s_d, s_u, feats)
+        prepare(t)
         tl.mlp_forward(P, feats, out=out, acts=acts)
         loss.zero_()
-        tl.mlp_mse_grad(out, target_of(t), weight, dout, loss)
+        tl.mlp_mse_grad(out, target, weight, dout, loss)
         grads.zero_()
         tl.mlp_backward(P, feats, acts, dout, grads)
         tl.mlp_adam(master, P, grads, m1, m2, lr=lr * (0.1 ** (it / max(1, iters))), step=it + 1)
         if (it + 1) % eval_every == 0 or it == iters - 1:
             vl = val_loss()
-            history.append((it + 1, loss.item(), vl))
+            history_.append((it + 1, loss.item(), vl))
             if vl < best[0]:
                 best = (vl, P.clone())
             if log_every and ((it + 1) % log_every == 0 or it == iters - 1):
                 print(f"  iter {it + 1}: train loss {loss.item():.4e}, validation loss {vl:.4e}", flush=True)
     P.copy_(best[1])
-    # output shrinkage fitted on the validation steps
-    num = den = 0.0
+    # output shrinkage alpha = argmin sum w |alpha out - target|^2 = B / A on the
+    # validation steps, from weighted squared norms the loss kernel forms:
+    # A = |out|^2_w, C = |target|^2_w, L = |out - target|^2_w, B = (A + C - L) / 2
+    A = B = 0.0
     for t in val_pick:
-        g.mlp_features(tr.q[t], tr.v[t], tr.v[t - 1], s_v, s_d, s_u, feats)
+        prepare(t)
         tl.mlp_forward(P, feats, out=out)
-        wt = weight.view(nn, 1).double()
-        num += (wt * out.double() * target_of(t).double()).sum().item()
-        den += (wt * out.double() * out.double()).sum().item()
-    alpha = float(min(1.0, max(0.0, num / den))) if den > 0 else 0.0
-    model = WarmStartModel(P, s_v, s_d, s_u, alpha * s_out)
+        a_, c_, l_ = weighted_sq(out, zeros3), weighted_sq(target, zeros3), weighted_sq(out, target)
+        A += a_
+        B += 0.5 * (a_ + c_ - l_)
+    alpha = float(min(1.0, max(0.0, B / A))) if A > 0 else 0.0
+    model = WarmStartModel(P, s1, s2, s3, alpha * s_out)
     model.alpha, model.val_loss = alpha, best[0]
-    return model, history
+    return model, history_
+
+
+START_ORDERS = {"v_n": 1, "linear": 2, "quadratic": 3, "cubic": 4}
 
 
 def evaluate(g, tr, test_idx, prm, model=None, modes=None):
     """Newton iterations and time to the same tolerance on the stored test
-    steps, from the starts in `modes`: "v_n" (the paper's), "extrapolation"
-    (2 v_n - v_{n-1}) and "mlp" (needs model).  g may be a handle of either
-    element precision; prm selects the linear solver."""
+    steps, from the starts in `modes`: "v_n" (the paper's), "linear",
+    "quadratic", "cubic" (polynomial extrapolations of the last 2, 3, 4
+    velocities) and "mlp" (needs model; its base is the cubic).  g may be a
+    handle of either element precision; prm selects the linear solver."""
     import torch
     if modes is None:
-        modes = ["v_n", "extrapolation"] + (["mlp"] if model is not None else [])
+        modes = ["v_n", "linear", "cubic"] + (["mlp"] if model is not None else [])
     res = {m: dict(iters=[], ms=[], ms_start=[], dev=[], g0=[], lin=[], ls=[]) for m in modes}
     work = torch.empty(13 * g.nn, dtype=torch.float32, device="cuda")
     vinit = torch.empty(g.ndof, dtype=torch.float64, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for t in test_idx:
-        v_prev = tr.v[t - 1] if t > 0 else tr.v[t]
         ref = tr.v[t + 1]
         for mode in modes:
             torch.cuda.synchronize()
@@ -211,12 +253,11 @@ def evaluate(g, tr, test_idx, prm, model=None, modes=None):
             e0.record()
             if mode == "v_n":
                 vi = None
-            elif mode == "extrapolation":
-                g.warm_start(None, tr.q[t], tr.v[t], v_prev, 1.0, 1.0, 1.0, 0.0, v_init=vinit)
+            elif mode == "mlp":
+                g.warm_start(model.params, history(tr, t), model.scales, model.s_out, work=work, v_init=vinit)
                 vi = vinit
             else:
-                g.warm_start(model.params, tr.q[t], tr.v[t], v_prev, model.s_v, model.s_d, model.s_u,
-                             model.s_out, work=work, v_init=vinit)
+                g.warm_start(None, history(tr, t, START_ORDERS[mode]), v_init=vinit)
                 vi = vinit
             e1.record()
             lam = tr.lam[t].clone()
@@ -231,8 +272,9 @@ def evaluate(g, tr, test_idx, prm, model=None, modes=None):
             r["lin"].append(st["lin_iters"])
             r["ls"].append(st["ls_trials"])
     summary = {m: dict(mean_iters=float(np.mean(r["iters"])), mean_ms=float(np.mean(r["ms"])),
+                       median_ms=float(np.median(r["ms"])),
                        mean_ms_start=float(np.mean(r["ms_start"])), max_rel_dev=float(np.max(r["dev"])),
                        median_g0_ratio=float(np.median(r["g0"])), mean_lin_iters=float(np.mean(r["lin"])),
-                       mean_ls_trials=float(np.mean(r["ls"])))
+                       mean_ls_trials=float(np.mean(r["ls"])), steps=len(r["ms"]))
                for m, r in res.items()}
     return summary, res

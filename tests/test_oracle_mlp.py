@@ -105,12 +105,19 @@ def test_features_layout_on_a_hand_built_history():
     v1 = np.array([[7.0, 1.0, -2.0], [0.0, 0.0, 0.0]])
     v0 = np.array([[13.0, 1.0, -5.0], [0.0, 0.0, 0.0]])
     f = mlp.features(v0, v1, v2, v3, np.array([False, True]), 2.0, 0.5, 4.0)
-    expect = np.array([[3.0, 0.0, -1.5, 4.0, 0.0, -2.0, 0.0, 0.0, 0.0, 0.0],
+    # scaled differences (3, 0, -1.5 | 4, 0, -2 | 0, 0, 0), norm sqrt(9 + 2.25 + 16 + 4) = 5.59...
+    r = np.sqrt(31.25)
+    expect = np.array([[3.0 / r, 0.0, -1.5 / r, 4.0 / r, 0.0, -2.0 / r, 0.0, 0.0, 0.0, 0.0],
                        [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
-    assert np.array_equal(f, expect)
-    # missing history: the differences that need it are zero
+    assert np.allclose(f, expect, rtol=0, atol=1e-15)
+    assert np.allclose(mlp.node_scale(v0, v1, v2, v3, 2.0, 0.5, 4.0), [r, 0.0], rtol=0, atol=1e-14)
+    # missing history: the differences that need it are zero (norm 3.354...)
     f2 = mlp.features(v0, v1, None, None, np.array([False, True]), 2.0, 0.5, 4.0)
-    assert np.array_equal(f2[:, 3:9], np.zeros((2, 6))) and np.array_equal(f2[:, :3], expect[:, :3])
+    assert np.array_equal(f2[:, 3:9], np.zeros((2, 6)))
+    assert np.allclose(f2[0, :3], np.array([3.0, 0.0, -1.5]) / np.sqrt(11.25), rtol=0, atol=1e-15)
+    # the inputs do not depend on the amplitude of the motion
+    assert np.allclose(mlp.features(7 * v0, 7 * v1, 7 * v2, 7 * v3, np.array([False, True]), 2.0, 0.5, 4.0), f,
+                       rtol=0, atol=1e-15)
 
 
 def test_start_velocity_round_trip_and_fixed_nodes():
@@ -120,8 +127,13 @@ def test_start_velocity_round_trip_and_fixed_nodes():
     hist = [rng.normal(size=(6, 3)) for _ in range(4)]
     v_next = rng.normal(size=(6, 3))
     fixed = np.array([True, False, False, True, False, False])
-    t = mlp.target(v_next, *hist, fixed, 0.25)
-    v0 = mlp.start_velocity(t, *hist, fixed, 0.25)
+    sc = (0.5, 2.0, 3.0)
+    t = mlp.target(v_next, *hist, fixed, *sc, 0.25)
+    v0 = mlp.start_velocity(t, *hist, fixed, *sc, 0.25)
     assert np.allclose(v0[~fixed], v_next[~fixed], rtol=0, atol=1e-12)
     assert np.array_equal(v0[fixed], np.zeros((2, 3))) and np.array_equal(t[fixed], np.zeros((2, 3)))
-    assert np.array_equal(mlp.start_velocity(rng.normal(size=(6, 3)), *hist, fixed, 3.0)[fixed], np.zeros((2, 3)))
+    assert np.array_equal(mlp.start_velocity(rng.normal(size=(6, 3)), *hist, fixed, *sc, 3.0)[fixed],
+                          np.zeros((2, 3)))
+    # the same motion 10x larger: the same target (the correction scales with the history)
+    t10 = mlp.target(10 * v_next, *(10 * h for h in hist), fixed, *sc, 0.25)
+    assert np.allclose(t10, t, rtol=1e-12, atol=1e-15)
