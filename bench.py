@@ -417,13 +417,15 @@ def run_newton(args):
     """Newton step ms to the 1e-8 relative residual on the 103,680-element
     cantilever (12 x 1.2 x 1.2 m, SVK, gravity + seeded tip loads), on the
     held-out steps of the warm-start trajectory (steps 1101.. of the trajectory
-    from rest; the network was trained on steps 1..1099).  'plain' = the
+    from rest; the network was trained on steps 3..1099).  'plain' = the
     paper's step: FP64 element form, start v_n, host-driven loop (||g|| read
-    back every iteration), PCG to 1e-10 (plus the vendor direct solver with
-    --newton-direct); 'chosen' = FP32 element form, learned warm start,
-    inexact-Newton PCG, the whole step as one captured CUDA graph.  Both from
-    the same stored states to the same target; the trajectory itself is
-    generated (untimed) with the plain step in its graph form."""
+    back every iteration), PCG to 1e-10; 'chosen' = FP32 element form,
+    inexact-Newton PCG, the whole step as one captured CUDA graph, from the
+    learned start (a correction of the cubic extrapolation of the velocity
+    history), beside the same arm from the linear (2 v_n - v_{n-1}) and cubic
+    extrapolations.  All from the same stored states to the same target; the
+    trajectory itself is generated (untimed) with the plain step in its graph
+    form.  Returns (compact summary, details)."""
     import torch
 
     from paper_2604_10357_gb300 import inputs, tl, warmstart
@@ -439,39 +441,37 @@ def run_newton(args):
                        use_graph=0 if args.newton_no_graph else 1)
     t0_step, n_eval = args.newton_start, args.newton_steps
     t_gen = time.time()
-    tr = warmstart.generate(g64, m.X, w["f_ext"], t0_step + n_eval + 1, gen, record_from=t0_step - 1)
+    tr = warmstart.generate(g64, m.X, w["f_ext"], t0_step + n_eval + 1, gen, record_from=t0_step - 3)
     t_gen = time.time() - t_gen
-    test_idx = list(range(1, n_eval + 1))          # trajectory-local indices (record_from offset)
+    test_idx = list(range(3, n_eval + 3))          # trajectory-local indices (record_from offset)
     model_path = os.path.join(ROOT, "paper_2604_10357_gb300", "data", "warmstart_box120x12x12.npz")
     model = warmstart.WarmStartModel.from_npz(model_path) if os.path.exists(model_path) else None
-    c_mode = "mlp" if model is not None else "extrapolation"
+    starts = ["linear", "cubic"] + (["mlp"] if model is not None else [])
     # launch shapes of both arms picked by the autotuner on the first held-out state (untimed)
-    shape_keys = ("elem_occ2", "elem_prefetch", "elem_xchg", "elem_full_grid", "elem_agg", "spmv_group", "spmv_row",
-                  "pcg_f32", "residual_split")
+    shape_keys = ("elem_pair", "elem_occ2", "elem_prefetch", "elem_xchg", "elem_full_grid", "elem_agg", "spmv_group",
+                  "spmv_row", "pcg_f32", "residual_split")
     shapes = {}
     for name, g in (("plain", g64), ("chosen", g32)):
         t = g.tune_get() if args.no_autotune else g.autotune(tr.q[test_idx[0]], tr.v[test_idx[0]], w["h"], reps=3)
         shapes[name] = {k: t[k] for k in shape_keys}
     # one untimed pass of each arm first (graph capture, first-use allocations)
     warmstart.evaluate(g64, tr, test_idx[:1], plain, modes=["v_n"])
-    warmstart.evaluate(g32, tr, test_idx[:1], chosen, model, modes=[c_mode])
+    warmstart.evaluate(g32, tr, test_idx[:1], chosen, model, modes=starts)
     p_sum, _ = warmstart.evaluate(g64, tr, test_idx, plain, modes=["v_n"])
-    c_sum, _ = warmstart.evaluate(g32, tr, test_idx, chosen, model, modes=[c_mode])
-    out = {"workload": w["name"], "ndof": 3 * m.nn, "steps": [t0_step, t0_step + n_eval - 1],
-           "target": "||g|| <= 1e-8 ||g(v_n)||", "trajectory_generation_s": t_gen,
-           "plain": dict(p_sum["v_n"], desc="FP64 element form, start v_n, host loop, PCG 1e-10"),
-           "chosen": dict(c_sum[c_mode], desc=f"FP32 element form, start {c_mode}, inexact-Newton PCG, "
-                                                + ("host loop" if args.newton_no_graph else "captured graph")),
-           "speedup": p_sum["v_n"]["mean_ms"] / c_sum[c_mode]["mean_ms"],
-           "launch_shapes": shapes,
-           "model": os.path.relpath(model_path, ROOT) if model is not None else None}
-    # the chosen arm with the Armijo line search of eq. armijo (trial residual
-    # per Newton step; here every full step is accepted)
+    c_sum, _ = warmstart.evaluate(g32, tr, test_idx, chosen, model, modes=starts)
+    best = "mlp" if model is not None else "cubic"
+    details = {"workload": w["name"], "ndof": 3 * m.nn, "steps": [t0_step, t0_step + n_eval - 1],
+               "target": "||g|| <= 1e-8 ||g(v_n)||", "trajectory_generation_s": t_gen,
+               "plain": dict(p_sum["v_n"], desc="FP64 element form, start v_n, host loop, PCG 1e-10"),
+               "chosen_starts": c_sum, "launch_shapes": shapes,
+               "model": os.path.relpath(model_path, ROOT) if model is not None else None,
+               "model_alpha": model.alpha if model is not None else None}
+    # the chosen arm with the Armijo line search of eq. armijo (trial residual per Newton step)
     chosen_ls = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, line_search=1,
                           use_graph=0 if args.newton_no_graph else 1)
-    warmstart.evaluate(g32, tr, test_idx[:1], chosen_ls, model, modes=[c_mode])
-    l_sum, _ = warmstart.evaluate(g32, tr, test_idx, chosen_ls, model, modes=[c_mode])
-    out["chosen_line_search"] = dict(l_sum[c_mode], desc="chosen arm with the Armijo line search")
+    warmstart.evaluate(g32, tr, test_idx[:1], chosen_ls, model, modes=[best])
+    l_sum, _ = warmstart.evaluate(g32, tr, test_idx[:10], chosen_ls, model, modes=[best])
+    details["chosen_line_search"] = dict(l_sum[best], desc="chosen arm with the Armijo line search (10 steps)")
     # the first-order inner solver (Algorithm 2) from the first held-out state:
     # cost per AdamW update and the gradient reduction a fixed budget reaches
     t_a = test_idx[0]
@@ -484,16 +484,315 @@ def run_newton(args):
     _, _, st_a = g32.adamw_step(tl.params(h=w["h"], max_outer=1), a_prm, tr.q[t_a], tr.v[t_a], lam_a,
                                 f_ext=tr.f_ext[t_a], raise_on_nonconvergence=False)
     ms_a = 1e3 * (time.perf_counter() - t0)
-    out["adamw"] = dict(inner_iters=st_a["inner_iters"], ms=ms_a, ms_per_update=ms_a / max(1, st_a["inner_iters"]),
-                        g_ratio=st_a["g_norm"] / g0, converged=st_a["converged"],
-                        desc="Algorithm 2, lr 1e-4, 200 updates from the first held-out state (not converged: "
-                             "a first-order rate)")
-    if args.newton_direct:
-        direct = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_DIRECT)
-        d_sum, _ = warmstart.evaluate(g64, tr, test_idx[:1], direct, modes=["v_n"])
-        out["plain_direct"] = dict(d_sum["v_n"], desc="FP64, start v_n, cuSOLVER sparse Cholesky (1 step)")
+    details["adamw"] = dict(inner_iters=st_a["inner_iters"], ms=ms_a, ms_per_update=ms_a / max(1, st_a["inner_iters"]),
+                            g_ratio=st_a["g_norm"] / g0, converged=st_a["converged"],
+                            desc="Algorithm 2, lr 1e-4, 200 updates from the first held-out state (not converged: "
+                                 "a first-order rate)")
     g64.close()
     g32.close()
+
+    def brief(d):
+        return {"ms": round(d["mean_ms"], 3), "newton_its": round(d["mean_iters"], 2),
+                "pcg_its": round(d["mean_lin_iters"], 1), "g0_ratio": float("%.3g" % d["median_g0_ratio"]),
+                "max_rel_dev": float("%.2g" % d["max_rel_dev"])}
+
+    summary = {"steps": n_eval, "first_step": t0_step, "ndof": 3 * m.nn,
+               "plain_ms": round(p_sum["v_n"]["mean_ms"], 3),
+               "chosen_ms": round(c_sum[best]["mean_ms"], 3), "chosen_start": best,
+               "speedup": round(p_sum["v_n"]["mean_ms"] / c_sum[best]["mean_ms"], 2),
+               "plain": brief(p_sum["v_n"]), **{f"chosen_{k}": brief(c_sum[k]) for k in starts}}
+    return summary, details
+
+
+class ErrorNorms:
+    """Comparison norms of a GPU result against the oracle (the paper gives
+    none): force error relative to the largest element force, element-tangent
+    error relative to each element's own Frobenius norm, CSR values relative to
+    the largest value and in the 2-norm."""
+
+    @staticmethod
+    def force_error(f_gpu, f_ora, fe_ora):
+        return float(np.abs(np.asarray(f_gpu) - np.asarray(f_ora)).max() / np.abs(fe_ora).max())
+
+    @staticmethod
+    def tangent_error(K_gpu, K_ora):
+        K_gpu = np.asarray(K_gpu, dtype=np.float64).reshape(-1, 900)
+        K_ora = np.asarray(K_ora, dtype=np.float64).reshape(-1, 900)
+        den = np.linalg.norm(K_ora, axis=1)
+        num = np.linalg.norm(K_gpu - K_ora, axis=1)
+        return float(np.max(num[den > 0] / den[den > 0]))
+
+    @staticmethod
+    def values_error(v_gpu, v_ora):
+        d = np.asarray(v_gpu, dtype=np.float64) - np.asarray(v_ora, dtype=np.float64)
+        return float(np.abs(d).max() / np.abs(v_ora).max()), float(np.linalg.norm(d) / np.linalg.norm(v_ora))
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def _oracle_rate_worker(budget_s):
+    return oracle_step_rate(budget_s=budget_s)
+
+
+def oracle_all_cores_rate(budget_s=8.0):
+    """The oracle's element loop on every host core: one process per core, each
+    assembling its own copy of the bounded sample (spawned processes, one BLAS
+    thread each); the rate is the sum over processes."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(ncores) as pool:
+            res = pool.map(_oracle_rate_worker, [budget_s] * ncores)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return sum(r[0] for r in res), ncores, res[0][2]
+
+
+def _time_passes(g, fn, reps=10, warm=3):
+    """Mean ms per call of fn over reps calls (CUDA events), and the library's
+    element-kernel ms per launch over the same calls."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    g.timing_read()
+    g.timing_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    t = g.timing_read()
+    g.timing_enable(False)
+    return e0.elapsed_time(e1) / reps, t["ms_element"] / max(1, t["n_element"]), t
+
+
+def run_fp64_large(args):
+    """The same 960,000-element step with the FP64 element form (the paper's
+    precision): element kernel ms against the float64 ALU roofline."""
+    import torch
+
+    from paper_2604_10357_gb300 import inputs, tl
+    w = inputs.workload_large_svk_kv(scale=args.scale)
+    m = w["mesh"]
+    g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+    nnz = g.build_pattern(m.fixed_nodes)
+    q = torch.as_tensor(w["q_n"].reshape(-1), device="cuda")
+    v = torch.as_tensor(w["v"].reshape(-1), device="cuda")
+    h = w["h"]
+    if not args.no_autotune:
+        g.autotune(q, v, h, reps=2)
+    vals = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    f = torch.empty(3 * m.nn, dtype=torch.float64, device="cuda")
+    res = torch.empty_like(f)
+    gn = torch.empty(1, dtype=torch.float64, device="cuda")
+    prm = tl.params(h=h, rho_alm=1e12)
+
+    def step():
+        g.assemble_hessian(q, v, h, 1e12, values=vals, f_int=f)
+        g.eval_residual(prm, q, v, v, f_int=f, g=res, g_norm=gn)
+
+    ms, kms, _ = _time_passes(g, step, reps=5)
+    g.close()
+    flops = FLOPS_PER_ELEM[("svk", True)] * m.ne
+    ach = flops / (kms * 1e-3) / 1e12
+    return {"workload": w["name"], "dtype": "f64", "ms_per_step": ms, "elems_per_s": m.ne / (ms * 1e-3),
+            "kernel_ms": kms, "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_alu_peak_tflops(),
+                                           "unit": "TFLOP/s", "frac": ach / fp64_alu_peak_tflops(),
+                                           "peak_source": "FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2070 MHz (derived)"}}
+
+
+def run_mid(args):
+    """The 15,360-element Mooney-Rivlin + Kelvin-Voigt box: element pass of both
+    forms (elems/s), and the errors of the FP32 form (and of FP64) against the
+    FP64 oracle for the internal force, the element tangents h K_t + D, the
+    CSR Hessian values, and one backward-Euler Newton step: the oracle's
+    residual at each form's converged velocity, and the distance between the
+    two forms' velocities."""
+    import torch
+
+    from oracle import assembly as asm
+    from paper_2604_10357_gb300 import inputs, tl
+    he = ErrorNorms
+    w = inputs.workload_mid_mr_kv()
+    m = w["mesh"]
+    h, rho = w["h"], 1e12
+    om = asm.OracleMesh(m.X, m.conn, [w["material"]], fixed_nodes=m.fixed_nodes)
+    x = w["q_n"] + h * w["v"]
+    fe = om.element_forces(x, w["v"])
+    f_ora = om.internal_force(w["q_n"], w["v"], h)
+    K_ora = om.element_tangents(x, w["v"], h, 1.0)
+    v_ora = om.hessian_values(w["q_n"], w["v"], h, rho)
+    _, _, row_ptr, col = om.pattern()
+    pen = asm.csr_positions(row_ptr, col, om.fixed_dofs, om.fixed_dofs)
+    rest = np.ones(len(v_ora), bool)
+    rest[pen] = False
+    q = torch.as_tensor(w["q_n"].reshape(-1), device="cuda")
+    v = torch.as_tensor(w["v"].reshape(-1), device="cuda")
+    qN_h = m.X.reshape(-1).copy()
+    qN = torch.as_tensor(qN_h, device="cuda")
+    out = {"workload": w["name"], "ne": m.ne, "ndof": 3 * m.nn}
+    vout = {}
+    for name, prec in (("fp64", tl.TL_FP64), ("fp32", tl.TL_FP32_ELEM)):
+        g = tl.Mesh(m.X, m.conn, [w["material"]], precision=prec)
+        nnz = g.build_pattern(m.fixed_nodes)
+        if not args.no_autotune:
+            g.autotune(q, v, h, reps=2)
+        vals = torch.empty(nnz, dtype=g.vdtype, device="cuda")
+        f = torch.empty(3 * m.nn, dtype=torch.float64, device="cuda")
+        ms, kms, _ = _time_passes(g, lambda: g.assemble_hessian(q, v, h, rho, values=vals, f_int=f), reps=10)
+        f_gpu = g.eval_force(q, v, h).cpu().numpy()
+        K_gpu = g.eval_tangent(q, v, h, h, 1.0).cpu().numpy()
+        vals_h = g.assemble_hessian(q, v, h, rho).cpu().numpy().astype(np.float64)
+        emax, e2 = he.values_error(vals_h[rest], v_ora[rest])
+        out[name] = {"element_pass_ms": ms, "kernel_ms": kms, "elems_per_s": m.ne / (ms * 1e-3),
+                     "err_force": he.force_error(f_gpu, f_ora, fe), "err_tangent": he.tangent_error(K_gpu, K_ora),
+                     "err_values_max": emax, "err_values_2": e2}
+        # one Newton step from (X, v_n) under gravity, start v_n (the deformed
+        # state's Newton matrix is indefinite, see newton_state)
+        try:
+            prm = (tl.params(h=h, rho_alm=rho, rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG) if prec == tl.TL_FP64 else
+                   tl.params(h=h, rho_alm=rho, rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1,
+                             use_graph=1))
+            lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+            g.newton_step(prm, qN, v, lam, raise_on_nonconvergence=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam = torch.zeros_like(lam)
+            vn, _, st = g.newton_step(prm, qN, v, lam, raise_on_nonconvergence=False)
+            torch.cuda.synchronize()
+            ms_newton = 1e3 * (time.perf_counter() - t0)
+            vout[name] = vn.cpu().numpy()
+            lam_inner = lam.cpu().numpy() - rho * om.constraint(qN_h + h * vout[name])
+            g_ref = np.linalg.norm(om.residual(w["v"].reshape(-1), qN_h, w["v"].reshape(-1), h, None,
+                                               (0.0, 0.0, -9.81), np.zeros(3 * len(m.fixed_nodes)), rho))
+            g_at = np.linalg.norm(om.residual(vout[name], qN_h, w["v"].reshape(-1), h, None,
+                                              (0.0, 0.0, -9.81), lam_inner, rho))
+            out[name]["newton"] = {"status": st["status"], "its": st["inner_iters"], "pcg_its": st["lin_iters"],
+                                   "ms": ms_newton, "oracle_residual_ratio": g_at / g_ref}
+        except Exception as exc:
+            out[name]["newton"] = {"error": f"{type(exc).__name__}: {exc}"}
+        g.close()
+    out["newton_fp32_vs_fp64_velocity"] = (float(np.linalg.norm(vout["fp32"] - vout["fp64"])
+                                                 / np.linalg.norm(vout["fp64"])) if len(vout) == 2 else None)
+    out["newton_state"] = ("q_n = X (reference configuration), v_n the workload's velocity field, gravity, "
+                           "lambda = 0: in the workload's deformed state the Mooney-Rivlin Newton matrix "
+                           "M/h + h K_t + D is indefinite at h = 1e-3 (compressive stresses make h K_t's negative "
+                           "geometric part exceed the smallest eigenvalues of M/h; the oracle's matrix on an 8x2x2 "
+                           "box of the same field has eigenvalues down to -121 at a tenth of the field, +31 at rest), "
+                           "so neither the Cholesky nor the CG inner solve applies there")
+    out["norms"] = ("force: max|df| / max element |f|; tangent: max over elements of ||dK||_F / ||K||_F (h K_t + D); "
+                    "values: max|dH| / max|H| and ||dH|| / ||H|| without the clamp-penalty diagonal; Newton: the "
+                    "oracle's residual at the GPU velocity over its residual at v_n")
+    return out
+
+
+def run_batched(args):
+    """48 bodies of uneven size (boxes and cylinders, SVK and Mooney-Rivlin; 1k to
+    60k T10 each) in one handle: the fused element pass over all bodies (one
+    persistent launch per kernel kind: the SVK segments in the pair kernel, the
+    Mooney-Rivlin ones in the generic kernel), and the batched Newton step of all
+    bodies from rest under gravity as one captured graph (FP32 element form).  The
+    bodies are independent, so H is block diagonal and one Newton loop serves all
+    of them: every body takes the same iteration count."""
+    import torch
+
+    from paper_2604_10357_gb300 import inputs, tl
+    w = inputs.workload_batched()
+    m = w["mesh"]
+    h, rho = w["h"], 1e12
+    g = tl.Mesh(m.X, m.conn, w["materials"], w["mat_of_elem"], precision=tl.TL_FP32_ELEM)
+    nnz = g.build_pattern(m.fixed_nodes)
+    q = torch.as_tensor(w["q_n"].reshape(-1), device="cuda")
+    v = torch.as_tensor(w["v"].reshape(-1), device="cuda")
+    if not args.no_autotune:
+        g.autotune(q, v, h, reps=2)
+    vals = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    f = torch.empty(3 * m.nn, dtype=torch.float64, device="cuda")
+    ms, kms, t = _time_passes(g, lambda: g.assemble_hessian(q, v, h, rho, values=vals, f_int=f), reps=10)
+    launches = t["launches"] / 10.0
+    prm = tl.params(h=h, rho_alm=rho, rtol=1e-8, linear_solver=tl.TL_SOLVER_PCG, lin_adaptive=1, use_graph=1)
+    qn = torch.as_tensor(m.X.reshape(-1), device="cuda")
+    vn = torch.zeros_like(qn)
+    lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+    steps = []
+    for k in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v1, q1, st = g.newton_step(prm, qn, vn, lam, raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        steps.append({"ms": 1e3 * (time.perf_counter() - t0), "its": st["inner_iters"], "pcg_its": st["lin_iters"],
+                      "converged": st["converged"], "g_ratio": st["g_norm"] / max(st["g_ref"], 1e-300)})
+        qn, vn = q1.clone(), v1.clone()
+    g.close()
+    return {"workload": w["name"], "bodies": len(w["meshes"]), "ne": m.ne, "nnz": int(nnz),
+            "element_pass_ms": ms, "kernel_ms": kms, "elems_per_s": m.ne / (ms * 1e-3),
+            "kernel_launches_per_pass": launches,
+            "newton_from_rest": {"first_step_incl_capture_ms": steps[0]["ms"],
+                                 "ms": statistics.median(s_["ms"] for s_ in steps[1:]),
+                                 "its_per_body": [s_["its"] for s_ in steps], "pcg_its": [s_["pcg_its"] for s_ in steps],
+                                 "converged": [s_["converged"] for s_ in steps],
+                                 "g_ratio": [float("%.3g" % s_["g_ratio"]) for s_ in steps]}}
+
+
+def run_direct(args):
+    """The vendor sparse direct solver (cuSOLVER Cholesky) inside the FP64 Newton
+    step on the 240-element box and on the 15,360-element box (from its
+    reference configuration with its velocity field: its deformed state's
+    Newton matrix is indefinite): the solver's
+    time reported apart from assembly (the step's own timers), three steps each
+    (the first one includes the symbolic analysis)."""
+    import torch
+
+    from paper_2604_10357_gb300 import inputs, tl
+    out = {}
+    for name, wf, scale in (("c1_240", inputs.workload_small_svk, 1.0), ("c2_15360", inputs.workload_mid_mr_kv, 0.0)):
+        try:
+            w = wf()
+            m = w["mesh"]
+            g = tl.Mesh(m.X, m.conn, [w["material"]], precision=tl.TL_FP64)
+            g.build_pattern(m.fixed_nodes)
+            prm = tl.params(h=w["h"], rtol=1e-8, linear_solver=tl.TL_SOLVER_DIRECT)
+            q = torch.as_tensor((m.X + scale * (w["q_n"] - m.X)).reshape(-1), device="cuda")
+            v = torch.as_tensor(w["v"].reshape(-1), device="cuda")
+            rows = []
+            for k in range(3):
+                lam = torch.zeros(3 * len(m.fixed_nodes), dtype=torch.float64, device="cuda")
+                _, _, st = g.newton_step(prm, q, v, lam, raise_on_nonconvergence=False)
+                rows.append({k2: st[k2] for k2 in ("ms_total", "ms_assembly", "ms_solver", "inner_iters",
+                                                   "converged")})
+            g.close()
+            out[name] = {"ndof": 3 * m.nn, "field_scale": scale, "first": rows[0],
+                         "ms_total": statistics.median(r["ms_total"] for r in rows[1:]),
+                         "ms_solver": statistics.median(r["ms_solver"] for r in rows[1:]),
+                         "ms_assembly": statistics.median(r["ms_assembly"] for r in rows[1:]),
+                         "newton_its": rows[-1]["inner_iters"]}
+        except Exception as exc:
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
     return out
 
 
@@ -525,7 +824,8 @@ def run_reference(args, rank, world):
             "data": "synthetic",
             "config": {"workload": "box 20x4x2 m, 200x40x20 hex x6 = 960,000 T10, SVK+KV",
                        "sample": f"{m.ne}-element sub-box (4x2x2 hexes, same hex size and field recipe) per step"},
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "cpu": cpu_model(),
+                             "host_cores": os.cpu_count(),
                              "sample": f"{m.ne} elements per step, {args.steps} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -775,7 +1075,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="hex-count scale of the box (1.0 = 960k T10)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-newton", action="store_true")
-    ap.add_argument("--newton-steps", type=int, default=10)
+    ap.add_argument("--newton-steps", type=int, default=50)
     ap.add_argument("--newton-direct", action="store_true")
     ap.add_argument("--newton-start", type=int, default=1101,
                     help="first evaluated step of the cantilever trajectory (1101: the held-out window)")
@@ -785,6 +1085,8 @@ def main():
                          "kernels inside conditional graph nodes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-constraints", action="store_true", help="skip the general-constraint cost measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64, mid-size, batched and direct-solver measurements")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--shape", action="append", default=[],
                     help="fix a launch shape of the element workload after the autotuner (key=value, repeatable)")
@@ -805,7 +1107,9 @@ def main():
         return
     if args.newton_only:
         if rank == 0:
-            print(json.dumps(run_newton(args)), flush=True)
+            summary, details = run_newton(args)
+            print("# newton_details: " + json.dumps(details), flush=True)
+            print(json.dumps({"newton": summary}), flush=True)
         return
     if args.ancf_only:
         if rank == 0:
@@ -817,17 +1121,48 @@ def main():
         torch.distributed.init_process_group("nccl")
     line = run_ours(args, rank, world)
     if line is not None:
-        if not args.no_cpu_baseline and world == 1:
-            rate, reps, n, el = oracle_step_rate()
-            line["cpu_baseline"] = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
-                                    "sample": f"{n}-element sub-box (10x4x4 hexes) of the same workload, "
-                                              f"{reps} passes in {el:.1f} s (numpy, one thread)"}
-        if not args.no_newton and world == 1:
-            line["newton"] = run_newton(args)
-        if not args.no_constraints and world == 1:
-            line["constraints"] = run_constraints(args)
-        if not args.no_ancf and world == 1:
-            line["ancf"] = run_ancf(args)
+        if world == 1:
+            # details go to lines of their own (prefixed "# "), before the JSON line
+            def extra(name, fn, *a):
+                try:
+                    return fn(*a)
+                except Exception as exc:                  # a failed extra must not lose the main line
+                    return {"error": f"{type(exc).__name__}: {exc}"}
+            if not args.no_extras:
+                line["fp64"] = extra("fp64", run_fp64_large, args)
+                line["mid_mr_kv"] = extra("mid", run_mid, args)
+                line["batched"] = extra("batched", run_batched, args)
+                line["direct_solver"] = extra("direct", run_direct, args)
+            if not args.no_constraints:
+                line["constraints"] = extra("constraints", run_constraints, args)
+            if not args.no_ancf:
+                anc = extra("ancf", run_ancf, args)
+                print("# ancf: " + json.dumps(anc), flush=True)
+                line["ancf"] = {k: {"assembly_frac_fp64_alu": v["assembly"]["frac"],
+                                    "assembly_fp32_frac_fp32_alu": v["assembly_fp32"]["frac_fp32_alu"],
+                                    "assembly_ms": v["assembly"]["ms"], "assembly_fp32_ms": v["assembly_fp32"]["ms"]}
+                                for k, v in anc.items() if isinstance(v, dict) and "assembly" in v} \
+                    if "error" not in anc else anc
+            if not args.no_cpu_baseline:
+                rate, reps, n, el = oracle_step_rate()
+                cb = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1, "cpu": cpu_model(),
+                      "host_cores": os.cpu_count(),
+                      "sample": f"{n}-element sub-box (10x4x4 hexes) of the same workload, "
+                                f"{reps} passes in {el:.1f} s (numpy, one thread)"}
+                try:
+                    rate_all, ncores, _ = oracle_all_cores_rate()
+                    cb["all_cores"] = {"value": rate_all, "cores": ncores,
+                                       "sample": "one copy of the same sub-box per process, one process per core"}
+                except Exception as exc:
+                    cb["all_cores"] = {"error": f"{type(exc).__name__}: {exc}"}
+                line["cpu_baseline"] = cb
+            if not args.no_newton:
+                nw = extra("newton", run_newton, args)
+                if isinstance(nw, tuple):
+                    print("# newton_details: " + json.dumps(nw[1]), flush=True)
+                    line["newton"] = nw[0]
+                else:
+                    line["newton"] = nw
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

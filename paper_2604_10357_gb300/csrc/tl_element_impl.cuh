@@ -1158,8 +1158,11 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   // (heavier, compiled per material) take one launch per run of segments of
   // the same (material, Kelvin-Voigt) pair.
   constexpr bool kMixed = std::is_same<T, float>::value;
-  size_t k = 0;
   int nlaunch = 0;
+  // pair mode: the SVK segments of all bodies first (pair kernel), then the
+  // Mooney-Rivlin ones (generic kernel), each in as few launches as possible
+  for (int pass = 0; pass < (pair_mode ? 2 : 1); ++pass) {
+  size_t k = 0;
   while (k < m->segs.size()) {
     SegTable<T> S;
     S.nseg = 0;
@@ -1173,8 +1176,8 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
       if (nt == 0) continue;
       const MaterialDev& md = m->mats[sg.mat];
       const int combo = 2 * (md.kind == TL_SVK ? 0 : 1) + (md.kv ? 1 : 0);
+      if (pair_mode && (combo < 2) != (pass == 0)) continue;   // the other pass's kind
       if (!kMixed && combo0 >= 0 && combo != combo0) break;   // next launch starts here
-      if (pair_mode && combo0 >= 0 && (combo < 2) != (combo0 < 2)) break;   // SVK and MR apart
       SegEntry<T>& se = S.s[S.nseg++];
       se.begin = sg.begin;
       se.real_end = sg.end;
@@ -1280,6 +1283,7 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
     TL_CUDA(m, cudaGetLastError());
     ++m->launches;
     }
+  }
   }
   timer_close(m, t0, kTimeElement);
   return TL_OK;

@@ -339,13 +339,17 @@ namespace {
 
 // w = lambda + rho c for the general constraint rows (their multipliers follow
 // the 3 nfixed clamp multipliers in lambda) and the C^T term of the residual.
-ConTerm con_prepare(tl_mesh* m, const tl_params* p, const double* q_n, const double* v, const double* lambda) {
-  if (m->ncon == 0) return ConTerm{nullptr, nullptr, nullptr, nullptr};
+tl_status con_prepare(tl_mesh* m, const tl_params* p, const double* q_n, const double* v, const double* lambda,
+                      ConTerm* ct) {
+  *ct = ConTerm{nullptr, nullptr, nullptr, nullptr};
+  if (m->ncon == 0) return TL_OK;
   con_eval<<<(unsigned)((m->ncon + 255) / 256), 256, 0, m->stream>>>(
       m->d_con_ptr, m->d_con_col, m->d_con_val, m->d_con_b, m->ncon, q_n, v, p->h,
       lambda ? lambda + 3 * m->nfixed : nullptr, p->rho_alm, m->d_con_w);
+  TL_CUDA(m, cudaGetLastError());
   ++m->launches;
-  return ConTerm{m->d_ct_ptr, m->d_ct_con, m->d_ct_val, m->d_con_w};
+  *ct = ConTerm{m->d_ct_ptr, m->d_ct_con, m->d_ct_val, m->d_con_w};
+  return TL_OK;
 }
 
 }  // namespace
@@ -394,7 +398,8 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
   cudaEvent_t t0 = timer_open(m);
   // f_int may alias g: each thread reads its own entries before writing them
   const int64_t n3 = 3 * m->nn;
-  const ConTerm ct = con_prepare(m, p, q_n, v, lambda);
+  ConTerm ct;
+  TL_TRY(con_prepare(m, p, q_n, v, lambda, &ct));
   if (m->tune.residual_split && m->d_mass2) {
     velocity_change_split<<<(unsigned)((n3 + 255) / 256), 256, 0, m->stream>>>(v, v_n, n3, m->d_dv2);
     if (m->tune.residual_lanes == 4)
@@ -496,7 +501,8 @@ extern "C" tl_status tl_eval_residual_noalloc(tl_mesh* m, const tl_params* p, co
   double* partials = nullptr;
   tl_status s = noalloc_scratch(m, dev, &partials);
   if (s != TL_OK) return s;
-  const ConTerm ct = con_prepare(m, p, q_n, v, lambda);
+  ConTerm ct;
+  TL_TRY(con_prepare(m, p, q_n, v, lambda, &ct));
   (ct.ptr ? residual_kernel<1, true> : residual_kernel<1, false>)<<<(unsigned)nb, kResBlock, 0, m->stream>>>(
       m->d_node_ptr, m->d_node_col, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h, p->rho_alm,
       p->gravity[0], p->gravity[1], p->gravity[2], q_n, v_n, v, nullptr, f_int, f_ext, lambda, g, partials, ct);
