@@ -127,7 +127,8 @@ class ClockSampler:
 
 
 ELEM_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2604_10357_gb300", "csrc", f)
-                       for f in ("tl_element_impl.cuh", "tl_element_common.cuh", "tl_tilemap.cu")]
+                       for f in ("tl_element_pair.cu", "tl_element_impl.cuh", "tl_element_common.cuh", "tl_tilemap.cu",
+                                 "tl_internal.cuh")]
 
 
 def kernel_source_hash(files=ELEM_KERNEL_SOURCES):
@@ -140,7 +141,7 @@ def kernel_source_hash(files=ELEM_KERNEL_SOURCES):
 def traffic_from_profile():
     """DRAM bytes per launch of the element kernel from the committed ncu
     summary, only if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "elem_kernel_traffic.json")
+    p = os.path.join(ROOT, "profiles", "pair_kernel_traffic_box120k.json")
     if not os.path.exists(p):
         return None
     try:
@@ -382,7 +383,9 @@ def run_ours(args, rank, world):
         roofline = {"bound": "alu", "achieved": flops / (elem_ms * 1e-3) / 1e12, "peak": None,
                     "unit": "TFLOP/s", "frac": None, "peak_source": "FP64 ALU peak not yet measured"}
     roofline["traffic"] = traffic_from_profile()
-    roofline["kernel"] = "elem_kernel (fused force + tangent + CSR scatter)"
+    roofline["kernel"] = ("pair_kernel (closed-form SVK pair tangent, fused force + tangent + CSR scatter)"
+                          if tune.get("elem_pair") and prec == tl.TL_FP32_ELEM else
+                          "elem_kernel (fused force + tangent + CSR scatter)")
     roofline["kernel_ms"] = elem_ms
     roofline["residual_ms"] = tim["ms_residual"] / max(1, tim["n_residual"])
     roofline["algorithmic_bytes_per_elem"] = bpe
