@@ -61,7 +61,7 @@ void free_mesh(tl_mesh* m) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
-  void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_ancf_me, m->d_geo32, m->d_geo_df, m->d_X, m->d_node_ptr, m->d_node_col,
+  void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_ancf_me, m->d_geo32, m->d_geo_df, m->d_uv32, m->d_X, m->d_node_ptr, m->d_node_col,
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
                   m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2,
                   m->d_con_ptr, m->d_con_col, m->d_con_val, m->d_con_b, m->d_ct_ptr, m->d_ct_con, m->d_ct_val,
@@ -253,6 +253,7 @@ tl_status upload_mesh(tl_mesh* m, int nmat, const std::vector<std::vector<int64_
     }
     TRYC(cudaMalloc(&m->d_geo_df, sizeof(float) * 32 * ne_pad));
     TRYC(cudaMemcpy(m->d_geo_df, h_geodf.data(), sizeof(float) * 32 * ne_pad, cudaMemcpyHostToDevice));
+    TRYC(cudaMalloc(&m->d_uv32, sizeof(float2) * 3 * std::max<int64_t>(m->nn, 1)));
   }
   TRYC(cudaMemcpy(m->d_X, X, sizeof(double) * 3 * m->nn, cudaMemcpyHostToDevice));
   TRYC(cudaMemset(m->d_flags, 0, sizeof(uint32_t) * 4));

@@ -89,6 +89,7 @@ struct Args {
   const uint16_t* agg_cptr;    // per tile: first contribution of each pair
   const uint16_t* agg_code;    // per tile: exchange-buffer block (+ transposed flag) of each contribution
   const int32_t* agg_nu;       // per tile: number of distinct pairs
+  const float2* uv;            // pair kernel: per DOF {q_n + h v - X, v} in float32 (pair_prep)
 };
 
 // Per-element shared-memory strides padded to odd word counts so that lanes
@@ -1090,6 +1091,7 @@ __global__ void __launch_bounds__(NTW, 1) elem_kernel_ws(Args<float> A, SegTable
 // (tl_element_pair.cu): one persistent launch over the segments of S.
 tl_status pair_launch(tl_mesh* m, const Args<float>& A, const SegTable<float>& S, bool kv, bool do_force,
                       int* counter);
+tl_status pair_prep(tl_mesh* m, const double* q_n, const double* v, double h);
 
 template <typename T, bool DO_FORCE, bool DO_TANGENT>
 tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, double alpha, double beta,
@@ -1148,11 +1150,25 @@ tl_status launch_all(tl_mesh* m, const double* q_n, const double* v, double h, d
   A.agg_cptr = m->agg_cptr;
   A.agg_code = m->agg_code;
   A.agg_nu = m->agg_nu;
+  A.uv = nullptr;
   // float32 tangent passes: SVK segments go to the closed-form pair kernel
   // (CSR values through the tile maps, or K_elem), in launches of their own
   const bool pair_mode = std::is_same<T, float>::value && DO_TANGENT && m->tune.elem_pair &&
                          ((K_elem && !values) || (values && !K_elem && m->tune.elem_agg && m->agg_nu));
   cudaEvent_t t0 = timer_open(m);
+  if constexpr (std::is_same<T, float>::value) {
+    if (pair_mode) {
+      // the pair kernel gathers float32 {u, v} per DOF, formed here once per pass
+      // instead of once per element that shares the node
+      bool any_svk = false;
+      for (const Segment& sg : m->segs) any_svk = any_svk || (m->mats[sg.mat].kind == TL_SVK && sg.padded_end > sg.begin);
+      if (any_svk) {
+        if (!m->d_uv32) return fail(m, TL_ERR_INVALID_ARG, "pair kernel without its float32 nodal buffer");
+        TL_TRY(pair_prep(m, q_n, v, h));
+        A.uv = m->d_uv32;
+      }
+    }
+  }
   // Segments in groups of at most kMaxSeg, one persistent launch per group.
   // The float32 kernels include an all-materials variant; the float64 ones
   // (heavier, compiled per material) take one launch per run of segments of

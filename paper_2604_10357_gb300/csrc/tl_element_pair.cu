@@ -17,7 +17,8 @@
 // 27-entry tangent row the generic kernel contracts with n_a and n_b from
 // shared memory for every block row.
 //
-// Layout: a CTA of 160 threads (5 warps, lanes = the 32 elements of a tile).
+// Layout: a CTA of 192 threads, lanes = the 32 elements of a tile; warps 0-4
+// compute, warp 5 helps to stage and scatter.
 //   phase A, warp q: the kinematics and the constitutive update at point q;
 //            it stores n_a (10 x float4), F, wJ0 S, c2 wJ0 B and wJ0 per
 //            (element, point) in shared memory;
@@ -32,7 +33,10 @@
 //   and the tile's distinct node pairs are reduced into the CSR values once
 //   per tile (tangent_agg_scatter), or written to K_elem.
 // The next tile's connectivity and geometry and the current tile's map are
-// copied into shared memory with cp.async while the tile computes.
+// copied into shared memory with cp.async while the tile computes.  The nodal
+// inputs are float32 {u = q_n + h v - X, v} per DOF, formed once per pass
+// (pair_prep), so the kernel itself holds no float64 arithmetic but the
+// conversion of its nodal forces for the float64 force vector.
 #include "tl_element_impl.cuh"
 
 namespace tl {
@@ -55,13 +59,15 @@ constexpr int kQStride = 5 * kQd + 4;
 constexpr int kNv = 40;           // 10 nodes x float4 (n_a, 0)
 constexpr int kNvStride = 5 * kNv + 4;
 
+// u and vel stay outside the exchange buffer, so the next tile's nodal data
+// can be stored while other warps still scatter this tile.
 struct SmemP {
   int32_t node[10][E];
   float geo[16][E];
+  float u[30 * E];
+  float vel[30 * E];
   union {
     struct {
-      float u[30 * E];
-      float vel[30 * E];
       float qd[E * kQStride];
       float nv[E * kNvStride];
     } a;
@@ -86,15 +92,16 @@ struct PrefP {
   int32_t pad[3];
 };
 
-// Nodal data of the 30 element DOFs of a tile, one thread's share: q_n, v, X
-// of DOF (c, e) for t = threadIdx.x + j NTP, c = t / 32, e = t % 32; the node
-// of (c, e) is conn_rows[e][c / 3] (element-major rows).  The loads of the
-// next tile are issued before the current tile's scatter and consumed after
-// it, so their latency hides behind the reductions.
+// Nodal data of the 30 element DOFs of a tile, one thread's share: {u, v}
+// of DOF (c, e) for t = threadIdx.x + j NTP, c = t / 32, e = t % 32, from the
+// float32 array that pair_prep forms once per pass; the node of (c, e) is
+// conn_rows[e][c / 3] (element-major rows).  The loads of the next tile are
+// issued before the current tile's scatter and consumed after it, so their
+// latency hides behind the reductions.
 constexpr int kNodalIt = E * 30 / NTP;
 static_assert(E * 30 % NTP == 0 && NTP % E == 0, "nodal gather");
 struct NodalRegs {
-  double qn[kNodalIt], vv[kNodalIt], xx[kNodalIt];
+  float2 uv[kNodalIt];
 };
 
 __device__ __forceinline__ void nodal_load(const Args<float>& A, const int32_t* conn_rows, NodalRegs& r) {
@@ -102,21 +109,27 @@ __device__ __forceinline__ void nodal_load(const Args<float>& A, const int32_t* 
   for (int j = 0; j < kNodalIt; ++j) {
     const int c = (int)(threadIdx.x >> 5) + j * (NTP / E), e = threadIdx.x & 31;
     const int64_t g = 3 * (int64_t)conn_rows[e * 10 + c / 3] + c % 3;
-    r.qn[j] = A.q_n[g];
-    r.vv[j] = A.v[g];
-    r.xx[j] = A.X[g];
+    r.uv[j] = A.uv[g];
   }
 }
 
-// u = q_n + h v - X formed in float64, then float32; v in float32 (KV).
 template <bool KV>
-__device__ __forceinline__ void nodal_store(const Args<float>& A, SmemP& sm, const NodalRegs& r) {
-  const double h = A.h;
+__device__ __forceinline__ void nodal_store(SmemP& sm, const NodalRegs& r) {
 #pragma unroll
   for (int j = 0; j < kNodalIt; ++j) {
     const int t = threadIdx.x + j * NTP;
-    sm.r.a.u[t] = float(r.qn[j] + h * r.vv[j] - r.xx[j]);
-    if (KV) sm.r.a.vel[t] = float(r.vv[j]);
+    sm.u[t] = r.uv[j].x;
+    if (KV) sm.vel[t] = r.uv[j].y;
+  }
+}
+
+// Per DOF: u = q_n + h v - X formed in float64, then rounded to float32, and
+// v rounded to float32 (the pair kernel's nodal inputs).
+__global__ void uv32_kernel(const double* __restrict__ q_n, const double* __restrict__ v,
+                            const double* __restrict__ X, double h, int64_t n, float2* __restrict__ uv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double vi = v[i];
+    uv[i] = make_float2(float(q_n[i] + h * vi - X[i]), float(vi));
   }
 }
 
@@ -134,7 +147,7 @@ __device__ __forceinline__ void load_tile_p(const Args<float>& A, SmemP& sm, int
   }
   NodalRegs r;
   nodal_load(A, A.conn + e0 * 10, r);
-  nodal_store<KV>(A, sm, r);
+  nodal_store<KV>(sm, r);
   __syncthreads();
 }
 
@@ -184,7 +197,7 @@ __device__ __forceinline__ void unpack_p(const Args<float>& A, SmemP& sm, const 
     const int e = t / 16, c = t % 16;
     sm.geo[c][e] = P.geo[t];
   }
-  nodal_store<KV>(A, sm, r);
+  nodal_store<KV>(sm, r);
   __syncthreads();
 }
 
@@ -261,9 +274,9 @@ __device__ __forceinline__ void phase_a(const MatT<float>& mat, float c2, SmemP&
   for (int a = 0; a < 10; ++a)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      const float ua = sm.r.a.u[(a * 3 + r) * E + e];
+      const float ua = sm.u[(a * 3 + r) * E + e];
       float va = 0.0f;
-      if (KV) va = sm.r.a.vel[(a * 3 + r) * E + e];
+      if (KV) va = sm.vel[(a * 3 + r) * E + e];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         Hm[r][c] += ua * n[a][c];
@@ -492,7 +505,11 @@ __global__ void __launch_bounds__(NTP, 2) pair_kernel(Args<float> A, SegTable<fl
     if (e0_next >= 0) nodal_load(A, P->conn, nr);
     if (M) map_scatter(A, sm.r.X, *M, nu);
     cp_async_wait_all();
-    __syncthreads();                                 // this tile's shared data is consumed
+    // with CSR values, the barrier after the exchange-buffer writes already
+    // put phase C's reads of node / geo before the unpack below, which writes
+    // nothing the scatter reads (u and vel lie outside the exchange buffer);
+    // the K_elem path has no such barrier
+    if (!M) __syncthreads();
     if (k_next >= S.ntiles) break;
     if (threadIdx.x == 0) s_next = counter ? (int)gridDim.x + atomicAdd(counter, 1) : k_next + (int)gridDim.x;
     k = k_next;
@@ -515,6 +532,18 @@ __global__ void __launch_bounds__(NTP, 2) pair_kernel(Args<float> A, SegTable<fl
 
 namespace tl {
 namespace elem {
+
+// The float32 {u, v} of every DOF for the pair kernel (m->d_uv32).
+tl_status pair_prep(tl_mesh* m, const double* q_n, const double* v, double h) {
+  const int64_t n = 3 * m->nn;
+  if (n == 0) return TL_OK;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, (int64_t)m->num_sms * 32);
+  uv32_kernel<<<(unsigned)blocks, threads, 0, m->stream>>>(q_n, v, m->d_X, h, n, m->d_uv32);
+  TL_CUDA(m, cudaGetLastError());
+  ++m->launches;
+  return TL_OK;
+}
 
 // One persistent launch of the pair kernel over the SVK segments of S.
 tl_status pair_launch(tl_mesh* m, const Args<float>& A0, const SegTable<float>& S, bool kv, bool do_force,

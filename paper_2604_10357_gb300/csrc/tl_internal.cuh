@@ -102,6 +102,8 @@ struct tl_mesh {
   double* d_ancf_me = nullptr;    // ANCF: ne_pad * nen(nen+1)/2 exact element mass (upper triangle)
   float* d_geo32 = nullptr;       // same in float32 (TL_FP32_ELEM)
   float* d_geo_df = nullptr;      // same as double-float pairs (TL_FP32_ELEM: float64-class residual force)
+  float2* d_uv32 = nullptr;       // TL_FP32_ELEM T10: per DOF {q_n + h v - X, v} in float32, formed once
+                                  // per element pass for the pair kernel's gather (3 nn)
   double* d_X = nullptr;          // 3 nn
 
   // pattern (tl_build_pattern)
