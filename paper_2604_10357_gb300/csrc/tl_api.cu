@@ -63,7 +63,7 @@ void free_mesh(tl_mesh* m) {
   cudaSetDevice(m->device);
   void* ptrs[] = {m->d_conn, m->d_user_of, m->d_geo64, m->d_ancf_me, m->d_geo32, m->d_geo_df, m->d_uv32, m->d_X, m->d_node_ptr, m->d_node_col,
                   m->d_row_ptr, m->d_col, m->d_blk, m->d_mass, m->d_mrow, m->d_fixed_of_node, m->d_fixed_diag,
-                  m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2,
+                  m->d_flags, m->d_tile_counters, m->d_partials, m->d_dv, m->d_dv2, m->d_mass2, m->d_sell_row, m->d_sell_ptr, m->d_sell_col, m->d_sell_m,
                   m->d_con_ptr, m->d_con_col, m->d_con_val, m->d_con_b, m->d_ct_ptr, m->d_ct_con, m->d_ct_val,
                   m->d_con_w, m->d_con_sq, m->nw_g, m->nw_f, m->nw_dv, m->nw_scal, m->nw_vt, m->nw_values,
                   m->aw_m1, m->aw_m2, m->aw_vn};

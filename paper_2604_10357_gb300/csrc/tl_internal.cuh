@@ -143,6 +143,13 @@ struct tl_mesh {
   double* d_dv = nullptr;         // v - v_n of the last residual (3 nn)
   float2* d_dv2 = nullptr;        // the same as float32 pairs (double-float mass product)
   float2* d_mass2 = nullptr;      // node-level mass as float32 pairs (nnz_node)
+  // the same rows in sliced ELL (tl_residual.cu): slices of 32 rows, rows by
+  // length within windows of 256; entry k of row lane l of slice s at
+  // d_sell_ptr[s] + 32 k + l (padding: own node, zero mass)
+  int32_t* d_sell_row = nullptr;  // node of each (slice, lane), -1 past nn (nslices x 32)
+  int64_t* d_sell_ptr = nullptr;  // nslices + 1 entry offsets
+  int32_t* d_sell_col = nullptr;
+  float2* d_sell_m = nullptr;
   int partials_cap = 0;
 
   tl::Solver* solver = nullptr;

@@ -13,6 +13,8 @@
 // is deterministic.
 #include <mutex>
 
+#include <cub/device/device_scan.cuh>
+
 #include "tl_internal.cuh"
 
 namespace tl {
@@ -246,6 +248,47 @@ __device__ __forceinline__ void df_combine(float& s_hi, float& s_lo, float o_hi,
   s_lo = __fadd_rn(s_lo, __fadd_rn(err, o_lo));
 }
 
+// The rest of node I's residual once its mass product acc = (M dv)_I is
+// formed: force, gravity, external force, clamp and general-constraint
+// terms; g written, its squared norm returned.
+template <bool CON>
+__device__ __forceinline__ double node_rest(int64_t I, const double (&acc)[3], const double* mrow,
+                                            const int32_t* fixed_of_node, const double* X, double h, double inv_h,
+                                            double rho, double gx, double gy, double gz, const double* q_n,
+                                            const double* v, const double* f_int, const double* f_ext,
+                                            const double* lambda, double* g, const ConTerm& ct) {
+  const double grav[3] = {gx, gy, gz};
+  const int j = fixed_of_node[I];
+  const double mr = mrow[I];
+  double sq = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t r = 3 * I + d;
+    double gd = acc[d] * inv_h + f_int[r] - mr * grav[d];
+    if (f_ext) gd -= f_ext[r];
+    if (j >= 0) {
+      const double c = (q_n[r] + h * v[r]) - X[r];
+      gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
+    }
+    if (CON) gd += h * con_term(ct, r);
+    g[r] = gd;
+    sq += gd * gd;
+  }
+  return sq;
+}
+
+// The block's sum of sq into partials[blockIdx.x] (every thread calls it).
+__device__ __forceinline__ void block_partial(double sq, double* red, double* partials) {
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
 // LANES lanes per node: lane l takes the mass-row entries l, l + LANES, ...;
 // the lanes' double-float sums are combined by shuffles (two-sums of the high
 // parts) and the first lane forms the node's residual.  A block holds
@@ -283,31 +326,144 @@ __global__ void __launch_bounds__(kResBlock * LANES)
   }
   if (I < nn && l == 0) {
     const double acc[3] = {(double)h0 + (double)l0, (double)h1 + (double)l1, (double)h2 + (double)l2};
-    const double grav[3] = {gx, gy, gz};
-    const int j = fixed_of_node[I];
-    const double mr = mrow[I];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int64_t r = 3 * I + d;
-      double gd = acc[d] * inv_h + f_int[r] - mr * grav[d];
-      if (f_ext) gd -= f_ext[r];
-      if (j >= 0) {
-        const double c = (q_n[r] + h * v[r]) - X[r];
-        gd += h * ((lambda ? lambda[3 * j + d] : 0.0) + rho * c);
-      }
-      if (CON) gd += h * con_term(ct, r);
-      g[r] = gd;
-      sq += gd * gd;
-    }
+    sq = node_rest<CON>(I, acc, mrow, fixed_of_node, X, h, inv_h, rho, gx, gy, gz, q_n, v, f_int, f_ext, lambda, g,
+                        ct);
   }
-  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  block_partial(sq, red, partials);
+}
+
+// Sliced ELL copy of the float32-pair mass rows (pattern build, once):
+// slices of kSellC = 32 rows, the rows of every window of kSellWin = 256
+// rows ordered by length, longest first (a stable sort, so equal lengths keep
+// node order), so the 32 rows of a slice have (nearly) one length; entry k
+// of the row at lane l of slice s sits at ptr[s] + 32 k + l, padded to the
+// slice's longest row with the row's own node and zero mass.  A warp then
+// reads entry k of its 32 rows as one contiguous run, where one thread per
+// CSR row touched 32 separate rows per load (the row-per-thread kernel was
+// bound by L1 wavefronts).
+constexpr int kSellC = 32, kSellWin = 256;
+// Row entries per round of the residual loop: two, measured on the 960k box
+// against one, three, four and eight (0.213 ms per residual pass against
+// 0.268, 0.258, 0.263 and 0.266 ms; more loads in flight per warp did not pay
+// beyond two).
+constexpr int kSellU = 2;
+static_assert(kResBlock == kSellWin, "one sorting window per residual block");
+
+__global__ void __launch_bounds__(kSellWin) sell_order(const int32_t* node_ptr, int64_t nn, int32_t* row_of) {
+  __shared__ uint32_t key[kSellWin];
+  const int64_t w0 = blockIdx.x * (int64_t)kSellWin;
+  const int i = threadIdx.x;
+  uint32_t k = 0xffffffffu;
+  if (w0 + i < nn) {
+    const int len = min(node_ptr[w0 + i + 1] - node_ptr[w0 + i], 0xffff);
+    k = ((uint32_t)(0xffff - len) << 16) | (uint32_t)i;
+  }
+  key[i] = k;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  for (int size = 2; size <= kSellWin; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int j = i ^ stride;
+      if (j > i) {
+        const bool up = (i & size) == 0;
+        const uint32_t a = key[i], c = key[j];
+        if ((a > c) == up) {
+          key[i] = c;
+          key[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  row_of[w0 + i] = key[i] == 0xffffffffu ? -1 : (int32_t)(w0 + (key[i] & 0xffffu));
+}
+
+// cnt[s] = 32 x the longest row of slice s; cnt[nslices] = 0.
+__global__ void sell_len(const int32_t* node_ptr, const int32_t* row_of, int64_t nslices, int64_t* cnt) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s > nslices) return;
+  int64_t L = 0;
+  if (s < nslices)
+    for (int r = 0; r < kSellC; ++r) {
+      const int32_t I = row_of[s * kSellC + r];
+      if (I >= 0) L = max(L, (int64_t)(node_ptr[I + 1] - node_ptr[I]));
+    }
+  cnt[s] = L * kSellC;
+}
+
+__global__ void sell_fill(const int32_t* node_ptr, const int32_t* node_col, const float2* mass2, const int32_t* row_of,
+                          const int64_t* ptr, int64_t nslices, int32_t* col, float2* mv) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nslices * kSellC) return;
+  const int64_t s = t / kSellC, b = ptr[s], L = (ptr[s + 1] - b) / kSellC;
+  const int32_t I = row_of[t];
+  int32_t p0 = 0, len = 0;
+  if (I >= 0) {
+    p0 = node_ptr[I];
+    len = node_ptr[I + 1] - p0;
   }
+  for (int64_t k = 0; k < L; ++k) {
+    const int64_t idx = b + k * kSellC + (t % kSellC);
+    const bool real = k < len;
+    col[idx] = real ? node_col[p0 + k] : (I >= 0 ? I : 0);
+    mv[idx] = real ? mass2[p0 + k] : make_float2(0.0f, 0.0f);
+  }
+}
+
+// The double-float residual over the sliced ELL rows: thread t -> the row at
+// lane t % 32 of slice t / 32 (a block = one sorting window of 256 rows),
+// the same arithmetic per entry as residual_split_kernel<1>.
+template <bool CON>
+__global__ void __launch_bounds__(kResBlock)
+    residual_sell_kernel(const int32_t* __restrict__ row_of, const int64_t* __restrict__ ptr,
+                         const int32_t* __restrict__ scol, const float2* __restrict__ smass,
+                         const double* mrow, const int32_t* fixed_of_node, const double* X, double h, double inv_h,
+                         double rho, double gx, double gy, double gz, const double* q_n, const double* v,
+                         const float2* __restrict__ dv2, const double* f_int, const double* f_ext,
+                         const double* lambda, double* g, double* partials, ConTerm ct) {
+  __shared__ double red[kResBlock / 32];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // the grid covers the slices exactly
+  const int64_t I = row_of[t];
+  double sq = 0.0;
+  if (I >= 0) {
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    const int64_t b = ptr[t / kSellC] + (t % kSellC);
+    const int L = (int)((ptr[t / kSellC + 1] - ptr[t / kSellC]) / kSellC);   // warp-uniform
+    const int32_t* cp = scol + b;
+    const float2* mp = smass + b;
+    // kSellU entries per round: their columns and masses, then the 3 kSellU
+    // gathers of dv, then the arithmetic, so that many loads are in flight
+    // (one entry per round left the kernel waiting on each dependent load)
+    int k = 0;
+    for (; k + kSellU <= L; k += kSellU) {
+      int32_t J[kSellU];
+      float2 mij[kSellU], d[kSellU][3];
+#pragma unroll
+      for (int u = 0; u < kSellU; ++u) {
+        J[u] = cp[(int64_t)(k + u) * kSellC];
+        mij[u] = mp[(int64_t)(k + u) * kSellC];
+      }
+#pragma unroll
+      for (int u = 0; u < kSellU; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[u][c] = dv2[3 * (int64_t)J[u] + c];
+#pragma unroll
+      for (int u = 0; u < kSellU; ++u) {
+        df_mac(h0, l0, mij[u], d[u][0]);
+        df_mac(h1, l1, mij[u], d[u][1]);
+        df_mac(h2, l2, mij[u], d[u][2]);
+      }
+    }
+    for (; k < L; ++k) {
+      const int64_t J = cp[(int64_t)k * kSellC];
+      const float2 mij = mp[(int64_t)k * kSellC];
+      df_mac(h0, l0, mij, dv2[3 * J]);
+      df_mac(h1, l1, mij, dv2[3 * J + 1]);
+      df_mac(h2, l2, mij, dv2[3 * J + 2]);
+    }
+    const double acc[3] = {(double)h0 + (double)l0, (double)h1 + (double)l1, (double)h2 + (double)l2};
+    sq = node_rest<CON>(I, acc, mrow, fixed_of_node, X, h, inv_h, rho, gx, gy, gz, q_n, v, f_int, f_ext, lambda, g,
+                        ct);
+  }
+  block_partial(sq, red, partials);
 }
 
 __global__ void finish_norm(const double* partials, int n, double* out, uint32_t* flags) {
@@ -364,15 +520,64 @@ tl_status launch_con_update(tl_mesh* m, const double* q_n, const double* v, doub
   return TL_OK;
 }
 
+tl_status mass_sell_build(tl_mesh* m, cudaStream_t s);
+
 // float32 pairs of the node-level mass (double-float mass product); once per
-// handle, after the mass is assembled.
+// handle, after the mass is assembled, and their sliced ELL copy.
 tl_status mass_split_build(tl_mesh* m, cudaStream_t s) {
   const int64_t n = std::max<int64_t>(m->nnz_node, 1);
   if (!m->d_mass2) TL_CUDA(m, cudaMalloc(&m->d_mass2, sizeof(float2) * n));
   split_array<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->d_mass, n, m->d_mass2);
   TL_CUDA(m, cudaGetLastError());
   ++m->launches;
-  return TL_OK;
+  return mass_sell_build(m, s);
+}
+
+// The sliced ELL copy of d_mass2 (pattern build, after mass_split_build).
+tl_status mass_sell_build(tl_mesh* m, cudaStream_t s) {
+  for (void* p : {(void*)m->d_sell_row, (void*)m->d_sell_ptr, (void*)m->d_sell_col, (void*)m->d_sell_m})
+    if (p) cudaFree(p);
+  m->d_sell_row = nullptr;
+  m->d_sell_ptr = nullptr;
+  m->d_sell_col = nullptr;
+  m->d_sell_m = nullptr;
+  if (m->nn == 0) return TL_OK;
+  const int64_t nwin = (m->nn + kSellWin - 1) / kSellWin, nslices = nwin * (kSellWin / kSellC);
+  int64_t* d_cnt = nullptr;
+  void* d_tmp = nullptr;
+  size_t tmp_bytes = 0;
+  int64_t total = 0;
+  tl_status st = TL_OK;
+  auto chk = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == TL_OK) st = cuda_fail(m, e, what);
+    return st == TL_OK;
+  };
+  if (chk(cudaMalloc(&m->d_sell_row, sizeof(int32_t) * nslices * kSellC), "cudaMalloc(sell_row)") &&
+      chk(cudaMalloc(&m->d_sell_ptr, sizeof(int64_t) * (nslices + 1)), "cudaMalloc(sell_ptr)") &&
+      chk(cudaMalloc(&d_cnt, sizeof(int64_t) * (nslices + 1)), "cudaMalloc(sell counts)")) {
+    sell_order<<<(unsigned)nwin, kSellWin, 0, s>>>(m->d_node_ptr, m->nn, m->d_sell_row);
+    sell_len<<<(unsigned)((nslices + 1 + 255) / 256), 256, 0, s>>>(m->d_node_ptr, m->d_sell_row, nslices, d_cnt);
+    if (chk(cudaGetLastError(), "sell_order / sell_len") &&
+        chk(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_cnt, m->d_sell_ptr, (int)(nslices + 1), s),
+            "cub scan size") &&
+        chk(cudaMalloc(&d_tmp, std::max<size_t>(tmp_bytes, 1)), "cudaMalloc(scan scratch)") &&
+        chk(cub::DeviceScan::ExclusiveSum(d_tmp, tmp_bytes, d_cnt, m->d_sell_ptr, (int)(nslices + 1), s),
+            "cub scan") &&
+        chk(cudaMemcpyAsync(&total, m->d_sell_ptr + nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+            "sell total") &&
+        chk(cudaStreamSynchronize(s), "sell total sync") &&
+        chk(cudaMalloc(&m->d_sell_col, sizeof(int32_t) * std::max<int64_t>(total, 1)), "cudaMalloc(sell_col)") &&
+        chk(cudaMalloc(&m->d_sell_m, sizeof(float2) * std::max<int64_t>(total, 1)), "cudaMalloc(sell_m)")) {
+      sell_fill<<<(unsigned)((nslices * kSellC + 255) / 256), 256, 0, s>>>(
+          m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_sell_row, m->d_sell_ptr, nslices, m->d_sell_col,
+          m->d_sell_m);
+      chk(cudaGetLastError(), "sell_fill");
+      m->launches += 4;
+    }
+  }
+  if (d_cnt) cudaFree(d_cnt);
+  if (d_tmp) cudaFree(d_tmp);
+  return st;
 }
 
 // Norm partials owned by the handle (one per block of kResBlock nodes).
@@ -407,6 +612,11 @@ tl_status launch_residual(tl_mesh* m, const tl_params* p, const double* q_n, con
           m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
           p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext, lambda, g,
           m->d_partials, ct);
+    else if (m->d_sell_m)   // one lane per row, rows in sliced ELL (nb blocks = the slices' windows)
+      (ct.ptr ? residual_sell_kernel<true> : residual_sell_kernel<false>)<<<nb, kResBlock, 0, m->stream>>>(
+          m->d_sell_row, m->d_sell_ptr, m->d_sell_col, m->d_sell_m, m->d_mrow, m->d_fixed_of_node, m->d_X, p->h,
+          1.0 / p->h, p->rho_alm, p->gravity[0], p->gravity[1], p->gravity[2], q_n, v, m->d_dv2, f_int, f_ext,
+          lambda, g, m->d_partials, ct);
     else
       (ct.ptr ? residual_split_kernel<1, true> : residual_split_kernel<1, false>)<<<nb, kResBlock, 0, m->stream>>>(
           m->d_node_ptr, m->d_node_col, m->d_mass2, m->d_mrow, m->d_fixed_of_node, m->d_X, m->nn, p->h, 1.0 / p->h,
