@@ -461,6 +461,11 @@ typedef struct tl_tune_result {
                                  per-tile maps, needs elem_agg; or K_elem); Mooney-Rivlin segments keep
                                  the generic kernel; default 1 */
   float ms_pair;              /* fastest measured pair-kernel variant (0: not measured) */
+  int32_t elem_fold;          /* pair kernel: 1 = folded form, where c1 + c2 >= max(|c1|, |c2|) / 4 for every
+                                 segment of the launch (else the unfolded form runs): Q_ab = sum over points of
+                                 wJ0 g_a g_b^T + [(n_a.n_b) c2 wJ0 B + (n_a.alpha wJ0 S n_b) I] / (c1 + c2),
+                                 then K_ab = c1 Q_ab + c2 Q_ab^T once per tile; 0 = the unfolded form always
+                                 (default 1) */
 } tl_tune_result;
 
 tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v, double h, int32_t reps,

@@ -77,6 +77,7 @@ struct Tune {
   int pcg_f32 = 1;        // float32 Hessian: 1 = PCG vectors in float32 (dot products float64)
   int elem_agg = 1;       // float32 exchanged assembly: 1 = per-tile aggregation of shared node pairs
   int elem_pair = 1;      // float32 tangent passes: 1 = closed-form pair kernel for SVK (+ KV) segments
+  int elem_fold = 1;      // pair kernel: 1 = folded form where c1 + c2 is not small (no cancellation)
   int tuned = 0;
   int64_t generation = 0; // bumped whenever a choice changes (captured graphs are rebuilt)
 };

@@ -269,6 +269,7 @@ extern "C" tl_status tl_autotune(tl_mesh* m, const double* q_n, const double* v,
   r.residual_split = chosen.residual_split;
   r.force_split = chosen.force_split;
   r.elem_pair = chosen.elem_pair;
+  r.elem_fold = chosen.elem_fold;
   if (out) *out = r;
   return TL_OK;
 }
@@ -290,6 +291,7 @@ extern "C" tl_status tl_tune_get(const tl_mesh* m, tl_tune_result* out) {
   r.residual_split = m->tune.residual_split;
   r.force_split = m->tune.force_split;
   r.elem_pair = m->tune.elem_pair;
+  r.elem_fold = m->tune.elem_fold;
   *out = r;
   return TL_OK;
 }
@@ -304,7 +306,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
       (in->elem_spread != 0 && in->elem_spread != 1) || (in->pcg_f32 != 0 && in->pcg_f32 != 1) ||
       (in->spmv_row != 0 && in->spmv_row != 1) || (in->elem_agg != 0 && in->elem_agg != 1) ||
       (in->residual_split != 0 && in->residual_split != 1) || (in->force_split != 0 && in->force_split != 1) ||
-      (in->elem_pair != 0 && in->elem_pair != 1))
+      (in->elem_pair != 0 && in->elem_pair != 1) || (in->elem_fold != 0 && in->elem_fold != 1))
     return TL_ERR_INVALID_ARG;
   if ((in->elem_agg || in->elem_pair) && m->precision == TL_FP32_ELEM) TL_TRY(tile_maps_ensure(m));
   m->tune.spmv_group = in->spmv_group;
@@ -321,6 +323,7 @@ extern "C" tl_status tl_tune_set(tl_mesh* m, const tl_tune_result* in) {
   m->tune.residual_split = in->residual_split;
   m->tune.force_split = in->force_split;
   m->tune.elem_pair = in->elem_pair;
+  m->tune.elem_fold = in->elem_fold;
   m->tune.generation += 1;
   return TL_OK;
 }

@@ -86,7 +86,7 @@ class tl_tune_result(C.Structure):
                 ("pcg_f32", C.c_int32), ("spmv_row", C.c_int32), ("ms_spmv_row", C.c_float * 3),
                 ("elem_agg", C.c_int32), ("ms_agg", C.c_float), ("residual_split", C.c_int32),
                 ("ms_residual_split", C.c_float * 2), ("force_split", C.c_int32), ("ms_force", C.c_float * 2),
-                ("elem_pair", C.c_int32), ("ms_pair", C.c_float)]
+                ("elem_pair", C.c_int32), ("ms_pair", C.c_float), ("elem_fold", C.c_int32)]
 
 
 # every symbol declared in include/tl.h, with (restype, argtypes)
@@ -196,7 +196,8 @@ def _tune_dict(r):
                 ms_spread=r.ms_spread, pcg_f32=r.pcg_f32,
                 spmv_row=r.spmv_row, ms_spmv_row=list(r.ms_spmv_row), elem_agg=r.elem_agg, ms_agg=r.ms_agg,
                 residual_split=r.residual_split, ms_residual_split=list(r.ms_residual_split),
-                force_split=r.force_split, ms_force=list(r.ms_force), elem_pair=r.elem_pair, ms_pair=r.ms_pair)
+                force_split=r.force_split, ms_force=list(r.ms_force), elem_pair=r.elem_pair, ms_pair=r.ms_pair,
+                elem_fold=r.elem_fold)
 
 
 def _stream_ptr():
@@ -408,7 +409,7 @@ class Mesh:
 
     TUNE_KEYS = ("spmv_group", "spmv_row", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws",
                  "residual_lanes", "elem_occ2", "elem_spread", "pcg_f32", "elem_agg", "residual_split",
-                 "force_split", "elem_pair")
+                 "force_split", "elem_pair", "elem_fold")
 
     def tune_set(self, **choice):
         """Set launch shapes by name (see tl_tune_result); the others keep

@@ -3,8 +3,10 @@ with and without Kelvin-Voigt) against the FP64 oracle: the fused internal
 force and the CSR Hessian values through the per-tile maps, and the element
 tangents alpha K_t + beta D written per element, in every launch shape the
 library compiles for it (prefetch on / off, persistent grid or one CTA per
-tile), on meshes with a ragged last tile, shuffled element order, and a
-multi-material mesh whose Mooney-Rivlin segments keep the generic kernel."""
+tile) and in both of its forms (folded: K = c1 Q + c2 Q^T formed once per
+tile; unfolded), on meshes with a ragged last tile, shuffled element order,
+and a multi-material mesh whose Mooney-Rivlin segments keep the generic
+kernel."""
 import numpy as np
 import pytest
 
@@ -85,11 +87,12 @@ def _mesh(tl, w, **shape):
     return g
 
 
+@pytest.mark.parametrize("fold", [1, 0])
 @pytest.mark.parametrize("prefetch,full_grid", [(1, 0), (0, 0), (1, 1), (0, 1)])
-def test_pair_kernel_hessian_and_force(case, prefetch, full_grid):
+def test_pair_kernel_hessian_and_force(case, prefetch, full_grid, fold):
     tl = _tl()
     name, w, om = case
-    g = _mesh(tl, w, elem_prefetch=prefetch, elem_full_grid=full_grid)
+    g = _mesh(tl, w, elem_prefetch=prefetch, elem_full_grid=full_grid, elem_fold=fold)
     h, rho = w["h"], 1e12
     f = torch.empty(3 * w["mesh"].nn, dtype=torch.float64, device="cuda")
     for rep in range(2):                                  # the second pass sees values from the first: zeroed
@@ -108,15 +111,16 @@ def test_pair_kernel_hessian_and_force(case, prefetch, full_grid):
     assert force_error(f.cpu().numpy(), om.internal_force(w["q_n"], w["v"], h), fe) < TOL_FP32
 
 
+@pytest.mark.parametrize("fold", [1, 0])
 @pytest.mark.parametrize("ab", [(1.0, 0.0), (0.0, 1.0), (1e-3, 1.0)], ids=["K", "D", "hK+D"])
-def test_pair_kernel_element_tangents(case, ab):
+def test_pair_kernel_element_tangents(case, ab, fold):
     tl = _tl()
     name, w, om = case
     alpha, beta = ab
     if beta != 0.0 and not any(m.get("eta_d", 0) or m.get("lambda_d", 0)
                                for m in w.get("materials", [w.get("material")])):
         pytest.skip("no Kelvin-Voigt material in this workload")
-    g = _mesh(tl, w)
+    g = _mesh(tl, w, elem_fold=fold)
     h = w["h"]
     K = g.eval_tangent(_dev(w["q_n"]), _dev(w["v"]), h, alpha, beta).cpu().numpy()
     g.sync()
@@ -141,3 +145,39 @@ def test_pair_kernel_matches_generic_kernel():
         g.close()
     emax, e2 = values_error(out[1], out[0])
     assert emax < 2e-6 and e2 < 2e-6, (emax, e2)
+
+
+def _svk_kv_tangents(tl, w, alpha, beta, fold):
+    g = _mesh(tl, w, elem_fold=fold)
+    K = g.eval_tangent(_dev(w["q_n"]), _dev(w["v"]), w["h"], alpha, beta).cpu().numpy()
+    g.sync()
+    g.close()
+    return K
+
+
+def test_pair_kernel_fold_taken_and_declined():
+    """With alpha = 1, beta = 1e-3 (c1 + c2 well away from zero) the folded
+    form runs: its tangents differ from the unfolded ones at float32 rounding
+    and both match the oracle.  With beta chosen so that c1 + c2 nearly
+    cancels (c1 = -1.4e6, c2 = 1.4e6, c1 + c2 = 2e4: below a quarter of
+    max(|c1|, |c2|)) the library declines the fold: both settings give the
+    same bits, and they match the oracle."""
+    tl = _tl()
+    w = svk_kv_ragged()
+    mat = w["material"]
+    E, nu = mat["E"], mat["nu"]
+    lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    om = asm.OracleMesh(w["mesh"].X, w["mesh"].conn, [mat], fixed_nodes=w["mesh"].fixed_nodes)
+    x = w["q_n"] + w["h"] * w["v"]
+    # well conditioned: the fold is taken
+    K1, K0 = (_svk_kv_tangents(tl, w, 1.0, 1e-3, f) for f in (1, 0))
+    assert not np.array_equal(K1, K0)
+    K_ora = om.element_tangents(x, w["v"], 1.0, 1e-3)
+    assert tangent_error(K1, K_ora) < TOL_FP32 and tangent_error(K0, K_ora) < TOL_FP32
+    # c1 + c2 = (lam + mu) + beta (lambda_d + eta) close to zero against c1 and c2
+    beta = -(lam + mu - 2e4) / (mat["lambda_d"] + mat["eta_d"])
+    c1, c2 = lam + beta * mat["lambda_d"], mu + beta * mat["eta_d"]
+    assert abs(c1 + c2) < 0.25 * max(abs(c1), abs(c2))
+    K1, K0 = (_svk_kv_tangents(tl, w, 1.0, beta, f) for f in (1, 0))
+    assert np.array_equal(K1, K0)
+    assert tangent_error(K1, om.element_tangents(x, w["v"], 1.0, beta)) < TOL_FP32

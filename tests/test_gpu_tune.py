@@ -67,7 +67,8 @@ def test_autotune_reports_and_keeps_a_choice():
     assert rep["force_split"] == 0                            # a precision trade: never chosen by the tuner
     cur = g.tune_get()
     keys = ("spmv_group", "elem_xchg", "elem_full_grid", "elem_prefetch", "elem_ws", "residual_lanes", "elem_occ2",
-            "elem_spread", "spmv_row", "pcg_f32", "elem_agg", "residual_split", "force_split", "elem_pair")
+            "elem_spread", "spmv_row", "pcg_f32", "elem_agg", "residual_split", "force_split", "elem_pair",
+            "elem_fold")
     assert all(cur[k] == rep[k] for k in keys)
     with pytest.raises(tl.TLError):
         g.tune_set(spmv_group=5)
