@@ -56,11 +56,18 @@ struct Cfg {
   static constexpr int NT = ET == kBeam ? 288 : 160;        // >= EPB * NP pair threads
 };
 
-// Resident CTAs per SM the register budget is capped for (float64: 1 beam /
-// 2 shell CTAs; the float32 form needs fewer registers: 2 / 3).
-template <typename T, int ET>
+// Resident CTAs per SM the register budget is capped for.  float64: 1 beam /
+// 2 shell CTAs.  The float32 form needs fewer registers; its St. Venant-
+// Kirchhoff kernels were measured at 2 to 7 CTAs (500,000-element beam,
+// 200 x 200 shell): the beam 1.64 / 1.33 / 1.26 / 1.23 ms at 2 / 3 / 4 / 5
+// CTAs (5: 4 bytes of spills, 160 with Kelvin-Voigt, which keeps 4), the
+// shell 1.14 / 1.08 / 1.10 ms at 3 / 6 / 7 (no spills at 6); the Mooney-Rivlin
+// kernels spill at those caps and keep 2 / 3.
+template <typename T, int ET, int MAT, bool KV>
 constexpr int min_blocks() {
-  return std::is_same<T, float>::value ? (ET == kBeam ? 2 : 3) : (ET == kBeam ? 1 : 2);
+  return std::is_same<T, float>::value
+             ? (ET == kBeam ? (MAT == TL_SVK ? (KV ? 4 : 5) : 2) : (MAT == TL_SVK ? 6 : 3))
+             : (ET == kBeam ? 1 : 2);
 }
 
 // Per-point record in shared memory (elements of type T).  WG (float64 SVK
@@ -99,7 +106,7 @@ constexpr size_t smem_bytes() {
 }
 
 template <typename T, int ET, int MAT, bool KV, bool DO_FORCE, bool DO_TANGENT>
-__global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET>()) elem_kernel(Args<T> A) {
+__global__ void __launch_bounds__(Cfg<ET>::NT, min_blocks<T, ET, MAT, KV>()) elem_kernel(Args<T> A) {
   constexpr int NEN = Cfg<ET>::NEN, NQP = Cfg<ET>::NQP, NP = Cfg<ET>::NP, EPB = Cfg<ET>::EPB, NT = Cfg<ET>::NT;
   constexpr bool MR = MAT == TL_MOONEY_RIVLIN;
   constexpr bool WG = weighted_g<T, DO_TANGENT, MR>();
