@@ -422,7 +422,8 @@ typedef struct tl_tune_result {
   int32_t elem_full_grid;     /* 1: one CTA per tile; 0: persistent grid */
   int32_t elem_prefetch;      /* 1: cp.async prefetch of the next tile (FP32) */
   int32_t elem_ws;            /* 1: warp-specialised scatter (FP32; with xchg, prefetch, persistent grid) */
-  int32_t residual_lanes;     /* lanes per node in the residual: 1 or 4 */
+  int32_t residual_lanes;     /* lanes per node in the residual: 1 or 4 (with residual_split, 1 = one lane
+                                 per row of the mass in sliced ELL: slices of 32 rows ordered by length) */
   int32_t elem_occ2;          /* 1: two CTAs per SM (FP32 exchanged assembly, one material kind) */
   int32_t elem_spread;        /* 1: tiles in flight spread over the mesh (permuted launch order) */
   float ms_element[8];        /* measured element-pass times without warp specialisation (0: not measured) */
