@@ -46,8 +46,9 @@
 // The next tile's connectivity and geometry and the current tile's map are
 // copied into shared memory with cp.async while the tile computes.  The nodal
 // inputs are float32 {u = q_n + h v - X, v} per DOF, formed once per pass
-// (pair_prep), so the kernel itself holds no float64 arithmetic but the
-// conversion of its nodal forces for the float64 force vector.
+// (pair_prep), so the kernel itself runs no float64 arithmetic, only a few
+// conversions (a point's barycentric coordinates, and its nodal forces for
+// the float64 force vector).
 #include "tl_element_impl.cuh"
 
 namespace tl {
