@@ -206,3 +206,34 @@ def test_create_rejects_bad_input():
     flipped[:, [1, 2]] = flipped[:, [2, 1]]
     with pytest.raises(tl.TLError):
         tl.Mesh(m.X, flipped, [dict(inputs.SVK_1E7)])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_residual_sliced_ell_matches_csr_rows(case, prec):
+    """The default residual reads the mass rows in sliced ELL (slices of 32
+    rows ordered by length within windows of 256, padded with zero mass);
+    the four-lane form reads the same double-float rows in CSR order.  Both
+    sum the same products of the same float32 pairs, in other orders, so g
+    agrees to a few units of 2^-48 of its largest terms (1e-13), on meshes
+    whose node count leaves a partial last window and whose rows differ in
+    length (vertex and midside nodes, two bodies and a cylinder)."""
+    tl = _tl()
+    name, w, om = case
+    m = w["mesh"]
+    assert m.nn % 256 != 0
+    g = _gpu_mesh(tl, w, tl.TL_FP64 if prec == "fp64" else tl.TL_FP32_ELEM)
+    rng = np.random.default_rng(6)
+    v_n = w["v"] + 0.01 * rng.normal(size=w["v"].shape)
+    v_n[m.fixed_nodes] = 0.0
+    f_int = _dev(rng.normal(size=3 * m.nn))
+    lam = _dev(rng.normal(size=3 * len(m.fixed_nodes)))
+    prm = tl.params(h=w["h"], rho_alm=1e6)
+    out = {}
+    for lanes in (1, 4):
+        g.tune_set(residual_split=1, residual_lanes=lanes)
+        gg, gn = g.eval_residual(prm, _dev(w["q_n"]), _dev(v_n), _dev(w["v"]), lam=lam, f_int=f_int)
+        g.sync()
+        out[lanes] = (gg.cpu().numpy(), gn.item())
+    scale = np.abs(out[4][0]).max()
+    assert np.abs(out[1][0] - out[4][0]).max() <= 1e-13 * scale
+    assert abs(out[1][1] - out[4][1]) <= 1e-13 * out[4][1]
