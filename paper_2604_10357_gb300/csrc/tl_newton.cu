@@ -170,16 +170,18 @@ __global__ void ctl_inner(NewtonCtl* c, const double* gnorm, int max_inner, doub
   cudaGraphSetConditional(h_in, c->l < max_inner ? 1u : 0u);
 }
 
-__global__ void ctl_pcg_arm(NewtonCtl* c, const double* pscal, int lin_max, cudaGraphConditionalHandle h_pcg) {
+__global__ void ctl_pcg_arm(NewtonCtl* c, double* pscal, int lin_max, cudaGraphConditionalHandle h_pcg) {
   const double rr0 = pscal[3];
   c->tol2 = c->eta * c->eta * rr0;
+  pscal[5] = c->tol2;            // the PCG kernels return at once past the target
   c->pcg_it = 0;
   cudaGraphSetConditional(h_pcg, (rr0 > c->tol2 && lin_max > 0) ? 1u : 0u);
 }
 
 __global__ void ctl_pcg(NewtonCtl* c, const double* pscal, int chunk, int lin_max,
                         cudaGraphConditionalHandle h_pcg) {
-  c->pcg_it += chunk;
+  (void)chunk;
+  c->pcg_it = (int)pscal[7];     // iterations that ran (those past the target returned at once)
   const double rr = pscal[3];
   if (!isfinite(rr)) {
     c->abort = 1;

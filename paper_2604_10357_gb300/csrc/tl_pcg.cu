@@ -16,7 +16,9 @@
 // the x / r / z update with r.z and r.r, the p update); alpha and beta are
 // formed on the device from alternating r.z slots.  The host reads the
 // residual norm every kCheck iterations, or the check runs on the device
-// inside the captured Newton graph.
+// inside the captured Newton graph; the kernels of the iterations after the
+// target is reached return at entry, so the check's granularity costs only
+// launches.
 #include <cmath>
 #include <type_traits>
 
@@ -98,6 +100,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// The solve has reached its target (r.r <= slot 5) or broken down (slot 6):
+// the remaining iterations of a chunk return at once, so a chunk that
+// converges early costs its launches, not its work.  Read at kernel entry by
+// every block alike (slot 3 changes only in the last block of update_xr*).
+__device__ __forceinline__ bool pcg_done(const double* scal) { return scal[3] <= scal[5] || scal[6] != 0.0; }
+
 // The last block to finish a pass sums the per-block partials in a fixed
 // order (deterministic) and writes the total: a ticket counter (zero between
 // passes; the last block resets it) replaces a separate one-block launch.
@@ -134,6 +142,7 @@ __global__ void spmv_node(const T* __restrict__ vals, const int32_t* __restrict_
                           unsigned* ticket) {
   using A = typename SpmvAcc<T>::type;
   __shared__ double red[kBlock / 32];
+  if (pcg_done(scal)) return;
   const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   const int l = threadIdx.x & (G - 1);
   A s0 = 0, s1 = 0, s2 = 0;
@@ -182,6 +191,12 @@ __global__ void spmv_node(const T* __restrict__ vals, const int32_t* __restrict_
 }
 
 // finish a partial sum: scal[slot] = sum(part)
+// No r.r target and no breakdown: the per-iteration kernels run.
+__global__ void pcg_clear_target(double* scal) {
+  scal[5] = -1.0;
+  scal[6] = 0.0;
+}
+
 __global__ void finish_sum(const double* part, int n, double* scal, int slot) {
   __shared__ double red[32];
   double t = 0.0;
@@ -191,12 +206,14 @@ __global__ void finish_sum(const double* part, int n, double* scal, int slot) {
 }
 
 // scal layout: 0 and 2 r.z of alternate iterations (iteration k reads slot
-// 2 (k % 2) and writes slot 2 ((k + 1) % 2)), 1 p.Ap, 3 r.r, 6 breakdown flag.
+// 2 (k % 2) and writes slot 2 ((k + 1) % 2)), 1 p.Ap, 3 r.r, 5 the r.r target
+// (-1: none), 6 breakdown flag, 7 iterations run.
 // x += alpha p; r -= alpha Ap; z = P r; r.z and r.r finished by the last block
 __global__ void update_xr(double* x, double* r, double* z, const double* p, const double* Ap, const double* binv,
                           double* scal, int64_t nn, double* part_rz, double* part_rr, int parity,
                           unsigned* ticket) {
   __shared__ double red[kBlock / 32];
+  if (pcg_done(scal)) return;
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // pAp <= 0: H is not positive definite along p (CG breakdown); stop moving
   // and raise the breakdown slot, which ends the iteration at the next check
@@ -236,6 +253,7 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
     if (threadIdx.x == 0) {
       scal[rz_new] = trz;
       scal[3] = trr;
+      scal[7] += 1.0;                    // iterations run
       *ticket = 0u;
     }
   }
@@ -243,6 +261,7 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
 
 // p = z + beta p with beta = (r.z new) / (r.z old)
 __global__ void update_p(double* p, float* p32, const double* z, int64_t n, const double* scal, int parity) {
+  if (pcg_done(scal)) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double rz_old = scal[2 * parity], rz_new = scal[2 - 2 * parity];
   const double beta = rz_old != 0.0 ? rz_new / rz_old : 0.0;
@@ -258,7 +277,11 @@ __global__ void pcg_start(const double* g, double* x, double* r, double* z, doub
                           const double* binv, int64_t nn, double* part_rz, double* part_rr, double* scal) {
   __shared__ double red[kBlock / 32];
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (I == 0) scal[6] = 0.0;
+  if (I == 0) {
+    scal[5] = -1.0;                      // no target until the caller sets one
+    scal[6] = 0.0;
+    scal[7] = 0.0;
+  }
   double rz = 0.0, rr = 0.0;
   if (I < nn) {
     double rv[3];
@@ -302,7 +325,11 @@ __global__ void pcg_start32(const double* g, float* x, float* r, float* z, float
                             int64_t nn, double* part_rz, double* part_rr, double* scal) {
   __shared__ double red[kBlock / 32];
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (I == 0) scal[6] = 0.0;
+  if (I == 0) {
+    scal[5] = -1.0;                      // no target until the caller sets one
+    scal[6] = 0.0;
+    scal[7] = 0.0;
+  }
   double rz = 0.0, rr = 0.0;
   if (I < nn) {
     float rv[3];
@@ -334,6 +361,7 @@ __global__ void spmv_node32(const float* __restrict__ vals, const int32_t* __res
                             const int32_t* __restrict__ node_col, int64_t nn, const float* __restrict__ p,
                             float* __restrict__ Ap, double* part, double* scal, unsigned* ticket) {
   __shared__ double red[kBlock / 32];
+  if (pcg_done(scal)) return;
   const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   const int l = threadIdx.x & (G - 1);
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
@@ -387,6 +415,7 @@ __global__ void spmv_row32(const float* __restrict__ vals, const int32_t* __rest
                            float* __restrict__ Ap, double* part, double* scal, unsigned* ticket) {
   static_assert(G >= 4 && G <= 32 && (G & (G - 1)) == 0, "G: power of two in [4, 32]");
   __shared__ double red[kBlock / 32];
+  if (pcg_done(scal)) return;
   const int l = threadIdx.x & (G - 1);
   const int64_t groups = (int64_t)gridDim.x * (kBlock / G);
   // the loop bound is tested on the warp's first group, so every lane of a
@@ -446,6 +475,7 @@ __global__ void update_xr32(float* x, float* r, float* z, const float* p, const 
                             double* scal, int64_t nn, double* part_rz, double* part_rr, int parity,
                             unsigned* ticket) {
   __shared__ double red[kBlock / 32];
+  if (pcg_done(scal)) return;
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int rz_old = 2 * parity, rz_new = 2 - 2 * parity;
   const bool ok = scal[1] > 0.0;
@@ -483,12 +513,14 @@ __global__ void update_xr32(float* x, float* r, float* z, const float* p, const 
     if (threadIdx.x == 0) {
       scal[rz_new] = trz;
       scal[3] = trr;
+      scal[7] += 1.0;                    // iterations run
       *ticket = 0u;
     }
   }
 }
 
 __global__ void update_p32(float* p, const float* z, int64_t n, const double* scal, int parity) {
+  if (pcg_done(scal)) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double rz_old = scal[2 * parity], rz_new = scal[2 - 2 * parity];
   const float beta = rz_old != 0.0 ? float(rz_new / rz_old) : 0.0f;
@@ -600,6 +632,8 @@ void launch_spmv(tl_mesh* m, const void* values, PcgWork* w, unsigned* nblocks) 
 tl_status pcg_spmv_only(tl_mesh* m, const void* values, int group) {
   TL_TRY(pcg_ensure(m));
   PcgWork* w = m->pcg;
+  pcg_clear_target<<<1, 1, 0, m->stream>>>(w->scal);   // the timed product must not return early
+  ++m->launches;
   unsigned nbs = 0;
   const bool fp32 = m->precision == TL_FP32_ELEM;
   if (group == 4) fp32 ? launch_spmv<float, 4>(m, values, w, &nbs) : launch_spmv<double, 4>(m, values, w, &nbs);
@@ -663,20 +697,23 @@ tl_status pcg_solve(tl_mesh* m, const void* values, const double* g, double* dv,
   TL_CUDA(m, cudaMemcpyAsync(&rr0, w->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
   TL_CUDA(m, cudaStreamSynchronize(s));
   const double tol2 = rtol * rtol * rr0;
-  int it = 0;
+  // the target in slot 5: iterations of a chunk after it is reached return at once
+  TL_CUDA(m, cudaMemcpyAsync(w->scal + 5, &tol2, sizeof(double), cudaMemcpyHostToDevice, s));
+  int it = 0, run = 0;
   while (it < max_iter && rr0 > tol2) {
     const int k = std::min(kCheck, max_iter - it);
     TL_TRY(pcg_iterations(m, values, dv, k));
     it += k;
-    double sc[4] = {0.0, 0.0, 0.0, 0.0};   // slots 3..6
+    double sc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // slots 3..7
     TL_CUDA(m, cudaMemcpyAsync(sc, w->scal + 3, sizeof(sc), cudaMemcpyDeviceToHost, s));
     TL_CUDA(m, cudaStreamSynchronize(s));
     const double rr = sc[0];
+    run = (int)sc[4];
     if (!std::isfinite(rr)) return fail(m, TL_ERR_NONFINITE, "PCG residual not finite");
     if (rr <= tol2 || sc[3] != 0.0) break;
   }
   TL_TRY(pcg_result(m, dv));
-  if (iters_out) *iters_out = it;
+  if (iters_out) *iters_out = run;
   return TL_OK;
 }
 
