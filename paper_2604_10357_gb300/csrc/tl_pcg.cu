@@ -519,12 +519,28 @@ __global__ void update_xr32(float* x, float* r, float* z, const float* p, const 
   }
 }
 
+// p = z + beta p, grid-stride over float4 groups (p and z from cudaMalloc:
+// 16-byte aligned) and the scalar tail; a small grid (a few blocks per SM)
+// keeps the launch short, which matters most for iterations that return at
+// entry.
 __global__ void update_p32(float* p, const float* z, int64_t n, const double* scal, int parity) {
   if (pcg_done(scal)) return;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double rz_old = scal[2 * parity], rz_new = scal[2 - 2 * parity];
   const float beta = rz_old != 0.0 ? float(rz_new / rz_old) : 0.0f;
-  if (i < n) p[i] = z[i] + beta * p[i];
+  const int64_t n4 = n / 4, stride = (int64_t)gridDim.x * blockDim.x;
+  float4* p4 = reinterpret_cast<float4*>(p);
+  const float4* z4 = reinterpret_cast<const float4*>(z);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 zv = z4[i];
+    float4 pv = p4[i];
+    pv.x = zv.x + beta * pv.x;
+    pv.y = zv.y + beta * pv.y;
+    pv.z = zv.z + beta * pv.z;
+    pv.w = zv.w + beta * pv.w;
+    p4[i] = pv;
+  }
+  const int64_t t = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) p[t] = z[t] + beta * p[t];
 }
 
 __global__ void widen(const float* x, int64_t n, double* y) {
@@ -653,6 +669,7 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
   const bool fp32 = m->precision == TL_FP32_ELEM;
   const unsigned nbn = (unsigned)((nn + kBlock - 1) / kBlock);
   const unsigned nbv = (unsigned)((n + kBlock - 1) / kBlock);
+  const unsigned nbp = (unsigned)std::min<int64_t>((n / 4 + kBlock - 1) / kBlock + 1, (int64_t)4 * m->num_sms);
   double* part_rz = w->part;
   double* part_rr = w->part + w->nparts;
   for (int k = 0; k < count; ++k) {
@@ -674,7 +691,7 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
     if (pcg_float32(m)) {
       update_xr32<<<nbn, kBlock, 0, s>>>(w->x32, w->r32, w->z32, w->p32, w->Ap32, w->binv32, w->scal, nn, part_rz,
                                          part_rr, parity, w->tickets + 1);
-      update_p32<<<nbv, kBlock, 0, s>>>(w->p32, w->z32, n, w->scal, parity);
+      update_p32<<<nbp, kBlock, 0, s>>>(w->p32, w->z32, n, w->scal, parity);
     } else {
       update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr,
                                        parity, w->tickets + 1);
