@@ -476,13 +476,13 @@ __global__ void update_xr32(float* x, float* r, float* z, const float* p, const 
                             unsigned* ticket) {
   __shared__ double red[kBlock / 32];
   if (pcg_done(scal)) return;
-  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int rz_old = 2 * parity, rz_new = 2 - 2 * parity;
   const bool ok = scal[1] > 0.0;
   const float alpha = ok ? float(scal[rz_old] / scal[1]) : 0.0f;
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) scal[6] = 1.0;
   double rz = 0.0, rr = 0.0;
-  if (I < nn) {
+  // grid-stride over the nodes (a small grid: short launches, few partials)
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nn; I += (int64_t)gridDim.x * blockDim.x) {
     float rv[3];
     for (int d = 0; d < 3; ++d) {
       const int64_t i = 3 * I + d;
@@ -670,6 +670,7 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
   const unsigned nbn = (unsigned)((nn + kBlock - 1) / kBlock);
   const unsigned nbv = (unsigned)((n + kBlock - 1) / kBlock);
   const unsigned nbp = (unsigned)std::min<int64_t>((n / 4 + kBlock - 1) / kBlock + 1, (int64_t)4 * m->num_sms);
+  const unsigned nbx = (unsigned)std::min<int64_t>(nbn, (int64_t)2 * m->num_sms);
   double* part_rz = w->part;
   double* part_rr = w->part + w->nparts;
   for (int k = 0; k < count; ++k) {
@@ -689,7 +690,7 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
     (void)nbs;
     const int parity = k & 1;            // chunks start at even iterations (count is 8 except the last)
     if (pcg_float32(m)) {
-      update_xr32<<<nbn, kBlock, 0, s>>>(w->x32, w->r32, w->z32, w->p32, w->Ap32, w->binv32, w->scal, nn, part_rz,
+      update_xr32<<<nbx, kBlock, 0, s>>>(w->x32, w->r32, w->z32, w->p32, w->Ap32, w->binv32, w->scal, nn, part_rz,
                                          part_rr, parity, w->tickets + 1);
       update_p32<<<nbp, kBlock, 0, s>>>(w->p32, w->z32, n, w->scal, parity);
     } else {
