@@ -214,7 +214,6 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
                           unsigned* ticket) {
   __shared__ double red[kBlock / 32];
   if (pcg_done(scal)) return;
-  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // pAp <= 0: H is not positive definite along p (CG breakdown); stop moving
   // and raise the breakdown slot, which ends the iteration at the next check
   const int rz_old = 2 * parity, rz_new = 2 - 2 * parity;
@@ -222,7 +221,8 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
   const double alpha = ok ? scal[rz_old] / scal[1] : 0.0;
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) scal[6] = 1.0;
   double rz = 0.0, rr = 0.0;
-  if (I < nn) {
+  // grid-stride over the nodes (a small grid: short launches, few partials)
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nn; I += (int64_t)gridDim.x * blockDim.x) {
     double rv[3];
     for (int d = 0; d < 3; ++d) {
       const int64_t i = 3 * I + d;
@@ -262,10 +262,9 @@ __global__ void update_xr(double* x, double* r, double* z, const double* p, cons
 // p = z + beta p with beta = (r.z new) / (r.z old)
 __global__ void update_p(double* p, float* p32, const double* z, int64_t n, const double* scal, int parity) {
   if (pcg_done(scal)) return;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double rz_old = scal[2 * parity], rz_new = scal[2 - 2 * parity];
   const double beta = rz_old != 0.0 ? rz_new / rz_old : 0.0;
-  if (i < n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = z[i] + beta * p[i];
     p[i] = v;
     if (p32) p32[i] = float(v);
@@ -671,6 +670,7 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
   const unsigned nbv = (unsigned)((n + kBlock - 1) / kBlock);
   const unsigned nbp = (unsigned)std::min<int64_t>((n / 4 + kBlock - 1) / kBlock + 1, (int64_t)4 * m->num_sms);
   const unsigned nbx = (unsigned)std::min<int64_t>(nbn, (int64_t)2 * m->num_sms);
+  const unsigned nbq = (unsigned)std::min<int64_t>(nbv, (int64_t)4 * m->num_sms);
   double* part_rz = w->part;
   double* part_rr = w->part + w->nparts;
   for (int k = 0; k < count; ++k) {
@@ -694,9 +694,9 @@ tl_status pcg_iterations(tl_mesh* m, const void* values, double* dv, int count) 
                                          part_rr, parity, w->tickets + 1);
       update_p32<<<nbp, kBlock, 0, s>>>(w->p32, w->z32, n, w->scal, parity);
     } else {
-      update_xr<<<nbn, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr,
+      update_xr<<<nbx, kBlock, 0, s>>>(dv, w->r, w->z, w->p, w->Ap, w->binv, w->scal, nn, part_rz, part_rr,
                                        parity, w->tickets + 1);
-      update_p<<<nbv, kBlock, 0, s>>>(w->p, fp32 ? w->p32 : nullptr, w->z, n, w->scal, parity);
+      update_p<<<nbq, kBlock, 0, s>>>(w->p, fp32 ? w->p32 : nullptr, w->z, n, w->scal, parity);
     }
     m->launches += 3;
   }
